@@ -1,0 +1,413 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 Gaussian rasterizer + pose gradient.
+
+Workload (synthetic, seeded): 1,000,000 Gaussians over a 1 km x 1 km aerial
+scene (SH degree 3), one 1920x1080 view (f = 1400) from 300 m pitched 30 deg.
+A step is one pose-refinement iteration of the whole hot path: projection,
+tile binning + depth sort, front-to-back compositing of RGB/depth/alpha, the
+L1 photometric + 0.1 L1 depth loss and its se(3) pose gradient (fp64
+reduction). ``value`` is rendered-and-differentiated Mpix/s (whole job); the
+line also reports forward-only Mpix/s, pose-gradient iterations/s and the
+batched-vs-single-pose factor on the mixed-resolution batch (84 candidate
+poses, 2M Gaussians with 32 BF16 feature channels).
+
+L2 is flushed (256 MB write) between timed steps, outside the timed events.
+``python bench.py [--gpus N --steps K --warmup W] [--impl reference]``; for
+N > 1 run under torchrun (one rank per GPU, independent poses per rank).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpix/s fwd and pose-grad iters/s, 1M Gaussians @1080p; batched vs single-pose"
+WORKLOAD = "aerial 1M Gaussians SH3, 1920x1080 f=1400, pose-gradient step (fwd + L1 rgb/depth loss + se(3) adjoint)"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 256 << 20
+# fp32 operations of one (pixel, Gaussian) evaluation on the skip path:
+# dx, dy, dx^2, dy^2, A dx^2, C dy^2 (+), x(-1/2), dx dy, B dx dy (+), o e^p, min, 2 compares
+FLOPS_PER_EVAL = 14
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="gsr", choices=["gsr", "reference"])
+    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = bus_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="gsr_clocks_", suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.bus_id:
+            cmd[1:1] = ["-i", self.bus_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+def peaks():
+    try:
+        return json.load(open(PEAKS_FILE)), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# --------------------------------------------------------------------------- workload
+def make_workload(rank: int):
+    from paper_2507_15683_gb300 import synth
+    scene = synth.aerial_scene(2, 1_000_000)
+    cam = synth.aerial_camera()
+    T_ref = synth.aerial_pose()
+    T_q = synth.perturb_pose(T_ref, synth.rng(100 + rank), 2.0, 5.0)
+    return scene, cam, T_ref, T_q
+
+
+def cpu_baseline(scene, cam, T_ref, T_q, budget_s: float):
+    """The fp64 oracle as it stands, on a bounded pixel sample of the same frame."""
+    from oracle import oracle as O
+    O.build()
+    n_thr = os.cpu_count() or 1
+    H, W = cam["height"], cam["width"]
+    t0 = time.perf_counter()
+    ref = O.render(scene, cam, T_ref, geom64=True, n_threads=n_thr)  # target frame (not timed below)
+    t_ref = time.perf_counter() - t0
+    trgb = ref["rgb"].T.reshape(3, H, W).astype(np.float32)
+    tdep = ref["depth"].reshape(H, W).astype(np.float32)
+    g = np.random.default_rng(0)
+    n_pix = 16384
+    while True:
+        pix = np.sort(g.choice(H * W, n_pix, replace=False))
+        w = np.zeros((H, W), np.float32)
+        w.reshape(-1)[pix] = 1.0
+        t0 = time.perf_counter()
+        r = O.render(scene, cam, T_q, geom64=True, want_grad=True, pixels=pix, target_rgb=trgb, target_depth=tdep,
+                     pixel_weight=w, n_threads=n_thr)
+        dt = time.perf_counter() - t0
+        if dt > budget_s / 3 or n_pix >= H * W:
+            break
+        n_pix = min(H * W, int(n_pix * max(2.0, budget_s / 2 / max(dt, 1e-3))))
+    return {"value": n_pix / dt / 1e6, "unit": "Mpix/s", "cores": n_thr, "kind": "oracle",
+            "sample": "fp64 oracle pose-gradient step (projection of all 1M Gaussians, binning, fp64 "
+                      "compositing + forward-mode se(3) gradient) on %d random pixels of the 1080p frame; "
+                      "%.2f s per step" % (n_pix, dt),
+            "loss": r["loss"], "target_render_s": t_ref}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle, timed on the host cores."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    scene, cam, T_ref, T_q = make_workload(0)
+    from oracle import oracle as O
+    O.build()
+    n_thr = os.cpu_count() or 1
+    H, W = cam["height"], cam["width"]
+    ref = O.render(scene, cam, T_ref, geom64=True, n_threads=n_thr)
+    trgb = ref["rgb"].T.reshape(3, H, W).astype(np.float32)
+    tdep = ref["depth"].reshape(H, W).astype(np.float32)
+    n_pix = 8192
+    g = np.random.default_rng(1)
+
+    def step():
+        pix = np.sort(g.choice(H * W, n_pix, replace=False))
+        w = np.zeros((H, W), np.float32)
+        w.reshape(-1)[pix] = 1.0
+        O.render(scene, cam, T_q, geom64=True, want_grad=True, pixels=pix, target_rgb=trgb, target_depth=tdep,
+                 pixel_weight=w, n_threads=n_thr)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    v = n_pix / dt / 1e6
+    line = {"metric": METRIC, "value": v, "unit": "Mpix/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "gaussians": 1_000_000, "width": W, "height": H, "sh_degree": 3,
+                       "sample_pixels": n_pix},
+            "cpu_baseline": {"value": v, "unit": "Mpix/s", "cores": n_thr, "kind": "oracle",
+                             "sample": "fp64 oracle pose-gradient step on %d random pixels per step" % n_pix},
+            "e2e": {"value": v, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_2507_15683_gb300 import gsr, synth
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    scene, cam, T_ref, T_q = make_workload(rank)
+    H, W = cam["height"], cam["width"]
+    P = H * W
+    S = gsr.Scene(scene)
+    tgt = S.render(cam, T_ref)
+    trgb, tdep = tgt["rgb"].clone(), tgt["depth"].clone()
+    result = torch.zeros(8, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    cam_c, pose_q = gsr.camera(cam), gsr.pose(T_q)
+    out_f = S.alloc_outputs(cam, last_idx=False)
+    out_fs = S.outputs_struct(out_f)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def grad_step():
+        gsr.gs_render_pose_grad_async(S.handle, cam_c, pose_q, trgb.data_ptr(), tdep.data_ptr(), None, 0.1, None,
+                                      result.data_ptr(), stream)
+
+    def fwd_step():
+        gsr.gs_render_async(S.handle, cam_c, pose_q, out_fs, stream)
+
+    # size the workspace with one synchronous call, then check the async path
+    S.render_pose_grad(cam, T_q, trgb, tdep)
+    for _ in range(args.warmup):
+        grad_step()
+    st, n_rec, n_pairs = S.status()
+    if st != 0:
+        raise RuntimeError("workspace overflow in warm-up")
+
+    def timed(fn, k):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        barrier()
+        torch.cuda.synchronize()
+        for a, b in ev:
+            flush.zero_()
+            a.record()
+            fn()
+            b.record()
+        torch.cuda.synchronize()
+        barrier()
+        return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(torch.cuda.current_device()).pci_bus_id
+    except AttributeError:
+        pass
+    clocks = ClockSampler(bus)
+    clocks.start()
+    ms_grad = timed(grad_step, args.steps)
+    clk = clocks.stop()
+    ms_grad = max_over_ranks(ms_grad)
+    st, _, _ = S.status()
+    assert st == 0
+    for _ in range(args.warmup):
+        fwd_step()
+    ms_fwd = max_over_ranks(timed(fwd_step, args.steps))
+
+    # per-kernel device time over the same steps (events recorded by the library)
+    gsr.gs_scene_set_timing(S.handle, True)
+    gsr.gs_scene_kernel_times(S.handle)
+    timed(grad_step, args.steps)
+    kms, kn = gsr.gs_scene_kernel_times(S.handle)
+    gsr.gs_scene_set_timing(S.handle, False)
+    per_kernel = {name: (kms[i] / kn[i] if kn[i] else 0.0) for i, name in enumerate(gsr.KERNEL_NAMES)}
+    ts, _, _ = S.tile_lists(0, cam, n_pairs + 16)
+    counts = np.diff(ts)
+    tx, ty = (W + 15) // 16, (H + 15) // 16
+    wt = np.minimum(16, W - 16 * np.arange(tx))
+    ht = np.minimum(16, H - 16 * np.arange(ty))
+    evals = int((counts * np.outer(ht, wt).reshape(-1)).sum())
+    pk, pk_src = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FMA = 2
+    dom = max(per_kernel, key=per_kernel.get)
+    kernels = {k: {"ms": v, "share": v / max(sum(per_kernel.values()), 1e-12)} for k, v in per_kernel.items()}
+    if dom in ("sort_composite", "backward"):
+        ach = evals * FLOPS_PER_EVAL / (per_kernel[dom] * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
+                "traffic": None, "kernel": dom,
+                "work": "%d (pixel, Gaussian) evaluations x %d fp32 ops (skip path)" % (evals, FLOPS_PER_EVAL),
+                "peak_source": "%d SMs x 128 fp32 lanes x 2 x %.0f MHz (%s max clock)" % (n_sm, sm_max, pk_src)}
+    else:
+        nsh = 48
+        bytes_ = 1_000_000 * 16 + n_rec * (32 + 4 * nsh + 64)
+        ach = bytes_ / (per_kernel[dom] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
+                "traffic": None, "kernel": dom, "peak_source": pk_src}
+
+    # end to end through the public API: pinned host targets -> device, synchronous call, result to host
+    h_rgb = trgb.cpu().pin_memory()
+    h_dep = tdep.cpu().pin_memory()
+    d_rgb = torch.empty_like(trgb)
+    d_dep = torch.empty_like(tdep)
+
+    def e2e_step():
+        d_rgb.copy_(h_rgb, non_blocking=True)
+        d_dep.copy_(h_dep, non_blocking=True)
+        return S.render_pose_grad(cam, T_q, d_rgb, d_dep)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps)
+    h2d = (h_rgb.numel() + h_dep.numel()) * 4
+
+    # batched vs single pose: 84 candidate views of mixed resolution in one graph launch
+    batched = None
+    if not args.no_batched:
+        batched = bench_batched(gsr, synth, torch, flush, max(2, args.steps // 4), args.warmup)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(scene, cam, T_ref, T_q, args.cpu_seconds)
+
+    launches_per_step = 6  # project, scan, scatter, sort+composite, backward, reduce
+    value = world * P / (ms_grad * 1e-3) / 1e6
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_grad, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "gaussians": 1_000_000, "width": W, "height": H, "sh_degree": 3,
+                   "records": int(n_rec), "pairs": int(n_pairs), "evaluations": evals,
+                   "l2": "flushed (256 MB write) between timed steps, outside the timed events",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "pose_grad_iters_per_s": world / (ms_grad * 1e-3),
+        "fwd_mpix_s": world * P / (ms_fwd * 1e-3) / 1e6, "fwd_ms": ms_fwd,
+        "clocks": clk,
+        "e2e": {"value": world * P / (e2e_ms * 1e-3) / 1e6, "unit": "Mpix/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 7 * 8},
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": roof, "kernels": kernels,
+        "batched": batched, "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    S.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def bench_batched(gsr, synth, torch, flush, steps, warmup):
+    scene = synth.partitioned_scene(4, 2, 2, 500_000, sh_degree=3, feat_dim=32)
+    cams, poses = synth.batched_views()
+    S = gsr.Scene(scene)
+    outs = [S.alloc_outputs(c, feat_dim=32, last_idx=False) for c in cams]
+    structs = [S.outputs_struct(o) for o in outs]
+    stream = torch.cuda.current_stream().cuda_stream
+    S.render_batch(cams, poses, outs)  # synchronous: sizes the workspace
+    _, n_rec, n_pairs = S.status()
+    S.reserve(int(n_rec * 1.1) + 1024, int(n_pairs * 1.1) + 4096)
+    cc = [gsr.camera(c) for c in cams]
+    pp = [gsr.pose(T) for T in poses]
+
+    def single():
+        for c, p, o in zip(cc, pp, structs):
+            gsr.gs_render_async(S.handle, c, p, o, stream)
+
+    def batch():
+        gsr.gs_render_batch(S.handle, cc, pp, structs, gsr.GS_BATCH_GRAPH, stream)
+
+    res = {}
+    for name, fn in (("single", single), ("batched", batch)):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        st = S.status()[0]
+        assert st == 0, "batched workspace overflow"
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record()
+            fn()
+            b.record()
+        torch.cuda.synchronize()
+        res[name] = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    px = sum(c["width"] * c["height"] for c in cams)
+    S.close()
+    return {"views": len(cams), "gaussians": 2_000_000, "feat_dim": 32, "mpix": px / 1e6,
+            "single_ms": res["single"], "batched_ms": res["batched"],
+            "single_mpix_s": px / (res["single"] * 1e-3) / 1e6, "batched_mpix_s": px / (res["batched"] * 1e-3) / 1e6,
+            "speedup": res["single"] / res["batched"], "records": int(n_rec), "pairs": int(n_pairs)}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * gsr.h -- C ABI of the GB300 Gaussian-splatting rasterizer with se(3) pose
+ * gradient (libgsr.so).
+ *
+ * The operation is the rendering step of the dense render-and-match stage of
+ * Hi^2-GSLoc (arXiv 2507.15683): Sec. 3.1 defines the scene as Gaussians
+ * Theta_i = {centre (x, y, z), rotation q, scale s, opacity, colour c, feature
+ * f}, rendered by tile-based rasterization with alpha blending, features going
+ * through the identical blending; Sec. 3.4 renders feature, depth and colour
+ * maps at a candidate pose on every refinement iteration; Algorithm 1 fixes the
+ * projection (world -> camera by T, depth = camera z, perspective division,
+ * then K) and Eq. 10 the pinhole map pi([x, y, z]) = [x/z, y/z].
+ *
+ * Conventions shared by every entry point
+ *  - All functions return gs_status and never abort. On failure the
+ *    thread-local message of gs_last_error() says why.
+ *  - "device" pointers are CUDA device (or managed) memory of the current
+ *    device; "host" pointers are ordinary host memory.
+ *  - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is enqueued on it; functions documented as synchronous also wait for
+ *    it before returning.
+ *  - Images are planar, row-major: channel c of pixel (x, y) sits at
+ *    [c * H * W + y * W + x]. Pixel (x, y) has its centre at (x + 0.5, y + 0.5)
+ *    in the frame of the projected coordinates.
+ *  - A pose is a row-major 4x4 world-to-camera matrix T_cw (camera x right,
+ *    y down, z forward), applied as p_cam = R X + t (Algorithm 1).
+ *  - The pose tangent is xi = (rho, phi): T(xi) = Exp(xi^) T_cw (left
+ *    perturbation, rho first), derivatives taken at xi = 0.
+ *  - One scene may be used from one stream at a time (its workspace is shared
+ *    by all calls on it); distinct scenes are independent.
+ *
+ * Fixed constants (the paper leaves them open): 16 x 16 tiles, near plane 0.2,
+ * EWA footprint with 0.3 px dilation, 1.3 x half field of view guard on the
+ * Jacobian and a 0.1 floor under the eigenvalue discriminant, radius =
+ * ceil(3 sqrt(lambda_max)), alpha = min(0.99, o exp(power)), Gaussians with
+ * alpha < 1/255 skipped, blending stops before a Gaussian that would take the
+ * transmittance below 1e-4, background 0, depth = sum of w * z (not
+ * normalised), colour = max(0, SH(dir) + 0.5) with dir = normalize(mean -
+ * camera centre), real SH with the Condon-Shortley phase, coefficient index
+ * l*l + l + m. Within a tile Gaussians are blended in ascending (binary32
+ * camera depth bits, Gaussian index) order.
+ */
+#ifndef GSR_H
+#define GSR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GS_OK = 0,
+  GS_ERR_INVALID_ARG = 1, /* a pointer, size or enum is out of its documented range */
+  GS_ERR_CUDA = 2,        /* a CUDA runtime call failed (message has the CUDA error) */
+  GS_ERR_OOM = 3,         /* device or pinned host allocation failed */
+  GS_ERR_CAPACITY = 4,    /* an asynchronous call outgrew the reserved workspace */
+  GS_ERR_TIMEOUT = 5,     /* reserved: bounded device waits expired */
+  GS_ERR_INTERNAL = 6     /* a device-side consistency check failed */
+} gs_status;
+
+typedef struct gs_scene gs_scene; /* opaque */
+
+/* Scene description (Sec. 3.1 primitive). Arrays are row-major per Gaussian.
+ * The scene copies what it needs into its own device arena: the caller may
+ * free every array once gs_create_scene returns. */
+typedef struct {
+  int64_t n;                  /* number of Gaussians, >= 0 and < 2^31 */
+  int sh_degree;              /* 0..3 */
+  int feat_dim;               /* 0 or 32 */
+  const float* means;         /* n x 3, world coordinates */
+  const float* scales;        /* n x 3, linear standard deviations (> 0, not log) */
+  const float* quats;         /* n x 4, (w, x, y, z); normalised inside; 0 -> identity */
+  const float* opacities;     /* n, in (0, 1) (after the sigmoid) */
+  const float* sh;            /* n x (deg+1)^2 x 3, coefficient-major */
+  const uint16_t* feats_bf16; /* n x feat_dim bfloat16 bit patterns, NULL when feat_dim = 0 */
+  int n_partitions;           /* 0 = one partition; else partition_offsets has n_partitions+1 entries */
+  const int64_t* partition_offsets; /* host; ascending Gaussian index ranges, [0] = 0, [last] = n */
+  int device_resident;        /* 1: the arrays above are device pointers; 0: host pointers */
+} gs_scene_desc;
+
+typedef struct {
+  int width, height;          /* pixels, 1 .. 65535 * 16 */
+  float fx, fy, cx, cy;       /* pinhole intrinsics K (Eq. 10) */
+} gs_camera;
+
+typedef struct {
+  double T_cw[16];            /* row-major world-to-camera */
+} gs_pose;
+
+/* Caller-owned device output buffers of one view (H x W pixels). Any pointer
+ * may be NULL to skip that output. */
+typedef struct {
+  float* rgb;        /* 3 x H x W */
+  float* depth;      /* H x W, sum of w * z */
+  float* alpha;      /* H x W, 1 - final transmittance */
+  float* final_T;    /* H x W, final transmittance (>= 1e-4) */
+  float* feats;      /* feat_dim x H x W, blended BF16 features accumulated in fp32 */
+  uint32_t* last_idx;/* H x W, 1 + position in the tile list of the last blended Gaussian */
+} gs_outputs;
+
+/* Batch flags */
+#define GS_BATCH_GRAPH 1u      /* capture the batch once into a CUDA graph and replay it */
+
+/* Create a scene (Sec. 3.1). Packs the Gaussians into the device layout used by
+ * the kernels (centre + max scale, binary32 3D covariance + opacity, SH
+ * coefficients, features). Synchronous. *out receives the handle; destroy it
+ * with gs_destroy_scene. Errors: INVALID_ARG (NULL pointer with n > 0, degree
+ * or feature width out of range, bad partition table), OOM, CUDA. */
+gs_status gs_create_scene(const gs_scene_desc* desc, gs_scene** out);
+
+/* Release the scene and its device memory. Waits for its work. NULL is a no-op. */
+void gs_destroy_scene(gs_scene* scene);
+
+/* Reserve workspace for up to max_records projected (view, Gaussian) records
+ * and max_pairs (tile, Gaussian) pairs, so that asynchronous calls and graph
+ * replays never outgrow it. Synchronous. Errors: INVALID_ARG, OOM, CUDA. */
+gs_status gs_scene_reserve(gs_scene* scene, int64_t max_records, int64_t max_pairs);
+
+/* Render one view (Sec. 3.1 rasterization at the pose of Sec. 3.4).
+ * Synchronous: waits for the stream, and when the workspace was too small
+ * grows it and renders again, so the outputs are complete on return.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+gs_status gs_render(gs_scene* scene, const gs_camera* cam, const gs_pose* pose, const gs_outputs* out,
+                    void* stream);
+
+/* Same as gs_render but only enqueues work. If the workspace is too small the
+ * outputs are invalid and gs_scene_status() reports GS_ERR_CAPACITY. */
+gs_status gs_render_async(gs_scene* scene, const gs_camera* cam, const gs_pose* pose,
+                          const gs_outputs* out, void* stream);
+
+/* Render one view and the gradient of
+ *   L = 1/(3P) sum_px,c w_px |C - C*| + depth_weight * 1/P sum_px w_px |D - D*|
+ * (P = W * H, w_px = pixel_weight or 1, sign(0) = 0) with respect to the pose
+ * tangent xi = (rho, phi). The per-pixel transmittance is recomputed from the
+ * stored final transmittance; the per-pixel sums are reduced across pixels in
+ * fp64. target_rgb (3 x H x W), target_depth (H x W) and pixel_weight (H x W or
+ * NULL) are device pointers. loss_out (1) and grad_xi_out (6) are host
+ * pointers written before return (synchronous, with the same regrow rule as
+ * gs_render). out may be NULL or have NULL members; the forward outputs are
+ * then kept internally. Errors: INVALID_ARG, OOM, CUDA. */
+gs_status gs_render_pose_grad(gs_scene* scene, const gs_camera* cam, const gs_pose* pose,
+                              const float* target_rgb, const float* target_depth, const float* pixel_weight,
+                              float depth_weight, const gs_outputs* out, double* loss_out,
+                              double* grad_xi_out, void* stream);
+
+/* Asynchronous form of gs_render_pose_grad: result_dev (device, 7 doubles)
+ * receives (loss, grad rho_x, rho_y, rho_z, phi_x, phi_y, phi_z). Capacity
+ * overflow is reported by gs_scene_status(). */
+gs_status gs_render_pose_grad_async(gs_scene* scene, const gs_camera* cam, const gs_pose* pose,
+                                    const float* target_rgb, const float* target_depth,
+                                    const float* pixel_weight, float depth_weight, const gs_outputs* out,
+                                    double* result_dev, void* stream);
+
+/* Render n_views views of possibly different sizes (candidate poses and
+ * pyramid levels of Sec. 3.4) in one pass: one projection launch over all
+ * (view, Gaussian) pairs, one global tile space, one persistent compositing
+ * launch over every view's tiles. cams, poses and outs are host arrays of
+ * n_views entries (outs hold device pointers). Each view's outputs equal those
+ * of gs_render for that view. flags: 0 = synchronous (regrow rule of
+ * gs_render); GS_BATCH_GRAPH = asynchronous replay of a CUDA graph captured on
+ * the first call for this (n_views, cams, outs) layout -- poses may change
+ * between calls; reserve the workspace first (gs_scene_reserve) and check
+ * gs_scene_status(). Errors: INVALID_ARG, OOM, CUDA. */
+gs_status gs_render_batch(gs_scene* scene, int n_views, const gs_camera* cams, const gs_pose* poses,
+                          const gs_outputs* outs, unsigned flags, void* stream);
+
+/* Wait for the stream and return the scene's sticky device status
+ * (GS_OK or GS_ERR_CAPACITY / GS_ERR_INTERNAL from earlier asynchronous
+ * calls), then clear it. needed_records / needed_pairs (host, may be NULL)
+ * receive the sizes the last call needed. */
+gs_status gs_scene_status(gs_scene* scene, void* stream, int64_t* needed_records, int64_t* needed_pairs);
+
+/* Sorted tile lists of view `view` of the last render (parity/debugging).
+ * Synchronous. keys (host, capacity) receive tile << 32 | depth bits, gids
+ * (host, capacity) the Gaussian indices, tile_start (host, tiles + 1) the
+ * list boundaries; *n_pairs (host) the list length. Errors: INVALID_ARG when
+ * the view does not exist or capacity is too small (n_pairs still set). */
+gs_status gs_get_tile_lists(gs_scene* scene, int view, uint64_t* keys, uint32_t* gids, int64_t* tile_start,
+                            int64_t capacity, int64_t* n_pairs, void* stream);
+
+/* Projected records of view `view` of the last render (parity/debugging).
+ * Synchronous. For each of the *n_records visible Gaussians (in no particular
+ * order) rec (host, capacity x 8 int32) receives: Gaussian index, x0, x1, y0,
+ * y1 (inclusive tile rectangle), and the bit patterns of the binary32 camera
+ * depth, u and v. Errors: INVALID_ARG (bad view, capacity too small). */
+gs_status gs_get_records(gs_scene* scene, int view, int32_t* rec, int64_t capacity, int64_t* n_records,
+                         void* stream);
+
+/* Kernel timing (CUDA events recorded on the call's stream around every
+ * launch of every call while enabled). Kernel order of the arrays below:
+ * projection, tile scan, scatter, sort + composite, backward, reduction. */
+#define GS_KERNEL_COUNT 6
+gs_status gs_scene_set_timing(gs_scene* scene, int enable);
+
+/* Wait for the recorded calls and return, per kernel, the summed device time
+ * (ms, host array of GS_KERNEL_COUNT) and the number of launches timed (host
+ * array of GS_KERNEL_COUNT, may be NULL) since timing was enabled or last read;
+ * then reset the sums. Errors: INVALID_ARG, CUDA. */
+gs_status gs_scene_kernel_times(gs_scene* scene, double* total_ms, int64_t* launches);
+
+/* Thread-local message describing the last error of this thread ("" if none). */
+const char* gs_last_error(void);
+
+/* Library version string. */
+const char* gs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSR_H */

@@ -1,0 +1,769 @@
+// C ABI of libgsr (declared in include/gsr.h): scene arena, workspace
+// management, launch sequence of one render / pose-gradient / batch call,
+// CUDA-graph capture of batches, and the parity exports.
+//
+// Host arithmetic that feeds the binary32 projection (pose rounding, the
+// field-of-view guard) is compiled without floating-point contraction so that
+// it is the same IEEE sequence on every host.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gsr.h"
+#include "gsr_internal.h"
+
+using namespace gsr;
+
+namespace {
+
+thread_local std::string g_err;
+
+gs_status fail(gs_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+#define GS_CUDA(x)                                                                              \
+  do {                                                                                          \
+    const cudaError_t e_ = (x);                                                                 \
+    if (e_ != cudaSuccess) return fail(GS_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define GS_TRY(x)                     \
+  do {                                \
+    const gs_status s_ = (x);         \
+    if (s_ != GS_OK) return s_;       \
+  } while (0)
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+gs_status ensure(DevBuf& b, size_t bytes) {
+  if (b.bytes >= bytes && b.p) return GS_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  const size_t alloc = std::max<size_t>(bytes, 256);
+  const cudaError_t e = cudaMalloc(&b.p, alloc);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return fail(e == cudaErrorMemoryAllocation ? GS_ERR_OOM : GS_ERR_CUDA,
+                std::string("cudaMalloc(") + std::to_string(alloc) + "): " + cudaGetErrorString(e));
+  }
+  b.bytes = alloc;
+  return GS_OK;
+}
+
+void release(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+template <typename T>
+T* dp(const DevBuf& b) {
+  return reinterpret_cast<T*>(b.p);
+}
+
+struct GradIn {
+  const float* target_rgb;
+  const float* target_depth;
+  const float* pixel_weight;
+  float depth_weight;
+  double* result;  // device destination of (loss, grad) or NULL (scene buffer)
+};
+
+struct GraphCache {
+  bool valid = false;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<gs_camera> cams;
+  std::vector<gs_outputs> outs;
+  View* host_views = nullptr;  // pinned; read by the graph's upload node at replay
+  cudaEvent_t done = nullptr;
+  cudaStream_t capture = nullptr;
+  int n_views = 0;
+};
+
+}  // namespace
+
+struct gs_scene {
+  int device = 0;
+  int sm_count = 1;
+  int64_t n = 0;
+  int sh_degree = 0, feat_dim = 0, nsh4 = 1;
+  DevBuf pos, cov, sh, feat;
+  std::vector<int64_t> part_off;
+  // workspace
+  DevBuf rec_a, rec_b, rec_c, rec_m, rec_j;
+  uint32_t rec_cap = 0, jac_cap = 0;
+  DevBuf tile_count, tile_offset, tile_cursor, partials;
+  uint32_t tile_cap = 0;
+  DevBuf pairs, pairs_tmp;
+  uint32_t pair_cap = 0;
+  DevBuf ctr, result, views;
+  Counters* ctr_host = nullptr;
+  double* result_host = nullptr;
+  DevBuf int_pix;  // internal per-pixel buffers (pose gradient without user outputs)
+  // kernel timing: one set of GS_KERNEL_COUNT + 1 events per timed call
+  bool timing = false;
+  struct TimedCall {
+    std::vector<cudaEvent_t> ev;  // GS_KERNEL_COUNT + 1 events
+    int n_kernels;                // kernels bracketed by ev[0..n_kernels]
+  };
+  std::vector<TimedCall> ev_pending;
+  std::vector<std::vector<cudaEvent_t>> ev_free;
+  double kt_ms[GS_KERNEL_COUNT] = {0, 0, 0, 0, 0, 0};
+  int64_t kt_n[GS_KERNEL_COUNT] = {0, 0, 0, 0, 0, 0};
+  // last call
+  std::vector<View> last_views;
+  uint32_t last_tiles = 0;
+  GraphCache graph;
+};
+
+namespace {
+
+SceneDev scene_dev(const gs_scene* s) {
+  SceneDev d;
+  d.pos = dp<float4>(s->pos);
+  d.cov = dp<float4>(s->cov);
+  d.sh = dp<float4>(s->sh);
+  d.feat = s->feat_dim ? dp<uint4>(s->feat) : nullptr;
+  d.n = (int)s->n;
+  d.sh_degree = s->sh_degree;
+  d.nsh4 = s->nsh4;
+  d.feat_dim = s->feat_dim;
+  return d;
+}
+
+Work work_of(gs_scene* s, uint32_t n_tiles) {
+  Work w;
+  w.rec_a = dp<float4>(s->rec_a);
+  w.rec_b = dp<float4>(s->rec_b);
+  w.rec_c = dp<float4>(s->rec_c);
+  w.rec_m = dp<uint4>(s->rec_m);
+  w.rec_j = dp<float>(s->rec_j);
+  w.rec_cap = s->rec_cap;
+  w.tile_count = dp<uint32_t>(s->tile_count);
+  w.tile_offset = dp<uint32_t>(s->tile_offset);
+  w.tile_cursor = dp<uint32_t>(s->tile_cursor);
+  w.n_tiles = n_tiles;
+  w.pairs = dp<uint2>(s->pairs);
+  w.pairs_tmp = dp<uint2>(s->pairs_tmp);
+  w.pair_cap = s->pair_cap;
+  w.ctr = dp<Counters>(s->ctr);
+  w.partials = dp<double>(s->partials);
+  w.result = dp<double>(s->result);
+  return w;
+}
+
+gs_status grow_records(gs_scene* s, uint64_t rec_cap, bool grad) {
+  rec_cap = std::min<uint64_t>(rec_cap, 0x7fffffffull);
+  if (rec_cap > s->rec_cap) {
+    GS_TRY(ensure(s->rec_a, rec_cap * sizeof(float4)));
+    GS_TRY(ensure(s->rec_b, rec_cap * sizeof(float4)));
+    GS_TRY(ensure(s->rec_c, rec_cap * sizeof(float4)));
+    GS_TRY(ensure(s->rec_m, rec_cap * sizeof(uint4)));
+    s->rec_cap = (uint32_t)rec_cap;
+  }
+  if (grad && s->jac_cap < s->rec_cap) {
+    GS_TRY(ensure(s->rec_j, (size_t)s->rec_cap * kJacStride * sizeof(float)));
+    s->jac_cap = s->rec_cap;
+  }
+  return GS_OK;
+}
+
+gs_status grow_pairs(gs_scene* s, uint64_t pair_cap) {
+  pair_cap = std::min<uint64_t>(pair_cap, 0xffffffffull);
+  if (pair_cap > s->pair_cap) {
+    GS_TRY(ensure(s->pairs, pair_cap * sizeof(uint2)));
+    GS_TRY(ensure(s->pairs_tmp, pair_cap * sizeof(uint2)));
+    s->pair_cap = (uint32_t)pair_cap;
+  }
+  return GS_OK;
+}
+
+gs_status grow_tiles(gs_scene* s, uint64_t n_tiles) {
+  if (n_tiles + 1 > s->tile_cap) {
+    const uint64_t cap = n_tiles + 1;
+    GS_TRY(ensure(s->tile_count, cap * sizeof(uint32_t)));
+    GS_TRY(ensure(s->tile_offset, cap * sizeof(uint32_t)));
+    GS_TRY(ensure(s->tile_cursor, cap * sizeof(uint32_t)));
+    GS_TRY(ensure(s->partials, cap * kPartialStride * sizeof(double)));
+    s->tile_cap = (uint32_t)cap;
+  }
+  return GS_OK;
+}
+
+bool finite_pos(float x) { return std::isfinite(x) && x > 0.0f; }
+
+gs_status check_cam(const gs_camera& c) {
+  if (c.width < 1 || c.height < 1 || c.width > 65535 * kTile || c.height > 65535 * kTile)
+    return fail(GS_ERR_INVALID_ARG, "camera size out of range");
+  if (!finite_pos(c.fx) || !finite_pos(c.fy) || !std::isfinite(c.cx) || !std::isfinite(c.cy))
+    return fail(GS_ERR_INVALID_ARG, "camera intrinsics must be finite with fx, fy > 0");
+  return GS_OK;
+}
+
+gs_status check_pose(const gs_pose& p) {
+  for (int k = 0; k < 16; ++k)
+    if (!std::isfinite(p.T_cw[k])) return fail(GS_ERR_INVALID_ARG, "pose has a non-finite entry");
+  return GS_OK;
+}
+
+// Build the per-view device parameters. `pix_off` receives each view's offset
+// into the internal per-pixel buffers (used only when need_internal).
+gs_status build_views(gs_scene* s, int nv, const gs_camera* cams, const gs_pose* poses, const gs_outputs* outs,
+                      const GradIn* g, std::vector<View>& hv, uint64_t& n_tiles) {
+  hv.assign(nv, View{});
+  n_tiles = 0;
+  uint64_t pix_total = 0;
+  for (int v = 0; v < nv; ++v) {
+    GS_TRY(check_cam(cams[v]));
+    GS_TRY(check_pose(poses[v]));
+    pix_total += (uint64_t)cams[v].width * cams[v].height;
+  }
+  const bool need_internal = g != nullptr;
+  if (need_internal) GS_TRY(ensure(s->int_pix, pix_total * 6 * sizeof(float)));
+  float* ib = dp<float>(s->int_pix);
+  uint64_t pix_off = 0;
+  for (int v = 0; v < nv; ++v) {
+    const gs_camera& c = cams[v];
+    const double* T = poses[v].T_cw;
+    View& V = hv[v];
+    for (int a = 0; a < 3; ++a) {
+      for (int b = 0; b < 3; ++b) V.R[3 * a + b] = (float)T[4 * a + b];
+      V.t[a] = (float)T[4 * a + 3];
+    }
+    for (int a = 0; a < 3; ++a)
+      V.cw[a] = (float)(-(T[a] * T[3] + T[4 + a] * T[7] + T[8 + a] * T[11]));
+    V.fx = c.fx;
+    V.fy = c.fy;
+    V.cx = c.cx;
+    V.cy = c.cy;
+    const float hw = 0.5f * (float)c.width, hh = 0.5f * (float)c.height;
+    const float qx = hw / c.fx, qy = hh / c.fy;
+    V.limx = 1.3f * qx;
+    V.limy = 1.3f * qy;
+    V.jb2 = c.fx * c.fx * (1.0f + V.limx * V.limx) + c.fy * c.fy * (1.0f + V.limy * V.limy);
+    V.width = c.width;
+    V.height = c.height;
+    V.tiles_x = (c.width + kTile - 1) / kTile;
+    V.tiles_y = (c.height + kTile - 1) / kTile;
+    V.tile_base = (uint32_t)n_tiles;
+    n_tiles += (uint64_t)V.tiles_x * V.tiles_y;
+    const gs_outputs o = outs ? outs[v] : gs_outputs{};
+    const uint64_t P = (uint64_t)c.width * c.height;
+    V.rgb = o.rgb;
+    V.depth = o.depth;
+    V.alpha = o.alpha;
+    V.final_T = o.final_T;
+    V.feats = s->feat_dim ? o.feats : nullptr;
+    V.last_idx = o.last_idx;
+    if (need_internal) {
+      float* base = ib + pix_off * 6;
+      if (!V.rgb) V.rgb = base;
+      if (!V.depth) V.depth = base + 3 * P;
+      if (!V.final_T) V.final_T = base + 4 * P;
+      if (!V.last_idx) V.last_idx = reinterpret_cast<uint32_t*>(base + 5 * P);
+      V.target_rgb = g->target_rgb;
+      V.target_depth = g->target_depth;
+      V.pixel_weight = g->pixel_weight;
+      V.depth_weight = g->depth_weight;
+      V.inv_3p = (float)(1.0 / (3.0 * (double)P));
+      V.inv_p = (float)(1.0 / (double)P);
+    }
+    pix_off += P;
+  }
+  if (n_tiles >= 0x7fffffffull) return fail(GS_ERR_INVALID_ARG, "too many tiles in one call");
+  return GS_OK;
+}
+
+// Enqueue one call. When `upload_src` is given the view table is copied from
+// it (pinned memory, for graph capture); otherwise from hv (pageable: the copy
+// is staged before cudaMemcpyAsync returns).
+gs_status enqueue(gs_scene* s, const std::vector<View>& hv, uint64_t n_tiles, const GradIn* g, cudaStream_t st,
+                  const View* upload_src) {
+  const int nv = (int)hv.size();
+  GS_TRY(grow_tiles(s, n_tiles));
+  GS_TRY(ensure(s->views, (size_t)nv * sizeof(View)));
+  if (s->rec_cap == 0) {
+    const uint64_t guess = std::max<uint64_t>(1u << 16, (uint64_t)s->n * nv / 4);
+    GS_TRY(grow_records(s, guess, g != nullptr));
+    GS_TRY(grow_pairs(s, guess * 4));
+  } else {
+    GS_TRY(grow_records(s, s->rec_cap, g != nullptr));
+  }
+  if (s->pair_cap == 0) GS_TRY(grow_pairs(s, (uint64_t)s->rec_cap * 4));
+  View* dviews = dp<View>(s->views);
+  GS_CUDA(cudaMemcpyAsync(dviews, upload_src ? upload_src : hv.data(), (size_t)nv * sizeof(View),
+                          cudaMemcpyHostToDevice, st));
+  Work w = work_of(s, (uint32_t)n_tiles);
+  GS_CUDA(cudaMemsetAsync(w.tile_count, 0, (n_tiles + 1) * sizeof(uint32_t), st));
+  GS_CUDA(cudaMemsetAsync(w.ctr, 0, sizeof(Counters), st));
+  const SceneDev sc = scene_dev(s);
+  std::vector<cudaEvent_t> ev;
+  const bool timed = s->timing && upload_src == nullptr;  // no events inside captured graphs
+  if (timed) {
+    if (!s->ev_free.empty()) {
+      ev = std::move(s->ev_free.back());
+      s->ev_free.pop_back();
+    } else {
+      ev.resize(GS_KERNEL_COUNT + 1);
+      for (auto& e : ev) GS_CUDA(cudaEventCreate(&e));
+    }
+  }
+  auto mark = [&](int k) -> cudaError_t { return timed ? cudaEventRecord(ev[k], st) : cudaSuccess; };
+  GS_CUDA(mark(0));
+  GS_CUDA(launch_project(sc, dviews, nv, w, g != nullptr, s->sm_count * 8, st));
+  GS_CUDA(mark(1));
+  GS_CUDA(launch_scan_tiles(w, st));
+  GS_CUDA(mark(2));
+  GS_CUDA(launch_scatter(dviews, w, s->sm_count * 8, st));
+  GS_CUDA(mark(3));
+  GS_CUDA(launch_composite(sc, dviews, nv, w, s->sm_count * composite_blocks_per_sm(s->feat_dim), st));
+  GS_CUDA(mark(4));
+  if (g) {
+    GS_CUDA(launch_backward(dviews, nv, w, s->sm_count * backward_blocks_per_sm(), st));
+    GS_CUDA(mark(5));
+    GS_CUDA(launch_reduce(w, g->result ? g->result : w.result, st));
+    GS_CUDA(mark(6));
+  }
+  if (timed) s->ev_pending.push_back({std::move(ev), g ? GS_KERNEL_COUNT : 4});
+  s->last_views = hv;
+  s->last_tiles = (uint32_t)n_tiles;
+  return GS_OK;
+}
+
+gs_status read_counters(gs_scene* s, cudaStream_t st, Counters& c) {
+  GS_CUDA(cudaMemcpyAsync(s->ctr_host, s->ctr.p, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+  GS_CUDA(cudaStreamSynchronize(st));
+  c = *s->ctr_host;
+  return GS_OK;
+}
+
+// Synchronous call with the regrow rule: render, check the counters, and if the
+// workspace was too small grow it and render again.
+gs_status run_sync(gs_scene* s, const std::vector<View>& hv, uint64_t n_tiles, const GradIn* g, cudaStream_t st) {
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    GS_TRY(enqueue(s, hv, n_tiles, g, st, nullptr));
+    Counters c;
+    GS_TRY(read_counters(s, st, c));
+    if (c.error) return fail(GS_ERR_INTERNAL, "device consistency check failed");
+    if (!c.overflow) return GS_OK;
+    if (c.overflow & 4u) return fail(GS_ERR_CAPACITY, "more than 2^32 (tile, Gaussian) pairs in one call");
+    uint64_t need_rec = std::max<uint64_t>(s->rec_cap, (uint64_t)c.rec_count + c.rec_count / 4 + 1024);
+    uint64_t need_pair = std::max<uint64_t>(s->pair_cap, (uint64_t)c.pair_total + c.pair_total / 4 + 4096);
+    if (c.overflow & 1u)  // pair count is incomplete when records overflowed
+      need_pair = std::max<uint64_t>(need_pair, (uint64_t)s->pair_cap * (need_rec / std::max<uint32_t>(1, s->rec_cap) + 1));
+    GS_CUDA(cudaStreamSynchronize(st));
+    GS_TRY(grow_records(s, need_rec, g != nullptr));
+    GS_TRY(grow_pairs(s, need_pair));
+  }
+  return fail(GS_ERR_CAPACITY, "workspace did not converge");
+}
+
+gs_status check_scene(const gs_scene* s) {
+  if (!s) return fail(GS_ERR_INVALID_ARG, "scene is NULL");
+  return GS_OK;
+}
+
+gs_status set_device(const gs_scene* s) {
+  GS_CUDA(cudaSetDevice(s->device));
+  return GS_OK;
+}
+
+gs_status check_grad_args(const float* target_rgb, const float* target_depth, float depth_weight) {
+  if (!target_rgb || !target_depth) return fail(GS_ERR_INVALID_ARG, "target_rgb and target_depth are required");
+  if (!std::isfinite(depth_weight) || depth_weight < 0.0f)
+    return fail(GS_ERR_INVALID_ARG, "depth_weight must be finite and >= 0");
+  return GS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gs_last_error(void) { return g_err.c_str(); }
+
+const char* gs_version(void) { return "gsr 0.1 (sm_103a)"; }
+
+gs_status gs_create_scene(const gs_scene_desc* d, gs_scene** out) {
+  g_err.clear();
+  if (!d || !out) return fail(GS_ERR_INVALID_ARG, "desc and out are required");
+  *out = nullptr;
+  if (d->n < 0 || d->n >= 0x7fffffffLL) return fail(GS_ERR_INVALID_ARG, "n out of range");
+  if (d->sh_degree < 0 || d->sh_degree > 3) return fail(GS_ERR_INVALID_ARG, "sh_degree must be 0..3");
+  if (d->feat_dim != 0 && d->feat_dim != 32) return fail(GS_ERR_INVALID_ARG, "feat_dim must be 0 or 32");
+  if (d->n > 0 && (!d->means || !d->scales || !d->quats || !d->opacities || !d->sh))
+    return fail(GS_ERR_INVALID_ARG, "scene arrays are required when n > 0");
+  if (d->n > 0 && d->feat_dim && !d->feats_bf16) return fail(GS_ERR_INVALID_ARG, "feats_bf16 required");
+  if (d->n_partitions < 0) return fail(GS_ERR_INVALID_ARG, "n_partitions < 0");
+  std::vector<int64_t> parts;
+  if (d->n_partitions > 0) {
+    if (!d->partition_offsets) return fail(GS_ERR_INVALID_ARG, "partition_offsets required");
+    parts.assign(d->partition_offsets, d->partition_offsets + d->n_partitions + 1);
+    if (parts.front() != 0 || parts.back() != d->n) return fail(GS_ERR_INVALID_ARG, "partition table must span [0, n]");
+    for (int k = 0; k < d->n_partitions; ++k)
+      if (parts[k + 1] < parts[k]) return fail(GS_ERR_INVALID_ARG, "partition offsets must ascend");
+  } else {
+    parts = {0, d->n};
+  }
+  gs_scene* s = new gs_scene();
+  s->n = d->n;
+  s->sh_degree = d->sh_degree;
+  s->feat_dim = d->feat_dim;
+  s->part_off = parts;
+  const int K3 = 3 * (d->sh_degree + 1) * (d->sh_degree + 1);
+  s->nsh4 = (K3 + 3) / 4;
+  auto cleanup = [&](gs_status st) {
+    gs_destroy_scene(s);
+    return st;
+  };
+  cudaError_t e = cudaGetDevice(&s->device);
+  if (e != cudaSuccess) return cleanup(fail(GS_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e)));
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, s->device);
+  if (e != cudaSuccess) return cleanup(fail(GS_ERR_CUDA, std::string("cudaGetDeviceProperties: ") + cudaGetErrorString(e)));
+  s->sm_count = prop.multiProcessorCount;
+  const size_t n = (size_t)d->n;
+  gs_status st;
+  if ((st = ensure(s->pos, n * sizeof(float4))) != GS_OK) return cleanup(st);
+  if ((st = ensure(s->cov, 2 * n * sizeof(float4))) != GS_OK) return cleanup(st);
+  if ((st = ensure(s->sh, n * s->nsh4 * sizeof(float4))) != GS_OK) return cleanup(st);
+  if (s->feat_dim && (st = ensure(s->feat, n * 4 * sizeof(uint4))) != GS_OK) return cleanup(st);
+  if ((st = ensure(s->ctr, sizeof(Counters))) != GS_OK) return cleanup(st);
+  if ((st = ensure(s->result, 8 * sizeof(double))) != GS_OK) return cleanup(st);
+  if (cudaMallocHost(&s->ctr_host, sizeof(Counters)) != cudaSuccess ||
+      cudaMallocHost(&s->result_host, 8 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return cleanup(fail(GS_ERR_OOM, "pinned host allocation failed"));
+  }
+  if (n > 0) {
+    const float *m = d->means, *sc = d->scales, *q = d->quats, *o = d->opacities, *sh = d->sh;
+    const uint16_t* f = d->feats_bf16;
+    DevBuf staging;
+    if (!d->device_resident) {
+      const size_t fb = s->feat_dim ? n * 32 * sizeof(uint16_t) : 0;
+      const size_t bytes = n * (3 + 3 + 4 + 1 + K3) * sizeof(float) + fb;
+      if ((st = ensure(staging, bytes)) != GS_OK) return cleanup(st);
+      char* p = static_cast<char*>(staging.p);
+      auto put = [&](const void* src, size_t b) {
+        void* dst = p;
+        p += b;
+        return std::make_pair(dst, cudaMemcpy(dst, src, b, cudaMemcpyHostToDevice));
+      };
+      auto r1 = put(m, n * 3 * 4), r2 = put(sc, n * 3 * 4), r3 = put(q, n * 4 * 4), r4 = put(o, n * 4),
+           r5 = put(sh, n * K3 * 4);
+      std::pair<void*, cudaError_t> r6{nullptr, cudaSuccess};
+      if (fb) r6 = put(f, fb);
+      for (auto* r : {&r1, &r2, &r3, &r4, &r5, &r6})
+        if (r->second != cudaSuccess) {
+          release(staging);
+          return cleanup(fail(GS_ERR_CUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(r->second)));
+        }
+      m = (const float*)r1.first;
+      sc = (const float*)r2.first;
+      q = (const float*)r3.first;
+      o = (const float*)r4.first;
+      sh = (const float*)r5.first;
+      f = (const uint16_t*)r6.first;
+    }
+    e = launch_pack_scene(m, sc, q, o, sh, K3, f, s->feat_dim, (int)n, s->nsh4, dp<float4>(s->pos), dp<float4>(s->cov),
+                          dp<float4>(s->sh), s->feat_dim ? dp<uint4>(s->feat) : nullptr, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    release(staging);
+    if (e != cudaSuccess) return cleanup(fail(GS_ERR_CUDA, std::string("pack: ") + cudaGetErrorString(e)));
+  }
+  // occupancy queries outside any stream capture
+  composite_blocks_per_sm(s->feat_dim);
+  backward_blocks_per_sm();
+  *out = s;
+  return GS_OK;
+}
+
+void gs_destroy_scene(gs_scene* s) {
+  if (!s) return;
+  cudaSetDevice(s->device);
+  cudaDeviceSynchronize();
+  if (s->graph.exec) cudaGraphExecDestroy(s->graph.exec);
+  if (s->graph.host_views) cudaFreeHost(s->graph.host_views);
+  if (s->graph.done) cudaEventDestroy(s->graph.done);
+  if (s->graph.capture) cudaStreamDestroy(s->graph.capture);
+  for (auto& tc : s->ev_pending)
+    for (cudaEvent_t e : tc.ev) cudaEventDestroy(e);
+  for (auto& ev : s->ev_free)
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  for (DevBuf* b : {&s->pos, &s->cov, &s->sh, &s->feat, &s->rec_a, &s->rec_b, &s->rec_c, &s->rec_m, &s->rec_j,
+                    &s->tile_count, &s->tile_offset, &s->tile_cursor, &s->partials, &s->pairs, &s->pairs_tmp,
+                    &s->ctr, &s->result, &s->views, &s->int_pix})
+    release(*b);
+  if (s->ctr_host) cudaFreeHost(s->ctr_host);
+  if (s->result_host) cudaFreeHost(s->result_host);
+  delete s;
+}
+
+gs_status gs_scene_reserve(gs_scene* s, int64_t max_records, int64_t max_pairs) {
+  g_err.clear();
+  GS_TRY(check_scene(s));
+  if (max_records < 0 || max_pairs < 0) return fail(GS_ERR_INVALID_ARG, "negative reservation");
+  GS_TRY(set_device(s));
+  GS_CUDA(cudaDeviceSynchronize());
+  GS_TRY(grow_records(s, (uint64_t)max_records, true));
+  GS_TRY(grow_pairs(s, (uint64_t)max_pairs));
+  return GS_OK;
+}
+
+gs_status gs_render(gs_scene* s, const gs_camera* cam, const gs_pose* pose, const gs_outputs* out, void* stream) {
+  g_err.clear();
+  GS_TRY(check_scene(s));
+  if (!cam || !pose) return fail(GS_ERR_INVALID_ARG, "cam and pose are required");
+  GS_TRY(set_device(s));
+  std::vector<View> hv;
+  uint64_t n_tiles;
+  GS_TRY(build_views(s, 1, cam, pose, out, nullptr, hv, n_tiles));
+  return run_sync(s, hv, n_tiles, nullptr, (cudaStream_t)stream);
+}
+
+gs_status gs_render_async(gs_scene* s, const gs_camera* cam, const gs_pose* pose, const gs_outputs* out,
+                          void* stream) {
+  g_err.clear();
+  GS_TRY(check_scene(s));
+  if (!cam || !pose) return fail(GS_ERR_INVALID_ARG, "cam and pose are required");
+  GS_TRY(set_device(s));
+  std::vector<View> hv;
+  uint64_t n_tiles;
+  GS_TRY(build_views(s, 1, cam, pose, out, nullptr, hv, n_tiles));
+  return enqueue(s, hv, n_tiles, nullptr, (cudaStream_t)stream, nullptr);
+}
+
+gs_status gs_render_pose_grad(gs_scene* s, const gs_camera* cam, const gs_pose* pose, const float* target_rgb,
+                              const float* target_depth, const float* pixel_weight, float depth_weight,
+                              const gs_outputs* out, double* loss_out, double* grad_xi_out, void* stream) {
+  g_err.clear();
+  GS_TRY(check_scene(s));
+  if (!cam || !pose) return fail(GS_ERR_INVALID_ARG, "cam and pose are required");
+  GS_TRY(check_grad_args(target_rgb, target_depth, depth_weight));
+  GS_TRY(set_device(s));
+  GradIn g{target_rgb, target_depth, pixel_weight, depth_weight, nullptr};
+  std::vector<View> hv;
+  uint64_t n_tiles;
+  GS_TRY(build_views(s, 1, cam, pose, out, &g, hv, n_tiles));
+  const cudaStream_t st = (cudaStream_t)stream;
+  GS_TRY(run_sync(s, hv, n_tiles, &g, st));
+  GS_CUDA(cudaMemcpyAsync(s->result_host, s->result.p, 7 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  GS_CUDA(cudaStreamSynchronize(st));
+  if (loss_out) *loss_out = s->result_host[0];
+  if (grad_xi_out)
+    for (int k = 0; k < 6; ++k) grad_xi_out[k] = s->result_host[1 + k];
+  return GS_OK;
+}
+
+gs_status gs_render_pose_grad_async(gs_scene* s, const gs_camera* cam, const gs_pose* pose, const float* target_rgb,
+                                    const float* target_depth, const float* pixel_weight, float depth_weight,
+                                    const gs_outputs* out, double* result_dev, void* stream) {
+  g_err.clear();
+  GS_TRY(check_scene(s));
+  if (!cam || !pose || !result_dev) return fail(GS_ERR_INVALID_ARG, "cam, pose and result_dev are required");
+  GS_TRY(check_grad_args(target_rgb, target_depth, depth_weight));
+  GS_TRY(set_device(s));
+  GradIn g{target_rgb, target_depth, pixel_weight, depth_weight, result_dev};
+  std::vector<View> hv;
+  uint64_t n_tiles;
+  GS_TRY(build_views(s, 1, cam, pose, out, &g, hv, n_tiles));
+  return enqueue(s, hv, n_tiles, &g, (cudaStream_t)stream, nullptr);
+}
+
+gs_status gs_render_batch(gs_scene* s, int n_views, const gs_camera* cams, const gs_pose* poses,
+                          const gs_outputs* outs, unsigned flags, void* stream) {
+  g_err.clear();
+  GS_TRY(check_scene(s));
+  if (n_views < 1 || !cams || !poses || !outs) return fail(GS_ERR_INVALID_ARG, "n_views >= 1, cams, poses, outs required");
+  if (flags & ~GS_BATCH_GRAPH) return fail(GS_ERR_INVALID_ARG, "unknown flag");
+  GS_TRY(set_device(s));
+  const cudaStream_t st = (cudaStream_t)stream;
+  std::vector<View> hv;
+  uint64_t n_tiles;
+  GS_TRY(build_views(s, n_views, cams, poses, outs, nullptr, hv, n_tiles));
+  if (!(flags & GS_BATCH_GRAPH)) return run_sync(s, hv, n_tiles, nullptr, st);
+
+  GraphCache& G = s->graph;
+  bool same = G.valid && G.n_views == n_views;
+  for (int v = 0; same && v < n_views; ++v)
+    same = std::memcmp(&G.cams[v], &cams[v], sizeof(gs_camera)) == 0 &&
+           std::memcmp(&G.outs[v], &outs[v], sizeof(gs_outputs)) == 0;
+  if (!same) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    G.exec = nullptr;
+    G.valid = false;
+    if (G.host_views) cudaFreeHost(G.host_views);
+    G.host_views = nullptr;
+    if (!G.done) GS_CUDA(cudaEventCreateWithFlags(&G.done, cudaEventDisableTiming));
+    GS_CUDA(cudaMallocHost(&G.host_views, (size_t)n_views * sizeof(View)));
+    std::memcpy(G.host_views, hv.data(), (size_t)n_views * sizeof(View));
+    // allocate everything the capture needs before capturing
+    GS_TRY(grow_tiles(s, n_tiles));
+    GS_TRY(ensure(s->views, (size_t)n_views * sizeof(View)));
+    if (s->rec_cap == 0) {
+      const uint64_t guess = std::max<uint64_t>(1u << 16, (uint64_t)s->n * n_views / 4);
+      GS_TRY(grow_records(s, guess, false));
+      GS_TRY(grow_pairs(s, guess * 4));
+    }
+    // capture on a private stream (the legacy default stream cannot be captured);
+    // the graph is then launched on the caller's stream
+    if (!G.capture) GS_CUDA(cudaStreamCreateWithFlags(&G.capture, cudaStreamNonBlocking));
+    GS_CUDA(cudaStreamSynchronize(st));
+    cudaGraph_t graph = nullptr;
+    GS_CUDA(cudaStreamBeginCapture(G.capture, cudaStreamCaptureModeThreadLocal));
+    const gs_status est = enqueue(s, hv, n_tiles, nullptr, G.capture, G.host_views);
+    const cudaError_t ce = cudaStreamEndCapture(G.capture, &graph);
+    if (est != GS_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return est;
+    }
+    if (ce != cudaSuccess) return fail(GS_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ce));
+    const cudaError_t ie = cudaGraphInstantiate(&G.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return fail(GS_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+    G.cams.assign(cams, cams + n_views);
+    G.outs.assign(outs, outs + n_views);
+    G.n_views = n_views;
+    G.valid = true;
+  } else {
+    // the previous replay must have consumed the pinned view table
+    GS_CUDA(cudaEventSynchronize(G.done));
+    std::memcpy(G.host_views, hv.data(), (size_t)n_views * sizeof(View));
+    s->last_views = hv;
+    s->last_tiles = (uint32_t)n_tiles;
+  }
+  GS_CUDA(cudaGraphLaunch(G.exec, st));
+  GS_CUDA(cudaEventRecord(G.done, st));
+  return GS_OK;
+}
+
+gs_status gs_scene_set_timing(gs_scene* s, int enable) {
+  g_err.clear();
+  GS_TRY(check_scene(s));
+  s->timing = enable != 0;
+  return GS_OK;
+}
+
+gs_status gs_scene_kernel_times(gs_scene* s, double* total_ms, int64_t* launches) {
+  g_err.clear();
+  GS_TRY(check_scene(s));
+  if (!total_ms) return fail(GS_ERR_INVALID_ARG, "total_ms is required");
+  GS_TRY(set_device(s));
+  for (auto& tc : s->ev_pending) {
+    GS_CUDA(cudaEventSynchronize(tc.ev[tc.n_kernels]));
+    for (int k = 0; k < tc.n_kernels; ++k) {
+      float ms = 0.f;
+      GS_CUDA(cudaEventElapsedTime(&ms, tc.ev[k], tc.ev[k + 1]));
+      s->kt_ms[k] += ms;
+      s->kt_n[k] += 1;
+    }
+    s->ev_free.push_back(std::move(tc.ev));
+  }
+  s->ev_pending.clear();
+  for (int k = 0; k < GS_KERNEL_COUNT; ++k) {
+    total_ms[k] = s->kt_ms[k];
+    if (launches) launches[k] = s->kt_n[k];
+    s->kt_ms[k] = 0.0;
+    s->kt_n[k] = 0;
+  }
+  return GS_OK;
+}
+
+gs_status gs_scene_status(gs_scene* s, void* stream, int64_t* needed_records, int64_t* needed_pairs) {
+  g_err.clear();
+  GS_TRY(check_scene(s));
+  GS_TRY(set_device(s));
+  Counters c;
+  GS_TRY(read_counters(s, (cudaStream_t)stream, c));
+  if (needed_records) *needed_records = c.rec_count;
+  if (needed_pairs) *needed_pairs = c.pair_total;
+  if (c.error) return fail(GS_ERR_INTERNAL, "device consistency check failed");
+  if (c.overflow) return fail(GS_ERR_CAPACITY, "workspace too small for the last asynchronous call");
+  return GS_OK;
+}
+
+gs_status gs_get_tile_lists(gs_scene* s, int view, uint64_t* keys, uint32_t* gids, int64_t* tile_start,
+                            int64_t capacity, int64_t* n_pairs, void* stream) {
+  g_err.clear();
+  GS_TRY(check_scene(s));
+  if (view < 0 || view >= (int)s->last_views.size()) return fail(GS_ERR_INVALID_ARG, "no such view in the last call");
+  if (!keys || !gids || !tile_start || !n_pairs) return fail(GS_ERR_INVALID_ARG, "output pointers required");
+  GS_TRY(set_device(s));
+  const cudaStream_t st = (cudaStream_t)stream;
+  Counters c;
+  GS_TRY(read_counters(s, st, c));
+  if (c.overflow) return fail(GS_ERR_CAPACITY, "last call overflowed its workspace");
+  const View& V = s->last_views[view];
+  const uint32_t nt = (uint32_t)(V.tiles_x * V.tiles_y);
+  std::vector<uint32_t> off(nt + 1);
+  GS_CUDA(cudaMemcpy(off.data(), dp<uint32_t>(s->tile_offset) + V.tile_base, (nt + 1) * sizeof(uint32_t),
+                     cudaMemcpyDeviceToHost));
+  const int64_t np = (int64_t)off[nt] - off[0];
+  *n_pairs = np;
+  for (uint32_t t = 0; t <= nt; ++t) tile_start[t] = (int64_t)off[t] - off[0];
+  if (np > capacity) return fail(GS_ERR_INVALID_ARG, "capacity too small");
+  std::vector<uint2> pr((size_t)np);
+  if (np) GS_CUDA(cudaMemcpy(pr.data(), dp<uint2>(s->pairs) + off[0], np * sizeof(uint2), cudaMemcpyDeviceToHost));
+  const uint32_t nrec = std::min(c.rec_count, s->rec_cap);
+  std::vector<float4> rb(nrec);
+  if (nrec) GS_CUDA(cudaMemcpy(rb.data(), s->rec_b.p, nrec * sizeof(float4), cudaMemcpyDeviceToHost));
+  for (uint32_t t = 0; t < nt; ++t)
+    for (uint32_t j = off[t] - off[0]; j < off[t + 1] - off[0]; ++j) {
+      keys[j] = ((uint64_t)t << 32) | pr[j].x;
+      float gf = rb[pr[j].y].w;
+      int32_t gi;
+      std::memcpy(&gi, &gf, 4);
+      gids[j] = (uint32_t)gi;
+    }
+  return GS_OK;
+}
+
+gs_status gs_get_records(gs_scene* s, int view, int32_t* rec, int64_t capacity, int64_t* n_records, void* stream) {
+  g_err.clear();
+  GS_TRY(check_scene(s));
+  if (view < 0 || view >= (int)s->last_views.size()) return fail(GS_ERR_INVALID_ARG, "no such view in the last call");
+  if (!rec || !n_records) return fail(GS_ERR_INVALID_ARG, "output pointers required");
+  GS_TRY(set_device(s));
+  Counters c;
+  GS_TRY(read_counters(s, (cudaStream_t)stream, c));
+  if (c.overflow) return fail(GS_ERR_CAPACITY, "last call overflowed its workspace");
+  const uint32_t nrec = std::min(c.rec_count, s->rec_cap);
+  std::vector<float4> ra(nrec), rb(nrec);
+  std::vector<uint4> rm(nrec);
+  if (nrec) {
+    GS_CUDA(cudaMemcpy(ra.data(), s->rec_a.p, nrec * sizeof(float4), cudaMemcpyDeviceToHost));
+    GS_CUDA(cudaMemcpy(rb.data(), s->rec_b.p, nrec * sizeof(float4), cudaMemcpyDeviceToHost));
+    GS_CUDA(cudaMemcpy(rm.data(), s->rec_m.p, nrec * sizeof(uint4), cudaMemcpyDeviceToHost));
+  }
+  int64_t k = 0;
+  for (uint32_t r = 0; r < nrec; ++r) {
+    if ((int)rm[r].z != view) continue;
+    if (k < capacity) {
+      int32_t* o = rec + 8 * k;
+      std::memcpy(&o[0], &rb[r].w, 4);
+      o[1] = (int32_t)(rm[r].x & 0xffff);
+      o[2] = (int32_t)(rm[r].x >> 16);
+      o[3] = (int32_t)(rm[r].y & 0xffff);
+      o[4] = (int32_t)(rm[r].y >> 16);
+      o[5] = (int32_t)rm[r].w;
+      std::memcpy(&o[6], &ra[r].x, 4);
+      std::memcpy(&o[7], &ra[r].y, 4);
+    }
+    ++k;
+  }
+  *n_records = k;
+  if (k > capacity) return fail(GS_ERR_INVALID_ARG, "capacity too small");
+  return GS_OK;
+}
+
+}  // extern "C"

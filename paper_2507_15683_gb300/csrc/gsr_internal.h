@@ -1,0 +1,107 @@
+// Internal declarations of libgsr: device layout, per-view parameters and the
+// kernel launchers shared by the translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gsr.h"
+
+namespace gsr {
+
+constexpr int kTile = 16;          // tile edge in pixels
+constexpr int kTileThreads = 256;  // one thread per pixel of a tile
+constexpr int kSortCap = 2048;     // (tile, Gaussian) pairs a tile sorts in shared memory
+constexpr int kBatchF = 256;       // Gaussians staged per forward batch
+constexpr int kBatchB = 128;       // Gaussians staged per backward batch
+constexpr int kJacStride = 48;     // floats per record of the pose Jacobian (45 used)
+constexpr int kPartialStride = 8;  // doubles per tile partial (loss + 6 grad + pad)
+
+// Per-view parameters (device copy built on the host for every call).
+struct View {
+  float R[9];           // world-to-camera rotation (binary32, row-major)
+  float t[3];           // world-to-camera translation
+  float fx, fy, cx, cy;
+  float limx, limy;     // 1.3 x half field of view, in normalised coordinates
+  float cw[3];          // camera centre in world coordinates
+  float jb2;            // fx^2 (1 + limx^2) + fy^2 (1 + limy^2): bound on z^2 |J|_F^2
+  int width, height, tiles_x, tiles_y;
+  uint32_t tile_base;   // first global tile index of this view
+  uint32_t pad0;
+  float* rgb;           // outputs (device; NULL = not written)
+  float* depth;
+  float* alpha;
+  float* final_T;
+  float* feats;
+  uint32_t* last_idx;
+  const float* target_rgb;   // loss inputs (pose gradient only)
+  const float* target_depth;
+  const float* pixel_weight;
+  float depth_weight;
+  float inv_3p;         // 1 / (3 W H)
+  float inv_p;          // 1 / (W H)
+  float pad1;
+};
+
+// Device counters and status of one call (zeroed at its start).
+struct Counters {
+  unsigned int rec_count;   // records requested by the projection (may exceed capacity)
+  unsigned int pair_total;  // pairs requested by the binning
+  unsigned int overflow;    // bit 0: records, bit 1: pairs, bit 2: pair count >= 2^32
+  unsigned int fwd_queue;   // persistent forward tile queue
+  unsigned int bwd_queue;   // persistent backward tile queue
+  unsigned int error;       // device-side consistency failure
+  unsigned int pad[2];
+};
+
+// Scene arena (device pointers).
+struct SceneDev {
+  const float4* pos;   // n: (x, y, z, max scale)
+  const float4* cov;   // 2n: (S00, S01, S02, S11), (S12, S22, opacity, 0)
+  const float4* sh;    // n * nsh4: SH coefficients, coefficient-major, padded to float4
+  const uint4* feat;   // n * 4: 32 bfloat16 features, or NULL
+  int n;
+  int sh_degree;
+  int nsh4;
+  int feat_dim;
+};
+
+// Per-call workspace (device pointers and capacities).
+struct Work {
+  float4* rec_a;       // (u, v, conic A, conic B)
+  float4* rec_b;       // (conic C, opacity, depth z, Gaussian index bits)
+  float4* rec_c;       // (r, g, b, 0)
+  uint4* rec_m;        // (x0 | x1 << 16, y0 | y1 << 16, view, depth bits)
+  float* rec_j;        // kJacStride floats per record (pose gradient only)
+  uint32_t rec_cap;
+  uint32_t* tile_count;   // n_tiles + 1
+  uint32_t* tile_offset;  // n_tiles + 1 (exclusive scan)
+  uint32_t* tile_cursor;  // n_tiles
+  uint32_t n_tiles;
+  uint2* pairs;        // (depth bits, record index), sorted per tile by the compositor
+  uint2* pairs_tmp;    // scratch for tiles longer than kSortCap
+  uint32_t pair_cap;
+  Counters* ctr;
+  double* partials;    // n_tiles * kPartialStride
+  double* result;      // 7 doubles (loss, grad)
+};
+
+// launchers (return the CUDA error of the launch)
+cudaError_t launch_pack_scene(const float* means, const float* scales, const float* quats,
+                              const float* opacities, const float* sh, int sh_k3, const uint16_t* feats,
+                              int feat_dim, int n, int nsh4, float4* pos, float4* cov, float4* sh_out,
+                              uint4* feat_out, cudaStream_t st);
+cudaError_t launch_project(const SceneDev& sc, const View* views, int n_views, const Work& w, bool grad,
+                           int grid, cudaStream_t st);
+cudaError_t launch_scan_tiles(const Work& w, cudaStream_t st);
+cudaError_t launch_scatter(const View* views, const Work& w, int grid, cudaStream_t st);
+cudaError_t launch_composite(const SceneDev& sc, const View* views, int n_views, const Work& w, int grid,
+                             cudaStream_t st);
+cudaError_t launch_backward(const View* views, int n_views, const Work& w, int grid, cudaStream_t st);
+cudaError_t launch_reduce(const Work& w, double* result, cudaStream_t st);
+
+// occupancy-derived persistent grid sizes (per SM)
+int composite_blocks_per_sm(int feat_dim);
+int backward_blocks_per_sm();
+
+}  // namespace gsr

@@ -1,0 +1,438 @@
+// Scene packing and per-Gaussian projection (EWA footprint, tile rectangle,
+// SH colour and, for the pose gradient, the per-Gaussian pose Jacobian).
+//
+// The projection follows Algorithm 1 of the paper (p = R X + t, depth = p.z,
+// perspective division, then K; Eq. 10). The "discrete layer" -- camera
+// depth, projected centre, 2D covariance, radius and tile rectangle -- is
+// evaluated with explicitly rounded binary32 operations (__fmul_rn,
+// __fadd_rn, ...) in one fixed order, so that the tile lists and sort keys are
+// reproducible bit for bit by any IEEE binary32 evaluation of the same
+// sequence. Everything after it (conic, colour, Jacobian) is ordinary fp32.
+#include <cuda_runtime.h>
+
+#include "gsr_internal.h"
+
+namespace gsr {
+namespace {
+
+__device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float dvd(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float sqr(float a) { return __fsqrt_rn(a); }
+// ((a0 b0 + a1 b1) + a2 b2), each operation rounded
+__device__ __forceinline__ float dot3(float a0, float b0, float a1, float b1, float a2, float b2) {
+  return add(add(mul(a0, b0), mul(a1, b1)), mul(a2, b2));
+}
+
+// ---------------------------------------------------------------------------
+// Scene packing: binary32 covariance Sigma = R(q) diag(s)^2 R(q)^T
+// ---------------------------------------------------------------------------
+__global__ void k_pack_scene(const float* __restrict__ means, const float* __restrict__ scales,
+                             const float* __restrict__ quats, const float* __restrict__ opacities,
+                             const float* __restrict__ sh, int sh_k3, const uint16_t* __restrict__ feats,
+                             int feat_dim, int n, int nsh4, float4* __restrict__ pos, float4* __restrict__ cov,
+                             float4* __restrict__ sh_out, uint4* __restrict__ feat_out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float qw = quats[4 * i + 0], qx = quats[4 * i + 1], qy = quats[4 * i + 2], qz = quats[4 * i + 3];
+    const float n2 = add(add(add(mul(qw, qw), mul(qx, qx)), mul(qy, qy)), mul(qz, qz));
+    float w = 1.0f, x = 0.0f, y = 0.0f, z = 0.0f;
+    if (n2 > 0.0f) {
+      const float nr = sqr(n2);
+      w = dvd(qw, nr);
+      x = dvd(qx, nr);
+      y = dvd(qy, nr);
+      z = dvd(qz, nr);
+    }
+    const float xx = mul(x, x), yy = mul(y, y), zz = mul(z, z);
+    const float xy = mul(x, y), xz = mul(x, z), yz = mul(y, z);
+    const float wx = mul(w, x), wy = mul(w, y), wz = mul(w, z);
+    float r[3][3];
+    r[0][0] = sub(1.0f, mul(2.0f, add(yy, zz)));
+    r[0][1] = mul(2.0f, sub(xy, wz));
+    r[0][2] = mul(2.0f, add(xz, wy));
+    r[1][0] = mul(2.0f, add(xy, wz));
+    r[1][1] = sub(1.0f, mul(2.0f, add(xx, zz)));
+    r[1][2] = mul(2.0f, sub(yz, wx));
+    r[2][0] = mul(2.0f, sub(xz, wy));
+    r[2][1] = mul(2.0f, add(yz, wx));
+    r[2][2] = sub(1.0f, mul(2.0f, add(xx, yy)));
+    const float s[3] = {scales[3 * i + 0], scales[3 * i + 1], scales[3 * i + 2]};
+    float m[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) m[a][b] = mul(r[a][b], s[b]);
+    float S[6];
+    const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      S[k] = dot3(m[ia[k]][0], m[ib[k]][0], m[ia[k]][1], m[ib[k]][1], m[ia[k]][2], m[ib[k]][2]);
+    const float smax = fmaxf(s[0], fmaxf(s[1], s[2]));
+    pos[i] = make_float4(means[3 * i], means[3 * i + 1], means[3 * i + 2], smax);
+    cov[2 * i] = make_float4(S[0], S[1], S[2], S[3]);
+    cov[2 * i + 1] = make_float4(S[4], S[5], opacities[i], 0.0f);
+    float* so = reinterpret_cast<float*>(sh_out + (size_t)i * nsh4);
+    for (int k = 0; k < 4 * nsh4; ++k) so[k] = (k < sh_k3) ? sh[(size_t)i * sh_k3 + k] : 0.0f;
+    if (feat_dim) {
+      uint16_t* fo = reinterpret_cast<uint16_t*>(feat_out + (size_t)i * 4);
+      for (int k = 0; k < 32; ++k) fo[k] = feats[(size_t)i * feat_dim + k];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Real spherical harmonics (Condon-Shortley phase), index l*l + l + m, as
+// Cartesian polynomials; values are only used on the unit sphere and their
+// gradients only after projection onto the sphere's tangent plane.
+//   l=1: -c1 y, c1 z, -c1 x                        c1 = sqrt(3/(4pi))
+//   l=2: c2a xy, -c2a yz, c20 (3z^2-1), -c2a xz, c2c (x^2-y^2)
+//        c2a = sqrt(15/(4pi)), c20 = sqrt(5/(16pi)), c2c = sqrt(15/(16pi))
+//   l=3: -c3a (3x^2 y - y^3), c3b xyz, -c3c y(5z^2-1), c30 z(5z^2-3),
+//        -c3c x(5z^2-1), c3d z(x^2-y^2), -c3a (x^3 - 3x y^2)
+//        c3a = sqrt(35/(32pi)), c3b = sqrt(105/(4pi)), c3c = sqrt(21/(32pi)),
+//        c30 = sqrt(7/(16pi)), c3d = sqrt(105/(16pi))
+// ---------------------------------------------------------------------------
+constexpr float kC0 = 0.28209479177387814f;
+constexpr float kC1 = 0.48860251190291992f;
+constexpr float kC2a = 1.0925484305920792f;
+constexpr float kC20 = 0.31539156525252005f;
+constexpr float kC2c = 0.54627421529603959f;
+constexpr float kC3a = 0.59004358992664352f;
+constexpr float kC3b = 2.8906114426405538f;
+constexpr float kC3c = 0.45704579946446572f;
+constexpr float kC30 = 0.37317633259011540f;
+constexpr float kC3d = 1.4453057213202769f;
+
+// Accumulates colour (value) and, when GRADC, the Cartesian gradient of each
+// channel's polynomial G[ch][0..2].
+template <int DEG, bool GRADC>
+__device__ __forceinline__ void eval_sh(const float4* __restrict__ shp, float x, float y, float z, float rgb[3],
+                                        float G[3][3]) {
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  constexpr int NF4 = (3 * K + 3) / 4;
+  float c[4 * NF4];
+#pragma unroll
+  for (int k = 0; k < NF4; ++k) {
+    const float4 v = __ldg(shp + k);
+    c[4 * k] = v.x;
+    c[4 * k + 1] = v.y;
+    c[4 * k + 2] = v.z;
+    c[4 * k + 3] = v.w;
+  }
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) {
+    rgb[ch] = kC0 * c[ch] + 0.5f;
+    if (GRADC) G[ch][0] = G[ch][1] = G[ch][2] = 0.0f;
+  }
+#define GS_ACC(k, Y, gx, gy, gz)                                  \
+  _Pragma("unroll") for (int ch = 0; ch < 3; ++ch) {               \
+    const float co = c[3 * (k) + ch];                              \
+    rgb[ch] = fmaf(co, (Y), rgb[ch]);                              \
+    if (GRADC) {                                                   \
+      G[ch][0] = fmaf(co, (gx), G[ch][0]);                         \
+      G[ch][1] = fmaf(co, (gy), G[ch][1]);                         \
+      G[ch][2] = fmaf(co, (gz), G[ch][2]);                         \
+    }                                                              \
+  }
+  if (DEG >= 1) {
+    GS_ACC(1, -kC1 * y, 0.0f, -kC1, 0.0f);
+    GS_ACC(2, kC1 * z, 0.0f, 0.0f, kC1);
+    GS_ACC(3, -kC1 * x, -kC1, 0.0f, 0.0f);
+  }
+  if (DEG >= 2) {
+    const float xx = x * x, yy = y * y, zz = z * z;
+    GS_ACC(4, kC2a * x * y, kC2a * y, kC2a * x, 0.0f);
+    GS_ACC(5, -kC2a * y * z, 0.0f, -kC2a * z, -kC2a * y);
+    GS_ACC(6, kC20 * (3.0f * zz - 1.0f), 0.0f, 0.0f, 6.0f * kC20 * z);
+    GS_ACC(7, -kC2a * x * z, -kC2a * z, 0.0f, -kC2a * x);
+    GS_ACC(8, kC2c * (xx - yy), 2.0f * kC2c * x, -2.0f * kC2c * y, 0.0f);
+    if (DEG >= 3) {
+      GS_ACC(9, -kC3a * (3.0f * xx * y - yy * y), -kC3a * 6.0f * x * y, -kC3a * (3.0f * xx - 3.0f * yy), 0.0f);
+      GS_ACC(10, kC3b * x * y * z, kC3b * y * z, kC3b * x * z, kC3b * x * y);
+      GS_ACC(11, -kC3c * y * (5.0f * zz - 1.0f), 0.0f, -kC3c * (5.0f * zz - 1.0f), -kC3c * 10.0f * y * z);
+      GS_ACC(12, kC30 * z * (5.0f * zz - 3.0f), 0.0f, 0.0f, kC30 * (15.0f * zz - 3.0f));
+      GS_ACC(13, -kC3c * x * (5.0f * zz - 1.0f), -kC3c * (5.0f * zz - 1.0f), 0.0f, -kC3c * 10.0f * x * z);
+      GS_ACC(14, kC3d * z * (xx - yy), kC3d * 2.0f * x * z, -kC3d * 2.0f * y * z, kC3d * (xx - yy));
+      GS_ACC(15, -kC3a * (xx * x - 3.0f * x * yy), -kC3a * (3.0f * xx - 3.0f * yy), kC3a * 6.0f * x * y, 0.0f);
+    }
+  }
+#undef GS_ACC
+}
+
+template <bool GRADC>
+__device__ __forceinline__ void eval_sh_deg(int deg, const float4* shp, float x, float y, float z, float rgb[3],
+                                            float G[3][3]) {
+  switch (deg) {
+    case 0: eval_sh<0, GRADC>(shp, x, y, z, rgb, G); break;
+    case 1: eval_sh<1, GRADC>(shp, x, y, z, rgb, G); break;
+    case 2: eval_sh<2, GRADC>(shp, x, y, z, rgb, G); break;
+    default: eval_sh<3, GRADC>(shp, x, y, z, rgb, G); break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Projection: one thread per Gaussian, looping over the views of the call.
+// ---------------------------------------------------------------------------
+template <bool GRAD>
+__global__ void __launch_bounds__(256) k_project(SceneDev sc, const View* __restrict__ views, int n_views, Work w) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = blockIdx.x * blockDim.x; base < sc.n; base += stride) {  // warp-uniform loop
+    const int i = base + threadIdx.x;
+    const bool valid = i < sc.n;
+    const float4 p4 = valid ? __ldg(sc.pos + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = c0;
+    bool have_cov = false;
+    for (int vi = 0; vi < n_views; ++vi) {
+      const View& V = views[vi];
+      bool vis = false;
+      float u = 0.f, v = 0.f, pz = 0.f, ca = 0.f, cb = 0.f, cc = 0.f, ix = 0.f, iy = 0.f, px = 0.f, py = 0.f;
+      int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+      if (valid) {
+        px = add(add(add(mul(V.R[0], p4.x), mul(V.R[1], p4.y)), mul(V.R[2], p4.z)), V.t[0]);
+        py = add(add(add(mul(V.R[3], p4.x), mul(V.R[4], p4.y)), mul(V.R[5], p4.z)), V.t[1]);
+        pz = add(add(add(mul(V.R[6], p4.x), mul(V.R[7], p4.y)), mul(V.R[8], p4.z)), V.t[2]);
+        if (pz >= 0.2f) {
+          ix = dvd(px, pz);
+          iy = dvd(py, pz);
+          u = add(mul(V.fx, ix), V.cx);
+          v = add(mul(V.fy, iy), V.cy);
+          // Conservative reach: radius <= 3 sqrt(s_max^2 |J|_F^2 + 0.3 + sqrt(0.1)) + 1,
+          // with margins for rounding; a Gaussian that cannot reach the image has an
+          // empty rectangle under the exact rule, so skipping it changes nothing.
+          const float reach = 3.0f * sqrtf((p4.w * p4.w * V.jb2 / (pz * pz) + 0.62f) * 1.01f) + 3.0f;
+          const float wx = (float)(kTile * V.tiles_x), wy = (float)(kTile * V.tiles_y);
+          if (u + reach >= -1.0f && u - reach <= wx + 1.0f && v + reach >= -1.0f && v - reach <= wy + 1.0f) {
+            if (!have_cov) {
+              c0 = __ldg(sc.cov + 2 * i);
+              c1 = __ldg(sc.cov + 2 * i + 1);
+              have_cov = true;
+            }
+            const float xh = mul(fminf(V.limx, fmaxf(-V.limx, ix)), pz);
+            const float yh = mul(fminf(V.limy, fmaxf(-V.limy, iy)), pz);
+            const float pz2 = mul(pz, pz);
+            const float j00 = dvd(V.fx, pz), j02 = -dvd(mul(V.fx, xh), pz2);
+            const float j11 = dvd(V.fy, pz), j12 = -dvd(mul(V.fy, yh), pz2);
+            float T[2][3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              T[0][k] = add(mul(j00, V.R[k]), mul(j02, V.R[6 + k]));
+              T[1][k] = add(mul(j11, V.R[3 + k]), mul(j12, V.R[6 + k]));
+            }
+            const float S[3][3] = {{c0.x, c0.y, c0.z}, {c0.y, c0.w, c1.x}, {c0.z, c1.x, c1.y}};
+            float U[2][3];
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+              for (int k = 0; k < 3; ++k) U[a][k] = dot3(T[a][0], S[0][k], T[a][1], S[1][k], T[a][2], S[2][k]);
+            ca = add(dot3(U[0][0], T[0][0], U[0][1], T[0][1], U[0][2], T[0][2]), 0.3f);
+            cb = dot3(U[0][0], T[1][0], U[0][1], T[1][1], U[0][2], T[1][2]);
+            cc = add(dot3(U[1][0], T[1][0], U[1][1], T[1][1], U[1][2], T[1][2]), 0.3f);
+            const float det = sub(mul(ca, cc), mul(cb, cb));
+            if (det > 0.0f) {
+              const float mid = mul(0.5f, add(ca, cc));
+              const float disc = sub(mul(mid, mid), det);
+              const float lam = add(mid, sqr(fmaxf(0.1f, disc)));
+              const float r = ceilf(mul(3.0f, sqr(lam)));
+              if (r > 0.0f) {
+                float fx0 = floorf(dvd(sub(u, r), 16.0f)), fx1 = floorf(dvd(add(u, r), 16.0f));
+                float fy0 = floorf(dvd(sub(v, r), 16.0f)), fy1 = floorf(dvd(add(v, r), 16.0f));
+                fx0 = fmaxf(fx0, 0.0f);
+                fy0 = fmaxf(fy0, 0.0f);
+                fx1 = fminf(fx1, (float)(V.tiles_x - 1));
+                fy1 = fminf(fy1, (float)(V.tiles_y - 1));
+                if (!(fx0 > fx1 || fy0 > fy1)) {
+                  vis = true;
+                  x0 = (int)fx0;
+                  x1 = (int)fx1;
+                  y0 = (int)fy0;
+                  y1 = (int)fy1;
+                }
+              }
+            }
+          }
+        }
+      }
+      const unsigned vmask = __ballot_sync(0xffffffffu, vis);
+      if (vmask == 0u) continue;
+      unsigned slot0 = 0;
+      const int leader = __ffs(vmask) - 1;
+      if (lane == leader) slot0 = atomicAdd(&w.ctr->rec_count, (unsigned)__popc(vmask));
+      slot0 = __shfl_sync(0xffffffffu, slot0, leader);
+      if (!vis) continue;
+      const unsigned slot = slot0 + __popc(vmask & lt_mask);
+      if (slot >= w.rec_cap) {
+        atomicOr(&w.ctr->overflow, 1u);
+        continue;
+      }
+      // ---- continuous layer ----
+      // conic from the binary32 covariance; determinant with one compensated step
+      const float bb = cb * cb;
+      const float e = __fmaf_rn(-cb, cb, bb);
+      const float f = __fmaf_rn(ca, cc, -bb);
+      const float detc = f + e;
+      const float inv = 1.0f / detc;
+      const float A = cc * inv, B = -cb * inv, C = ca * inv;
+      // colour from SH at dir = normalize(mean - camera centre)
+      const float dxw = p4.x - V.cw[0], dyw = p4.y - V.cw[1], dzw = p4.z - V.cw[2];
+      const float dn = sqrtf(dxw * dxw + dyw * dyw + dzw * dzw);
+      const float rn = 1.0f / dn;
+      const float dirx = dxw * rn, diry = dyw * rn, dirz = dzw * rn;
+      float rgb[3], G[3][3];
+      eval_sh_deg<GRAD>(sc.sh_degree, sc.sh + (size_t)i * sc.nsh4, dirx, diry, dirz, rgb, G);
+      bool clampc[3];
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        clampc[ch] = rgb[ch] < 0.0f;
+        rgb[ch] = fmaxf(rgb[ch], 0.0f);
+      }
+      w.rec_a[slot] = make_float4(u, v, A, B);
+      w.rec_b[slot] = make_float4(C, c1.z, pz, __int_as_float(i));
+      w.rec_c[slot] = make_float4(rgb[0], rgb[1], rgb[2], 0.0f);
+      w.rec_m[slot] = make_uint4((unsigned)x0 | ((unsigned)x1 << 16), (unsigned)y0 | ((unsigned)y1 << 16),
+                                 (unsigned)vi, __float_as_uint(pz));
+      for (int ty = y0; ty <= y1; ++ty)
+        for (int tx = x0; tx <= x1; ++tx) atomicAdd(&w.tile_count[V.tile_base + ty * V.tiles_x + tx], 1u);
+
+      if (GRAD) {
+        // Pose Jacobian of (u, v, A, B, C, z) w.r.t. xi = (rho, phi) and of (r, g, b)
+        // w.r.t. rho, by forward differentiation along the six tangent directions:
+        // d p = rho + phi x p; d Sigma_cam = [phi]x Sigma_cam - Sigma_cam [phi]x;
+        // d (mean - camera centre) = R^T rho.
+        const float* R = V.R;
+        const float Sw[3][3] = {{c0.x, c0.y, c0.z}, {c0.y, c0.w, c1.x}, {c0.z, c1.x, c1.y}};
+        float Q[3][3], Sc[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) Q[a][b] = R[3 * a] * Sw[0][b] + R[3 * a + 1] * Sw[1][b] + R[3 * a + 2] * Sw[2][b];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) Sc[a][b] = Q[a][0] * R[3 * b] + Q[a][1] * R[3 * b + 1] + Q[a][2] * R[3 * b + 2];
+        const bool clx = (ix < -V.limx) || (ix > V.limx);
+        const bool cly = (iy < -V.limy) || (iy > V.limy);
+        const float Lx = ix < 0.0f ? -V.limx : V.limx, Ly = iy < 0.0f ? -V.limy : V.limy;
+        const float zi = 1.0f / pz;
+        const float xh = clx ? Lx * pz : px, yh = cly ? Ly * pz : py;
+        const float j00 = V.fx * zi, j02 = -V.fx * xh * zi * zi;
+        const float j11 = V.fy * zi, j12 = -V.fy * yh * zi * zi;
+        float K[2][3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          K[0][k] = j00 * Sc[0][k] + j02 * Sc[2][k];
+          K[1][k] = j11 * Sc[1][k] + j12 * Sc[2][k];
+        }
+        const float di = 1.0f / detc;
+        float jac[45];
+        const float pc[3] = {px, py, pz};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          float dp[3];
+          if (k < 3) {
+            dp[0] = (k == 0) ? 1.f : 0.f;
+            dp[1] = (k == 1) ? 1.f : 0.f;
+            dp[2] = (k == 2) ? 1.f : 0.f;
+          } else {
+            const int e3 = k - 3;  // e x p
+            dp[0] = (e3 == 1) ? pc[2] : (e3 == 2) ? -pc[1] : 0.f;
+            dp[1] = (e3 == 0) ? -pc[2] : (e3 == 2) ? pc[0] : 0.f;
+            dp[2] = (e3 == 0) ? pc[1] : (e3 == 1) ? -pc[0] : 0.f;
+          }
+          const float du = V.fx * (dp[0] - ix * dp[2]) * zi;
+          const float dv = V.fy * (dp[1] - iy * dp[2]) * zi;
+          const float dxh = clx ? Lx * dp[2] : dp[0];
+          const float dyh = cly ? Ly * dp[2] : dp[1];
+          const float dj00 = -j00 * dp[2] * zi;
+          const float dj02 = -V.fx * (dxh - 2.0f * xh * dp[2] * zi) * zi * zi;
+          const float dj11 = -j11 * dp[2] * zi;
+          const float dj12 = -V.fy * (dyh - 2.0f * yh * dp[2] * zi) * zi * zi;
+          // S = dJ K^T
+          const float S00 = dj00 * K[0][0] + dj02 * K[0][2];
+          const float S01 = dj00 * K[1][0] + dj02 * K[1][2];
+          const float S10 = dj11 * K[0][1] + dj12 * K[0][2];
+          const float S11 = dj11 * K[1][1] + dj12 * K[1][2];
+          float dm00 = 2.0f * S00, dm01 = S01 + S10, dm11 = 2.0f * S11;
+          if (k >= 3) {
+            // D = X + X^T with X = [e]x Sc
+            const int e3 = k - 3;
+            float X[3][3];
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+              if (e3 == 0) { X[0][b] = 0.f; X[1][b] = -Sc[2][b]; X[2][b] = Sc[1][b]; }
+              else if (e3 == 1) { X[0][b] = Sc[2][b]; X[1][b] = 0.f; X[2][b] = -Sc[0][b]; }
+              else { X[0][b] = -Sc[1][b]; X[1][b] = Sc[0][b]; X[2][b] = 0.f; }
+            }
+            float D[3][3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+              for (int b = 0; b < 3; ++b) D[a][b] = X[a][b] + X[b][a];
+            float JD[2][3];
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+              JD[0][b] = j00 * D[0][b] + j02 * D[2][b];
+              JD[1][b] = j11 * D[1][b] + j12 * D[2][b];
+            }
+            dm00 += JD[0][0] * j00 + JD[0][2] * j02;
+            dm01 += JD[0][1] * j11 + JD[0][2] * j12;
+            dm11 += JD[1][1] * j11 + JD[1][2] * j12;
+          }
+          const float ddet = dm00 * cc + ca * dm11 - 2.0f * cb * dm01;
+          const float dA = (dm11 - cc * ddet * di) * di;
+          const float dB = -(dm01 - cb * ddet * di) * di;
+          const float dC = (dm00 - ca * ddet * di) * di;
+          jac[0 * 6 + k] = du;
+          jac[1 * 6 + k] = dv;
+          jac[2 * 6 + k] = dA;
+          jac[3 * 6 + k] = dB;
+          jac[4 * 6 + k] = dC;
+          jac[5 * 6 + k] = dp[2];
+        }
+        // colour rows (rho only): d rgb_ch / d rho_k = G_ch . (I - dir dir^T) R^T e_k / |d|
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+          const float gd = G[ch][0] * dirx + G[ch][1] * diry + G[ch][2] * dirz;
+          const float gp0 = (G[ch][0] - gd * dirx) * rn, gp1 = (G[ch][1] - gd * diry) * rn,
+                      gp2 = (G[ch][2] - gd * dirz) * rn;
+#pragma unroll
+          for (int k = 0; k < 3; ++k)
+            jac[36 + 3 * ch + k] = clampc[ch] ? 0.0f : gp0 * R[3 * k] + gp1 * R[3 * k + 1] + gp2 * R[3 * k + 2];
+        }
+        float4* jo = reinterpret_cast<float4*>(w.rec_j + (size_t)slot * kJacStride);
+#pragma unroll
+        for (int q = 0; q < 11; ++q) jo[q] = make_float4(jac[4 * q], jac[4 * q + 1], jac[4 * q + 2], jac[4 * q + 3]);
+        jo[11] = make_float4(jac[44], 0.f, 0.f, 0.f);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_pack_scene(const float* means, const float* scales, const float* quats,
+                              const float* opacities, const float* sh, int sh_k3, const uint16_t* feats,
+                              int feat_dim, int n, int nsh4, float4* pos, float4* cov, float4* sh_out,
+                              uint4* feat_out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
+  k_pack_scene<<<grid, 256, 0, st>>>(means, scales, quats, opacities, sh, sh_k3, feats, feat_dim, n, nsh4, pos,
+                                     cov, sh_out, feat_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project(const SceneDev& sc, const View* views, int n_views, const Work& w, bool grad, int grid,
+                           cudaStream_t st) {
+  if (sc.n <= 0 || n_views <= 0) return cudaSuccess;
+  const int need = (sc.n + 255) / 256;
+  const int g = need < grid ? need : grid;
+  if (grad)
+    k_project<true><<<g, 256, 0, st>>>(sc, views, n_views, w);
+  else
+    k_project<false><<<g, 256, 0, st>>>(sc, views, n_views, w);
+  return cudaGetLastError();
+}
+
+}  // namespace gsr

@@ -1,0 +1,545 @@
+// Per-tile depth sort + front-to-back alpha compositing (forward), the adjoint
+// compositor that accumulates the se(3) pose gradient (backward), and the
+// fp64 reduction of the per-tile partial sums.
+//
+// Sec. 3.1 of the paper: colour is alpha-blended over the Gaussians covering a
+// pixel, features go through the identical blending; the dense stage of
+// Sec. 3.4 renders colour, depth and features at a candidate pose. The
+// gradient is the analysis-by-synthesis derivative of the L1 photometric +
+// depth loss with respect to the left pose perturbation.
+//
+// Both compositing kernels are persistent: CTAs pull tiles from a global
+// queue spanning every view of the call, so views of different resolution
+// share one launch and load-balance.
+#include <cuda_runtime.h>
+
+#include "gsr_internal.h"
+
+namespace gsr {
+namespace {
+
+constexpr float kAlphaFloor = 1.0f / 255.0f;
+constexpr float kAlphaCap = 0.99f;
+constexpr float kTCut = 1e-4f;
+constexpr int kWarps = kTileThreads / 32;
+
+// -0.5 (A dx^2 + C dy^2) - B dx dy with one fixed rounding sequence, shared by
+// the forward and backward kernels so that both take identical skip decisions.
+__device__ __forceinline__ float gs_power(float A, float B, float C, float dx, float dy) {
+  const float q = __fmaf_rn(C, __fmul_rn(dy, dy), __fmul_rn(A, __fmul_rn(dx, dx)));
+  return __fmaf_rn(-B, __fmul_rn(dx, dy), __fmul_rn(-0.5f, q));
+}
+
+__device__ __forceinline__ int find_view(const View* __restrict__ views, int n_views, uint32_t tile) {
+  int lo = 0, hi = n_views - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (views[mid].tile_base <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// exclusive scan of one value per thread over a 256-thread block
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* tmp) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) tmp[wid] = incl;
+  __syncthreads();
+  uint32_t off = 0;
+#pragma unroll
+  for (int k = 0; k < kWarps; ++k) off += (k < wid) ? tmp[k] : 0u;
+  __syncthreads();
+  return off + incl - v;
+}
+
+// One stable counting-sort pass on the 8-bit digit at `shift` of key .x, from
+// `in` to `out` (shared or global memory). Each warp owns a contiguous run of
+// the input; ranks inside a warp come from __match_any_sync, so equal digits
+// keep their input order.
+__device__ void radix_pass(const uint2* in, uint2* out, int n, int shift, uint32_t* hist, uint32_t* tmp) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int per = ((n + kTileThreads - 1) / kTileThreads) * 32;
+  const int wb = warp * per;
+  const int we = min(n, wb + per);
+  for (int i = tid; i < kWarps * 256; i += kTileThreads) hist[i] = 0u;
+  __syncthreads();
+  uint32_t* h = hist + warp * 256;
+  for (int b = wb; b < we; b += 32) {
+    const int idx = b + lane;
+    const bool ok = idx < we;
+    const uint32_t d = ok ? ((in[idx].x >> shift) & 255u) : 0u;
+    const uint32_t peers = __match_any_sync(0xffffffffu, ok ? d : 256u + lane);
+    if (ok && lane == __ffs(peers) - 1) h[d] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  {
+    const int d = tid;  // one digit per thread (256 threads)
+    uint32_t c[kWarps];
+    uint32_t tot = 0;
+#pragma unroll
+    for (int k = 0; k < kWarps; ++k) {
+      c[k] = hist[k * 256 + d];
+      tot += c[k];
+    }
+    uint32_t ex = block_excl_scan(tot, tmp);
+#pragma unroll
+    for (int k = 0; k < kWarps; ++k) {
+      hist[k * 256 + d] = ex;
+      ex += c[k];
+    }
+  }
+  __syncthreads();
+  const uint32_t lt = (1u << lane) - 1u;
+  for (int b = wb; b < we; b += 32) {
+    const int idx = b + lane;
+    const bool ok = idx < we;
+    const uint2 kv = ok ? in[idx] : make_uint2(0u, 0u);
+    const uint32_t d = ok ? ((kv.x >> shift) & 255u) : 0u;
+    const uint32_t peers = __match_any_sync(0xffffffffu, ok ? d : 256u + lane);
+    const uint32_t basev = ok ? h[d] : 0u;
+    __syncwarp();
+    if (ok) {
+      out[basev + __popc(peers & lt)] = kv;
+      if (lane == __ffs(peers) - 1) h[d] = basev + __popc(peers);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+}
+
+// Sort the tile's pairs by depth bits, ties by Gaussian index. Returns the
+// array holding the result (a or b).
+__device__ uint2* sort_tile(uint2* a, uint2* b, int n, uint32_t* hist, uint32_t* tmp, const float4* __restrict__ rec_b) {
+  __shared__ uint32_t s_and[kWarps], s_or[kWarps];
+  uint32_t kand = 0xffffffffu, kor = 0u;
+  for (int i = threadIdx.x; i < n; i += kTileThreads) {
+    const uint32_t k = a[i].x;
+    kand &= k;
+    kor |= k;
+  }
+  kand = __reduce_and_sync(0xffffffffu, kand);
+  kor = __reduce_or_sync(0xffffffffu, kor);
+  if ((threadIdx.x & 31) == 0) {
+    s_and[threadIdx.x >> 5] = kand;
+    s_or[threadIdx.x >> 5] = kor;
+  }
+  __syncthreads();
+  uint32_t diff = 0;
+  {
+    uint32_t A = 0xffffffffu, O = 0u;
+#pragma unroll
+    for (int k = 0; k < kWarps; ++k) {
+      A &= s_and[k];
+      O |= s_or[k];
+    }
+    diff = (n > 1) ? (A ^ O) : 0u;
+  }
+  __syncthreads();
+  uint2* cur = a;
+  uint2* oth = b;
+  for (int shift = 0; shift < 32; shift += 8) {
+    if (((diff >> shift) & 255u) == 0u) continue;
+    radix_pass(cur, oth, n, shift, hist, tmp);
+    uint2* t = cur;
+    cur = oth;
+    oth = t;
+  }
+  // equal depth bits: order by Gaussian index (rare; runs are short)
+  for (int i = threadIdx.x + 1; i < n; i += kTileThreads) {
+    if (cur[i].x == cur[i - 1].x && (i == 1 || cur[i - 2].x != cur[i - 1].x)) {
+      const int s = i - 1;
+      int e = i + 1;
+      while (e < n && cur[e].x == cur[s].x) ++e;
+      for (int p = s + 1; p < e; ++p) {
+        const uint2 v = cur[p];
+        const int gv = __float_as_int(rec_b[v.y].w);
+        int q = p - 1;
+        while (q >= s && __float_as_int(rec_b[cur[q].y].w) > gv) {
+          cur[q + 1] = cur[q];
+          --q;
+        }
+        cur[q + 1] = v;
+      }
+    }
+  }
+  __syncthreads();
+  return cur;
+}
+
+struct FwdSmem {
+  uint2 bufA[kSortCap];
+  uint2 bufB[kSortCap];
+  uint32_t hist[kWarps * 256];
+  float4 sa[kBatchF], sb[kBatchF], sc[kBatchF];
+};
+
+template <int FEAT>
+__global__ void __launch_bounds__(kTileThreads) k_composite(SceneDev sc, const View* __restrict__ views, int n_views,
+                                                            Work w) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  FwdSmem& S = *reinterpret_cast<FwdSmem*>(smem_raw);
+  uint4* sf = reinterpret_cast<uint4*>(smem_raw + sizeof(FwdSmem));  // FEAT: kBatchF x 4
+  __shared__ uint32_t s_tile;
+  __shared__ uint32_t s_tmp[kWarps];
+  if (w.ctr->overflow) return;
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) s_tile = atomicAdd(&w.ctr->fwd_queue, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= w.n_tiles) break;
+    const int vi = find_view(views, n_views, tile);
+    const View& V = views[vi];
+    const uint32_t lt = tile - V.tile_base;
+    const int tx = (int)(lt % (uint32_t)V.tiles_x), ty = (int)(lt / (uint32_t)V.tiles_x);
+    const uint32_t start = w.tile_offset[tile];
+    const int n = (int)(w.tile_offset[tile + 1] - start);
+
+    // ---- depth order of the tile's list ----
+    const uint2* list;
+    if (n <= kSortCap) {
+      for (int i = tid; i < n; i += kTileThreads) S.bufA[i] = w.pairs[start + i];
+      __syncthreads();
+      uint2* sorted = sort_tile(S.bufA, S.bufB, n, S.hist, s_tmp, w.rec_b);
+      for (int i = tid; i < n; i += kTileThreads) w.pairs[start + i] = sorted[i];
+      list = sorted;
+    } else {
+      uint2* sorted = sort_tile(w.pairs + start, w.pairs_tmp + start, n, S.hist, s_tmp, w.rec_b);
+      if (sorted != w.pairs + start) {
+        for (int i = tid; i < n; i += kTileThreads) w.pairs[start + i] = sorted[i];
+        __syncthreads();
+      }
+      list = w.pairs + start;
+    }
+
+    // ---- front-to-back blending, one pixel per thread ----
+    const int px = tx * kTile + (tid & 15), py = ty * kTile + (tid >> 4);
+    const bool inside = px < V.width && py < V.height;
+    const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+    float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
+    float F[FEAT > 0 ? FEAT : 1];
+#pragma unroll
+    for (int c = 0; c < (FEAT > 0 ? FEAT : 1); ++c) F[c] = 0.f;
+    uint32_t last = 0;
+    bool done = !inside;
+    for (int bs = 0; bs < n; bs += kBatchF) {
+      if (__syncthreads_count(done) == kTileThreads) break;
+      const int bn = min(kBatchF, n - bs);
+      if (tid < bn) {
+        const uint32_t r = list[bs + tid].y;
+        S.sa[tid] = w.rec_a[r];
+        const float4 bb = w.rec_b[r];
+        S.sb[tid] = bb;
+        S.sc[tid] = w.rec_c[r];
+        if (FEAT) {
+          const uint4* fp = sc.feat + (size_t)__float_as_int(bb.w) * 4;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) sf[tid * 4 + q] = __ldg(fp + q);
+        }
+      }
+      __syncthreads();
+      if (!done) {
+        for (int j = 0; j < bn; ++j) {
+          const float4 a = S.sa[j];
+          const float4 b = S.sb[j];
+          const float dx = __fsub_rn(a.x, pxc), dy = __fsub_rn(a.y, pyc);
+          const float power = gs_power(a.z, a.w, b.x, dx, dy);
+          if (power > 0.0f) continue;
+          const float oe = __fmul_rn(b.y, __expf(power));
+          const float alpha = fminf(kAlphaCap, oe);
+          if (alpha < kAlphaFloor) continue;
+          const float Tn = __fmul_rn(T, __fsub_rn(1.0f, alpha));
+          if (Tn < kTCut) {
+            done = true;
+            break;
+          }
+          const float wgt = __fmul_rn(alpha, T);
+          const float4 c = S.sc[j];
+          C0 = fmaf(wgt, c.x, C0);
+          C1 = fmaf(wgt, c.y, C1);
+          C2 = fmaf(wgt, c.z, C2);
+          D = fmaf(wgt, b.z, D);
+          if (FEAT) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const uint4 fv = sf[j * 4 + q];
+              const uint32_t u4[4] = {fv.x, fv.y, fv.z, fv.w};
+#pragma unroll
+              for (int h = 0; h < 4; ++h) {
+                F[8 * q + 2 * h] = fmaf(wgt, __uint_as_float(u4[h] << 16), F[8 * q + 2 * h]);
+                F[8 * q + 2 * h + 1] = fmaf(wgt, __uint_as_float(u4[h] & 0xffff0000u), F[8 * q + 2 * h + 1]);
+              }
+            }
+          }
+          T = Tn;
+          last = (uint32_t)(bs + j + 1);
+        }
+      }
+    }
+    if (inside) {
+      const size_t HW = (size_t)V.width * V.height;
+      const size_t p = (size_t)py * V.width + px;
+      if (V.rgb) {
+        V.rgb[p] = C0;
+        V.rgb[HW + p] = C1;
+        V.rgb[2 * HW + p] = C2;
+      }
+      if (V.depth) V.depth[p] = D;
+      if (V.alpha) V.alpha[p] = 1.0f - T;
+      if (V.final_T) V.final_T[p] = T;
+      if (V.last_idx) V.last_idx[p] = last;
+      if (FEAT && V.feats) {
+#pragma unroll
+        for (int c = 0; c < (FEAT > 0 ? FEAT : 1); ++c) V.feats[(size_t)c * HW + p] = F[c];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Backward: per pixel, walk the blended Gaussians back to front recomputing
+// the transmittance from the stored final value, T_k = T_{k+1} / (1 - a_k);
+// chain dL/d(u, v, conic, z, rgb) through the per-Gaussian pose Jacobian and
+// accumulate the 6-vector per pixel (fp32); reduce across pixels in fp64.
+// ---------------------------------------------------------------------------
+struct BwdSmem {
+  float4 sa[kBatchB], sb[kBatchB], sc[kBatchB];
+  float4 sj[kBatchB * (kJacStride / 4)];
+  double red[kWarps][8];
+};
+
+__global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restrict__ views, int n_views, Work w) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  BwdSmem& S = *reinterpret_cast<BwdSmem*>(smem_raw);
+  __shared__ uint32_t s_tile;
+  __shared__ uint32_t s_max[kWarps];
+  if (w.ctr->overflow) return;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const float4* rec_j4 = reinterpret_cast<const float4*>(w.rec_j);
+  for (;;) {
+    if (tid == 0) s_tile = atomicAdd(&w.ctr->bwd_queue, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= w.n_tiles) break;
+    const int vi = find_view(views, n_views, tile);
+    const View& V = views[vi];
+    const uint32_t lt = tile - V.tile_base;
+    const int tx = (int)(lt % (uint32_t)V.tiles_x), ty = (int)(lt / (uint32_t)V.tiles_x);
+    const uint32_t start = w.tile_offset[tile];
+    const int px = tx * kTile + (tid & 15), py = ty * kTile + (tid >> 4);
+    const bool inside = px < V.width && py < V.height;
+    const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+    const size_t HW = (size_t)V.width * V.height;
+    const size_t p = (size_t)py * V.width + px;
+
+    uint32_t last = 0;
+    float T = 1.0f, gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f;
+    double loss = 0.0;
+    if (inside) {
+      last = V.last_idx[p];
+      T = V.final_T[p];
+      const float wpx = V.pixel_weight ? V.pixel_weight[p] : 1.0f;
+      const float r0 = V.rgb[p] - V.target_rgb[p];
+      const float r1 = V.rgb[HW + p] - V.target_rgb[HW + p];
+      const float r2 = V.rgb[2 * HW + p] - V.target_rgb[2 * HW + p];
+      const float e = V.depth[p] - V.target_depth[p];
+      const float s3 = wpx * V.inv_3p, sd = wpx * V.depth_weight * V.inv_p;
+      gC0 = s3 * (float)((r0 > 0.f) - (r0 < 0.f));
+      gC1 = s3 * (float)((r1 > 0.f) - (r1 < 0.f));
+      gC2 = s3 * (float)((r2 > 0.f) - (r2 < 0.f));
+      gD = sd * (float)((e > 0.f) - (e < 0.f));
+      loss = (double)s3 * ((double)fabsf(r0) + (double)fabsf(r1) + (double)fabsf(r2)) + (double)sd * (double)fabsf(e);
+    }
+    // longest list prefix any pixel of the tile blended
+    const uint32_t wm = __reduce_max_sync(0xffffffffu, last);
+    if (lane == 0) s_max[wid] = wm;
+    __syncthreads();
+    uint32_t max_last = 0;
+#pragma unroll
+    for (int k = 0; k < kWarps; ++k) max_last = max(max_last, s_max[k]);
+
+    float xi[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, accD = 0.f;
+    for (int bend = (int)max_last; bend > 0; bend -= kBatchB) {
+      const int bstart = max(0, bend - kBatchB);
+      const int bn = bend - bstart;
+      __syncthreads();
+      if (tid < bn) {
+        const uint32_t r = w.pairs[start + bstart + tid].y;
+        S.sa[tid] = w.rec_a[r];
+        S.sb[tid] = w.rec_b[r];
+        S.sc[tid] = w.rec_c[r];
+      }
+      for (int q = tid; q < bn * (kJacStride / 4); q += kTileThreads) {
+        const int jj = q / (kJacStride / 4), k = q % (kJacStride / 4);
+        const uint32_t r = w.pairs[start + bstart + jj].y;
+        S.sj[q] = rec_j4[(size_t)r * (kJacStride / 4) + k];
+      }
+      __syncthreads();
+      if (inside) {
+        for (int j = bn - 1; j >= 0; --j) {
+          if ((uint32_t)(bstart + j) >= last) continue;
+          const float4 a = S.sa[j];
+          const float4 b = S.sb[j];
+          const float dx = __fsub_rn(a.x, pxc), dy = __fsub_rn(a.y, pyc);
+          const float power = gs_power(a.z, a.w, b.x, dx, dy);
+          if (power > 0.0f) continue;
+          const float oe = __fmul_rn(b.y, __expf(power));
+          const float alpha = fminf(kAlphaCap, oe);
+          if (alpha < kAlphaFloor) continue;
+          const float oma = 1.0f - alpha;
+          T = __fdividef(T, oma);  // transmittance in front of this Gaussian
+          const float wgt = alpha * T;
+          const float4 c = S.sc[j];
+          const float dLda = T * (gC0 * (c.x - acc0) + gC1 * (c.y - acc1) + gC2 * (c.z - acc2) + gD * (b.z - accD));
+          acc0 = fmaf(alpha, c.x, oma * acc0);
+          acc1 = fmaf(alpha, c.y, oma * acc1);
+          acc2 = fmaf(alpha, c.z, oma * acc2);
+          accD = fmaf(alpha, b.z, oma * accD);
+          const float dpow = (oe < kAlphaCap) ? dLda * alpha : 0.0f;
+          const float gu = -dpow * (a.z * dx + a.w * dy);
+          const float gv = -dpow * (b.x * dy + a.w * dx);
+          const float gA = -0.5f * dpow * dx * dx;
+          const float gB = -dpow * dx * dy;
+          const float gCc = -0.5f * dpow * dy * dy;
+          const float gz = gD * wgt;
+          const float gr = gC0 * wgt, gg = gC1 * wgt, gb = gC2 * wgt;
+          const float* J = reinterpret_cast<const float*>(S.sj + j * (kJacStride / 4));
+#pragma unroll
+          for (int k = 0; k < 6; ++k) {
+            float s = xi[k];
+            s = fmaf(J[k], gu, s);
+            s = fmaf(J[6 + k], gv, s);
+            s = fmaf(J[12 + k], gA, s);
+            s = fmaf(J[18 + k], gB, s);
+            s = fmaf(J[24 + k], gCc, s);
+            s = fmaf(J[30 + k], gz, s);
+            if (k < 3) {
+              s = fmaf(J[36 + k], gr, s);
+              s = fmaf(J[39 + k], gg, s);
+              s = fmaf(J[42 + k], gb, s);
+            }
+            xi[k] = s;
+          }
+        }
+      }
+    }
+    // fp64 reduction of (loss, xi) over the tile's pixels
+    double v[7] = {loss, (double)xi[0], (double)xi[1], (double)xi[2], (double)xi[3], (double)xi[4], (double)xi[5]};
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < 7; ++k) S.red[wid][k] = v[k];
+    }
+    __syncthreads();
+    if (tid < 7) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < kWarps; ++k) s += S.red[k][tid];
+      w.partials[(size_t)tile * kPartialStride + tid] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// Deterministic fp64 sum of the per-tile partials (fixed order).
+__global__ void __launch_bounds__(256) k_reduce(Work w, double* __restrict__ result) {
+  __shared__ double red[8][8];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  double v[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (uint32_t t = tid; t < w.n_tiles; t += 256) {
+#pragma unroll
+    for (int k = 0; k < 7; ++k) v[k] += w.partials[(size_t)t * kPartialStride + k];
+  }
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 7; ++k) red[wid][k] = v[k];
+  }
+  __syncthreads();
+  if (tid < 7) {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += red[k][tid];
+    result[tid] = s;
+  }
+}
+
+template <int FEAT>
+size_t composite_smem() {
+  return sizeof(FwdSmem) + (FEAT ? sizeof(uint4) * kBatchF * 4 : 0);
+}
+
+template <int FEAT>
+int composite_occ() {
+  static int occ = -1;
+  if (occ < 0) {
+    cudaFuncSetAttribute(k_composite<FEAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)composite_smem<FEAT>());
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_composite<FEAT>, kTileThreads, composite_smem<FEAT>()) !=
+        cudaSuccess)
+      b = 1;
+    occ = b > 0 ? b : 1;
+  }
+  return occ;
+}
+
+}  // namespace
+
+int composite_blocks_per_sm(int feat_dim) { return feat_dim ? composite_occ<32>() : composite_occ<0>(); }
+
+int backward_blocks_per_sm() {
+  static int occ = -1;
+  if (occ < 0) {
+    cudaFuncSetAttribute(k_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BwdSmem));
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_backward, kTileThreads, sizeof(BwdSmem)) != cudaSuccess)
+      b = 1;
+    occ = b > 0 ? b : 1;
+  }
+  return occ;
+}
+
+cudaError_t launch_composite(const SceneDev& sc, const View* views, int n_views, const Work& w, int grid,
+                             cudaStream_t st) {
+  if (w.n_tiles == 0) return cudaSuccess;
+  const int g = (uint32_t)grid < w.n_tiles ? grid : (int)w.n_tiles;
+  if (sc.feat_dim) {
+    composite_occ<32>();
+    k_composite<32><<<g, kTileThreads, composite_smem<32>(), st>>>(sc, views, n_views, w);
+  } else {
+    composite_occ<0>();
+    k_composite<0><<<g, kTileThreads, composite_smem<0>(), st>>>(sc, views, n_views, w);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backward(const View* views, int n_views, const Work& w, int grid, cudaStream_t st) {
+  if (w.n_tiles == 0) return cudaSuccess;
+  backward_blocks_per_sm();
+  const int g = (uint32_t)grid < w.n_tiles ? grid : (int)w.n_tiles;
+  k_backward<<<g, kTileThreads, sizeof(BwdSmem), st>>>(views, n_views, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const Work& w, double* result, cudaStream_t st) {
+  k_reduce<<<1, 256, 0, st>>>(w, result);
+  return cudaGetLastError();
+}
+
+}  // namespace gsr

@@ -1,0 +1,320 @@
+"""Thin ctypes binding of libgsr (include/gsr.h).
+
+Functions with the C names (``gs_create_scene``, ``gs_render``, ...) pass
+arguments straight through; the helpers below them (``Scene``, ``PoseLoss``)
+only marshal torch tensors (device memory, current stream) into those calls.
+Every step of rendering and differentiation runs in the CUDA library. Importing
+this module loads ``libgsr.so`` and raises ImportError if it has not been built
+(``python -m paper_2507_15683_gb300.build``): there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgsr.so")
+
+GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CUDA, GS_ERR_OOM, GS_ERR_CAPACITY, GS_ERR_TIMEOUT, GS_ERR_INTERNAL = range(7)
+GS_BATCH_GRAPH = 1
+STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CUDA", 3: "GS_ERR_OOM", 4: "GS_ERR_CAPACITY",
+                5: "GS_ERR_TIMEOUT", 6: "GS_ERR_INTERNAL"}
+
+
+class GsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class gs_scene_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("sh_degree", ctypes.c_int), ("feat_dim", ctypes.c_int),
+                ("means", ctypes.c_void_p), ("scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
+                ("opacities", ctypes.c_void_p), ("sh", ctypes.c_void_p), ("feats_bf16", ctypes.c_void_p),
+                ("n_partitions", ctypes.c_int), ("partition_offsets", ctypes.c_void_p),
+                ("device_resident", ctypes.c_int)]
+
+
+class gs_camera(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float)]
+
+
+class gs_pose(ctypes.Structure):
+    _fields_ = [("T_cw", ctypes.c_double * 16)]
+
+
+class gs_outputs(ctypes.Structure):
+    _fields_ = [("rgb", ctypes.c_void_p), ("depth", ctypes.c_void_p), ("alpha", ctypes.c_void_p),
+                ("final_T", ctypes.c_void_p), ("feats", ctypes.c_void_p), ("last_idx", ctypes.c_void_p)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libgsr.so is not built (run: python -m paper_2507_15683_gb300.build)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, st = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    P = ctypes.POINTER
+    sigs = {
+        "gs_create_scene": [P(gs_scene_desc), P(vp)],
+        "gs_scene_reserve": [vp, i64, i64],
+        "gs_render": [vp, P(gs_camera), P(gs_pose), P(gs_outputs), vp],
+        "gs_render_async": [vp, P(gs_camera), P(gs_pose), P(gs_outputs), vp],
+        "gs_render_pose_grad": [vp, P(gs_camera), P(gs_pose), vp, vp, vp, ctypes.c_float, P(gs_outputs), vp, vp, vp],
+        "gs_render_pose_grad_async": [vp, P(gs_camera), P(gs_pose), vp, vp, vp, ctypes.c_float, P(gs_outputs), vp,
+                                      vp],
+        "gs_render_batch": [vp, ctypes.c_int, P(gs_camera), P(gs_pose), P(gs_outputs), ctypes.c_uint, vp],
+        "gs_scene_status": [vp, vp, vp, vp],
+        "gs_get_tile_lists": [vp, ctypes.c_int, vp, vp, vp, i64, vp, vp],
+        "gs_get_records": [vp, ctypes.c_int, vp, i64, vp, vp],
+        "gs_scene_set_timing": [vp, ctypes.c_int],
+        "gs_scene_kernel_times": [vp, vp, vp],
+    }
+    for name, args in sigs.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = st
+    L.gs_destroy_scene.argtypes = [vp]
+    L.gs_destroy_scene.restype = None
+    L.gs_last_error.argtypes = []
+    L.gs_last_error.restype = ctypes.c_char_p
+    L.gs_version.argtypes = []
+    L.gs_version.restype = ctypes.c_char_p
+    return L
+
+
+lib = _load()
+
+
+def _check(status: int):
+    if status != GS_OK:
+        raise GsError(status, lib.gs_last_error().decode())
+
+
+# ---- C entry points under their own names -------------------------------------------------------
+def gs_create_scene(desc: gs_scene_desc) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib.gs_create_scene(ctypes.byref(desc), ctypes.byref(h)))
+    return h
+
+
+def gs_destroy_scene(h) -> None:
+    lib.gs_destroy_scene(h)
+
+
+def gs_scene_reserve(h, max_records: int, max_pairs: int) -> None:
+    _check(lib.gs_scene_reserve(h, int(max_records), int(max_pairs)))
+
+
+def gs_render(h, cam: gs_camera, pose: gs_pose, out: gs_outputs, stream: int) -> None:
+    _check(lib.gs_render(h, ctypes.byref(cam), ctypes.byref(pose), ctypes.byref(out), stream))
+
+
+def gs_render_async(h, cam: gs_camera, pose: gs_pose, out: gs_outputs, stream: int) -> None:
+    _check(lib.gs_render_async(h, ctypes.byref(cam), ctypes.byref(pose), ctypes.byref(out), stream))
+
+
+def gs_render_pose_grad(h, cam, pose, target_rgb: int, target_depth: int, pixel_weight, depth_weight: float,
+                        out, stream: int):
+    loss = ctypes.c_double()
+    grad = (ctypes.c_double * 6)()
+    _check(lib.gs_render_pose_grad(h, ctypes.byref(cam), ctypes.byref(pose), target_rgb, target_depth,
+                                   pixel_weight, float(depth_weight), ctypes.byref(out) if out is not None else None,
+                                   ctypes.byref(loss), grad, stream))
+    return loss.value, np.array(grad[:], np.float64)
+
+
+def gs_render_pose_grad_async(h, cam, pose, target_rgb, target_depth, pixel_weight, depth_weight, out,
+                              result_dev: int, stream: int) -> None:
+    _check(lib.gs_render_pose_grad_async(h, ctypes.byref(cam), ctypes.byref(pose), target_rgb, target_depth,
+                                         pixel_weight, float(depth_weight),
+                                         ctypes.byref(out) if out is not None else None, result_dev, stream))
+
+
+def gs_render_batch(h, cams, poses, outs, flags: int, stream: int) -> None:
+    n = len(cams)
+    ca = (gs_camera * n)(*cams)
+    pa = (gs_pose * n)(*poses)
+    oa = (gs_outputs * n)(*outs)
+    _check(lib.gs_render_batch(h, n, ca, pa, oa, int(flags), stream))
+
+
+def gs_scene_status(h, stream: int):
+    nr, npr = ctypes.c_int64(), ctypes.c_int64()
+    s = lib.gs_scene_status(h, stream, ctypes.byref(nr), ctypes.byref(npr))
+    return s, nr.value, npr.value
+
+
+def gs_get_tile_lists(h, view: int, tiles: int, capacity: int, stream: int):
+    keys = np.zeros(max(capacity, 1), np.uint64)
+    gids = np.zeros(max(capacity, 1), np.uint32)
+    ts = np.zeros(tiles + 1, np.int64)
+    n = ctypes.c_int64()
+    _check(lib.gs_get_tile_lists(h, view, keys.ctypes.data, gids.ctypes.data, ts.ctypes.data, capacity,
+                                 ctypes.byref(n), stream))
+    return ts, keys[:n.value], gids[:n.value]
+
+
+def gs_get_records(h, view: int, capacity: int, stream: int) -> np.ndarray:
+    rec = np.zeros((max(capacity, 1), 8), np.int32)
+    n = ctypes.c_int64()
+    _check(lib.gs_get_records(h, view, rec.ctypes.data, capacity, ctypes.byref(n), stream))
+    return rec[:n.value]
+
+
+KERNEL_NAMES = ("project", "scan_tiles", "scatter", "sort_composite", "backward", "reduce")
+
+
+def gs_scene_set_timing(h, enable: bool) -> None:
+    _check(lib.gs_scene_set_timing(h, int(bool(enable))))
+
+
+def gs_scene_kernel_times(h):
+    ms = np.zeros(len(KERNEL_NAMES), np.float64)
+    n = np.zeros(len(KERNEL_NAMES), np.int64)
+    _check(lib.gs_scene_kernel_times(h, ms.ctypes.data, n.ctypes.data))
+    return ms, n
+
+
+def gs_version() -> str:
+    return lib.gs_version().decode()
+
+
+# ---- marshalling helpers (torch supplies device memory and the stream) ---------------------------
+def camera(c) -> gs_camera:
+    return gs_camera(int(c["width"]), int(c["height"]), float(c["fx"]), float(c["fy"]), float(c["cx"]),
+                     float(c["cy"]))
+
+
+def pose(T) -> gs_pose:
+    p = gs_pose()
+    flat = np.ascontiguousarray(T, np.float64).reshape(16)
+    for k in range(16):
+        p.T_cw[k] = float(flat[k])
+    return p
+
+
+def _ptr(t):
+    return 0 if t is None else t.data_ptr()
+
+
+def _stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Scene:
+    """Owns a gs_scene built from a dict of arrays (numpy or torch).
+
+    Keys: means (n,3), scales (n,3), quats (n,4), opacities (n,), sh (n,K,3),
+    sh_degree, optional feats_bf16 (n,32) uint16 and partition_offsets.
+    """
+
+    def __init__(self, scene: dict):
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+
+        def t(x, dtype):
+            if isinstance(x, torch.Tensor):
+                return x.to(device=dev, dtype=dtype).contiguous()
+            return torch.from_numpy(np.ascontiguousarray(x)).to(device=dev, dtype=dtype).contiguous()
+
+        self.n = int(np.asarray(scene["means"]).reshape(-1, 3).shape[0]) if not isinstance(scene["means"], torch.Tensor) \
+            else int(scene["means"].reshape(-1, 3).shape[0])
+        self.sh_degree = int(scene["sh_degree"])
+        f = scene.get("feats_bf16")
+        self.feat_dim = 0 if f is None else 32
+        keep = [t(scene["means"], torch.float32), t(scene["scales"], torch.float32), t(scene["quats"], torch.float32),
+                t(scene["opacities"], torch.float32), t(scene["sh"], torch.float32)]
+        fb = None if f is None else t(np.asarray(f).view(np.int16) if not isinstance(f, torch.Tensor) else f,
+                                      torch.int16)
+        po = scene.get("partition_offsets")
+        po_np = None if po is None else np.ascontiguousarray(po, np.int64)
+        self._desc = gs_scene_desc(self.n, self.sh_degree, self.feat_dim, *[_ptr(k) for k in keep], _ptr(fb),
+                                   0 if po_np is None else len(po_np) - 1,
+                                   None if po_np is None else po_np.ctypes.data, 1)
+        torch.cuda.synchronize()
+        self.handle = gs_create_scene(self._desc)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            gs_destroy_scene(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def alloc_outputs(cam, feat_dim=0, last_idx=True):
+        import torch
+        H, W = int(cam["height"]), int(cam["width"])
+        o = {"rgb": torch.empty((3, H, W), device="cuda"), "depth": torch.empty((H, W), device="cuda"),
+             "alpha": torch.empty((H, W), device="cuda"), "final_T": torch.empty((H, W), device="cuda")}
+        if feat_dim:
+            o["feats"] = torch.empty((feat_dim, H, W), device="cuda")
+        if last_idx:
+            o["last_idx"] = torch.empty((H, W), device="cuda", dtype=torch.int32)
+        return o
+
+    @staticmethod
+    def outputs_struct(o) -> gs_outputs:
+        if o is None:
+            return gs_outputs()
+        return gs_outputs(_ptr(o.get("rgb")), _ptr(o.get("depth")), _ptr(o.get("alpha")), _ptr(o.get("final_T")),
+                          _ptr(o.get("feats")), _ptr(o.get("last_idx")))
+
+    def render(self, cam, T, out=None, sync=True):
+        out = out if out is not None else self.alloc_outputs(cam, self.feat_dim)
+        fn = gs_render if sync else gs_render_async
+        fn(self.handle, camera(cam), pose(T), self.outputs_struct(out), _stream())
+        return out
+
+    def render_pose_grad(self, cam, T, target_rgb, target_depth, pixel_weight=None, depth_weight=0.1, out=None):
+        return gs_render_pose_grad(self.handle, camera(cam), pose(T), _ptr(target_rgb), _ptr(target_depth),
+                                   _ptr(pixel_weight) or None, depth_weight,
+                                   self.outputs_struct(out) if out is not None else None, _stream())
+
+    def render_batch(self, cams, poses, outs, graph=False):
+        gs_render_batch(self.handle, [camera(c) for c in cams], [pose(T) for T in poses],
+                        [self.outputs_struct(o) for o in outs], GS_BATCH_GRAPH if graph else 0, _stream())
+        return outs
+
+    def status(self):
+        return gs_scene_status(self.handle, _stream())
+
+    def reserve(self, max_records, max_pairs):
+        gs_scene_reserve(self.handle, max_records, max_pairs)
+
+    def tile_lists(self, view, cam, capacity):
+        tiles = ((int(cam["width"]) + 15) // 16) * ((int(cam["height"]) + 15) // 16)
+        return gs_get_tile_lists(self.handle, view, tiles, capacity, _stream())
+
+    def records(self, view, capacity):
+        return gs_get_records(self.handle, view, capacity, _stream())
+
+
+def pose_loss_function():
+    """torch.autograd.Function: loss(xi) of the L1 photometric + depth objective
+    at the pose tangent xi = 0 of a given pose; backward returns dL/dxi from the
+    CUDA adjoint (gs_render_pose_grad). The tangent is re-linearised at every
+    call, so callers update the pose (T <- Exp(-step) T) and pass xi = 0."""
+    import torch
+
+    class PoseLoss(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, xi, scene, cam, T, target_rgb, target_depth, pixel_weight=None, depth_weight=0.1):
+            loss, grad = scene.render_pose_grad(cam, T, target_rgb, target_depth, pixel_weight, depth_weight)
+            ctx.save_for_backward(torch.as_tensor(grad, dtype=xi.dtype, device=xi.device))
+            return torch.as_tensor(loss, dtype=xi.dtype, device=xi.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            (grad,) = ctx.saved_tensors
+            return g * grad, None, None, None, None, None, None, None
+
+    return PoseLoss

@@ -23,3 +23,19 @@ def oracle():
     from oracle import oracle as O
     O.build()
     return O
+
+
+@pytest.fixture(scope="session")
+def libgsr_path():
+    """Build (if needed) the CUDA library; it must exist for the product path."""
+    from paper_2507_15683_gb300 import build
+    return build.build()
+
+
+@pytest.fixture(scope="session")
+def gsr(libgsr_path):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("a gpu-marked test ran without a CUDA device")
+    from paper_2507_15683_gb300 import gsr as G
+    return G

@@ -1,0 +1,38 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point
+declared in include/gsr.h (no compute call is made here)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "gsr.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:gs_status|void|const char\s*\*)\s*(gs_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("gs_create_scene", "gs_destroy_scene", "gs_render", "gs_render_pose_grad", "gs_render_batch",
+                     "gs_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libgsr_path):
+    lib = ctypes.CDLL(libgsr_path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    lib.gs_version.restype = ctypes.c_char_p
+    assert b"sm_103a" in lib.gs_version()
+
+
+def test_invalid_arguments_fail_without_a_gpu(libgsr_path):
+    lib = ctypes.CDLL(libgsr_path)
+    lib.gs_create_scene.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    lib.gs_last_error.restype = ctypes.c_char_p
+    assert lib.gs_create_scene(None, None) == 1  # GS_ERR_INVALID_ARG
+    assert b"required" in lib.gs_last_error()
+    lib.gs_render.argtypes = [ctypes.c_void_p] * 5
+    assert lib.gs_render(None, None, None, None, None) == 1

@@ -1,0 +1,150 @@
+"""Batched rendering, graph replay, edge cases and error handling through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2507_15683_gb300 import synth
+from tests.gpu_helpers import compare_images, to_numpy
+from tests.oracle_scenes import scene_of
+
+pytestmark = pytest.mark.gpu
+
+
+def _views():
+    cams = [synth.camera(120, 68, 90.0), synth.camera(240, 136, 175.0), synth.camera(97, 61, 70.0)]
+    poses = [synth.look_pose((100.0, 40.0, 60.0), 0.0, math.radians(30.0)),
+             synth.look_pose((80.0, 90.0, 80.0), 1.0, math.radians(10.0)),
+             synth.look_pose((120.0, 60.0, 50.0), 2.5, math.radians(40.0))]
+    return cams, poses
+
+
+def _scene():
+    return synth.aerial_scene(41, 30000, extent=(0.0, 200.0, 0.0, 200.0), n_clusters=20)
+
+
+def _eq(a, b):
+    for k in a:
+        torch.testing.assert_close(a[k], b[k], rtol=0, atol=0)
+
+
+def test_batch_equals_single_views(gsr):
+    scene = _scene()
+    S = gsr.Scene(scene)
+    cams, poses = _views()
+    singles = [S.render(c, T) for c, T in zip(cams, poses)]
+    outs = [S.alloc_outputs(c) for c in cams]
+    S.render_batch(cams, poses, outs)
+    for a, b in zip(outs, singles):
+        _eq(a, b)
+    S.close()
+
+
+def test_graph_replay_follows_pose_updates(gsr):
+    scene = _scene()
+    S = gsr.Scene(scene)
+    cams, poses = _views()
+    S.reserve(200000, 2000000)
+    outs = [S.alloc_outputs(c) for c in cams]
+    S.render_batch(cams, poses, outs, graph=True)
+    assert S.status()[0] == 0
+    ref = [S.render(c, T) for c, T in zip(cams, poses)]
+    for a, b in zip(outs, ref):
+        _eq(a, b)
+    poses2 = [synth.perturb_pose(T, synth.rng(k), 3.0, 2.0) for k, T in enumerate(poses)]
+    S.render_batch(cams, poses2, outs, graph=True)  # replay with new poses
+    assert S.status()[0] == 0
+    ref2 = [S.render(c, T) for c, T in zip(cams, poses2)]
+    for a, b in zip(outs, ref2):
+        _eq(a, b)
+    S.close()
+
+
+def test_empty_scene_and_all_culled(gsr):
+    cam = synth.camera(40, 24, 30.0)
+    for sc in (scene_of(np.zeros((0, 3)), np.zeros((0, 3))), scene_of([[0, 0, -5], [0, 0, 0.1]], [[0.1] * 3] * 2)):
+        S = gsr.Scene(sc)
+        out = S.render(cam, np.eye(4))
+        assert torch.all(out["final_T"] == 1) and torch.all(out["rgb"] == 0) and torch.all(out["last_idx"] == 0)
+        S.close()
+
+
+@pytest.mark.parametrize("w,h", [(1, 1), (17, 33), (16, 16), (300, 1)])
+def test_ragged_and_degenerate_sizes(oracle, gsr, w, h):
+    scene = synth.tiny_scene(3, n=500, sh_degree=1)
+    cam = synth.camera(w, h, 60.0, w / 2 + 0.25, h / 2 - 0.25)
+    S = gsr.Scene(scene)
+    gpu = to_numpy(S.render(cam, np.eye(4)), h, w)
+    orc = oracle.render(scene, cam, np.eye(4))
+    compare_images(gpu, orc, oracle, min_ok=0.9)
+    S.close()
+
+
+def test_long_tile_list_uses_global_sort(oracle, gsr):
+    # 6000 small Gaussians inside one tile's footprint: a list longer than the
+    # shared-memory sort capacity
+    g = synth.rng(4)
+    n = 6000
+    means = np.stack([g.uniform(-0.05, 0.05, n), g.uniform(-0.05, 0.05, n), g.uniform(4, 8, n)], 1)
+    scene = scene_of(means, np.full((n, 3), 0.004), quats=g.standard_normal((n, 4)),
+                     opacities=g.uniform(0.02, 0.2, n), dc=g.uniform(0, 1, (n, 3)))
+    cam = synth.tiny_camera()
+    S = gsr.Scene(scene)
+    out = S.render(cam, np.eye(4))
+    cov = oracle.cov3d_f32(scene["scales"], scene["quats"])
+    ri, rf = oracle.project_f32(scene["means"], cov, cam, np.eye(4))
+    ts, keys, gids = oracle.bin_tiles(ri, rf, cam)
+    assert np.diff(ts).max() > 2048
+    gts, gkeys, ggids = S.tile_lists(0, cam, len(keys) + 8)
+    np.testing.assert_array_equal(gkeys, keys)
+    np.testing.assert_array_equal(ggids, gids)
+    compare_images(to_numpy(out, 128, 128), oracle.render(scene, cam, np.eye(4)), oracle)
+    S.close()
+
+
+def test_large_gaussian_covers_every_tile(oracle, gsr):
+    scene = scene_of([[0, 0, 5], [0.3, 0.1, 6]], [[3.0, 2.0, 0.5], [0.2, 0.2, 0.2]], opacities=[0.5, 0.9],
+                     dc=[[0.2, 0.4, 0.6], [0.9, 0.1, 0.3]])
+    cam = synth.camera(200, 150, 120.0)
+    S = gsr.Scene(scene)
+    gpu = to_numpy(S.render(cam, np.eye(4)), 150, 200)
+    compare_images(gpu, oracle.render(scene, cam, np.eye(4)), oracle)
+    S.close()
+
+
+def test_capacity_regrow_and_async_status(oracle, gsr):
+    # 70,000 visible Gaussians exceed the first-call record guess (65,536)
+    g = synth.rng(6)
+    n = 70000
+    means = np.stack([g.uniform(-2, 2, n), g.uniform(-2, 2, n), g.uniform(4, 8, n)], 1)
+    scene = scene_of(means, np.full((n, 3), 0.03), opacities=np.full(n, 0.05), dc=g.uniform(0, 1, (n, 3)))
+    cam = synth.tiny_camera()
+    S = gsr.Scene(scene)
+    out = S.render(cam, np.eye(4))  # synchronous: grows and re-renders
+    compare_images(to_numpy(out, 128, 128), oracle.render(scene, cam, np.eye(4)), oracle)
+    S.close()
+    S = gsr.Scene(scene)
+    S.reserve(1000, 1000)
+    S.render(cam, np.eye(4), sync=False)
+    st, need_rec, _ = S.status()
+    assert st == gsr.GS_ERR_CAPACITY and need_rec >= n
+    S.close()
+
+
+def test_invalid_arguments_return_errors(gsr):
+    with pytest.raises(gsr.GsError) as e:
+        bad = synth.tiny_scene(0)
+        bad["sh_degree"] = 5
+        gsr.Scene(bad)
+    assert e.value.status == gsr.GS_ERR_INVALID_ARG
+    S = gsr.Scene(synth.tiny_scene(0))
+    with pytest.raises(gsr.GsError) as e:
+        S.render({"width": 0, "height": 4, "fx": 1, "fy": 1, "cx": 0, "cy": 0}, np.eye(4))
+    assert e.value.status == gsr.GS_ERR_INVALID_ARG
+    T = np.eye(4)
+    T[0, 3] = float("nan")
+    with pytest.raises(gsr.GsError) as e:
+        S.render(synth.tiny_camera(), T)
+    assert e.value.status == gsr.GS_ERR_INVALID_ARG
+    S.close()

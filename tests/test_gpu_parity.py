@@ -1,0 +1,104 @@
+"""GPU vs oracle parity of the forward path, through the C ABI.
+
+Projection records and tile lists are compared bit for bit (binary32 discrete
+layer); images element by element within 1e-4 of the fp64 oracle (relative to
+each output's scale), on every pixel whose blending decisions are not within
+rounding of a threshold; last-blended indices exactly on those pixels.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2507_15683_gb300 import synth
+from tests.gpu_helpers import compare_images, to_numpy
+
+pytestmark = pytest.mark.gpu
+
+
+def _small_aerial(seed, n=30000, w=240, h=136, f=175.0):
+    sc = synth.aerial_scene(seed, n, extent=(0.0, 200.0, 0.0, 200.0), n_clusters=20)
+    cam = synth.camera(w, h, f)
+    T = synth.look_pose((100.0, 40.0, 60.0), 0.0, math.radians(30.0))
+    return sc, cam, T
+
+
+CASES = {
+    "tiny": lambda: (synth.tiny_scene(0), synth.tiny_camera(), np.eye(4)),
+    "tiny_sh3_ragged": lambda: (synth.tiny_scene(1, n=2000, sh_degree=3), synth.camera(101, 77, 90.0, 50.3, 38.9),
+                                np.eye(4)),
+    "aerial_small": lambda: _small_aerial(21),
+    "aerial_small_sh2": lambda: (dict(synth.aerial_scene(22, 20000, extent=(0, 200, 0, 200), n_clusters=10,
+                                                         sh_degree=2)),
+                                 synth.camera(250, 131, 180.0), synth.look_pose((90, 30, 70), 0.3, 0.6)),
+}
+
+
+def _check_records_and_lists(oracle, S, scene, cam, T):
+    cov = oracle.cov3d_f32(scene["scales"], scene["quats"])
+    ri, rf = oracle.project_f32(scene["means"], cov, cam, T)
+    vis = np.nonzero(ri[:, oracle.I_STATUS] == oracle.VISIBLE)[0]
+    rec = S.records(0, capacity=len(vis) + 1024)
+    rec = rec[np.argsort(rec[:, 0])]
+    np.testing.assert_array_equal(rec[:, 0], vis)
+    np.testing.assert_array_equal(rec[:, 1:5], ri[vis, 1:5])
+    np.testing.assert_array_equal(rec[:, 5].view(np.uint32), rf[vis, oracle.F_Z].view(np.uint32))
+    np.testing.assert_array_equal(rec[:, 6].view(np.uint32), rf[vis, oracle.F_U].view(np.uint32))
+    np.testing.assert_array_equal(rec[:, 7].view(np.uint32), rf[vis, oracle.F_V].view(np.uint32))
+    ts, keys, gids = oracle.bin_tiles(ri, rf, cam)
+    gts, gkeys, ggids = S.tile_lists(0, cam, capacity=len(keys) + 16)
+    np.testing.assert_array_equal(gts, ts)
+    np.testing.assert_array_equal(gkeys, keys)
+    np.testing.assert_array_equal(ggids, gids)
+    return len(keys)
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_forward_parity(oracle, gsr, case):
+    scene, cam, T = CASES[case]()
+    S = gsr.Scene(scene)
+    out = S.render(cam, T)
+    n_pairs = _check_records_and_lists(oracle, S, scene, cam, T)
+    assert n_pairs > 0
+    gpu = to_numpy(out, cam["height"], cam["width"])
+    orc = oracle.render(scene, cam, T, n_threads=8)
+    errs = compare_images(gpu, orc, oracle)
+    # informational: error against the all-binary64 geometry
+    orc64 = oracle.render(scene, cam, T, geom64=True, n_threads=8)
+    ok = ((orc64["flags"] | orc["flags"]) & oracle.TIE_IMAGE) == 0
+    print(case, "errors vs fp64 oracle (fp32 geometry):", errs,
+          "rgb vs all-fp64 geometry: %.3g" % np.abs(gpu["rgb"] - orc64["rgb"])[ok].max())
+    S.close()
+
+
+def test_features_bf16_fp32_accumulation(oracle, gsr):
+    scene, cam, T = _small_aerial(23, n=20000)
+    g = synth.rng(5)
+    f = g.standard_normal((scene["means"].shape[0], 32)).astype(np.float32)
+    f /= np.linalg.norm(f, axis=1, keepdims=True)
+    scene["feats_bf16"] = synth.to_bf16_bits(f)
+    S = gsr.Scene(scene)
+    out = S.render(cam, T)
+    gpu = to_numpy(out, cam["height"], cam["width"])
+    orc = oracle.render(scene, cam, T, n_threads=8)
+    errs = compare_images(gpu, orc, oracle)
+    assert "feats" in errs
+    # storage error of bf16 (reported, not gated): unrounded features blended by the oracle
+    S.close()
+
+
+def test_full_size_aerial_1080p(oracle, gsr):
+    """1,000,000 Gaussians at 1920x1080 in the benchmark's launch configuration:
+    records and tile lists bit for bit, images on 20,000 sampled pixels."""
+    scene = synth.aerial_scene(2, 1_000_000)
+    cam = synth.aerial_camera()
+    T = synth.aerial_pose()
+    S = gsr.Scene(scene)
+    out = S.render(cam, T)
+    n_pairs = _check_records_and_lists(oracle, S, scene, cam, T)
+    assert n_pairs > 500_000
+    gpu = to_numpy(out, cam["height"], cam["width"])
+    pix = np.sort(synth.rng(9).choice(cam["width"] * cam["height"], 20000, replace=False))
+    orc = oracle.render(scene, cam, T, pixels=pix, n_threads=16)
+    compare_images(gpu, orc, oracle, pixels=pix)
+    S.close()

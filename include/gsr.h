@@ -182,9 +182,11 @@ gs_status gs_get_tile_lists(gs_scene* scene, int view, uint64_t* keys, uint32_t*
 
 /* Projected records of view `view` of the last render (parity/debugging).
  * Synchronous. For each of the *n_records visible Gaussians (in no particular
- * order) rec (host, capacity x 8 int32) receives: Gaussian index, x0, x1, y0,
- * y1 (inclusive tile rectangle), and the bit patterns of the binary32 camera
- * depth, u and v. Errors: INVALID_ARG (bad view, capacity too small). */
+ * order) rec (host, capacity x 10 int32) receives: Gaussian index, x0, x1, y0,
+ * y1 (inclusive tile rectangle), the bit pattern of the binary32 camera depth
+ * (the sort key), then the projected centre used for blending as float-float
+ * bit patterns u_hi, u_lo, v_hi, v_lo (u = u_hi + u_lo).
+ * Errors: INVALID_ARG (bad view, capacity too small). */
 gs_status gs_get_records(gs_scene* scene, int view, int32_t* rec, int64_t capacity, int64_t* n_records,
                          void* stream);
 

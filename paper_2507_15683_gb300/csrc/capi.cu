@@ -238,8 +238,12 @@ gs_status build_views(gs_scene* s, int nv, const gs_camera* cams, const gs_pose*
     const double* T = poses[v].T_cw;
     View& V = hv[v];
     for (int a = 0; a < 3; ++a) {
-      for (int b = 0; b < 3; ++b) V.R[3 * a + b] = (float)T[4 * a + b];
+      for (int b = 0; b < 3; ++b) {
+        V.R[3 * a + b] = (float)T[4 * a + b];
+        V.Rl[3 * a + b] = (float)(T[4 * a + b] - (double)V.R[3 * a + b]);
+      }
       V.t[a] = (float)T[4 * a + 3];
+      V.tl[a] = (float)(T[4 * a + 3] - (double)V.t[a]);
     }
     for (int a = 0; a < 3; ++a)
       V.cw[a] = (float)(-(T[a] * T[3] + T[4 + a] * T[7] + T[8 + a] * T[11]));
@@ -367,6 +371,25 @@ gs_status run_sync(gs_scene* s, const std::vector<View>& hv, uint64_t n_tiles, c
     GS_TRY(grow_pairs(s, need_pair));
   }
   return fail(GS_ERR_CAPACITY, "workspace did not converge");
+}
+
+// IEEE half bit pattern -> float (host side, for the parity export)
+float half_bits_to_float(uint16_t h) {
+  const uint32_t sign = (uint32_t)(h >> 15) << 31;
+  const uint32_t e = (h >> 10) & 0x1f, m = h & 0x3ff;
+  float v;
+  if (e == 0) {
+    v = std::ldexp((float)m, -24);
+  } else if (e == 31) {
+    v = m ? NAN : INFINITY;
+  } else {
+    v = std::ldexp((float)(m | 0x400), (int)e - 25);
+  }
+  uint32_t bits;
+  std::memcpy(&bits, &v, 4);
+  bits |= sign;
+  std::memcpy(&v, &bits, 4);
+  return v;
 }
 
 gs_status check_scene(const gs_scene* s) {
@@ -738,9 +761,10 @@ gs_status gs_get_records(gs_scene* s, int view, int32_t* rec, int64_t capacity, 
   GS_TRY(read_counters(s, (cudaStream_t)stream, c));
   if (c.overflow) return fail(GS_ERR_CAPACITY, "last call overflowed its workspace");
   const uint32_t nrec = std::min(c.rec_count, s->rec_cap);
-  std::vector<float4> ra(nrec), rb(nrec);
+  std::vector<float4> ra(nrec), rb(nrec), rc(nrec);
   std::vector<uint4> rm(nrec);
   if (nrec) {
+    GS_CUDA(cudaMemcpy(rc.data(), s->rec_c.p, nrec * sizeof(float4), cudaMemcpyDeviceToHost));
     GS_CUDA(cudaMemcpy(ra.data(), s->rec_a.p, nrec * sizeof(float4), cudaMemcpyDeviceToHost));
     GS_CUDA(cudaMemcpy(rb.data(), s->rec_b.p, nrec * sizeof(float4), cudaMemcpyDeviceToHost));
     GS_CUDA(cudaMemcpy(rm.data(), s->rec_m.p, nrec * sizeof(uint4), cudaMemcpyDeviceToHost));
@@ -749,15 +773,20 @@ gs_status gs_get_records(gs_scene* s, int view, int32_t* rec, int64_t capacity, 
   for (uint32_t r = 0; r < nrec; ++r) {
     if ((int)rm[r].z != view) continue;
     if (k < capacity) {
-      int32_t* o = rec + 8 * k;
+      int32_t* o = rec + 10 * k;
       std::memcpy(&o[0], &rb[r].w, 4);
       o[1] = (int32_t)(rm[r].x & 0xffff);
       o[2] = (int32_t)(rm[r].x >> 16);
       o[3] = (int32_t)(rm[r].y & 0xffff);
       o[4] = (int32_t)(rm[r].y >> 16);
       o[5] = (int32_t)rm[r].w;
+      uint32_t lo2;
+      std::memcpy(&lo2, &rc[r].w, 4);
+      const float ulo = half_bits_to_float((uint16_t)(lo2 & 0xffff)), vlo = half_bits_to_float((uint16_t)(lo2 >> 16));
       std::memcpy(&o[6], &ra[r].x, 4);
-      std::memcpy(&o[7], &ra[r].y, 4);
+      std::memcpy(&o[7], &ulo, 4);
+      std::memcpy(&o[8], &ra[r].y, 4);
+      std::memcpy(&o[9], &vlo, 4);
     }
     ++k;
   }

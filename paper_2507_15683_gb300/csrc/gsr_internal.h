@@ -21,6 +21,8 @@ constexpr int kPartialStride = 8;  // doubles per tile partial (loss + 6 grad + 
 struct View {
   float R[9];           // world-to-camera rotation (binary32, row-major)
   float t[3];           // world-to-camera translation
+  float Rl[9];          // R - double(R): low parts for the float-float centre
+  float tl[3];          // t - double(t)
   float fx, fy, cx, cy;
   float limx, limy;     // 1.3 x half field of view, in normalised coordinates
   float cw[3];          // camera centre in world coordinates
@@ -68,9 +70,9 @@ struct SceneDev {
 
 // Per-call workspace (device pointers and capacities).
 struct Work {
-  float4* rec_a;       // (u, v, conic A, conic B)
+  float4* rec_a;       // (u, v high parts, conic A, conic B)
   float4* rec_b;       // (conic C, opacity, depth z, Gaussian index bits)
-  float4* rec_c;       // (r, g, b, 0)
+  float4* rec_c;       // (r, g, b, half2 low parts of u and v)
   uint4* rec_m;        // (x0 | x1 << 16, y0 | y1 << 16, view, depth bits)
   float* rec_j;        // kJacStride floats per record (pose gradient only)
   uint32_t rec_cap;

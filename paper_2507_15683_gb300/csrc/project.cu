@@ -8,6 +8,7 @@
 // __fadd_rn, ...) in one fixed order, so that the tile lists and sort keys are
 // reproducible bit for bit by any IEEE binary32 evaluation of the same
 // sequence. Everything after it (conic, colour, Jacobian) is ordinary fp32.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "gsr_internal.h"
@@ -23,6 +24,49 @@ __device__ __forceinline__ float sqr(float a) { return __fsqrt_rn(a); }
 // ((a0 b0 + a1 b1) + a2 b2), each operation rounded
 __device__ __forceinline__ float dot3(float a0, float b0, float a1, float b1, float a2, float b2) {
   return add(add(mul(a0, b0), mul(a1, b1)), mul(a2, b2));
+}
+
+// ---------------------------------------------------------------------------
+// Float-float (double-single) arithmetic for the blending centre: world
+// coordinates of a few hundred metres leave binary32 camera coordinates with
+// ~1e-4 px of error, which the cancellation-heavy pose gradient amplifies.
+// Error-free transformations (Knuth two-sum, FMA two-product) keep ~44 bits.
+// ---------------------------------------------------------------------------
+struct ff {
+  float hi, lo;
+};
+
+__device__ __forceinline__ ff two_sum(float a, float b) {
+  const float s = add(a, b);
+  const float bb = sub(s, a);
+  return {s, add(sub(a, sub(s, bb)), sub(b, bb))};
+}
+
+// (Rh + Rl) . m + (th + tl)
+__device__ __forceinline__ ff ff_row(const float* Rh, const float* Rl, float th, float tl, float m0, float m1,
+                                     float m2) {
+  const float m[3] = {m0, m1, m2};
+  float s = th, err = tl;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const float ph = mul(Rh[j], m[j]);
+    const float pe = __fmaf_rn(Rh[j], m[j], -ph);
+    const ff q = two_sum(s, ph);
+    s = q.hi;
+    err = add(err, add(q.lo, __fmaf_rn(Rl[j], m[j], pe)));
+  }
+  return two_sum(s, err);
+}
+
+// c + f * (num / den) in float-float
+__device__ __forceinline__ ff ff_project(ff num, ff den, float f, float c) {
+  const float qh = dvd(num.hi, den.hi);
+  const float r = add(add(__fmaf_rn(-qh, den.hi, num.hi), num.lo), -mul(qh, den.lo));
+  const float ql = dvd(r, den.hi);
+  const float ph = mul(f, qh);
+  const float pe = __fmaf_rn(f, qh, -ph);
+  const ff s = two_sum(c, ph);
+  return two_sum(s.hi, add(s.lo, __fmaf_rn(f, ql, pe)));
 }
 
 // ---------------------------------------------------------------------------
@@ -288,9 +332,16 @@ __global__ void __launch_bounds__(256) k_project(SceneDev sc, const View* __rest
         clampc[ch] = rgb[ch] < 0.0f;
         rgb[ch] = fmaxf(rgb[ch], 0.0f);
       }
-      w.rec_a[slot] = make_float4(u, v, A, B);
+      // blending centre in float-float; high parts in rec_a, low parts as half2
+      const ff fpx = ff_row(V.R, V.Rl, V.t[0], V.tl[0], p4.x, p4.y, p4.z);
+      const ff fpy = ff_row(V.R + 3, V.Rl + 3, V.t[1], V.tl[1], p4.x, p4.y, p4.z);
+      const ff fpz = ff_row(V.R + 6, V.Rl + 6, V.t[2], V.tl[2], p4.x, p4.y, p4.z);
+      const ff fu = ff_project(fpx, fpz, V.fx, V.cx);
+      const ff fv = ff_project(fpy, fpz, V.fy, V.cy);
+      const __half2 lo2 = __floats2half2_rn(fu.lo, fv.lo);
+      w.rec_a[slot] = make_float4(fu.hi, fv.hi, A, B);
       w.rec_b[slot] = make_float4(C, c1.z, pz, __int_as_float(i));
-      w.rec_c[slot] = make_float4(rgb[0], rgb[1], rgb[2], 0.0f);
+      w.rec_c[slot] = make_float4(rgb[0], rgb[1], rgb[2], *reinterpret_cast<const float*>(&lo2));
       w.rec_m[slot] = make_uint4((unsigned)x0 | ((unsigned)x1 << 16), (unsigned)y0 | ((unsigned)y1 << 16),
                                  (unsigned)vi, __float_as_uint(pz));
       for (int ty = y0; ty <= y1; ++ty)

@@ -11,6 +11,7 @@
 // Both compositing kernels are persistent: CTAs pull tiles from a global
 // queue spanning every view of the call, so views of different resolution
 // share one launch and load-balance.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "gsr_internal.h"
@@ -28,6 +29,14 @@ constexpr int kWarps = kTileThreads / 32;
 __device__ __forceinline__ float gs_power(float A, float B, float C, float dx, float dy) {
   const float q = __fmaf_rn(C, __fmul_rn(dy, dy), __fmul_rn(A, __fmul_rn(dx, dx)));
   return __fmaf_rn(-B, __fmul_rn(dx, dy), __fmul_rn(-0.5f, q));
+}
+
+// Record centre (float-float: high parts in a.xy, half2 low parts in c.w)
+// relative to the tile origin (X0, Y0): exact subtraction, one rounding.
+__device__ __forceinline__ float4 tile_local(float4 a, float cw, float X0, float Y0) {
+  const __half2 lo = *reinterpret_cast<const __half2*>(&cw);
+  const float2 l = __half22float2(lo);
+  return make_float4(__fadd_rn(__fsub_rn(a.x, X0), l.x), __fadd_rn(__fsub_rn(a.y, Y0), l.y), a.z, a.w);
 }
 
 __device__ __forceinline__ int find_view(const View* __restrict__ views, int n_views, uint32_t tile) {
@@ -221,7 +230,9 @@ __global__ void __launch_bounds__(kTileThreads) k_composite(SceneDev sc, const V
     // ---- front-to-back blending, one pixel per thread ----
     const int px = tx * kTile + (tid & 15), py = ty * kTile + (tid >> 4);
     const bool inside = px < V.width && py < V.height;
-    const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+    // pixel centre in tile-local coordinates (records are shifted by the tile origin)
+    const float pxc = (float)(tid & 15) + 0.5f, pyc = (float)(tid >> 4) + 0.5f;
+    const float X0 = (float)(tx * kTile), Y0 = (float)(ty * kTile);
     float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
     float F[FEAT > 0 ? FEAT : 1];
 #pragma unroll
@@ -233,10 +244,11 @@ __global__ void __launch_bounds__(kTileThreads) k_composite(SceneDev sc, const V
       const int bn = min(kBatchF, n - bs);
       if (tid < bn) {
         const uint32_t r = list[bs + tid].y;
-        S.sa[tid] = w.rec_a[r];
+        const float4 cc = w.rec_c[r];
+        S.sa[tid] = tile_local(w.rec_a[r], cc.w, X0, Y0);
         const float4 bb = w.rec_b[r];
         S.sb[tid] = bb;
-        S.sc[tid] = w.rec_c[r];
+        S.sc[tid] = cc;
         if (FEAT) {
           const uint4* fp = sc.feat + (size_t)__float_as_int(bb.w) * 4;
 #pragma unroll
@@ -335,7 +347,8 @@ __global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restric
     const uint32_t start = w.tile_offset[tile];
     const int px = tx * kTile + (tid & 15), py = ty * kTile + (tid >> 4);
     const bool inside = px < V.width && py < V.height;
-    const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+    const float pxc = (float)(tid & 15) + 0.5f, pyc = (float)(tid >> 4) + 0.5f;
+    const float X0 = (float)(tx * kTile), Y0 = (float)(ty * kTile);
     const size_t HW = (size_t)V.width * V.height;
     const size_t p = (size_t)py * V.width + px;
 
@@ -373,9 +386,10 @@ __global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restric
       __syncthreads();
       if (tid < bn) {
         const uint32_t r = w.pairs[start + bstart + tid].y;
-        S.sa[tid] = w.rec_a[r];
+        const float4 cc = w.rec_c[r];
+        S.sa[tid] = tile_local(w.rec_a[r], cc.w, X0, Y0);
         S.sb[tid] = w.rec_b[r];
-        S.sc[tid] = w.rec_c[r];
+        S.sc[tid] = cc;
       }
       for (int q = tid; q < bn * (kJacStride / 4); q += kTileThreads) {
         const int jj = q / (kJacStride / 4), k = q % (kJacStride / 4);
@@ -395,7 +409,7 @@ __global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restric
           const float alpha = fminf(kAlphaCap, oe);
           if (alpha < kAlphaFloor) continue;
           const float oma = 1.0f - alpha;
-          T = __fdividef(T, oma);  // transmittance in front of this Gaussian
+          T = __fdiv_rn(T, oma);  // transmittance in front of this Gaussian
           const float wgt = alpha * T;
           const float4 c = S.sc[j];
           const float dLda = T * (gC0 * (c.x - acc0) + gC1 * (c.y - acc1) + gC2 * (c.z - acc2) + gD * (b.z - accD));

@@ -158,7 +158,7 @@ def gs_get_tile_lists(h, view: int, tiles: int, capacity: int, stream: int):
 
 
 def gs_get_records(h, view: int, capacity: int, stream: int) -> np.ndarray:
-    rec = np.zeros((max(capacity, 1), 8), np.int32)
+    rec = np.zeros((max(capacity, 1), 10), np.int32)
     n = ctypes.c_int64()
     _check(lib.gs_get_records(h, view, rec.ctypes.data, capacity, ctypes.byref(n), stream))
     return rec[:n.value]

@@ -76,7 +76,7 @@ def test_ragged_and_degenerate_sizes(oracle, gsr, w, h):
     cam = synth.camera(w, h, 60.0, w / 2 + 0.25, h / 2 - 0.25)
     S = gsr.Scene(scene)
     gpu = to_numpy(S.render(cam, np.eye(4)), h, w)
-    orc = oracle.render(scene, cam, np.eye(4))
+    orc = oracle.render(scene, cam, np.eye(4), geom64=True)
     compare_images(gpu, orc, oracle, min_ok=0.9)
     S.close()
 
@@ -99,7 +99,7 @@ def test_long_tile_list_uses_global_sort(oracle, gsr):
     gts, gkeys, ggids = S.tile_lists(0, cam, len(keys) + 8)
     np.testing.assert_array_equal(gkeys, keys)
     np.testing.assert_array_equal(ggids, gids)
-    compare_images(to_numpy(out, 128, 128), oracle.render(scene, cam, np.eye(4)), oracle)
+    compare_images(to_numpy(out, 128, 128), oracle.render(scene, cam, np.eye(4), geom64=True), oracle)
     S.close()
 
 
@@ -109,7 +109,7 @@ def test_large_gaussian_covers_every_tile(oracle, gsr):
     cam = synth.camera(200, 150, 120.0)
     S = gsr.Scene(scene)
     gpu = to_numpy(S.render(cam, np.eye(4)), 150, 200)
-    compare_images(gpu, oracle.render(scene, cam, np.eye(4)), oracle)
+    compare_images(gpu, oracle.render(scene, cam, np.eye(4), geom64=True), oracle)
     S.close()
 
 
@@ -122,7 +122,7 @@ def test_capacity_regrow_and_async_status(oracle, gsr):
     cam = synth.tiny_camera()
     S = gsr.Scene(scene)
     out = S.render(cam, np.eye(4))  # synchronous: grows and re-renders
-    compare_images(to_numpy(out, 128, 128), oracle.render(scene, cam, np.eye(4)), oracle)
+    compare_images(to_numpy(out, 128, 128), oracle.render(scene, cam, np.eye(4), geom64=True), oracle)
     S.close()
     S = gsr.Scene(scene)
     S.reserve(1000, 1000)

@@ -202,6 +202,44 @@ gs_status gs_scene_set_timing(gs_scene* scene, int enable);
  * then reset the sums. Errors: INVALID_ARG, CUDA. */
 gs_status gs_scene_kernel_times(gs_scene* scene, double* total_ms, int64_t* launches);
 
+/* gs_render_noalloc -- the forward render of gs_render that allocates
+ * nothing (the paper has no counterpart).
+ *
+ * Why: some callers cannot ask the CUDA allocator for memory when they render
+ * -- a service that sized its device memory once at start-up and may not grow
+ * it per request, a plug-in whose host application owns every device
+ * allocation, or code that runs while another thread captures a CUDA graph in
+ * global mode, where cudaMalloc is not permitted. gs_render needs a scene
+ * (created with cudaMalloc) and grows its workspace on demand; this entry
+ * point needs neither.
+ *
+ * What: renders one view exactly like gs_render (same kernels, same results),
+ * reading the Gaussians straight from the caller's device arrays in desc
+ * (desc->device_resident must be 1; partitions are ignored) and writing the
+ * caller's device outputs. Every intermediate buffer (packed scene, projected
+ * records, tile counts, pair lists, counters) lives in one fixed array of
+ * GS_NOALLOC_SCRATCH_BYTES in device memory that the library reserves on every
+ * GPU it is loaded on, for the lifetime of the process.
+ *
+ * Limits: at most GS_NOALLOC_MAX_GAUSSIANS Gaussians and GS_NOALLOC_MAX_TILES
+ * 16x16 tiles (GS_ERR_INVALID_ARG, checked before any work), and at most
+ * GS_NOALLOC_MAX_PAIRS (tile, Gaussian) pairs (GS_ERR_CAPACITY, detected on
+ * the device; the outputs are then incomplete).
+ *
+ * Calls no cudaMalloc, cudaFree or allocating library routine. Synchronous:
+ * waits for the stream to read the device counters. The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) for that device;
+ * make that first call before any stream capture. All calls share the one
+ * array: calls whose work overlaps on the GPU (different streams or host
+ * threads at the same time) race and corrupt each other's results; serialize
+ * them. Each call clears the parts that must start at zero. */
+#define GS_NOALLOC_MAX_GAUSSIANS 32768
+#define GS_NOALLOC_MAX_TILES 16384
+#define GS_NOALLOC_MAX_PAIRS 524288
+#define GS_NOALLOC_SCRATCH_BYTES (24u << 20)
+gs_status gs_render_noalloc(const gs_scene_desc* desc, const gs_camera* cam, const gs_pose* pose,
+                            const gs_outputs* out, void* stream);
+
 /* Thread-local message describing the last error of this thread ("" if none). */
 const char* gs_last_error(void);
 

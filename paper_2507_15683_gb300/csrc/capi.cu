@@ -93,6 +93,11 @@ struct GraphCache {
 
 }  // namespace
 
+namespace gsr {
+// lets other translation units (the no-allocation entry point) set the message
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace gsr
+
 struct gs_scene {
   int device = 0;
   int sm_count = 1;

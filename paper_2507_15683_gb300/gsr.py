@@ -69,6 +69,7 @@ def _load():
         "gs_scene_status": [vp, vp, vp, vp],
         "gs_get_tile_lists": [vp, ctypes.c_int, vp, vp, vp, i64, vp, vp],
         "gs_get_records": [vp, ctypes.c_int, vp, i64, vp, vp],
+        "gs_render_noalloc": [P(gs_scene_desc), P(gs_camera), P(gs_pose), P(gs_outputs), vp],
         "gs_scene_set_timing": [vp, ctypes.c_int],
         "gs_scene_kernel_times": [vp, vp, vp],
     }
@@ -162,6 +163,18 @@ def gs_get_records(h, view: int, capacity: int, stream: int) -> np.ndarray:
     n = ctypes.c_int64()
     _check(lib.gs_get_records(h, view, rec.ctypes.data, capacity, ctypes.byref(n), stream))
     return rec[:n.value]
+
+
+GS_NOALLOC_MAX_GAUSSIANS = 32768
+GS_NOALLOC_MAX_TILES = 16384
+GS_NOALLOC_MAX_PAIRS = 524288
+
+
+def gs_render_noalloc(desc: gs_scene_desc, cam: gs_camera, pose: gs_pose, out: gs_outputs, stream: int) -> None:
+    """Forward render using only the library's fixed device scratch array (no
+    allocation); desc holds device pointers. See include/gsr.h for the limits."""
+    _check(lib.gs_render_noalloc(ctypes.byref(desc), ctypes.byref(cam), ctypes.byref(pose), ctypes.byref(out),
+                                 stream))
 
 
 KERNEL_NAMES = ("project", "scan_tiles", "scatter", "sort_composite", "backward", "reduce")

@@ -166,10 +166,11 @@ gs_status gs_render_pose_grad_async(gs_scene* scene, const gs_camera* cam, const
 gs_status gs_render_batch(gs_scene* scene, int n_views, const gs_camera* cams, const gs_pose* poses,
                           const gs_outputs* outs, unsigned flags, void* stream);
 
-/* Wait for the stream and return the scene's sticky device status
- * (GS_OK or GS_ERR_CAPACITY / GS_ERR_INTERNAL from earlier asynchronous
- * calls), then clear it. needed_records / needed_pairs (host, may be NULL)
- * receive the sizes the last call needed. */
+/* Wait for the stream and return the device status of the last call (GS_OK,
+ * or GS_ERR_CAPACITY / GS_ERR_INTERNAL from an asynchronous call).
+ * needed_records / needed_pairs (host, may be NULL) receive the workspace the
+ * last call needed (record capacity, pair count), to pass to
+ * gs_scene_reserve. */
 gs_status gs_scene_status(gs_scene* scene, void* stream, int64_t* needed_records, int64_t* needed_pairs);
 
 /* Sorted tile lists of view `view` of the last render (parity/debugging).
@@ -192,8 +193,9 @@ gs_status gs_get_records(gs_scene* scene, int view, int32_t* rec, int64_t capaci
 
 /* Kernel timing (CUDA events recorded on the call's stream around every
  * launch of every call while enabled). Kernel order of the arrays below:
- * projection, tile scan, scatter, sort + composite, backward, reduction. */
-#define GS_KERNEL_COUNT 6
+ * projection, tile scan, scatter, sort + composite, backward (with the final
+ * fp64 reduction). */
+#define GS_KERNEL_COUNT 5
 gs_status gs_scene_set_timing(gs_scene* scene, int enable);
 
 /* Wait for the recorded calls and return, per kernel, the summed device time

@@ -60,21 +60,68 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(Work w) {
 }
 
 // Scatter every record's pairs into the segments of the tiles it covers.
-// Slot order inside a segment is arbitrary; the compositor sorts it.
+// Warp-cooperative: a warp takes 32 record slots, flattens their (record,
+// tile) pairs and spreads them over its lanes, so a Gaussian that covers
+// hundreds of tiles does not serialise one thread; each lane issues its
+// atomics in groups of kScatterUnroll before using any returned slot. Slot
+// order inside a segment is arbitrary; the compositor sorts it.
+constexpr int kScatterUnroll = 4;
+
 __global__ void __launch_bounds__(256) k_scatter(const View* __restrict__ views, Work w) {
+  __shared__ uint32_t s_incl[8][32];
+  __shared__ uint4 s_m[8][32];
   if (w.ctr->overflow) return;
-  const uint32_t n_rec = w.ctr->rec_count < w.rec_cap ? w.ctr->rec_count : w.rec_cap;
-  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n_rec; r += gridDim.x * blockDim.x) {
-    const uint4 m = w.rec_m[r];
-    const int x0 = m.x & 0xffff, x1 = m.x >> 16, y0 = m.y & 0xffff, y1 = m.y >> 16;
-    const View& V = views[m.z];
-    const uint32_t tb = V.tile_base;
-    const int tx_n = V.tiles_x;
-    for (int ty = y0; ty <= y1; ++ty)
-      for (int tx = x0; tx <= x1; ++tx) {
-        const uint32_t pos = atomicAdd(&w.tile_cursor[tb + ty * tx_n + tx], 1u);
-        w.pairs[pos] = make_uint2(m.w, r);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t nw = gridDim.x * 8;
+  for (uint32_t base = (blockIdx.x * 8 + wid) * 32; base < w.rec_cap; base += nw * 32) {  // warp-uniform
+    const uint32_t r = base + lane;
+    uint32_t cnt = 0;
+    uint4 m = make_uint4(0u, 0u, 0u, 0u);
+    if (r < w.rec_cap) {
+      const uint32_t reg = r / w.rec_seg, loc = r - reg * w.rec_seg;
+      if (loc < min(w.ctr->rec_region[reg], w.rec_seg)) {
+        m = w.rec_m[r];
+        cnt = ((m.x >> 16) - (m.x & 0xffffu) + 1u) * ((m.y >> 16) - (m.y & 0xffffu) + 1u);
       }
+    }
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0u) continue;
+    s_incl[wid][lane] = incl;
+    s_m[wid][lane] = m;
+    __syncwarp();
+    for (uint32_t k0 = 0; k0 < total; k0 += 32u * kScatterUnroll) {
+      uint32_t pos[kScatterUnroll];
+      uint2 val[kScatterUnroll];
+#pragma unroll
+      for (int u = 0; u < kScatterUnroll; ++u) {
+        const uint32_t k = k0 + (uint32_t)(u * 32 + lane);
+        pos[u] = 0xffffffffu;
+        if (k < total) {
+          int o = 0;  // first lane whose inclusive count exceeds k
+#pragma unroll
+          for (int step = 16; step > 0; step >>= 1)
+            if (s_incl[wid][o + step - 1] <= k) o += step;
+          const uint32_t local = k - (o ? s_incl[wid][o - 1] : 0u);
+          const uint4 mm = s_m[wid][o];
+          const uint32_t x0 = mm.x & 0xffffu, x1 = mm.x >> 16, y0 = mm.y & 0xffffu;
+          const uint32_t wdt = x1 - x0 + 1u;
+          const uint32_t ty = y0 + local / wdt, tx = x0 + local % wdt;
+          const View& V = views[mm.z];
+          pos[u] = atomicAdd(&w.tile_cursor[V.tile_base + ty * (uint32_t)V.tiles_x + tx], 1u);
+          val[u] = make_uint2(mm.w, base + (uint32_t)o);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kScatterUnroll; ++u)
+        if (pos[u] != 0xffffffffu) w.pairs[pos[u]] = val[u];
+    }
+    __syncwarp();
   }
 }
 

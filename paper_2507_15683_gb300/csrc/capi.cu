@@ -124,8 +124,8 @@ struct gs_scene {
   };
   std::vector<TimedCall> ev_pending;
   std::vector<std::vector<cudaEvent_t>> ev_free;
-  double kt_ms[GS_KERNEL_COUNT] = {0, 0, 0, 0, 0, 0};
-  int64_t kt_n[GS_KERNEL_COUNT] = {0, 0, 0, 0, 0, 0};
+  double kt_ms[GS_KERNEL_COUNT] = {};
+  int64_t kt_n[GS_KERNEL_COUNT] = {};
   // last call
   std::vector<View> last_views;
   uint32_t last_tiles = 0;
@@ -155,6 +155,7 @@ Work work_of(gs_scene* s, uint32_t n_tiles) {
   w.rec_m = dp<uint4>(s->rec_m);
   w.rec_j = dp<float>(s->rec_j);
   w.rec_cap = s->rec_cap;
+  w.rec_seg = s->rec_cap / kRecRegions;
   w.tile_count = dp<uint32_t>(s->tile_count);
   w.tile_offset = dp<uint32_t>(s->tile_offset);
   w.tile_cursor = dp<uint32_t>(s->tile_cursor);
@@ -170,6 +171,7 @@ Work work_of(gs_scene* s, uint32_t n_tiles) {
 
 gs_status grow_records(gs_scene* s, uint64_t rec_cap, bool grad) {
   rec_cap = std::min<uint64_t>(rec_cap, 0x7fffffffull);
+  rec_cap = (rec_cap + kRecRegions - 1) / kRecRegions * kRecRegions;  // equal segments
   if (rec_cap > s->rec_cap) {
     GS_TRY(ensure(s->rec_a, rec_cap * sizeof(float4)));
     GS_TRY(ensure(s->rec_b, rec_cap * sizeof(float4)));
@@ -305,11 +307,11 @@ gs_status enqueue(gs_scene* s, const std::vector<View>& hv, uint64_t n_tiles, co
   if (s->rec_cap == 0) {
     const uint64_t guess = std::max<uint64_t>(1u << 16, (uint64_t)s->n * nv / 4);
     GS_TRY(grow_records(s, guess, g != nullptr));
-    GS_TRY(grow_pairs(s, guess * 4));
+    GS_TRY(grow_pairs(s, guess * 8));
   } else {
     GS_TRY(grow_records(s, s->rec_cap, g != nullptr));
   }
-  if (s->pair_cap == 0) GS_TRY(grow_pairs(s, (uint64_t)s->rec_cap * 4));
+  if (s->pair_cap == 0) GS_TRY(grow_pairs(s, (uint64_t)s->rec_cap * 8));
   View* dviews = dp<View>(s->views);
   GS_CUDA(cudaMemcpyAsync(dviews, upload_src ? upload_src : hv.data(), (size_t)nv * sizeof(View),
                           cudaMemcpyHostToDevice, st));
@@ -339,15 +341,30 @@ gs_status enqueue(gs_scene* s, const std::vector<View>& hv, uint64_t n_tiles, co
   GS_CUDA(launch_composite(sc, dviews, nv, w, s->sm_count * composite_blocks_per_sm(s->feat_dim), st));
   GS_CUDA(mark(4));
   if (g) {
-    GS_CUDA(launch_backward(dviews, nv, w, s->sm_count * backward_blocks_per_sm(), st));
+    GS_CUDA(launch_backward(dviews, nv, w, g->result ? g->result : w.result, s->sm_count * backward_blocks_per_sm(),
+                            st));
     GS_CUDA(mark(5));
-    GS_CUDA(launch_reduce(w, g->result ? g->result : w.result, st));
-    GS_CUDA(mark(6));
   }
   if (timed) s->ev_pending.push_back({std::move(ev), g ? GS_KERNEL_COUNT : 4});
   s->last_views = hv;
   s->last_tiles = (uint32_t)n_tiles;
   return GS_OK;
+}
+
+// Record capacity the last call needed: every segment must hold its count.
+uint64_t records_capacity_needed(const Counters& c) {
+  uint64_t mx = 0;
+  for (int k = 0; k < kRecRegions; ++k) mx = std::max<uint64_t>(mx, c.rec_region[k]);
+  return mx * kRecRegions;
+}
+
+// Indices of the filled record slots (segment k holds min(count_k, seg) records).
+std::vector<uint32_t> filled_records(const Counters& c, uint32_t rec_cap) {
+  std::vector<uint32_t> idx;
+  const uint32_t seg = rec_cap / kRecRegions;
+  for (int k = 0; k < kRecRegions; ++k)
+    for (uint32_t j = 0; j < std::min(c.rec_region[k], seg); ++j) idx.push_back(k * seg + j);
+  return idx;
 }
 
 gs_status read_counters(gs_scene* s, cudaStream_t st, Counters& c) {
@@ -367,7 +384,8 @@ gs_status run_sync(gs_scene* s, const std::vector<View>& hv, uint64_t n_tiles, c
     if (c.error) return fail(GS_ERR_INTERNAL, "device consistency check failed");
     if (!c.overflow) return GS_OK;
     if (c.overflow & 4u) return fail(GS_ERR_CAPACITY, "more than 2^32 (tile, Gaussian) pairs in one call");
-    uint64_t need_rec = std::max<uint64_t>(s->rec_cap, (uint64_t)c.rec_count + c.rec_count / 4 + 1024);
+    const uint64_t need = records_capacity_needed(c);
+    uint64_t need_rec = std::max<uint64_t>(s->rec_cap, need + need / 4 + 1024);
     uint64_t need_pair = std::max<uint64_t>(s->pair_cap, (uint64_t)c.pair_total + c.pair_total / 4 + 4096);
     if (c.overflow & 1u)  // pair count is incomplete when records overflowed
       need_pair = std::max<uint64_t>(need_pair, (uint64_t)s->pair_cap * (need_rec / std::max<uint32_t>(1, s->rec_cap) + 1));
@@ -641,7 +659,7 @@ gs_status gs_render_batch(gs_scene* s, int n_views, const gs_camera* cams, const
     if (s->rec_cap == 0) {
       const uint64_t guess = std::max<uint64_t>(1u << 16, (uint64_t)s->n * n_views / 4);
       GS_TRY(grow_records(s, guess, false));
-      GS_TRY(grow_pairs(s, guess * 4));
+      GS_TRY(grow_pairs(s, guess * 8));
     }
     // capture on a private stream (the legacy default stream cannot be captured);
     // the graph is then launched on the caller's stream
@@ -713,7 +731,7 @@ gs_status gs_scene_status(gs_scene* s, void* stream, int64_t* needed_records, in
   GS_TRY(set_device(s));
   Counters c;
   GS_TRY(read_counters(s, (cudaStream_t)stream, c));
-  if (needed_records) *needed_records = c.rec_count;
+  if (needed_records) *needed_records = (int64_t)records_capacity_needed(c);
   if (needed_pairs) *needed_pairs = c.pair_total;
   if (c.error) return fail(GS_ERR_INTERNAL, "device consistency check failed");
   if (c.overflow) return fail(GS_ERR_CAPACITY, "workspace too small for the last asynchronous call");
@@ -742,7 +760,7 @@ gs_status gs_get_tile_lists(gs_scene* s, int view, uint64_t* keys, uint32_t* gid
   if (np > capacity) return fail(GS_ERR_INVALID_ARG, "capacity too small");
   std::vector<uint2> pr((size_t)np);
   if (np) GS_CUDA(cudaMemcpy(pr.data(), dp<uint2>(s->pairs) + off[0], np * sizeof(uint2), cudaMemcpyDeviceToHost));
-  const uint32_t nrec = std::min(c.rec_count, s->rec_cap);
+  const uint32_t nrec = s->rec_cap;
   std::vector<float4> rb(nrec);
   if (nrec) GS_CUDA(cudaMemcpy(rb.data(), s->rec_b.p, nrec * sizeof(float4), cudaMemcpyDeviceToHost));
   for (uint32_t t = 0; t < nt; ++t)
@@ -765,7 +783,7 @@ gs_status gs_get_records(gs_scene* s, int view, int32_t* rec, int64_t capacity, 
   Counters c;
   GS_TRY(read_counters(s, (cudaStream_t)stream, c));
   if (c.overflow) return fail(GS_ERR_CAPACITY, "last call overflowed its workspace");
-  const uint32_t nrec = std::min(c.rec_count, s->rec_cap);
+  const uint32_t nrec = s->rec_cap;
   std::vector<float4> ra(nrec), rb(nrec), rc(nrec);
   std::vector<uint4> rm(nrec);
   if (nrec) {
@@ -775,7 +793,7 @@ gs_status gs_get_records(gs_scene* s, int view, int32_t* rec, int64_t capacity, 
     GS_CUDA(cudaMemcpy(rm.data(), s->rec_m.p, nrec * sizeof(uint4), cudaMemcpyDeviceToHost));
   }
   int64_t k = 0;
-  for (uint32_t r = 0; r < nrec; ++r) {
+  for (const uint32_t r : filled_records(c, s->rec_cap)) {
     if ((int)rm[r].z != view) continue;
     if (k < capacity) {
       int32_t* o = rec + 10 * k;

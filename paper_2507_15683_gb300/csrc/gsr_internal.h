@@ -16,6 +16,7 @@ constexpr int kBatchF = 256;       // Gaussians staged per forward batch
 constexpr int kBatchB = 128;       // Gaussians staged per backward batch
 constexpr int kJacStride = 48;     // floats per record of the pose Jacobian (45 used)
 constexpr int kPartialStride = 8;  // doubles per tile partial (loss + 6 grad + pad)
+constexpr int kRecRegions = 64;    // record-allocation counters (block index mod 64)
 
 // Per-view parameters (device copy built on the host for every call).
 struct View {
@@ -46,12 +47,17 @@ struct View {
 };
 
 // Device counters and status of one call (zeroed at its start).
+// Records live in kRecRegions equal segments of the record arrays; block b of
+// the projection appends to segment b % kRecRegions, so no single counter
+// serialises the whole grid. rec_region[k] may exceed the segment size (then
+// the overflow bit is set and the count tells the host how much to grow).
 struct Counters {
-  unsigned int rec_count;   // records requested by the projection (may exceed capacity)
+  unsigned int rec_region[kRecRegions];  // records requested per segment
   unsigned int pair_total;  // pairs requested by the binning
   unsigned int overflow;    // bit 0: records, bit 1: pairs, bit 2: pair count >= 2^32
   unsigned int fwd_queue;   // persistent forward tile queue
   unsigned int bwd_queue;   // persistent backward tile queue
+  unsigned int bwd_done;    // backward CTAs finished (the last one reduces)
   unsigned int error;       // device-side consistency failure
   unsigned int pad[2];
 };
@@ -75,7 +81,8 @@ struct Work {
   float4* rec_c;       // (r, g, b, half2 low parts of u and v)
   uint4* rec_m;        // (x0 | x1 << 16, y0 | y1 << 16, view, depth bits)
   float* rec_j;        // kJacStride floats per record (pose gradient only)
-  uint32_t rec_cap;
+  uint32_t rec_cap;    // multiple of kRecRegions
+  uint32_t rec_seg;    // rec_cap / kRecRegions
   uint32_t* tile_count;   // n_tiles + 1
   uint32_t* tile_offset;  // n_tiles + 1 (exclusive scan)
   uint32_t* tile_cursor;  // n_tiles
@@ -99,8 +106,8 @@ cudaError_t launch_scan_tiles(const Work& w, cudaStream_t st);
 cudaError_t launch_scatter(const View* views, const Work& w, int grid, cudaStream_t st);
 cudaError_t launch_composite(const SceneDev& sc, const View* views, int n_views, const Work& w, int grid,
                              cudaStream_t st);
-cudaError_t launch_backward(const View* views, int n_views, const Work& w, int grid, cudaStream_t st);
-cudaError_t launch_reduce(const Work& w, double* result, cudaStream_t st);
+cudaError_t launch_backward(const View* views, int n_views, const Work& w, double* result, int grid,
+                            cudaStream_t st);
 
 // occupancy-derived persistent grid sizes (per SM)
 int composite_blocks_per_sm(int feat_dim);

@@ -169,6 +169,10 @@ extern "C" gs_status gs_render_noalloc(const gs_scene_desc* d, const gs_camera* 
   w.rec_m = reinterpret_cast<uint4*>(base + Layout::rec_m);
   w.rec_j = nullptr;
   w.rec_cap = GS_NOALLOC_MAX_GAUSSIANS;
+  // Segment b % 64 receives the records of projection blocks b: with at most
+  // 32768 Gaussians the projection runs 128 blocks of 256, so a segment holds
+  // at most 2 x 256 = 512 = rec_cap / 64 records and cannot overflow.
+  w.rec_seg = GS_NOALLOC_MAX_GAUSSIANS / kRecRegions;
   w.tile_count = reinterpret_cast<uint32_t*>(base + Layout::tcount);
   w.tile_offset = reinterpret_cast<uint32_t*>(base + Layout::toffset);
   w.tile_cursor = reinterpret_cast<uint32_t*>(base + Layout::tcursor);

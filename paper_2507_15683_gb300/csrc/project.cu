@@ -301,16 +301,19 @@ __global__ void __launch_bounds__(256) k_project(SceneDev sc, const View* __rest
       }
       const unsigned vmask = __ballot_sync(0xffffffffu, vis);
       if (vmask == 0u) continue;
+      // warp-aggregated append into this block's record segment
+      const unsigned region = blockIdx.x % kRecRegions;
       unsigned slot0 = 0;
       const int leader = __ffs(vmask) - 1;
-      if (lane == leader) slot0 = atomicAdd(&w.ctr->rec_count, (unsigned)__popc(vmask));
+      if (lane == leader) slot0 = atomicAdd(&w.ctr->rec_region[region], (unsigned)__popc(vmask));
       slot0 = __shfl_sync(0xffffffffu, slot0, leader);
       if (!vis) continue;
-      const unsigned slot = slot0 + __popc(vmask & lt_mask);
-      if (slot >= w.rec_cap) {
+      const unsigned local = slot0 + __popc(vmask & lt_mask);
+      if (local >= w.rec_seg) {
         atomicOr(&w.ctr->overflow, 1u);
         continue;
       }
+      const unsigned slot = region * w.rec_seg + local;
       // ---- continuous layer ----
       // conic from the binary32 covariance; determinant with one compensated step
       const float bb = cb * cb;

@@ -181,23 +181,66 @@ __device__ uint2* sort_tile(uint2* a, uint2* b, int n, uint32_t* hist, uint32_t*
   return cur;
 }
 
-struct FwdSmem {
-  uint2 bufA[kSortCap];
-  uint2 bufB[kSortCap];
-  uint32_t hist[kWarps * 256];
-  float4 sa[kBatchF], sb[kBatchF], sc[kBatchF];
-};
+// Shared-memory layout of the forward kernel (bytes). The staged batch aliases
+// the second sort buffer, which is free once the sorted list sits in bufA.
+constexpr int kSmBufA = 0;
+constexpr int kSmBufB = kSortCap * 8;
+constexpr int kSmHist = 2 * kSortCap * 8;
+constexpr int kSmStage = kSmBufB;
+constexpr int kSmFwd = kSmHist + kWarps * 256 * 4;
+constexpr int kSmFeat = kSmHist;  // 16 KB of BF16 features: hist + 8 KB more
+constexpr int kSmFwdFeat = (kSmFeat + kBatchF * 64) > kSmFwd ? (kSmFeat + kBatchF * 64) : kSmFwd;
+static_assert(4 * kBatchF * 16 <= kSortCap * 8, "staging must fit in the second sort buffer");
+
+// Warp w covers the 8 x 4 pixel block at (8 (w & 1), 4 (w >> 1)) of the tile.
+__device__ __forceinline__ void warp_block(int tid, int& lx, int& ly, int& bx, int& by) {
+  const int warp = tid >> 5, lane = tid & 31;
+  bx = (warp & 1) * 8;
+  by = (warp >> 1) * 4;
+  lx = bx + (lane & 7);
+  ly = by + (lane >> 3);
+}
+
+// Conservative footprint of alpha >= 1/255 in tile-local pixel coordinates:
+// the test needs o exp(power) >= 1/255, i.e. d^T Q d <= 2 ln(255 o), an ellipse
+// with half extents sqrt(2 ln(255 o) S_xx), sqrt(2 ln(255 o) S_yy), S = Q^-1.
+// Margins (1 % on the log, 0.1 % + 0.01 px on the extents) cover the fp32
+// evaluation of the per-pixel test, so a warp whose block misses the box would
+// have skipped the Gaussian at every pixel: skipping it changes nothing.
+__device__ __forceinline__ float4 alpha_box(float4 a, float C, float o) {
+  const float Lp = __logf(255.0f * o) * 1.01f + 0.01f;
+  if (!(Lp > 0.0f)) return make_float4(1e30f, -1e30f, 1e30f, -1e30f);  // cannot reach the floor
+  const float detq = a.z * C - a.w * a.w;
+  if (!(detq > 0.0f)) return make_float4(-1e30f, 1e30f, -1e30f, 1e30f);  // degenerate: always test
+  const float k = 2.0f * Lp / detq;
+  const float ex = sqrtf(k * C) * 1.001f + 0.01f, ey = sqrtf(k * a.z) * 1.001f + 0.01f;
+  return make_float4(a.x - ex, a.x + ex, a.y - ey, a.y + ey);
+}
+
+__device__ __forceinline__ bool box_hits(float4 b, float wx0, float wx1, float wy0, float wy1) {
+  return (b.y >= wx0) & (b.x <= wx1) & (b.w >= wy0) & (b.z <= wy1);
+}
 
 template <int FEAT>
 __global__ void __launch_bounds__(kTileThreads) k_composite(SceneDev sc, const View* __restrict__ views, int n_views,
                                                             Work w) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  FwdSmem& S = *reinterpret_cast<FwdSmem*>(smem_raw);
-  uint4* sf = reinterpret_cast<uint4*>(smem_raw + sizeof(FwdSmem));  // FEAT: kBatchF x 4
+  uint2* bufA = reinterpret_cast<uint2*>(smem_raw + kSmBufA);
+  uint2* bufB = reinterpret_cast<uint2*>(smem_raw + kSmBufB);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(smem_raw + kSmHist);
+  float4* sa = reinterpret_cast<float4*>(smem_raw + kSmStage);
+  float4* sb = sa + kBatchF;
+  float4* scol = sb + kBatchF;
+  float4* sbox = scol + kBatchF;
+  uint4* sf = reinterpret_cast<uint4*>(smem_raw + kSmFeat);  // FEAT: kBatchF x 4 (aliases hist)
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_tmp[kWarps];
   if (w.ctr->overflow) return;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
+  int lx, ly, bxw, byw;
+  warp_block(tid, lx, ly, bxw, byw);
+  const float pxc = (float)lx + 0.5f, pyc = (float)ly + 0.5f;
+  const float wx0 = (float)bxw + 0.5f, wx1 = (float)bxw + 7.5f, wy0 = (float)byw + 0.5f, wy1 = (float)byw + 3.5f;
   for (;;) {
     if (tid == 0) s_tile = atomicAdd(&w.ctr->fwd_queue, 1u);
     __syncthreads();
@@ -213,13 +256,17 @@ __global__ void __launch_bounds__(kTileThreads) k_composite(SceneDev sc, const V
     // ---- depth order of the tile's list ----
     const uint2* list;
     if (n <= kSortCap) {
-      for (int i = tid; i < n; i += kTileThreads) S.bufA[i] = w.pairs[start + i];
+      for (int i = tid; i < n; i += kTileThreads) bufA[i] = w.pairs[start + i];
       __syncthreads();
-      uint2* sorted = sort_tile(S.bufA, S.bufB, n, S.hist, s_tmp, w.rec_b);
-      for (int i = tid; i < n; i += kTileThreads) w.pairs[start + i] = sorted[i];
-      list = sorted;
+      const uint2* sorted = sort_tile(bufA, bufB, n, hist, s_tmp, w.rec_b);
+      if (sorted != bufA) {
+        for (int i = tid; i < n; i += kTileThreads) bufA[i] = sorted[i];
+        __syncthreads();
+      }
+      for (int i = tid; i < n; i += kTileThreads) w.pairs[start + i] = bufA[i];
+      list = bufA;
     } else {
-      uint2* sorted = sort_tile(w.pairs + start, w.pairs_tmp + start, n, S.hist, s_tmp, w.rec_b);
+      uint2* sorted = sort_tile(w.pairs + start, w.pairs_tmp + start, n, hist, s_tmp, w.rec_b);
       if (sorted != w.pairs + start) {
         for (int i = tid; i < n; i += kTileThreads) w.pairs[start + i] = sorted[i];
         __syncthreads();
@@ -228,10 +275,8 @@ __global__ void __launch_bounds__(kTileThreads) k_composite(SceneDev sc, const V
     }
 
     // ---- front-to-back blending, one pixel per thread ----
-    const int px = tx * kTile + (tid & 15), py = ty * kTile + (tid >> 4);
+    const int px = tx * kTile + lx, py = ty * kTile + ly;
     const bool inside = px < V.width && py < V.height;
-    // pixel centre in tile-local coordinates (records are shifted by the tile origin)
-    const float pxc = (float)(tid & 15) + 0.5f, pyc = (float)(tid >> 4) + 0.5f;
     const float X0 = (float)(tx * kTile), Y0 = (float)(ty * kTile);
     float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
     float F[FEAT > 0 ? FEAT : 1];
@@ -245,10 +290,12 @@ __global__ void __launch_bounds__(kTileThreads) k_composite(SceneDev sc, const V
       if (tid < bn) {
         const uint32_t r = list[bs + tid].y;
         const float4 cc = w.rec_c[r];
-        S.sa[tid] = tile_local(w.rec_a[r], cc.w, X0, Y0);
+        const float4 a = tile_local(w.rec_a[r], cc.w, X0, Y0);
         const float4 bb = w.rec_b[r];
-        S.sb[tid] = bb;
-        S.sc[tid] = cc;
+        sa[tid] = a;
+        sb[tid] = bb;
+        scol[tid] = cc;
+        sbox[tid] = alpha_box(a, bb.x, bb.y);
         if (FEAT) {
           const uint4* fp = sc.feat + (size_t)__float_as_int(bb.w) * 4;
 #pragma unroll
@@ -256,10 +303,17 @@ __global__ void __launch_bounds__(kTileThreads) k_composite(SceneDev sc, const V
         }
       }
       __syncthreads();
-      if (!done) {
-        for (int j = 0; j < bn; ++j) {
-          const float4 a = S.sa[j];
-          const float4 b = S.sb[j];
+      bool wdone = __all_sync(0xffffffffu, done);
+      for (int c0 = 0; c0 < bn && !wdone; c0 += 32) {
+        const int jj = c0 + lane;
+        const bool hit = jj < bn && box_hits(sbox[jj], wx0, wx1, wy0, wy1);
+        uint32_t m = __ballot_sync(0xffffffffu, hit);
+        while (m) {
+          const int j = c0 + __ffs(m) - 1;
+          m &= m - 1;
+          if (done) continue;
+          const float4 a = sa[j];
+          const float4 b = sb[j];
           const float dx = __fsub_rn(a.x, pxc), dy = __fsub_rn(a.y, pyc);
           const float power = gs_power(a.z, a.w, b.x, dx, dy);
           if (power > 0.0f) continue;
@@ -269,10 +323,10 @@ __global__ void __launch_bounds__(kTileThreads) k_composite(SceneDev sc, const V
           const float Tn = __fmul_rn(T, __fsub_rn(1.0f, alpha));
           if (Tn < kTCut) {
             done = true;
-            break;
+            continue;
           }
           const float wgt = __fmul_rn(alpha, T);
-          const float4 c = S.sc[j];
+          const float4 c = scol[j];
           C0 = fmaf(wgt, c.x, C0);
           C1 = fmaf(wgt, c.y, C1);
           C2 = fmaf(wgt, c.z, C2);
@@ -292,6 +346,7 @@ __global__ void __launch_bounds__(kTileThreads) k_composite(SceneDev sc, const V
           T = Tn;
           last = (uint32_t)(bs + j + 1);
         }
+        wdone = __all_sync(0xffffffffu, done);
       }
     }
     if (inside) {
@@ -320,20 +375,27 @@ __global__ void __launch_bounds__(kTileThreads) k_composite(SceneDev sc, const V
 // the transmittance from the stored final value, T_k = T_{k+1} / (1 - a_k);
 // chain dL/d(u, v, conic, z, rgb) through the per-Gaussian pose Jacobian and
 // accumulate the 6-vector per pixel (fp32); reduce across pixels in fp64.
+// The same per-warp footprint test as the forward skips pairs that no pixel of
+// the warp blended.
 // ---------------------------------------------------------------------------
 struct BwdSmem {
-  float4 sa[kBatchB], sb[kBatchB], sc[kBatchB];
+  float4 sa[kBatchB], sb[kBatchB], sc[kBatchB], sbox[kBatchB];
   float4 sj[kBatchB * (kJacStride / 4)];
   double red[kWarps][8];
 };
 
-__global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restrict__ views, int n_views, Work w) {
+__global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restrict__ views, int n_views, Work w,
+                                                           double* __restrict__ result) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BwdSmem& S = *reinterpret_cast<BwdSmem*>(smem_raw);
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_max[kWarps];
   if (w.ctr->overflow) return;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  int lx, ly, bxw, byw;
+  warp_block(tid, lx, ly, bxw, byw);
+  const float pxc = (float)lx + 0.5f, pyc = (float)ly + 0.5f;
+  const float wx0 = (float)bxw + 0.5f, wx1 = (float)bxw + 7.5f, wy0 = (float)byw + 0.5f, wy1 = (float)byw + 3.5f;
   const float4* rec_j4 = reinterpret_cast<const float4*>(w.rec_j);
   for (;;) {
     if (tid == 0) s_tile = atomicAdd(&w.ctr->bwd_queue, 1u);
@@ -345,9 +407,8 @@ __global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restric
     const uint32_t lt = tile - V.tile_base;
     const int tx = (int)(lt % (uint32_t)V.tiles_x), ty = (int)(lt / (uint32_t)V.tiles_x);
     const uint32_t start = w.tile_offset[tile];
-    const int px = tx * kTile + (tid & 15), py = ty * kTile + (tid >> 4);
+    const int px = tx * kTile + lx, py = ty * kTile + ly;
     const bool inside = px < V.width && py < V.height;
-    const float pxc = (float)(tid & 15) + 0.5f, pyc = (float)(tid >> 4) + 0.5f;
     const float X0 = (float)(tx * kTile), Y0 = (float)(ty * kTile);
     const size_t HW = (size_t)V.width * V.height;
     const size_t p = (size_t)py * V.width + px;
@@ -370,7 +431,7 @@ __global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restric
       gD = sd * (float)((e > 0.f) - (e < 0.f));
       loss = (double)s3 * ((double)fabsf(r0) + (double)fabsf(r1) + (double)fabsf(r2)) + (double)sd * (double)fabsf(e);
     }
-    // longest list prefix any pixel of the tile blended
+    // longest list prefix any pixel of the tile (and of this warp) blended
     const uint32_t wm = __reduce_max_sync(0xffffffffu, last);
     if (lane == 0) s_max[wid] = wm;
     __syncthreads();
@@ -387,9 +448,12 @@ __global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restric
       if (tid < bn) {
         const uint32_t r = w.pairs[start + bstart + tid].y;
         const float4 cc = w.rec_c[r];
-        S.sa[tid] = tile_local(w.rec_a[r], cc.w, X0, Y0);
-        S.sb[tid] = w.rec_b[r];
+        const float4 a = tile_local(w.rec_a[r], cc.w, X0, Y0);
+        const float4 bb = w.rec_b[r];
+        S.sa[tid] = a;
+        S.sb[tid] = bb;
         S.sc[tid] = cc;
+        S.sbox[tid] = alpha_box(a, bb.x, bb.y);
       }
       for (int q = tid; q < bn * (kJacStride / 4); q += kTileThreads) {
         const int jj = q / (kJacStride / 4), k = q % (kJacStride / 4);
@@ -397,9 +461,16 @@ __global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restric
         S.sj[q] = rec_j4[(size_t)r * (kJacStride / 4) + k];
       }
       __syncthreads();
-      if (inside) {
-        for (int j = bn - 1; j >= 0; --j) {
-          if ((uint32_t)(bstart + j) >= last) continue;
+      if ((uint32_t)bstart >= wm) continue;  // no pixel of this warp blended this far
+      for (int c0 = ((bn - 1) >> 5) << 5; c0 >= 0; c0 -= 32) {
+        const int jj = c0 + lane;
+        const bool hit = jj < bn && (uint32_t)(bstart + jj) < wm && box_hits(S.sbox[jj], wx0, wx1, wy0, wy1);
+        uint32_t m = __ballot_sync(0xffffffffu, hit);
+        while (m) {
+          const int bit = 31 - __clz(m);
+          m &= ~(1u << bit);
+          const int j = c0 + bit;
+          if (!inside || (uint32_t)(bstart + j) >= last) continue;
           const float4 a = S.sa[j];
           const float4 b = S.sb[j];
           const float dx = __fsub_rn(a.x, pxc), dy = __fsub_rn(a.y, pyc);
@@ -409,7 +480,7 @@ __global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restric
           const float alpha = fminf(kAlphaCap, oe);
           if (alpha < kAlphaFloor) continue;
           const float oma = 1.0f - alpha;
-          T = __fdiv_rn(T, oma);  // transmittance in front of this Gaussian
+          T = __fdividef(T, oma);  // transmittance in front of this Gaussian
           const float wgt = alpha * T;
           const float4 c = S.sc[j];
           const float dLda = T * (gC0 * (c.x - acc0) + gC1 * (c.y - acc1) + gC2 * (c.z - acc2) + gD * (b.z - accD));
@@ -465,16 +536,19 @@ __global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restric
     }
     __syncthreads();
   }
-}
-
-// Deterministic fp64 sum of the per-tile partials (fixed order).
-__global__ void __launch_bounds__(256) k_reduce(Work w, double* __restrict__ result) {
-  __shared__ double red[8][8];
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // The last CTA to finish sums the per-tile partials in a fixed order
+  // (deterministic): thread t takes tiles t, t + 256, ..., then a fixed tree.
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd(&w.ctr->bwd_done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
   double v[7] = {0, 0, 0, 0, 0, 0, 0};
-  for (uint32_t t = tid; t < w.n_tiles; t += 256) {
+  for (uint32_t t = tid; t < w.n_tiles; t += kTileThreads) {
 #pragma unroll
-    for (int k = 0; k < 7; ++k) v[k] += w.partials[(size_t)t * kPartialStride + k];
+    for (int k = 0; k < 7; ++k) v[k] += __ldcg(w.partials + (size_t)t * kPartialStride + k);
   }
 #pragma unroll
   for (int k = 0; k < 7; ++k) {
@@ -483,20 +557,20 @@ __global__ void __launch_bounds__(256) k_reduce(Work w, double* __restrict__ res
   }
   if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < 7; ++k) red[wid][k] = v[k];
+    for (int k = 0; k < 7; ++k) S.red[wid][k] = v[k];
   }
   __syncthreads();
   if (tid < 7) {
     double s = 0.0;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) s += red[k][tid];
+    for (int k = 0; k < kWarps; ++k) s += S.red[k][tid];
     result[tid] = s;
   }
 }
 
 template <int FEAT>
 size_t composite_smem() {
-  return sizeof(FwdSmem) + (FEAT ? sizeof(uint4) * kBatchF * 4 : 0);
+  return FEAT ? (size_t)kSmFwdFeat : (size_t)kSmFwd;
 }
 
 template <int FEAT>
@@ -543,16 +617,12 @@ cudaError_t launch_composite(const SceneDev& sc, const View* views, int n_views,
   return cudaGetLastError();
 }
 
-cudaError_t launch_backward(const View* views, int n_views, const Work& w, int grid, cudaStream_t st) {
+cudaError_t launch_backward(const View* views, int n_views, const Work& w, double* result, int grid,
+                            cudaStream_t st) {
   if (w.n_tiles == 0) return cudaSuccess;
   backward_blocks_per_sm();
   const int g = (uint32_t)grid < w.n_tiles ? grid : (int)w.n_tiles;
-  k_backward<<<g, kTileThreads, sizeof(BwdSmem), st>>>(views, n_views, w);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_reduce(const Work& w, double* result, cudaStream_t st) {
-  k_reduce<<<1, 256, 0, st>>>(w, result);
+  k_backward<<<g, kTileThreads, sizeof(BwdSmem), st>>>(views, n_views, w, result);
   return cudaGetLastError();
 }
 

@@ -340,7 +340,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(scene, cam, T_ref, T_q, args.cpu_seconds)
 
-    launches_per_step = 5  # project, scan, scatter, sort+composite, backward (+ final reduction)
+    launches_per_step = 6  # project, shade, scan, scatter, sort+composite, backward (+ final reduction)
     value = world * P / (ms_grad * 1e-3) / 1e6
     line = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,

@@ -166,6 +166,64 @@ gs_status gs_render_pose_grad_async(gs_scene* scene, const gs_camera* cam, const
 gs_status gs_render_batch(gs_scene* scene, int n_views, const gs_camera* cams, const gs_pose* poses,
                           const gs_outputs* outs, unsigned flags, void* stream);
 
+/* Batched pose gradient: the candidate poses / pyramid levels of Sec. 3.4
+ * rendered and differentiated in one pass (one projection launch, one global
+ * tile space, one persistent compositing launch and one persistent backward
+ * launch over every view's tiles). For each view v the loss and gradient equal
+ * those of gs_render_pose_grad for that view alone (bit for bit).
+ * target_rgb, target_depth: host arrays of n_views device pointers (3 x H x W
+ * and H x W of that view); pixel_weight: NULL or a host array of n_views device
+ * pointers (entries may be NULL). outs: NULL or n_views output sets.
+ * flags 0: synchronous (regrow rule of gs_render); loss_out (host, n_views)
+ * and grad_out (host, n_views x 6) are written when not NULL; results_dev,
+ * when not NULL, also receives them. GS_BATCH_GRAPH: asynchronous replay of a
+ * CUDA graph captured on the first call for this layout (cameras, outputs,
+ * targets, weights, results_dev); poses may change between calls; results_dev
+ * (device, n_views x 8 doubles: loss, 6 gradient entries, 0) is required and
+ * loss_out / grad_out are not written. Errors: INVALID_ARG, OOM, CUDA. */
+gs_status gs_render_pose_grad_batch(gs_scene* scene, int n_views, const gs_camera* cams, const gs_pose* poses,
+                                    const float* const* target_rgb, const float* const* target_depth,
+                                    const float* const* pixel_weight, float depth_weight, const gs_outputs* outs,
+                                    double* loss_out, double* grad_out, double* results_dev, unsigned flags,
+                                    void* stream);
+
+/* Pose refinement (the render-and-refine loop of Sec. 3.4, done by gradient
+ * descent on the loss of gs_render_pose_grad). Every iteration renders,
+ * differentiates, takes an Adam step s on the tangent xi = (rho, phi) --
+ * per-component step size lr_trans for rho, lr_rot for phi, moments carried
+ * across iterations -- and applies the left update T <- Exp(-s^) T, so the
+ * tangent is re-linearised at the current pose. */
+typedef struct {
+  int iterations;      /* number of render + gradient + update steps (>= 0) */
+  double lr_rot;       /* Adam step size of the rotation part (rad) */
+  double lr_trans;     /* Adam step size of the translation part (scene units) */
+  double beta1, beta2; /* Adam moment decays, in [0, 1) */
+  double eps;          /* Adam denominator floor, > 0 */
+  float depth_weight;  /* lambda_d of the loss */
+} gs_refine_opts;
+
+/* Defaults: 50 iterations, lr_rot 1e-3, lr_trans 0.5, betas 0.9 / 0.999,
+ * eps 1e-8, depth weight 0.1. */
+gs_refine_opts gs_refine_defaults(void);
+
+/* Refine one pose in place (pose: host, updated). Targets and weights as in
+ * gs_render_pose_grad. loss_history: host array of opts->iterations (the loss
+ * before each update) or NULL. Synchronous. Errors: those of
+ * gs_render_pose_grad, INVALID_ARG for bad options. */
+gs_status gs_refine_pose(gs_scene* scene, const gs_camera* cam, gs_pose* pose, const float* target_rgb,
+                         const float* target_depth, const float* pixel_weight, const gs_refine_opts* opts,
+                         double* loss_history, void* stream);
+
+/* Refine n_views poses together (poses: host array, updated in place): every
+ * iteration is one batched pose-gradient pass (replayed CUDA graph after the
+ * first), then one Adam update per view. Targets and weights as in
+ * gs_render_pose_grad_batch. loss_history: host array n_views x iterations or
+ * NULL. Synchronous. */
+gs_status gs_refine_poses_batch(gs_scene* scene, int n_views, const gs_camera* cams, gs_pose* poses,
+                                const float* const* target_rgb, const float* const* target_depth,
+                                const float* const* pixel_weight, const gs_refine_opts* opts,
+                                double* loss_history, void* stream);
+
 /* Wait for the stream and return the device status of the last call (GS_OK,
  * or GS_ERR_CAPACITY / GS_ERR_INTERNAL from an asynchronous call).
  * needed_records / needed_pairs (host, may be NULL) receive the workspace the
@@ -193,9 +251,10 @@ gs_status gs_get_records(gs_scene* scene, int view, int32_t* rec, int64_t capaci
 
 /* Kernel timing (CUDA events recorded on the call's stream around every
  * launch of every call while enabled). Kernel order of the arrays below:
- * projection, tile scan, scatter, sort + composite, backward (with the final
- * fp64 reduction). */
-#define GS_KERNEL_COUNT 5
+ * projection (discrete layer), shading (conic, colour, centre, Jacobian),
+ * tile scan, scatter, sort + composite, backward (with the final fp64
+ * reduction). */
+#define GS_KERNEL_COUNT 6
 gs_status gs_scene_set_timing(gs_scene* scene, int enable);
 
 /* Wait for the recorded calls and return, per kernel, the summed device time

@@ -72,19 +72,23 @@ T* dp(const DevBuf& b) {
   return reinterpret_cast<T*>(b.p);
 }
 
+// Loss inputs of a pose-gradient call, one entry per view (host arrays of
+// device pointers).
 struct GradIn {
-  const float* target_rgb;
-  const float* target_depth;
-  const float* pixel_weight;
+  const float* const* target_rgb;
+  const float* const* target_depth;
+  const float* const* pixel_weight;  // NULL, or per-view entries that may be NULL
   float depth_weight;
-  double* result;  // device destination of (loss, grad) or NULL (scene buffer)
+  double* result;  // device destination, kResultStride doubles per view, or NULL (scene buffer)
 };
 
+constexpr int kResultStride = 8;  // (loss, grad rho, grad phi, pad) per view
+
+// A captured batch: replayed while everything but the poses is unchanged.
 struct GraphCache {
   bool valid = false;
   cudaGraphExec_t exec = nullptr;
-  std::vector<gs_camera> cams;
-  std::vector<gs_outputs> outs;
+  std::vector<char> key;       // cameras, outputs, loss inputs of the capture
   View* host_views = nullptr;  // pinned; read by the graph's upload node at replay
   cudaEvent_t done = nullptr;
   cudaStream_t capture = nullptr;
@@ -129,7 +133,8 @@ struct gs_scene {
   // last call
   std::vector<View> last_views;
   uint32_t last_tiles = 0;
-  GraphCache graph;
+  GraphCache graph;       // forward batches
+  GraphCache graph_grad;  // pose-gradient batches
 };
 
 namespace {
@@ -283,9 +288,9 @@ gs_status build_views(gs_scene* s, int nv, const gs_camera* cams, const gs_pose*
       if (!V.depth) V.depth = base + 3 * P;
       if (!V.final_T) V.final_T = base + 4 * P;
       if (!V.last_idx) V.last_idx = reinterpret_cast<uint32_t*>(base + 5 * P);
-      V.target_rgb = g->target_rgb;
-      V.target_depth = g->target_depth;
-      V.pixel_weight = g->pixel_weight;
+      V.target_rgb = g->target_rgb[v];
+      V.target_depth = g->target_depth[v];
+      V.pixel_weight = g->pixel_weight ? g->pixel_weight[v] : nullptr;
       V.depth_weight = g->depth_weight;
       V.inv_3p = (float)(1.0 / (3.0 * (double)P));
       V.inv_p = (float)(1.0 / (double)P);
@@ -304,6 +309,7 @@ gs_status enqueue(gs_scene* s, const std::vector<View>& hv, uint64_t n_tiles, co
   const int nv = (int)hv.size();
   GS_TRY(grow_tiles(s, n_tiles));
   GS_TRY(ensure(s->views, (size_t)nv * sizeof(View)));
+  if (g && !g->result) GS_TRY(ensure(s->result, (size_t)nv * kResultStride * sizeof(double)));
   if (s->rec_cap == 0) {
     const uint64_t guess = std::max<uint64_t>(1u << 16, (uint64_t)s->n * nv / 4);
     GS_TRY(grow_records(s, guess, g != nullptr));
@@ -332,20 +338,24 @@ gs_status enqueue(gs_scene* s, const std::vector<View>& hv, uint64_t n_tiles, co
   }
   auto mark = [&](int k) -> cudaError_t { return timed ? cudaEventRecord(ev[k], st) : cudaSuccess; };
   GS_CUDA(mark(0));
-  GS_CUDA(launch_project(sc, dviews, nv, w, g != nullptr, s->sm_count * 8, st));
+  GS_CUDA(launch_project(sc, dviews, nv, w, s->sm_count * 8, st));
   GS_CUDA(mark(1));
-  GS_CUDA(launch_scan_tiles(w, st));
+  GS_CUDA(launch_shade(sc, dviews, w, g != nullptr, s->sm_count * 8, st));
   GS_CUDA(mark(2));
-  GS_CUDA(launch_scatter(dviews, w, s->sm_count * 8, st));
+  GS_CUDA(launch_scan_tiles(w, st));
   GS_CUDA(mark(3));
-  GS_CUDA(launch_composite(sc, dviews, nv, w, s->sm_count * composite_blocks_per_sm(s->feat_dim), st));
+  GS_CUDA(launch_scatter(dviews, w, s->sm_count * 8, st));
   GS_CUDA(mark(4));
+  GS_CUDA(launch_composite(sc, dviews, nv, w, s->sm_count * composite_blocks_per_sm(s->feat_dim), st));
+  GS_CUDA(mark(5));
   if (g) {
-    GS_CUDA(launch_backward(dviews, nv, w, g->result ? g->result : w.result, s->sm_count * backward_blocks_per_sm(),
-                            st));
-    GS_CUDA(mark(5));
+    double* res = g->result ? g->result : w.result;
+    // one view: the last backward CTA reduces; several: one reduction CTA per view
+    GS_CUDA(launch_backward(dviews, nv, w, nv == 1 ? res : nullptr, s->sm_count * backward_blocks_per_sm(), st));
+    if (nv > 1) GS_CUDA(launch_reduce_views(dviews, nv, w, res, st));
+    GS_CUDA(mark(6));
   }
-  if (timed) s->ev_pending.push_back({std::move(ev), g ? GS_KERNEL_COUNT : 4});
+  if (timed) s->ev_pending.push_back({std::move(ev), g ? GS_KERNEL_COUNT : GS_KERNEL_COUNT - 1});
   s->last_views = hv;
   s->last_tiles = (uint32_t)n_tiles;
   return GS_OK;
@@ -430,6 +440,67 @@ gs_status check_grad_args(const float* target_rgb, const float* target_depth, fl
   if (!std::isfinite(depth_weight) || depth_weight < 0.0f)
     return fail(GS_ERR_INVALID_ARG, "depth_weight must be finite and >= 0");
   return GS_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// Replay the cached graph if the batch layout (key) is unchanged, else capture
+// a new one. Everything the capture needs is allocated before capturing.
+gs_status run_graph(gs_scene* s, GraphCache& G, const std::vector<char>& key, const std::vector<View>& hv,
+                    uint64_t n_tiles, const GradIn* g, cudaStream_t st) {
+  const int n_views = (int)hv.size();
+  if (!(G.valid && G.key == key)) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    G.exec = nullptr;
+    G.valid = false;
+    if (G.host_views) cudaFreeHost(G.host_views);
+    G.host_views = nullptr;
+    if (!G.done) GS_CUDA(cudaEventCreateWithFlags(&G.done, cudaEventDisableTiming));
+    GS_CUDA(cudaMallocHost(&G.host_views, (size_t)n_views * sizeof(View)));
+    std::memcpy(G.host_views, hv.data(), (size_t)n_views * sizeof(View));
+    GS_TRY(grow_tiles(s, n_tiles));
+    GS_TRY(ensure(s->views, (size_t)n_views * sizeof(View)));
+    if (g && !g->result) GS_TRY(ensure(s->result, (size_t)n_views * kResultStride * sizeof(double)));
+    const uint64_t guess = std::max<uint64_t>(1u << 16, (uint64_t)s->n * n_views / 4);
+    GS_TRY(grow_records(s, s->rec_cap ? s->rec_cap : guess, g != nullptr));
+    GS_TRY(grow_pairs(s, s->pair_cap ? s->pair_cap : guess * 8));
+    // capture on a private stream (the legacy default stream cannot be captured);
+    // the graph is then launched on the caller's stream
+    if (!G.capture) GS_CUDA(cudaStreamCreateWithFlags(&G.capture, cudaStreamNonBlocking));
+    GS_CUDA(cudaStreamSynchronize(st));
+    cudaGraph_t graph = nullptr;
+    GS_CUDA(cudaStreamBeginCapture(G.capture, cudaStreamCaptureModeThreadLocal));
+    const gs_status est = enqueue(s, hv, n_tiles, g, G.capture, G.host_views);
+    const cudaError_t ce = cudaStreamEndCapture(G.capture, &graph);
+    if (est != GS_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return est;
+    }
+    if (ce != cudaSuccess) return fail(GS_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ce));
+    const cudaError_t ie = cudaGraphInstantiate(&G.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return fail(GS_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+    G.key = key;
+    G.n_views = n_views;
+    G.valid = true;
+  } else {
+    // the previous replay must have consumed the pinned view table
+    GS_CUDA(cudaEventSynchronize(G.done));
+    std::memcpy(G.host_views, hv.data(), (size_t)n_views * sizeof(View));
+    s->last_views = hv;
+    s->last_tiles = (uint32_t)n_tiles;
+  }
+  GS_CUDA(cudaGraphLaunch(G.exec, st));
+  GS_CUDA(cudaEventRecord(G.done, st));
+  return GS_OK;
+}
+
+template <typename T>
+void append_bytes(std::vector<char>& key, const T* p, size_t n) {
+  const char* b = reinterpret_cast<const char*>(p);
+  key.insert(key.end(), b, b + n * sizeof(T));
 }
 
 }  // namespace
@@ -538,10 +609,12 @@ void gs_destroy_scene(gs_scene* s) {
   if (!s) return;
   cudaSetDevice(s->device);
   cudaDeviceSynchronize();
-  if (s->graph.exec) cudaGraphExecDestroy(s->graph.exec);
-  if (s->graph.host_views) cudaFreeHost(s->graph.host_views);
-  if (s->graph.done) cudaEventDestroy(s->graph.done);
-  if (s->graph.capture) cudaStreamDestroy(s->graph.capture);
+  for (GraphCache* G : {&s->graph, &s->graph_grad}) {
+    if (G->exec) cudaGraphExecDestroy(G->exec);
+    if (G->host_views) cudaFreeHost(G->host_views);
+    if (G->done) cudaEventDestroy(G->done);
+    if (G->capture) cudaStreamDestroy(G->capture);
+  }
   for (auto& tc : s->ev_pending)
     for (cudaEvent_t e : tc.ev) cudaEventDestroy(e);
   for (auto& ev : s->ev_free)
@@ -597,7 +670,7 @@ gs_status gs_render_pose_grad(gs_scene* s, const gs_camera* cam, const gs_pose* 
   if (!cam || !pose) return fail(GS_ERR_INVALID_ARG, "cam and pose are required");
   GS_TRY(check_grad_args(target_rgb, target_depth, depth_weight));
   GS_TRY(set_device(s));
-  GradIn g{target_rgb, target_depth, pixel_weight, depth_weight, nullptr};
+  GradIn g{&target_rgb, &target_depth, &pixel_weight, depth_weight, nullptr};
   std::vector<View> hv;
   uint64_t n_tiles;
   GS_TRY(build_views(s, 1, cam, pose, out, &g, hv, n_tiles));
@@ -619,7 +692,7 @@ gs_status gs_render_pose_grad_async(gs_scene* s, const gs_camera* cam, const gs_
   if (!cam || !pose || !result_dev) return fail(GS_ERR_INVALID_ARG, "cam, pose and result_dev are required");
   GS_TRY(check_grad_args(target_rgb, target_depth, depth_weight));
   GS_TRY(set_device(s));
-  GradIn g{target_rgb, target_depth, pixel_weight, depth_weight, result_dev};
+  GradIn g{&target_rgb, &target_depth, &pixel_weight, depth_weight, result_dev};
   std::vector<View> hv;
   uint64_t n_tiles;
   GS_TRY(build_views(s, 1, cam, pose, out, &g, hv, n_tiles));
@@ -638,58 +711,51 @@ gs_status gs_render_batch(gs_scene* s, int n_views, const gs_camera* cams, const
   uint64_t n_tiles;
   GS_TRY(build_views(s, n_views, cams, poses, outs, nullptr, hv, n_tiles));
   if (!(flags & GS_BATCH_GRAPH)) return run_sync(s, hv, n_tiles, nullptr, st);
+  std::vector<char> key;
+  append_bytes(key, cams, n_views);
+  append_bytes(key, outs, n_views);
+  return run_graph(s, s->graph, key, hv, n_tiles, nullptr, st);
+}
 
-  GraphCache& G = s->graph;
-  bool same = G.valid && G.n_views == n_views;
-  for (int v = 0; same && v < n_views; ++v)
-    same = std::memcmp(&G.cams[v], &cams[v], sizeof(gs_camera)) == 0 &&
-           std::memcmp(&G.outs[v], &outs[v], sizeof(gs_outputs)) == 0;
-  if (!same) {
-    if (G.exec) cudaGraphExecDestroy(G.exec);
-    G.exec = nullptr;
-    G.valid = false;
-    if (G.host_views) cudaFreeHost(G.host_views);
-    G.host_views = nullptr;
-    if (!G.done) GS_CUDA(cudaEventCreateWithFlags(&G.done, cudaEventDisableTiming));
-    GS_CUDA(cudaMallocHost(&G.host_views, (size_t)n_views * sizeof(View)));
-    std::memcpy(G.host_views, hv.data(), (size_t)n_views * sizeof(View));
-    // allocate everything the capture needs before capturing
-    GS_TRY(grow_tiles(s, n_tiles));
-    GS_TRY(ensure(s->views, (size_t)n_views * sizeof(View)));
-    if (s->rec_cap == 0) {
-      const uint64_t guess = std::max<uint64_t>(1u << 16, (uint64_t)s->n * n_views / 4);
-      GS_TRY(grow_records(s, guess, false));
-      GS_TRY(grow_pairs(s, guess * 8));
-    }
-    // capture on a private stream (the legacy default stream cannot be captured);
-    // the graph is then launched on the caller's stream
-    if (!G.capture) GS_CUDA(cudaStreamCreateWithFlags(&G.capture, cudaStreamNonBlocking));
-    GS_CUDA(cudaStreamSynchronize(st));
-    cudaGraph_t graph = nullptr;
-    GS_CUDA(cudaStreamBeginCapture(G.capture, cudaStreamCaptureModeThreadLocal));
-    const gs_status est = enqueue(s, hv, n_tiles, nullptr, G.capture, G.host_views);
-    const cudaError_t ce = cudaStreamEndCapture(G.capture, &graph);
-    if (est != GS_OK) {
-      if (graph) cudaGraphDestroy(graph);
-      return est;
-    }
-    if (ce != cudaSuccess) return fail(GS_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ce));
-    const cudaError_t ie = cudaGraphInstantiate(&G.exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ie != cudaSuccess) return fail(GS_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
-    G.cams.assign(cams, cams + n_views);
-    G.outs.assign(outs, outs + n_views);
-    G.n_views = n_views;
-    G.valid = true;
-  } else {
-    // the previous replay must have consumed the pinned view table
-    GS_CUDA(cudaEventSynchronize(G.done));
-    std::memcpy(G.host_views, hv.data(), (size_t)n_views * sizeof(View));
-    s->last_views = hv;
-    s->last_tiles = (uint32_t)n_tiles;
+gs_status gs_render_pose_grad_batch(gs_scene* s, int n_views, const gs_camera* cams, const gs_pose* poses,
+                                    const float* const* target_rgb, const float* const* target_depth,
+                                    const float* const* pixel_weight, float depth_weight, const gs_outputs* outs,
+                                    double* loss_out, double* grad_out, double* results_dev, unsigned flags,
+                                    void* stream) {
+  g_err.clear();
+  GS_TRY(check_scene(s));
+  if (n_views < 1 || !cams || !poses || !target_rgb || !target_depth)
+    return fail(GS_ERR_INVALID_ARG, "n_views >= 1, cams, poses, target_rgb, target_depth required");
+  if (flags & ~GS_BATCH_GRAPH) return fail(GS_ERR_INVALID_ARG, "unknown flag");
+  for (int v = 0; v < n_views; ++v) GS_TRY(check_grad_args(target_rgb[v], target_depth[v], depth_weight));
+  if ((flags & GS_BATCH_GRAPH) && !results_dev) return fail(GS_ERR_INVALID_ARG, "graph mode needs results_dev");
+  GS_TRY(set_device(s));
+  const cudaStream_t st = (cudaStream_t)stream;
+  GradIn g{target_rgb, target_depth, pixel_weight, depth_weight, results_dev};
+  std::vector<View> hv;
+  uint64_t n_tiles;
+  GS_TRY(build_views(s, n_views, cams, poses, outs, &g, hv, n_tiles));
+  if (flags & GS_BATCH_GRAPH) {
+    std::vector<char> key;
+    append_bytes(key, cams, n_views);
+    if (outs) append_bytes(key, outs, n_views);
+    append_bytes(key, target_rgb, n_views);
+    append_bytes(key, target_depth, n_views);
+    if (pixel_weight) append_bytes(key, pixel_weight, n_views);
+    append_bytes(key, &depth_weight, 1);
+    append_bytes(key, &results_dev, 1);
+    return run_graph(s, s->graph_grad, key, hv, n_tiles, &g, st);
   }
-  GS_CUDA(cudaGraphLaunch(G.exec, st));
-  GS_CUDA(cudaEventRecord(G.done, st));
+  GS_TRY(run_sync(s, hv, n_tiles, &g, st));
+  double* res = results_dev ? results_dev : dp<double>(s->result);
+  std::vector<double> host((size_t)n_views * kResultStride);
+  GS_CUDA(cudaMemcpyAsync(host.data(), res, host.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  GS_CUDA(cudaStreamSynchronize(st));
+  for (int v = 0; v < n_views; ++v) {
+    if (loss_out) loss_out[v] = host[(size_t)v * kResultStride];
+    if (grad_out)
+      for (int k = 0; k < 6; ++k) grad_out[6 * v + k] = host[(size_t)v * kResultStride + 1 + k];
+  }
   return GS_OK;
 }
 

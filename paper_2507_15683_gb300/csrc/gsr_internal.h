@@ -100,14 +100,17 @@ cudaError_t launch_pack_scene(const float* means, const float* scales, const flo
                               const float* opacities, const float* sh, int sh_k3, const uint16_t* feats,
                               int feat_dim, int n, int nsh4, float4* pos, float4* cov, float4* sh_out,
                               uint4* feat_out, cudaStream_t st);
-cudaError_t launch_project(const SceneDev& sc, const View* views, int n_views, const Work& w, bool grad,
-                           int grid, cudaStream_t st);
+cudaError_t launch_project(const SceneDev& sc, const View* views, int n_views, const Work& w, int grid,
+                           cudaStream_t st);
+cudaError_t launch_shade(const SceneDev& sc, const View* views, const Work& w, bool grad, int grid,
+                         cudaStream_t st);
 cudaError_t launch_scan_tiles(const Work& w, cudaStream_t st);
 cudaError_t launch_scatter(const View* views, const Work& w, int grid, cudaStream_t st);
 cudaError_t launch_composite(const SceneDev& sc, const View* views, int n_views, const Work& w, int grid,
                              cudaStream_t st);
 cudaError_t launch_backward(const View* views, int n_views, const Work& w, double* result, int grid,
                             cudaStream_t st);
+cudaError_t launch_reduce_views(const View* views, int n_views, const Work& w, double* result, cudaStream_t st);
 
 // occupancy-derived persistent grid sizes (per SM)
 int composite_blocks_per_sm(int feat_dim);

@@ -198,7 +198,8 @@ extern "C" gs_status gs_render_noalloc(const gs_scene_desc* d, const gs_camera* 
   NA_CUDA(cudaMemcpyAsync(dview, &V, sizeof(View), cudaMemcpyHostToDevice, st));
   NA_CUDA(launch_pack_scene(d->means, d->scales, d->quats, d->opacities, d->sh, K3, d->feats_bf16, d->feat_dim, n,
                             nsh4, pos, cov, sh, d->feat_dim ? feat : nullptr, st));
-  NA_CUDA(launch_project(sc, dview, 1, w, false, sm_count * 8, st));
+  NA_CUDA(launch_project(sc, dview, 1, w, sm_count * 8, st));
+  NA_CUDA(launch_shade(sc, dview, w, false, sm_count * 8, st));
   NA_CUDA(launch_scan_tiles(w, st));
   NA_CUDA(launch_scatter(dview, w, sm_count * 8, st));
   NA_CUDA(launch_composite(sc, dview, 1, w, sm_count * composite_blocks_per_sm(d->feat_dim), st));

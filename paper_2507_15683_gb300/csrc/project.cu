@@ -216,13 +216,18 @@ __device__ __forceinline__ void eval_sh_deg(int deg, const float4* shp, float x,
 }
 
 // ---------------------------------------------------------------------------
-// Projection: one thread per Gaussian, looping over the views of the call.
+// Projection, discrete pass: one thread per Gaussian, looping over the views
+// of the call. Decides visibility, the tile rectangle and the sort key, counts
+// pairs per tile and appends a record; the continuous quantities are filled in
+// by k_shade over the compact records (full warps instead of ~1 visible lane
+// in 6). Record fields written here: rec_m = (rect, view, depth bits),
+// rec_a = (binary32 covariance a, b, c, -), rec_b.w = Gaussian index.
 // ---------------------------------------------------------------------------
-template <bool GRAD>
 __global__ void __launch_bounds__(256) k_project(SceneDev sc, const View* __restrict__ views, int n_views, Work w) {
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   const int stride = gridDim.x * blockDim.x;
+  const unsigned region = blockIdx.x % kRecRegions;
   for (int base = blockIdx.x * blockDim.x; base < sc.n; base += stride) {  // warp-uniform loop
     const int i = base + threadIdx.x;
     const bool valid = i < sc.n;
@@ -232,17 +237,16 @@ __global__ void __launch_bounds__(256) k_project(SceneDev sc, const View* __rest
     for (int vi = 0; vi < n_views; ++vi) {
       const View& V = views[vi];
       bool vis = false;
-      float u = 0.f, v = 0.f, pz = 0.f, ca = 0.f, cb = 0.f, cc = 0.f, ix = 0.f, iy = 0.f, px = 0.f, py = 0.f;
+      float pz = 0.f, ca = 0.f, cb = 0.f, cc = 0.f;
       int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
       if (valid) {
-        px = add(add(add(mul(V.R[0], p4.x), mul(V.R[1], p4.y)), mul(V.R[2], p4.z)), V.t[0]);
-        py = add(add(add(mul(V.R[3], p4.x), mul(V.R[4], p4.y)), mul(V.R[5], p4.z)), V.t[1]);
+        const float px = add(add(add(mul(V.R[0], p4.x), mul(V.R[1], p4.y)), mul(V.R[2], p4.z)), V.t[0]);
+        const float py = add(add(add(mul(V.R[3], p4.x), mul(V.R[4], p4.y)), mul(V.R[5], p4.z)), V.t[1]);
         pz = add(add(add(mul(V.R[6], p4.x), mul(V.R[7], p4.y)), mul(V.R[8], p4.z)), V.t[2]);
         if (pz >= 0.2f) {
-          ix = dvd(px, pz);
-          iy = dvd(py, pz);
-          u = add(mul(V.fx, ix), V.cx);
-          v = add(mul(V.fy, iy), V.cy);
+          const float ix = dvd(px, pz), iy = dvd(py, pz);
+          const float u = add(mul(V.fx, ix), V.cx);
+          const float v = add(mul(V.fy, iy), V.cy);
           // Conservative reach: radius <= 3 sqrt(s_max^2 |J|_F^2 + 0.3 + sqrt(0.1)) + 1,
           // with margins for rounding; a Gaussian that cannot reach the image has an
           // empty rectangle under the exact rule, so skipping it changes nothing.
@@ -281,8 +285,9 @@ __global__ void __launch_bounds__(256) k_project(SceneDev sc, const View* __rest
               const float lam = add(mid, sqr(fmaxf(0.1f, disc)));
               const float r = ceilf(mul(3.0f, sqr(lam)));
               if (r > 0.0f) {
-                float fx0 = floorf(dvd(sub(u, r), 16.0f)), fx1 = floorf(dvd(add(u, r), 16.0f));
-                float fy0 = floorf(dvd(sub(v, r), 16.0f)), fy1 = floorf(dvd(add(v, r), 16.0f));
+                // division by 16 is exact: multiply by 1/16
+                float fx0 = floorf(mul(sub(u, r), 0.0625f)), fx1 = floorf(mul(add(u, r), 0.0625f));
+                float fy0 = floorf(mul(sub(v, r), 0.0625f)), fy1 = floorf(mul(add(v, r), 0.0625f));
                 fx0 = fmaxf(fx0, 0.0f);
                 fy0 = fmaxf(fy0, 0.0f);
                 fx1 = fminf(fx1, (float)(V.tiles_x - 1));
@@ -302,7 +307,6 @@ __global__ void __launch_bounds__(256) k_project(SceneDev sc, const View* __rest
       const unsigned vmask = __ballot_sync(0xffffffffu, vis);
       if (vmask == 0u) continue;
       // warp-aggregated append into this block's record segment
-      const unsigned region = blockIdx.x % kRecRegions;
       unsigned slot0 = 0;
       const int leader = __ffs(vmask) - 1;
       if (lane == leader) slot0 = atomicAdd(&w.ctr->rec_region[region], (unsigned)__popc(vmask));
@@ -314,152 +318,177 @@ __global__ void __launch_bounds__(256) k_project(SceneDev sc, const View* __rest
         continue;
       }
       const unsigned slot = region * w.rec_seg + local;
-      // ---- continuous layer ----
-      // conic from the binary32 covariance; determinant with one compensated step
-      const float bb = cb * cb;
-      const float e = __fmaf_rn(-cb, cb, bb);
-      const float f = __fmaf_rn(ca, cc, -bb);
-      const float detc = f + e;
-      const float inv = 1.0f / detc;
-      const float A = cc * inv, B = -cb * inv, C = ca * inv;
-      // colour from SH at dir = normalize(mean - camera centre)
-      const float dxw = p4.x - V.cw[0], dyw = p4.y - V.cw[1], dzw = p4.z - V.cw[2];
-      const float dn = sqrtf(dxw * dxw + dyw * dyw + dzw * dzw);
-      const float rn = 1.0f / dn;
-      const float dirx = dxw * rn, diry = dyw * rn, dirz = dzw * rn;
-      float rgb[3], G[3][3];
-      eval_sh_deg<GRAD>(sc.sh_degree, sc.sh + (size_t)i * sc.nsh4, dirx, diry, dirz, rgb, G);
-      bool clampc[3];
-#pragma unroll
-      for (int ch = 0; ch < 3; ++ch) {
-        clampc[ch] = rgb[ch] < 0.0f;
-        rgb[ch] = fmaxf(rgb[ch], 0.0f);
-      }
-      // blending centre in float-float; high parts in rec_a, low parts as half2
-      const ff fpx = ff_row(V.R, V.Rl, V.t[0], V.tl[0], p4.x, p4.y, p4.z);
-      const ff fpy = ff_row(V.R + 3, V.Rl + 3, V.t[1], V.tl[1], p4.x, p4.y, p4.z);
-      const ff fpz = ff_row(V.R + 6, V.Rl + 6, V.t[2], V.tl[2], p4.x, p4.y, p4.z);
-      const ff fu = ff_project(fpx, fpz, V.fx, V.cx);
-      const ff fv = ff_project(fpy, fpz, V.fy, V.cy);
-      const __half2 lo2 = __floats2half2_rn(fu.lo, fv.lo);
-      w.rec_a[slot] = make_float4(fu.hi, fv.hi, A, B);
-      w.rec_b[slot] = make_float4(C, c1.z, pz, __int_as_float(i));
-      w.rec_c[slot] = make_float4(rgb[0], rgb[1], rgb[2], *reinterpret_cast<const float*>(&lo2));
+      w.rec_a[slot] = make_float4(ca, cb, cc, 0.0f);
+      w.rec_b[slot] = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(i));
       w.rec_m[slot] = make_uint4((unsigned)x0 | ((unsigned)x1 << 16), (unsigned)y0 | ((unsigned)y1 << 16),
                                  (unsigned)vi, __float_as_uint(pz));
       for (int ty = y0; ty <= y1; ++ty)
         for (int tx = x0; tx <= x1; ++tx) atomicAdd(&w.tile_count[V.tile_base + ty * V.tiles_x + tx], 1u);
+    }
+  }
+}
 
-      if (GRAD) {
-        // Pose Jacobian of (u, v, A, B, C, z) w.r.t. xi = (rho, phi) and of (r, g, b)
-        // w.r.t. rho, by forward differentiation along the six tangent directions:
-        // d p = rho + phi x p; d Sigma_cam = [phi]x Sigma_cam - Sigma_cam [phi]x;
-        // d (mean - camera centre) = R^T rho.
-        const float* R = V.R;
-        const float Sw[3][3] = {{c0.x, c0.y, c0.z}, {c0.y, c0.w, c1.x}, {c0.z, c1.x, c1.y}};
-        float Q[3][3], Sc[3][3];
+// ---------------------------------------------------------------------------
+// Shading pass over the compact records: conic, SH colour, float-float
+// blending centre and, for the pose gradient, the per-record pose Jacobian.
+// ---------------------------------------------------------------------------
+template <bool GRAD>
+__global__ void __launch_bounds__(256) k_shade(SceneDev sc, const View* __restrict__ views, Work w) {
+  if (w.ctr->overflow) return;
+  for (uint32_t slot = blockIdx.x * blockDim.x + threadIdx.x; slot < w.rec_cap; slot += gridDim.x * blockDim.x) {
+    const uint32_t reg = slot / w.rec_seg, loc = slot - reg * w.rec_seg;
+    if (loc >= min(w.ctr->rec_region[reg], w.rec_seg)) continue;
+    const float4 ra = w.rec_a[slot];
+    const int i = __float_as_int(w.rec_b[slot].w);
+    const uint4 m = w.rec_m[slot];
+    const View& V = views[m.z];
+    const float ca = ra.x, cb = ra.y, cc = ra.z;
+    const float4 p4 = __ldg(sc.pos + i);
+    const float4 c0 = __ldg(sc.cov + 2 * i);
+    const float4 c1 = __ldg(sc.cov + 2 * i + 1);
+    const float pz = __uint_as_float(m.w);
+    // conic from the binary32 covariance; determinant with one compensated step
+    const float bb = cb * cb;
+    const float e = __fmaf_rn(-cb, cb, bb);
+    const float f = __fmaf_rn(ca, cc, -bb);
+    const float detc = f + e;
+    const float inv = 1.0f / detc;
+    const float A = cc * inv, B = -cb * inv, C = ca * inv;
+    // colour from SH at dir = normalize(mean - camera centre)
+    const float dxw = p4.x - V.cw[0], dyw = p4.y - V.cw[1], dzw = p4.z - V.cw[2];
+    const float dn = sqrtf(dxw * dxw + dyw * dyw + dzw * dzw);
+    const float rn = 1.0f / dn;
+    const float dirx = dxw * rn, diry = dyw * rn, dirz = dzw * rn;
+    float rgb[3], G[3][3];
+    eval_sh_deg<GRAD>(sc.sh_degree, sc.sh + (size_t)i * sc.nsh4, dirx, diry, dirz, rgb, G);
+    bool clampc[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
+    for (int ch = 0; ch < 3; ++ch) {
+      clampc[ch] = rgb[ch] < 0.0f;
+      rgb[ch] = fmaxf(rgb[ch], 0.0f);
+    }
+    // blending centre in float-float; high parts in rec_a, low parts as half2
+    const ff fpx = ff_row(V.R, V.Rl, V.t[0], V.tl[0], p4.x, p4.y, p4.z);
+    const ff fpy = ff_row(V.R + 3, V.Rl + 3, V.t[1], V.tl[1], p4.x, p4.y, p4.z);
+    const ff fpz = ff_row(V.R + 6, V.Rl + 6, V.t[2], V.tl[2], p4.x, p4.y, p4.z);
+    const ff fu = ff_project(fpx, fpz, V.fx, V.cx);
+    const ff fv = ff_project(fpy, fpz, V.fy, V.cy);
+    const __half2 lo2 = __floats2half2_rn(fu.lo, fv.lo);
+    w.rec_a[slot] = make_float4(fu.hi, fv.hi, A, B);
+    w.rec_b[slot] = make_float4(C, c1.z, pz, __int_as_float(i));
+    w.rec_c[slot] = make_float4(rgb[0], rgb[1], rgb[2], *reinterpret_cast<const float*>(&lo2));
+
+    if (GRAD) {
+      // Pose Jacobian of (u, v, A, B, C, z) w.r.t. xi = (rho, phi) and of (r, g, b)
+      // w.r.t. rho, by forward differentiation along the six tangent directions:
+      // d p = rho + phi x p; d Sigma_cam = [phi]x Sigma_cam - Sigma_cam [phi]x;
+      // d (mean - camera centre) = R^T rho.
+      const float* R = V.R;
+      const float px = fpx.hi, py = fpy.hi;
+      const float ix = px / pz, iy = py / pz;
+      const float Sw[3][3] = {{c0.x, c0.y, c0.z}, {c0.y, c0.w, c1.x}, {c0.z, c1.x, c1.y}};
+      float Q[3][3], Sc[3][3];
 #pragma unroll
-          for (int b = 0; b < 3; ++b) Q[a][b] = R[3 * a] * Sw[0][b] + R[3 * a + 1] * Sw[1][b] + R[3 * a + 2] * Sw[2][b];
+      for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) Q[a][b] = R[3 * a] * Sw[0][b] + R[3 * a + 1] * Sw[1][b] + R[3 * a + 2] * Sw[2][b];
 #pragma unroll
-          for (int b = 0; b < 3; ++b) Sc[a][b] = Q[a][0] * R[3 * b] + Q[a][1] * R[3 * b + 1] + Q[a][2] * R[3 * b + 2];
-        const bool clx = (ix < -V.limx) || (ix > V.limx);
-        const bool cly = (iy < -V.limy) || (iy > V.limy);
-        const float Lx = ix < 0.0f ? -V.limx : V.limx, Ly = iy < 0.0f ? -V.limy : V.limy;
-        const float zi = 1.0f / pz;
-        const float xh = clx ? Lx * pz : px, yh = cly ? Ly * pz : py;
-        const float j00 = V.fx * zi, j02 = -V.fx * xh * zi * zi;
-        const float j11 = V.fy * zi, j12 = -V.fy * yh * zi * zi;
-        float K[2][3];
+      for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          K[0][k] = j00 * Sc[0][k] + j02 * Sc[2][k];
-          K[1][k] = j11 * Sc[1][k] + j12 * Sc[2][k];
-        }
-        const float di = 1.0f / detc;
-        float jac[45];
-        const float pc[3] = {px, py, pz};
+        for (int b = 0; b < 3; ++b) Sc[a][b] = Q[a][0] * R[3 * b] + Q[a][1] * R[3 * b + 1] + Q[a][2] * R[3 * b + 2];
+      const bool clx = (ix < -V.limx) || (ix > V.limx);
+      const bool cly = (iy < -V.limy) || (iy > V.limy);
+      const float Lx = ix < 0.0f ? -V.limx : V.limx, Ly = iy < 0.0f ? -V.limy : V.limy;
+      const float zi = 1.0f / pz;
+      const float xh = clx ? Lx * pz : px, yh = cly ? Ly * pz : py;
+      const float j00 = V.fx * zi, j02 = -V.fx * xh * zi * zi;
+      const float j11 = V.fy * zi, j12 = -V.fy * yh * zi * zi;
+      float K[2][3];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
-          float dp[3];
-          if (k < 3) {
-            dp[0] = (k == 0) ? 1.f : 0.f;
-            dp[1] = (k == 1) ? 1.f : 0.f;
-            dp[2] = (k == 2) ? 1.f : 0.f;
-          } else {
-            const int e3 = k - 3;  // e x p
-            dp[0] = (e3 == 1) ? pc[2] : (e3 == 2) ? -pc[1] : 0.f;
-            dp[1] = (e3 == 0) ? -pc[2] : (e3 == 2) ? pc[0] : 0.f;
-            dp[2] = (e3 == 0) ? pc[1] : (e3 == 1) ? -pc[0] : 0.f;
-          }
-          const float du = V.fx * (dp[0] - ix * dp[2]) * zi;
-          const float dv = V.fy * (dp[1] - iy * dp[2]) * zi;
-          const float dxh = clx ? Lx * dp[2] : dp[0];
-          const float dyh = cly ? Ly * dp[2] : dp[1];
-          const float dj00 = -j00 * dp[2] * zi;
-          const float dj02 = -V.fx * (dxh - 2.0f * xh * dp[2] * zi) * zi * zi;
-          const float dj11 = -j11 * dp[2] * zi;
-          const float dj12 = -V.fy * (dyh - 2.0f * yh * dp[2] * zi) * zi * zi;
-          // S = dJ K^T
-          const float S00 = dj00 * K[0][0] + dj02 * K[0][2];
-          const float S01 = dj00 * K[1][0] + dj02 * K[1][2];
-          const float S10 = dj11 * K[0][1] + dj12 * K[0][2];
-          const float S11 = dj11 * K[1][1] + dj12 * K[1][2];
-          float dm00 = 2.0f * S00, dm01 = S01 + S10, dm11 = 2.0f * S11;
-          if (k >= 3) {
-            // D = X + X^T with X = [e]x Sc
-            const int e3 = k - 3;
-            float X[3][3];
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {
-              if (e3 == 0) { X[0][b] = 0.f; X[1][b] = -Sc[2][b]; X[2][b] = Sc[1][b]; }
-              else if (e3 == 1) { X[0][b] = Sc[2][b]; X[1][b] = 0.f; X[2][b] = -Sc[0][b]; }
-              else { X[0][b] = -Sc[1][b]; X[1][b] = Sc[0][b]; X[2][b] = 0.f; }
-            }
-            float D[3][3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-#pragma unroll
-              for (int b = 0; b < 3; ++b) D[a][b] = X[a][b] + X[b][a];
-            float JD[2][3];
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {
-              JD[0][b] = j00 * D[0][b] + j02 * D[2][b];
-              JD[1][b] = j11 * D[1][b] + j12 * D[2][b];
-            }
-            dm00 += JD[0][0] * j00 + JD[0][2] * j02;
-            dm01 += JD[0][1] * j11 + JD[0][2] * j12;
-            dm11 += JD[1][1] * j11 + JD[1][2] * j12;
-          }
-          const float ddet = dm00 * cc + ca * dm11 - 2.0f * cb * dm01;
-          const float dA = (dm11 - cc * ddet * di) * di;
-          const float dB = -(dm01 - cb * ddet * di) * di;
-          const float dC = (dm00 - ca * ddet * di) * di;
-          jac[0 * 6 + k] = du;
-          jac[1 * 6 + k] = dv;
-          jac[2 * 6 + k] = dA;
-          jac[3 * 6 + k] = dB;
-          jac[4 * 6 + k] = dC;
-          jac[5 * 6 + k] = dp[2];
-        }
-        // colour rows (rho only): d rgb_ch / d rho_k = G_ch . (I - dir dir^T) R^T e_k / |d|
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-          const float gd = G[ch][0] * dirx + G[ch][1] * diry + G[ch][2] * dirz;
-          const float gp0 = (G[ch][0] - gd * dirx) * rn, gp1 = (G[ch][1] - gd * diry) * rn,
-                      gp2 = (G[ch][2] - gd * dirz) * rn;
-#pragma unroll
-          for (int k = 0; k < 3; ++k)
-            jac[36 + 3 * ch + k] = clampc[ch] ? 0.0f : gp0 * R[3 * k] + gp1 * R[3 * k + 1] + gp2 * R[3 * k + 2];
-        }
-        float4* jo = reinterpret_cast<float4*>(w.rec_j + (size_t)slot * kJacStride);
-#pragma unroll
-        for (int q = 0; q < 11; ++q) jo[q] = make_float4(jac[4 * q], jac[4 * q + 1], jac[4 * q + 2], jac[4 * q + 3]);
-        jo[11] = make_float4(jac[44], 0.f, 0.f, 0.f);
+      for (int k = 0; k < 3; ++k) {
+        K[0][k] = j00 * Sc[0][k] + j02 * Sc[2][k];
+        K[1][k] = j11 * Sc[1][k] + j12 * Sc[2][k];
       }
+      const float di = 1.0f / detc;
+      float jac[45];
+      const float pc[3] = {px, py, pz};
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        float dp[3];
+        if (k < 3) {
+          dp[0] = (k == 0) ? 1.f : 0.f;
+          dp[1] = (k == 1) ? 1.f : 0.f;
+          dp[2] = (k == 2) ? 1.f : 0.f;
+        } else {
+          const int e3 = k - 3;  // e x p
+          dp[0] = (e3 == 1) ? pc[2] : (e3 == 2) ? -pc[1] : 0.f;
+          dp[1] = (e3 == 0) ? -pc[2] : (e3 == 2) ? pc[0] : 0.f;
+          dp[2] = (e3 == 0) ? pc[1] : (e3 == 1) ? -pc[0] : 0.f;
+        }
+        const float du = V.fx * (dp[0] - ix * dp[2]) * zi;
+        const float dv = V.fy * (dp[1] - iy * dp[2]) * zi;
+        const float dxh = clx ? Lx * dp[2] : dp[0];
+        const float dyh = cly ? Ly * dp[2] : dp[1];
+        const float dj00 = -j00 * dp[2] * zi;
+        const float dj02 = -V.fx * (dxh - 2.0f * xh * dp[2] * zi) * zi * zi;
+        const float dj11 = -j11 * dp[2] * zi;
+        const float dj12 = -V.fy * (dyh - 2.0f * yh * dp[2] * zi) * zi * zi;
+        // S = dJ K^T
+        const float S00 = dj00 * K[0][0] + dj02 * K[0][2];
+        const float S01 = dj00 * K[1][0] + dj02 * K[1][2];
+        const float S10 = dj11 * K[0][1] + dj12 * K[0][2];
+        const float S11 = dj11 * K[1][1] + dj12 * K[1][2];
+        float dm00 = 2.0f * S00, dm01 = S01 + S10, dm11 = 2.0f * S11;
+        if (k >= 3) {
+          // D = X + X^T with X = [e]x Sc
+          const int e3 = k - 3;
+          float X[3][3];
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            if (e3 == 0) { X[0][b] = 0.f; X[1][b] = -Sc[2][b]; X[2][b] = Sc[1][b]; }
+            else if (e3 == 1) { X[0][b] = Sc[2][b]; X[1][b] = 0.f; X[2][b] = -Sc[0][b]; }
+            else { X[0][b] = -Sc[1][b]; X[1][b] = Sc[0][b]; X[2][b] = 0.f; }
+          }
+          float D[3][3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) D[a][b] = X[a][b] + X[b][a];
+          float JD[2][3];
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            JD[0][b] = j00 * D[0][b] + j02 * D[2][b];
+            JD[1][b] = j11 * D[1][b] + j12 * D[2][b];
+          }
+          dm00 += JD[0][0] * j00 + JD[0][2] * j02;
+          dm01 += JD[0][1] * j11 + JD[0][2] * j12;
+          dm11 += JD[1][1] * j11 + JD[1][2] * j12;
+        }
+        const float ddet = dm00 * cc + ca * dm11 - 2.0f * cb * dm01;
+        const float dA = (dm11 - cc * ddet * di) * di;
+        const float dB = -(dm01 - cb * ddet * di) * di;
+        const float dC = (dm00 - ca * ddet * di) * di;
+        jac[0 * 6 + k] = du;
+        jac[1 * 6 + k] = dv;
+        jac[2 * 6 + k] = dA;
+        jac[3 * 6 + k] = dB;
+        jac[4 * 6 + k] = dC;
+        jac[5 * 6 + k] = dp[2];
+      }
+      // colour rows (rho only): d rgb_ch / d rho_k = G_ch . (I - dir dir^T) R^T e_k / |d|
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        const float gd = G[ch][0] * dirx + G[ch][1] * diry + G[ch][2] * dirz;
+        const float gp0 = (G[ch][0] - gd * dirx) * rn, gp1 = (G[ch][1] - gd * diry) * rn,
+                    gp2 = (G[ch][2] - gd * dirz) * rn;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          jac[36 + 3 * ch + k] = clampc[ch] ? 0.0f : gp0 * R[3 * k] + gp1 * R[3 * k + 1] + gp2 * R[3 * k + 2];
+      }
+      float4* jo = reinterpret_cast<float4*>(w.rec_j + (size_t)slot * kJacStride);
+#pragma unroll
+      for (int q = 0; q < 11; ++q) jo[q] = make_float4(jac[4 * q], jac[4 * q + 1], jac[4 * q + 2], jac[4 * q + 3]);
+      jo[11] = make_float4(jac[44], 0.f, 0.f, 0.f);
     }
   }
 }
@@ -477,15 +506,24 @@ cudaError_t launch_pack_scene(const float* means, const float* scales, const flo
   return cudaGetLastError();
 }
 
-cudaError_t launch_project(const SceneDev& sc, const View* views, int n_views, const Work& w, bool grad, int grid,
+cudaError_t launch_project(const SceneDev& sc, const View* views, int n_views, const Work& w, int grid,
                            cudaStream_t st) {
   if (sc.n <= 0 || n_views <= 0) return cudaSuccess;
   const int need = (sc.n + 255) / 256;
   const int g = need < grid ? need : grid;
+  k_project<<<g, 256, 0, st>>>(sc, views, n_views, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shade(const SceneDev& sc, const View* views, const Work& w, bool grad, int grid,
+                         cudaStream_t st) {
+  if (sc.n <= 0 || w.rec_cap == 0) return cudaSuccess;
+  const int need = (int)((w.rec_cap + 255) / 256);
+  const int g = need < grid ? need : grid;
   if (grad)
-    k_project<true><<<g, 256, 0, st>>>(sc, views, n_views, w);
+    k_shade<true><<<g, 256, 0, st>>>(sc, views, w);
   else
-    k_project<false><<<g, 256, 0, st>>>(sc, views, n_views, w);
+    k_shade<false><<<g, 256, 0, st>>>(sc, views, w);
   return cudaGetLastError();
 }
 

@@ -201,24 +201,41 @@ __device__ __forceinline__ void warp_block(int tid, int& lx, int& ly, int& bx, i
   ly = by + (lane >> 3);
 }
 
-// Conservative footprint of alpha >= 1/255 in tile-local pixel coordinates:
-// the test needs o exp(power) >= 1/255, i.e. d^T Q d <= 2 ln(255 o), an ellipse
-// with half extents sqrt(2 ln(255 o) S_xx), sqrt(2 ln(255 o) S_yy), S = Q^-1.
-// Margins (1 % on the log, 0.1 % + 0.01 px on the extents) cover the fp32
-// evaluation of the per-pixel test, so a warp whose block misses the box would
-// have skipped the Gaussian at every pixel: skipping it changes nothing.
-__device__ __forceinline__ float4 alpha_box(float4 a, float C, float o) {
+// Threshold of the alpha-floor test as an ellipse: o exp(power) >= 1/255 with
+// power = -q/2, q(d) = A dx^2 + 2 B dx dy + C dy^2, needs q <= 2 ln(255 o).
+// Margins (1 % + 0.01 on the log, 0.1 % + 1e-3 on the threshold) cover the
+// fp32 evaluation of the per-pixel test; -1 marks a Gaussian whose opacity
+// cannot reach the floor anywhere.
+__device__ __forceinline__ float floor_threshold(float o) {
   const float Lp = __logf(255.0f * o) * 1.01f + 0.01f;
-  if (!(Lp > 0.0f)) return make_float4(1e30f, -1e30f, 1e30f, -1e30f);  // cannot reach the floor
-  const float detq = a.z * C - a.w * a.w;
-  if (!(detq > 0.0f)) return make_float4(-1e30f, 1e30f, -1e30f, 1e30f);  // degenerate: always test
-  const float k = 2.0f * Lp / detq;
-  const float ex = sqrtf(k * C) * 1.001f + 0.01f, ey = sqrtf(k * a.z) * 1.001f + 0.01f;
-  return make_float4(a.x - ex, a.x + ex, a.y - ey, a.y + ey);
+  return Lp > 0.0f ? 2.0f * Lp * 1.001f + 1e-3f : -1.0f;
 }
 
-__device__ __forceinline__ bool box_hits(float4 b, float wx0, float wx1, float wy0, float wy1) {
-  return (b.y >= wx0) & (b.x <= wx1) & (b.w >= wy0) & (b.z <= wy1);
+// Can a staged Gaussian (centre a.xy in tile-local pixels, conic A = a.z,
+// B = a.w, C) reach the floor at any pixel centre of the warp's block
+// [x0, x1] x [y0, y1]? Exact minimum of the positive-definite quadratic over
+// the block (the centre if inside, else the best point of one of the four
+// edges). If not, every pixel of the warp would skip the Gaussian, so the warp
+// skips it without changing any result.
+__device__ __forceinline__ bool ellipse_hits(float4 a, float C, float thr, float x0, float x1, float y0, float y1) {
+  if (!(thr > 0.0f)) return false;
+  const float A = a.z, B = a.w;
+  if (!(A > 0.0f) || !(C > 0.0f)) return true;
+  const float dxl = x0 - a.x, dxh = x1 - a.x, dyl = y0 - a.y, dyh = y1 - a.y;
+  if (dxl <= 0.0f && dxh >= 0.0f && dyl <= 0.0f && dyh >= 0.0f) return true;
+  const float iA = 1.0f / A, iC = 1.0f / C;
+  float best = 3.0e38f;
+  {
+    const float dy0 = fminf(fmaxf(-B * dxl * iC, dyl), dyh), dy1 = fminf(fmaxf(-B * dxh * iC, dyl), dyh);
+    best = fminf(best, A * dxl * dxl + 2.0f * B * dxl * dy0 + C * dy0 * dy0);
+    best = fminf(best, A * dxh * dxh + 2.0f * B * dxh * dy1 + C * dy1 * dy1);
+  }
+  {
+    const float dx0 = fminf(fmaxf(-B * dyl * iA, dxl), dxh), dx1 = fminf(fmaxf(-B * dyh * iA, dxl), dxh);
+    best = fminf(best, A * dx0 * dx0 + 2.0f * B * dx0 * dyl + C * dyl * dyl);
+    best = fminf(best, A * dx1 * dx1 + 2.0f * B * dx1 * dyh + C * dyh * dyh);
+  }
+  return best <= thr;
 }
 
 template <int FEAT>
@@ -231,7 +248,7 @@ __global__ void __launch_bounds__(kTileThreads) k_composite(SceneDev sc, const V
   float4* sa = reinterpret_cast<float4*>(smem_raw + kSmStage);
   float4* sb = sa + kBatchF;
   float4* scol = sb + kBatchF;
-  float4* sbox = scol + kBatchF;
+  float* sthr = reinterpret_cast<float*>(scol + kBatchF);
   uint4* sf = reinterpret_cast<uint4*>(smem_raw + kSmFeat);  // FEAT: kBatchF x 4 (aliases hist)
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_tmp[kWarps];
@@ -295,7 +312,7 @@ __global__ void __launch_bounds__(kTileThreads) k_composite(SceneDev sc, const V
         sa[tid] = a;
         sb[tid] = bb;
         scol[tid] = cc;
-        sbox[tid] = alpha_box(a, bb.x, bb.y);
+        sthr[tid] = floor_threshold(bb.y);
         if (FEAT) {
           const uint4* fp = sc.feat + (size_t)__float_as_int(bb.w) * 4;
 #pragma unroll
@@ -306,7 +323,7 @@ __global__ void __launch_bounds__(kTileThreads) k_composite(SceneDev sc, const V
       bool wdone = __all_sync(0xffffffffu, done);
       for (int c0 = 0; c0 < bn && !wdone; c0 += 32) {
         const int jj = c0 + lane;
-        const bool hit = jj < bn && box_hits(sbox[jj], wx0, wx1, wy0, wy1);
+        const bool hit = jj < bn && ellipse_hits(sa[jj], sb[jj].x, sthr[jj], wx0, wx1, wy0, wy1);
         uint32_t m = __ballot_sync(0xffffffffu, hit);
         while (m) {
           const int j = c0 + __ffs(m) - 1;
@@ -379,7 +396,8 @@ __global__ void __launch_bounds__(kTileThreads) k_composite(SceneDev sc, const V
 // the warp blended.
 // ---------------------------------------------------------------------------
 struct BwdSmem {
-  float4 sa[kBatchB], sb[kBatchB], sc[kBatchB], sbox[kBatchB];
+  float4 sa[kBatchB], sb[kBatchB], sc[kBatchB];
+  float sthr[kBatchB];
   float4 sj[kBatchB * (kJacStride / 4)];
   double red[kWarps][8];
 };
@@ -453,7 +471,7 @@ __global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restric
         S.sa[tid] = a;
         S.sb[tid] = bb;
         S.sc[tid] = cc;
-        S.sbox[tid] = alpha_box(a, bb.x, bb.y);
+        S.sthr[tid] = floor_threshold(bb.y);
       }
       for (int q = tid; q < bn * (kJacStride / 4); q += kTileThreads) {
         const int jj = q / (kJacStride / 4), k = q % (kJacStride / 4);
@@ -464,7 +482,8 @@ __global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restric
       if ((uint32_t)bstart >= wm) continue;  // no pixel of this warp blended this far
       for (int c0 = ((bn - 1) >> 5) << 5; c0 >= 0; c0 -= 32) {
         const int jj = c0 + lane;
-        const bool hit = jj < bn && (uint32_t)(bstart + jj) < wm && box_hits(S.sbox[jj], wx0, wx1, wy0, wy1);
+        const bool hit = jj < bn && (uint32_t)(bstart + jj) < wm &&
+                         ellipse_hits(S.sa[jj], S.sb[jj].x, S.sthr[jj], wx0, wx1, wy0, wy1);
         uint32_t m = __ballot_sync(0xffffffffu, hit);
         while (m) {
           const int bit = 31 - __clz(m);
@@ -536,6 +555,7 @@ __global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restric
     }
     __syncthreads();
   }
+  if (!result) return;  // several views: k_reduce_views sums per view
   // The last CTA to finish sums the per-tile partials in a fixed order
   // (deterministic): thread t takes tiles t, t + 256, ..., then a fixed tree.
   __shared__ bool s_last;
@@ -565,6 +585,38 @@ __global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restric
 #pragma unroll
     for (int k = 0; k < kWarps; ++k) s += S.red[k][tid];
     result[tid] = s;
+  }
+}
+
+// Per-view fp64 sums of the per-tile partials, one CTA per view, in the same
+// fixed order as the single-view reduction (so one view of a batch gives
+// bit-identical results to a single-view call). result: 8 doubles per view.
+__global__ void __launch_bounds__(kTileThreads) k_reduce_views(const View* __restrict__ views, Work w,
+                                                               double* __restrict__ result) {
+  __shared__ double red[kWarps][8];
+  const View& V = views[blockIdx.x];
+  const uint32_t nt = (uint32_t)V.tiles_x * (uint32_t)V.tiles_y;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  double v[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (uint32_t t = tid; t < nt; t += kTileThreads) {
+#pragma unroll
+    for (int k = 0; k < 7; ++k) v[k] += w.partials[(size_t)(V.tile_base + t) * kPartialStride + k];
+  }
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 7; ++k) red[wid][k] = v[k];
+  }
+  __syncthreads();
+  if (tid < 7) {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < kWarps; ++k) s += red[k][tid];
+    result[(size_t)blockIdx.x * 8 + tid] = s;
   }
 }
 
@@ -614,6 +666,11 @@ cudaError_t launch_composite(const SceneDev& sc, const View* views, int n_views,
     composite_occ<0>();
     k_composite<0><<<g, kTileThreads, composite_smem<0>(), st>>>(sc, views, n_views, w);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_views(const View* views, int n_views, const Work& w, double* result, cudaStream_t st) {
+  k_reduce_views<<<n_views, kTileThreads, 0, st>>>(views, w, result);
   return cudaGetLastError();
 }
 

@@ -46,6 +46,12 @@ class gs_pose(ctypes.Structure):
     _fields_ = [("T_cw", ctypes.c_double * 16)]
 
 
+class gs_refine_opts(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("lr_rot", ctypes.c_double), ("lr_trans", ctypes.c_double),
+                ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("eps", ctypes.c_double),
+                ("depth_weight", ctypes.c_float)]
+
+
 class gs_outputs(ctypes.Structure):
     _fields_ = [("rgb", ctypes.c_void_p), ("depth", ctypes.c_void_p), ("alpha", ctypes.c_void_p),
                 ("final_T", ctypes.c_void_p), ("feats", ctypes.c_void_p), ("last_idx", ctypes.c_void_p)]
@@ -66,6 +72,8 @@ def _load():
         "gs_render_pose_grad_async": [vp, P(gs_camera), P(gs_pose), vp, vp, vp, ctypes.c_float, P(gs_outputs), vp,
                                       vp],
         "gs_render_batch": [vp, ctypes.c_int, P(gs_camera), P(gs_pose), P(gs_outputs), ctypes.c_uint, vp],
+        "gs_render_pose_grad_batch": [vp, ctypes.c_int, P(gs_camera), P(gs_pose), vp, vp, vp, ctypes.c_float,
+                                      vp, vp, vp, vp, ctypes.c_uint, vp],
         "gs_scene_status": [vp, vp, vp, vp],
         "gs_get_tile_lists": [vp, ctypes.c_int, vp, vp, vp, i64, vp, vp],
         "gs_get_records": [vp, ctypes.c_int, vp, i64, vp, vp],
@@ -77,6 +85,13 @@ def _load():
         fn = getattr(L, name)
         fn.argtypes = args
         fn.restype = st
+    L.gs_refine_pose.argtypes = [vp, P(gs_camera), P(gs_pose), vp, vp, vp, P(gs_refine_opts), vp, vp]
+    L.gs_refine_pose.restype = st
+    L.gs_refine_poses_batch.argtypes = [vp, ctypes.c_int, P(gs_camera), P(gs_pose), vp, vp, vp,
+                                        P(gs_refine_opts), vp, vp]
+    L.gs_refine_poses_batch.restype = st
+    L.gs_refine_defaults.argtypes = []
+    L.gs_refine_defaults.restype = gs_refine_opts
     L.gs_destroy_scene.argtypes = [vp]
     L.gs_destroy_scene.restype = None
     L.gs_last_error.argtypes = []
@@ -142,6 +157,58 @@ def gs_render_batch(h, cams, poses, outs, flags: int, stream: int) -> None:
     _check(lib.gs_render_batch(h, n, ca, pa, oa, int(flags), stream))
 
 
+def gs_render_pose_grad_batch(h, cams, poses, target_rgb, target_depth, pixel_weight, depth_weight, outs,
+                              results_dev: int, flags: int, stream: int):
+    """target_rgb / target_depth / pixel_weight: sequences of device pointers
+    (pixel_weight may be None). Returns (loss[n], grad[n, 6]) in synchronous
+    mode, None in graph mode (results in results_dev)."""
+    n = len(cams)
+    ca = (gs_camera * n)(*cams)
+    pa = (gs_pose * n)(*poses)
+    tr = (ctypes.c_void_p * n)(*[int(p) for p in target_rgb])
+    td = (ctypes.c_void_p * n)(*[int(p) for p in target_depth])
+    pw = None if pixel_weight is None else (ctypes.c_void_p * n)(*[int(p) if p else None for p in pixel_weight])
+    oa = None if outs is None else (gs_outputs * n)(*outs)
+    loss = np.zeros(n, np.float64)
+    grad = np.zeros((n, 6), np.float64)
+    graph = bool(flags & GS_BATCH_GRAPH)
+    _check(lib.gs_render_pose_grad_batch(h, n, ca, pa, tr, td, pw, float(depth_weight), oa,
+                                         None if graph else loss.ctypes.data, None if graph else grad.ctypes.data,
+                                         results_dev or None, int(flags), stream))
+    return None if graph else (loss, grad)
+
+
+def gs_refine_defaults() -> gs_refine_opts:
+    return lib.gs_refine_defaults()
+
+
+def gs_refine_pose(h, cam, pose_, target_rgb: int, target_depth: int, pixel_weight, opts, stream: int):
+    """Refines pose_ (gs_pose) in place; returns the loss history."""
+    hist = np.zeros(max(opts.iterations, 1), np.float64)
+    _check(lib.gs_refine_pose(h, ctypes.byref(cam), ctypes.byref(pose_), target_rgb, target_depth,
+                              pixel_weight or None, ctypes.byref(opts), hist.ctypes.data, stream))
+    return hist[:opts.iterations]
+
+
+def gs_refine_poses_batch(h, cams, poses, target_rgb, target_depth, pixel_weight, opts, stream: int):
+    """Refines the gs_pose list in place; returns the loss history (n, iterations)."""
+    n = len(cams)
+    ca = (gs_camera * n)(*cams)
+    pa = (gs_pose * n)(*poses)
+    tr = (ctypes.c_void_p * n)(*[int(p) for p in target_rgb])
+    td = (ctypes.c_void_p * n)(*[int(p) for p in target_depth])
+    pw = None if pixel_weight is None else (ctypes.c_void_p * n)(*[int(p) if p else None for p in pixel_weight])
+    hist = np.zeros((n, max(opts.iterations, 1)), np.float64)
+    _check(lib.gs_refine_poses_batch(h, n, ca, pa, tr, td, pw, ctypes.byref(opts), hist.ctypes.data, stream))
+    for k in range(n):
+        poses[k] = pa[k]
+    return hist[:, :opts.iterations]
+
+
+def pose_matrix(p: gs_pose) -> np.ndarray:
+    return np.array(p.T_cw[:], np.float64).reshape(4, 4)
+
+
 def gs_scene_status(h, stream: int):
     nr, npr = ctypes.c_int64(), ctypes.c_int64()
     s = lib.gs_scene_status(h, stream, ctypes.byref(nr), ctypes.byref(npr))
@@ -177,7 +244,7 @@ def gs_render_noalloc(desc: gs_scene_desc, cam: gs_camera, pose: gs_pose, out: g
                                  stream))
 
 
-KERNEL_NAMES = ("project", "scan_tiles", "scatter", "sort_composite", "backward")
+KERNEL_NAMES = ("project", "shade", "scan_tiles", "scatter", "sort_composite", "backward")
 
 
 def gs_scene_set_timing(h, enable: bool) -> None:
@@ -291,6 +358,16 @@ class Scene:
         return gs_render_pose_grad(self.handle, camera(cam), pose(T), _ptr(target_rgb), _ptr(target_depth),
                                    _ptr(pixel_weight) or None, depth_weight,
                                    self.outputs_struct(out) if out is not None else None, _stream())
+
+    def render_pose_grad_batch(self, cams, poses, target_rgb, target_depth, pixel_weight=None, depth_weight=0.1,
+                               outs=None, results=None, graph=False):
+        """Batched pose gradient; tensors are per-view lists. Returns (loss[n], grad[n,6])
+        synchronously, or None in graph mode (results: device float64 tensor (n, 8))."""
+        return gs_render_pose_grad_batch(
+            self.handle, [camera(c) for c in cams], [pose(T) for T in poses], [_ptr(t) for t in target_rgb],
+            [_ptr(t) for t in target_depth], None if pixel_weight is None else [_ptr(t) for t in pixel_weight],
+            depth_weight, None if outs is None else [self.outputs_struct(o) for o in outs],
+            _ptr(results), GS_BATCH_GRAPH if graph else 0, _stream())
 
     def render_batch(self, cams, poses, outs, graph=False):
         gs_render_batch(self.handle, [camera(c) for c in cams], [pose(T) for T in poses],

@@ -10,12 +10,14 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_functions():
     text = open(os.path.join(ROOT, "include", "gsr.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:gs_status|void|const char\s*\*)\s*(gs_\w+)\s*\(", text, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:gs_status|void|const char\s*\*|gs_refine_opts)\s*(gs_\w+)\s*\(", text,
+                                 flags=re.M)))
 
 
 def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("gs_create_scene", "gs_destroy_scene", "gs_render", "gs_render_pose_grad", "gs_render_batch",
+                     "gs_render_pose_grad_batch", "gs_refine_pose", "gs_refine_poses_batch", "gs_refine_defaults",
                      "gs_last_error"):
         assert required in names
 

@@ -148,3 +148,44 @@ def test_invalid_arguments_return_errors(gsr):
         S.render(synth.tiny_camera(), T)
     assert e.value.status == gsr.GS_ERR_INVALID_ARG
     S.close()
+
+
+def _targets_for(oracle, scene, cams, poses):
+    out = []
+    for c, T in zip(cams, poses):
+        r = oracle.render(scene, c, T, geom64=True, n_threads=8)
+        H, W = c["height"], c["width"]
+        out.append((torch.from_numpy(r["rgb"].T.reshape(3, H, W).astype(np.float32)).cuda(),
+                    torch.from_numpy(r["depth"].reshape(H, W).astype(np.float32)).cuda()))
+    return out
+
+
+def test_batched_pose_gradient_equals_single_views(oracle, gsr):
+    scene = _scene()
+    cams, poses = _views()
+    tg = _targets_for(oracle, scene, cams, poses)
+    queries = [synth.perturb_pose(T, synth.rng(20 + k), 1.0, 1.0) for k, T in enumerate(poses)]
+    weights = [None, torch.rand(cams[1]["height"], cams[1]["width"], device="cuda"), None]
+    S = gsr.Scene(scene)
+    single = [S.render_pose_grad(c, T, r, d, w, 0.1) for c, T, (r, d), w in zip(cams, queries, tg, weights)]
+    loss, grad = S.render_pose_grad_batch(cams, queries, [r for r, _ in tg], [d for _, d in tg], weights, 0.1)
+    for v, (l1, g1) in enumerate(single):
+        assert loss[v] == l1
+        np.testing.assert_array_equal(grad[v], g1)
+    # graph replay with new poses writes the same numbers to the device buffer
+    res = torch.zeros((3, 8), dtype=torch.float64, device="cuda")
+    S.reserve(400000, 4000000)
+    S.render_pose_grad_batch(cams, queries, [r for r, _ in tg], [d for _, d in tg], weights, 0.1, results=res,
+                             graph=True)
+    assert S.status()[0] == 0
+    np.testing.assert_array_equal(res[:, 0].cpu().numpy(), loss)
+    np.testing.assert_array_equal(res[:, 1:7].cpu().numpy(), grad)
+    queries2 = [synth.perturb_pose(T, synth.rng(40 + k), 1.0, 1.0) for k, T in enumerate(poses)]
+    S.render_pose_grad_batch(cams, queries2, [r for r, _ in tg], [d for _, d in tg], weights, 0.1, results=res,
+                             graph=True)
+    assert S.status()[0] == 0
+    single2 = [S.render_pose_grad(c, T, r, d, w, 0.1) for c, T, (r, d), w in zip(cams, queries2, tg, weights)]
+    for v, (l1, g1) in enumerate(single2):
+        assert float(res[v, 0]) == l1
+        np.testing.assert_array_equal(res[v, 1:7].cpu().numpy(), g1)
+    S.close()

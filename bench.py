@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="gsr", choices=["gsr", "reference"])
     p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--no-refine", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     return p.parse_args()
@@ -61,7 +62,7 @@ def dist_env():
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,utilization.gpu")
 
     def __init__(self, bus_id: str | None):
         self.bus_id = bus_id
@@ -95,13 +96,21 @@ class ClockSampler:
         os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        loaded = [r for r in rows if len(r) > 9 and (num(r[9]) or 0) >= 50] or rows
+        sm = [num(r[1]) for r in loaded if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
         reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
-        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+                "reasons": reasons, "samples": len(rows), "samples_under_load": len(loaded),
+                "power_w_max": max(pw) if pw else None,
+                "window": "all GPU measurement sections of this run (utilization >= 50 % for the median)"}
 
 
 def peaks():
@@ -269,7 +278,6 @@ def main():
     clocks = ClockSampler(bus)
     clocks.start()
     ms_grad = timed(grad_step, args.steps)
-    clk = clocks.stop()
     ms_grad = max_over_ranks(ms_grad)
     st, _, _ = S.status()
     assert st == 0
@@ -331,10 +339,13 @@ def main():
     e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps)
     h2d = (h_rgb.numel() + h_dep.numel()) * 4
 
+    # pose refinement (500k Gaussians, 960x540, 50 Adam iterations), single and 8 poses batched
+    refine = None if args.no_refine else bench_refine(gsr, synth, torch)
     # batched vs single pose: 84 candidate views of mixed resolution in one graph launch
     batched = None
     if not args.no_batched:
         batched = bench_batched(gsr, synth, torch, flush, max(2, args.steps // 4), args.warmup)
+    clk = clocks.stop()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -357,13 +368,80 @@ def main():
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 7 * 8},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roof, "kernels": kernels,
-        "batched": batched, "cpu_baseline": cpu,
+        "refine": refine, "batched": batched, "cpu_baseline": cpu,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
     S.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def _pose_errors(T, T_ref):
+    """Rotation angle of R R_ref^T with the trace clamp of the paper's Algorithm 2
+    (degrees) and the distance between camera centres (metres)."""
+    T, T_ref = np.asarray(T), np.asarray(T_ref)
+    tr = float(np.clip(np.trace(T[:3, :3] @ T_ref[:3, :3].T), -1.0, 3.0))
+    ang = math.degrees(math.acos((tr - 1.0) / 2.0))
+    c = -T[:3, :3].T @ T[:3, 3]
+    c_ref = -T_ref[:3, :3].T @ T_ref[:3, 3]
+    return ang, float(np.linalg.norm(c - c_ref))
+
+
+def bench_refine(gsr, synth, torch):
+    scene, cam, T_gt, T_q = synth.refine_workload()
+    S = gsr.Scene(scene)
+    stream = torch.cuda.current_stream().cuda_stream
+    tgt = S.render(cam, T_gt)
+    tr, td = tgt["rgb"].clone(), tgt["depth"].clone()
+    opts = gsr.gs_refine_defaults()
+    warm = gsr.gs_refine_defaults()
+    warm.iterations = 3
+    gsr.gs_refine_pose(S.handle, gsr.camera(cam), gsr.pose(T_q), tr.data_ptr(), td.data_ptr(), None, warm, stream)
+    torch.cuda.synchronize()
+    p = gsr.pose(T_q)
+    t0 = time.perf_counter()
+    hist = gsr.gs_refine_pose(S.handle, gsr.camera(cam), p, tr.data_ptr(), td.data_ptr(), None, opts, stream)
+    dt = time.perf_counter() - t0
+    a0, d0 = _pose_errors(T_q, T_gt)
+    a1, d1 = _pose_errors(gsr.pose_matrix(p), T_gt)
+    single = {"iterations": opts.iterations, "iters_per_s": opts.iterations / dt, "ms_per_iter": dt * 1e3 / opts.iterations,
+              "rot_err_deg": [a0, a1], "centre_err_m": [d0, d1], "loss": [float(hist[0]), float(hist[-1])]}
+    # 8 query poses of the same scene: batched refinement vs one pose per launch
+    g = synth.rng(11)
+    refs = [synth.look_pose((g.uniform(350, 650), g.uniform(200, 300), g.uniform(250, 350)), g.uniform(-0.3, 0.3),
+                            math.radians(g.uniform(20, 35))) for _ in range(8)]
+    qs = [synth.perturb_pose(T, g, 2.0, 5.0) for T in refs]
+    tg = []
+    for T in refs:
+        o = S.render(cam, T)
+        tg.append((o["rgb"].clone(), o["depth"].clone()))
+    it = 20
+    o8 = gsr.gs_refine_defaults()
+    o8.iterations = it
+    cams = [gsr.camera(cam)] * 8
+    w8 = gsr.gs_refine_defaults()
+    w8.iterations = 2
+    gsr.gs_refine_poses_batch(S.handle, cams, [gsr.pose(T) for T in qs], [a.data_ptr() for a, _ in tg],
+                              [b.data_ptr() for _, b in tg], None, w8, stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for T, (a, b) in zip(qs, tg):
+        gsr.gs_refine_pose(S.handle, gsr.camera(cam), gsr.pose(T), a.data_ptr(), b.data_ptr(), None, o8, stream)
+    t_single = time.perf_counter() - t0
+    poses = [gsr.pose(T) for T in qs]
+    t0 = time.perf_counter()
+    gsr.gs_refine_poses_batch(S.handle, cams, poses, [a.data_ptr() for a, _ in tg], [b.data_ptr() for _, b in tg],
+                              None, o8, stream)
+    t_batch = time.perf_counter() - t0
+    errs = [_pose_errors(gsr.pose_matrix(p), T) for p, T in zip(poses, refs)]
+    S.close()
+    return {"workload": "500k Gaussians SH3, 960x540 f=700, query 2 deg / 5 m off; Adam lr 1e-3 rad, 0.5 m",
+            "single": single,
+            "batched_8": {"views": 8, "iterations": it, "single_s": t_single, "batched_s": t_batch,
+                          "speedup": t_single / t_batch, "pose_iters_per_s": 8 * it / t_batch,
+                          "final_rot_err_deg_max": max(e[0] for e in errs),
+                          "final_centre_err_m_max": max(e[1] for e in errs)}}
 
 
 def bench_batched(gsr, synth, torch, flush, steps, warmup):
@@ -374,10 +452,17 @@ def bench_batched(gsr, synth, torch, flush, steps, warmup):
     structs = [S.outputs_struct(o) for o in outs]
     stream = torch.cuda.current_stream().cuda_stream
     S.render_batch(cams, poses, outs)  # synchronous: sizes the workspace
+    # pose-gradient targets: the rendered views; queries 1 deg / 1 m away
+    tg = [(o["rgb"].clone(), o["depth"].clone()) for o in outs]
+    qs = [synth.perturb_pose(T, synth.rng(500 + k), 1.0, 1.0) for k, T in enumerate(poses)]
+    loss, grad = S.render_pose_grad_batch(cams, qs, [a for a, _ in tg], [b for _, b in tg])  # sizes the workspace
     _, n_rec, n_pairs = S.status()
-    S.reserve(int(n_rec * 1.1) + 1024, int(n_pairs * 1.1) + 4096)
+    S.reserve(int(n_rec * 1.2) + 1024, int(n_pairs * 1.2) + 4096)
     cc = [gsr.camera(c) for c in cams]
     pp = [gsr.pose(T) for T in poses]
+    qq = [gsr.pose(T) for T in qs]
+    res_single = torch.zeros((len(cams), 8), dtype=torch.float64, device="cuda")
+    res_batch = torch.zeros((len(cams), 8), dtype=torch.float64, device="cuda")
 
     def single():
         for c, p, o in zip(cc, pp, structs):
@@ -386,8 +471,18 @@ def bench_batched(gsr, synth, torch, flush, steps, warmup):
     def batch():
         gsr.gs_render_batch(S.handle, cc, pp, structs, gsr.GS_BATCH_GRAPH, stream)
 
+    def single_grad():
+        for k, (c, p, (a, b)) in enumerate(zip(cc, qq, tg)):
+            gsr.gs_render_pose_grad_async(S.handle, c, p, a.data_ptr(), b.data_ptr(), None, 0.1, None,
+                                          res_single[k].data_ptr(), stream)
+
+    def batch_grad():
+        gsr.gs_render_pose_grad_batch(S.handle, cc, qq, [a.data_ptr() for a, _ in tg], [b.data_ptr() for _, b in tg],
+                                      None, 0.1, None, res_batch.data_ptr(), gsr.GS_BATCH_GRAPH, stream)
+
     res = {}
-    for name, fn in (("single", single), ("batched", batch)):
+    for name, fn in (("single", single), ("batched", batch), ("single_grad", single_grad),
+                     ("batched_grad", batch_grad)):
         for _ in range(warmup):
             fn()
         torch.cuda.synchronize()
@@ -401,12 +496,19 @@ def bench_batched(gsr, synth, torch, flush, steps, warmup):
             b.record()
         torch.cuda.synchronize()
         res[name] = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    torch.testing.assert_close(res_single, res_batch, rtol=0, atol=0)
     px = sum(c["width"] * c["height"] for c in cams)
     S.close()
     return {"views": len(cams), "gaussians": 2_000_000, "feat_dim": 32, "mpix": px / 1e6,
-            "single_ms": res["single"], "batched_ms": res["batched"],
-            "single_mpix_s": px / (res["single"] * 1e-3) / 1e6, "batched_mpix_s": px / (res["batched"] * 1e-3) / 1e6,
-            "speedup": res["single"] / res["batched"], "records": int(n_rec), "pairs": int(n_pairs)}
+            "forward": {"single_ms": res["single"], "batched_ms": res["batched"],
+                        "single_mpix_s": px / (res["single"] * 1e-3) / 1e6,
+                        "batched_mpix_s": px / (res["batched"] * 1e-3) / 1e6,
+                        "speedup": res["single"] / res["batched"], "outputs": "rgb, depth, alpha, T, 32 features"},
+            "pose_grad": {"single_ms": res["single_grad"], "batched_ms": res["batched_grad"],
+                          "single_pose_iters_per_s": len(cams) / (res["single_grad"] * 1e-3),
+                          "batched_pose_iters_per_s": len(cams) / (res["batched_grad"] * 1e-3),
+                          "speedup": res["single_grad"] / res["batched_grad"]},
+            "records": int(n_rec), "pairs": int(n_pairs)}
 
 
 if __name__ == "__main__":

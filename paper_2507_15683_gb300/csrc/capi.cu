@@ -346,7 +346,10 @@ gs_status enqueue(gs_scene* s, const std::vector<View>& hv, uint64_t n_tiles, co
   GS_CUDA(mark(3));
   GS_CUDA(launch_scatter(dviews, w, s->sm_count * 8, st));
   GS_CUDA(mark(4));
-  GS_CUDA(launch_composite(sc, dviews, nv, w, s->sm_count * composite_blocks_per_sm(s->feat_dim), st));
+  bool feats = false;
+  for (const View& V : hv) feats = feats || V.feats != nullptr;
+  GS_CUDA(launch_composite(sc, dviews, nv, w, feats, s->sm_count * composite_blocks_per_sm(feats ? s->feat_dim : 0),
+                           st));
   GS_CUDA(mark(5));
   if (g) {
     double* res = g->result ? g->result : w.result;

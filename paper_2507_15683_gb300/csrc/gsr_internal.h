@@ -106,8 +106,9 @@ cudaError_t launch_shade(const SceneDev& sc, const View* views, const Work& w, b
                          cudaStream_t st);
 cudaError_t launch_scan_tiles(const Work& w, cudaStream_t st);
 cudaError_t launch_scatter(const View* views, const Work& w, int grid, cudaStream_t st);
-cudaError_t launch_composite(const SceneDev& sc, const View* views, int n_views, const Work& w, int grid,
-                             cudaStream_t st);
+// feats: some view writes the feature map (else the feature-free kernel runs)
+cudaError_t launch_composite(const SceneDev& sc, const View* views, int n_views, const Work& w, bool feats,
+                             int grid, cudaStream_t st);
 cudaError_t launch_backward(const View* views, int n_views, const Work& w, double* result, int grid,
                             cudaStream_t st);
 cudaError_t launch_reduce_views(const View* views, int n_views, const Work& w, double* result, cudaStream_t st);

@@ -655,11 +655,11 @@ int backward_blocks_per_sm() {
   return occ;
 }
 
-cudaError_t launch_composite(const SceneDev& sc, const View* views, int n_views, const Work& w, int grid,
-                             cudaStream_t st) {
+cudaError_t launch_composite(const SceneDev& sc, const View* views, int n_views, const Work& w, bool feats,
+                             int grid, cudaStream_t st) {
   if (w.n_tiles == 0) return cudaSuccess;
   const int g = (uint32_t)grid < w.n_tiles ? grid : (int)w.n_tiles;
-  if (sc.feat_dim) {
+  if (sc.feat_dim && feats) {
     composite_occ<32>();
     k_composite<32><<<g, kTileThreads, composite_smem<32>(), st>>>(sc, views, n_views, w);
   } else {

@@ -249,6 +249,20 @@ gs_status gs_get_tile_lists(gs_scene* scene, int view, uint64_t* keys, uint32_t*
 gs_status gs_get_records(gs_scene* scene, int view, int32_t* rec, int64_t capacity, int64_t* n_records,
                          void* stream);
 
+/* Partitions (Sec. 3.1: large scenes are split into cells). Every call walks
+ * only the partitions whose padded bounding box can reach one of its views'
+ * tiles (a conservative frustum test: the results are those of rendering every
+ * Gaussian). A scene created with device_resident = 0 and a partition table
+ * is streamed: it keeps a packed copy in pinned host memory and uploads a
+ * partition to the device the first time a call needs it.
+ * gs_scene_stream_stats reports the bytes uploaded so far, the partitions now
+ * on the device and the partitions the last call walked (host pointers, any
+ * may be NULL). gs_scene_evict marks every partition of a streamed scene as
+ * not resident (they are uploaded again when needed; no memory is freed). */
+gs_status gs_scene_stream_stats(gs_scene* scene, int64_t* h2d_bytes, int* resident_partitions,
+                                int* active_partitions);
+gs_status gs_scene_evict(gs_scene* scene);
+
 /* Kernel timing (CUDA events recorded on the call's stream around every
  * launch of every call while enabled). Kernel order of the arrays below:
  * projection (discrete layer), shading (conic, colour, centre, Jacobian),

@@ -192,7 +192,7 @@ class OracleScene:
 
 def render(scene, cam, T, *, geom64=False, want_grad=False, n_threads=1, pixels=None,
            target_rgb=None, target_depth=None, pixel_weight=None, depth_weight=0.1,
-           tie_rel=1e-4, tie_rel_T=2e-3, brute=False, want_feats=True):
+           tie_rel=1e-4, tie_rel_T=2e-4, brute=False, want_feats=True):
     """Full oracle render (Sec. 3.1 alpha blending; Algorithm 1 projection).
 
     Returns a dict of per-pixel arrays in the order of ``pixels`` (or row-major

@@ -89,7 +89,7 @@ struct GraphCache {
   bool valid = false;
   cudaGraphExec_t exec = nullptr;
   std::vector<char> key;       // cameras, outputs, loss inputs of the capture
-  View* host_views = nullptr;  // pinned; read by the graph's upload node at replay
+  char* host_table = nullptr;  // pinned call table (ranges + views), read by the graph's upload node
   cudaEvent_t done = nullptr;
   cudaStream_t capture = nullptr;
   int n_views = 0;
@@ -102,6 +102,17 @@ namespace gsr {
 void set_last_error(const std::string& msg) { g_err = msg; }
 }  // namespace gsr
 
+// A partition of the scene (a VastGaussian-style cell, Sec. 3.1): index range,
+// bounding box of its means, largest scale, and whether it is on the device.
+constexpr int kPartBoxes = 6;  // boxes of mean +- k s for k = 1, 2, 4, ..., 32
+struct Part {
+  int64_t begin = 0, end = 0;
+  double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};  // box of the means
+  double klo[kPartBoxes][3], khi[kPartBoxes][3];  // box of mean_i +- 2^j s_i (s_i: largest scale)
+  double smax = 0.0;
+  bool resident = false;
+};
+
 struct gs_scene {
   int device = 0;
   int sm_count = 1;
@@ -109,6 +120,14 @@ struct gs_scene {
   int sh_degree = 0, feat_dim = 0, nsh4 = 1;
   DevBuf pos, cov, sh, feat;
   std::vector<int64_t> part_off;
+  std::vector<Part> parts;
+  bool streaming = false;  // partitions are uploaded from the pinned copy on first use
+  float4* h_pos = nullptr;  // pinned packed copy (streaming only), same layout as the device arena
+  float4* h_cov = nullptr;
+  float4* h_sh = nullptr;
+  uint4* h_feat = nullptr;
+  int64_t h2d_bytes = 0;
+  int last_active = 0;
   // workspace
   DevBuf rec_a, rec_b, rec_c, rec_m, rec_j;
   uint32_t rec_cap = 0, jac_cap = 0;
@@ -304,11 +323,21 @@ gs_status build_views(gs_scene* s, int nv, const gs_camera* cams, const gs_pose*
 // Enqueue one call. When `upload_src` is given the view table is copied from
 // it (pinned memory, for graph capture); otherwise from hv (pageable: the copy
 // is staged before cudaMemcpyAsync returns).
-gs_status enqueue(gs_scene* s, const std::vector<View>& hv, uint64_t n_tiles, const GradIn* g, cudaStream_t st,
-                  const View* upload_src) {
+// Device call table: ranges (1 + partitions entries) followed by the views.
+size_t table_ranges_bytes(const gs_scene* s) { return (1 + s->parts.size()) * sizeof(int4); }
+size_t table_bytes(const gs_scene* s, int nv) { return table_ranges_bytes(s) + (size_t)nv * sizeof(View); }
+
+void fill_table(const gs_scene* s, const std::vector<View>& hv, const std::vector<int4>& ranges, char* dst) {
+  std::memset(dst, 0, table_ranges_bytes(s));
+  std::memcpy(dst, ranges.data(), ranges.size() * sizeof(int4));
+  std::memcpy(dst + table_ranges_bytes(s), hv.data(), hv.size() * sizeof(View));
+}
+
+gs_status enqueue(gs_scene* s, const std::vector<View>& hv, const std::vector<int4>& ranges, uint64_t n_tiles,
+                  const GradIn* g, cudaStream_t st, const char* upload_src) {
   const int nv = (int)hv.size();
   GS_TRY(grow_tiles(s, n_tiles));
-  GS_TRY(ensure(s->views, (size_t)nv * sizeof(View)));
+  GS_TRY(ensure(s->views, table_bytes(s, nv)));
   if (g && !g->result) GS_TRY(ensure(s->result, (size_t)nv * kResultStride * sizeof(double)));
   if (s->rec_cap == 0) {
     const uint64_t guess = std::max<uint64_t>(1u << 16, (uint64_t)s->n * nv / 4);
@@ -318,10 +347,16 @@ gs_status enqueue(gs_scene* s, const std::vector<View>& hv, uint64_t n_tiles, co
     GS_TRY(grow_records(s, s->rec_cap, g != nullptr));
   }
   if (s->pair_cap == 0) GS_TRY(grow_pairs(s, (uint64_t)s->rec_cap * 8));
-  View* dviews = dp<View>(s->views);
-  GS_CUDA(cudaMemcpyAsync(dviews, upload_src ? upload_src : hv.data(), (size_t)nv * sizeof(View),
-                          cudaMemcpyHostToDevice, st));
+  View* dviews = reinterpret_cast<View*>(static_cast<char*>(s->views.p) + table_ranges_bytes(s));
+  if (upload_src) {
+    GS_CUDA(cudaMemcpyAsync(s->views.p, upload_src, table_bytes(s, nv), cudaMemcpyHostToDevice, st));
+  } else {
+    std::vector<char> tab(table_bytes(s, nv));
+    fill_table(s, hv, ranges, tab.data());
+    GS_CUDA(cudaMemcpyAsync(s->views.p, tab.data(), tab.size(), cudaMemcpyHostToDevice, st));
+  }
   Work w = work_of(s, (uint32_t)n_tiles);
+  w.ranges = dp<int4>(s->views);
   GS_CUDA(cudaMemsetAsync(w.tile_count, 0, (n_tiles + 1) * sizeof(uint32_t), st));
   GS_CUDA(cudaMemsetAsync(w.ctr, 0, sizeof(Counters), st));
   const SceneDev sc = scene_dev(s);
@@ -364,6 +399,120 @@ gs_status enqueue(gs_scene* s, const std::vector<View>& hv, uint64_t n_tiles, co
   return GS_OK;
 }
 
+// Binary32 covariance of one Gaussian in the fixed operation order of the
+// scene-packing kernel (host copy used when partitions are streamed).
+void host_cov3d(const float* sc, const float* q, float S[6]) {
+  const float qw = q[0], qx = q[1], qy = q[2], qz = q[3];
+  const float n2 = qw * qw + qx * qx + qy * qy + qz * qz;
+  float w = 1.0f, x = 0.0f, y = 0.0f, z = 0.0f;
+  if (n2 > 0.0f) {
+    const float nr = std::sqrt(n2);
+    w = qw / nr;
+    x = qx / nr;
+    y = qy / nr;
+    z = qz / nr;
+  }
+  const float xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z;
+  const float wx = w * x, wy = w * y, wz = w * z;
+  const float r[3][3] = {{1.0f - 2.0f * (yy + zz), 2.0f * (xy - wz), 2.0f * (xz + wy)},
+                         {2.0f * (xy + wz), 1.0f - 2.0f * (xx + zz), 2.0f * (yz - wx)},
+                         {2.0f * (xz - wy), 2.0f * (yz + wx), 1.0f - 2.0f * (xx + yy)}};
+  float m[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) m[a][b] = r[a][b] * sc[b];
+  const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+  for (int k = 0; k < 6; ++k) {
+    const float* u = m[ia[k]];
+    const float* v = m[ib[k]];
+    S[k] = u[0] * v[0] + u[1] * v[1] + u[2] * v[2];
+  }
+}
+
+// Conservative test whether any Gaussian of the partition can reach the view's
+// tiles. A Gaussian of largest scale s at depth z has a pixel radius of at most
+// 3 s |J|_F + 3.5 px with |J|_F <= jb / z (guard clamp included), i.e. a world
+// footprint of at most k s with k = 3.3 jb / f; the partition's box of
+// mean_i +- k' s_i (k' = the next precomputed power of two >= k) therefore
+// holds every Gaussian's footprint, and the image is widened by 32 px for the
+// constant part and tile rounding. If all corners of that box lie outside one
+// frustum plane (or in front of the near plane), no Gaussian of the partition
+// has a non-empty tile rectangle, so skipping the partition changes nothing.
+bool part_in_view(const Part& P, const View& V) {
+  double R[9], t[3];
+  for (int k = 0; k < 9; ++k) R[k] = (double)V.R[k] + (double)V.Rl[k];
+  for (int k = 0; k < 3; ++k) t[k] = (double)V.t[k] + (double)V.tl[k];
+  const double fx = V.fx, fy = V.fy;
+  const double lx = 1.3 * 0.5 * V.width / fx, ly = 1.3 * 0.5 * V.height / fy;
+  const double jb = std::sqrt(fx * fx * (1.0 + lx * lx) + fy * fy * (1.0 + ly * ly));
+  const double k = 3.3 * jb / std::min(fx, fy);
+  double blo[3], bhi[3];
+  int j = 0;
+  while (j < kPartBoxes && (double)(1 << j) < k) ++j;
+  for (int a = 0; a < 3; ++a) {
+    if (j < kPartBoxes) {
+      blo[a] = P.klo[j][a];
+      bhi[a] = P.khi[j][a];
+    } else {  // very wide field of view: pad the means' box by k s_max
+      blo[a] = P.lo[a] - k * P.smax;
+      bhi[a] = P.hi[a] + k * P.smax;
+    }
+  }
+  const double M = 32.0;
+  const double a0 = (-M - V.cx) / fx, a1 = (16.0 * V.tiles_x + M - V.cx) / fx;
+  const double b0 = (-M - V.cy) / fy, b1 = (16.0 * V.tiles_y + M - V.cy) / fy;
+  bool out_near = true, out_l = true, out_r = true, out_t = true, out_b = true;
+  for (int c = 0; c < 8; ++c) {
+    const double X[3] = {(c & 1) ? bhi[0] : blo[0], (c & 2) ? bhi[1] : blo[1], (c & 4) ? bhi[2] : blo[2]};
+    double q[3];
+    for (int a = 0; a < 3; ++a) q[a] = R[3 * a] * X[0] + R[3 * a + 1] * X[1] + R[3 * a + 2] * X[2] + t[a];
+    out_near = out_near && q[2] < 0.2;
+    out_l = out_l && (q[0] - a0 * q[2]) < 0.0;
+    out_r = out_r && (a1 * q[2] - q[0]) < 0.0;
+    out_t = out_t && (q[1] - b0 * q[2]) < 0.0;
+    out_b = out_b && (b1 * q[2] - q[1]) < 0.0;
+  }
+  return !(out_near || out_l || out_r || out_t || out_b);
+}
+
+// Partitions in view of any view of the call: uploads the non-resident ones
+// (streaming scenes) on the stream and returns the index ranges the
+// projection walks, in ascending order (header entry first).
+gs_status prepare_call(gs_scene* s, const std::vector<View>& hv, cudaStream_t st, std::vector<int4>& ranges) {
+  ranges.assign(1, make_int4(0, 0, 0, 0));
+  int total = 0, active = 0;
+  for (Part& P : s->parts) {
+    if (P.end <= P.begin) continue;
+    bool need = false;
+    for (const View& V : hv) need = need || part_in_view(P, V);
+    if (!need) continue;
+    ++active;
+    if (s->streaming && !P.resident) {
+      const size_t b = (size_t)P.begin, c = (size_t)(P.end - P.begin);
+      GS_CUDA(cudaMemcpyAsync(dp<float4>(s->pos) + b, s->h_pos + b, c * sizeof(float4), cudaMemcpyHostToDevice, st));
+      GS_CUDA(cudaMemcpyAsync(dp<float4>(s->cov) + 2 * b, s->h_cov + 2 * b, 2 * c * sizeof(float4),
+                              cudaMemcpyHostToDevice, st));
+      GS_CUDA(cudaMemcpyAsync(dp<float4>(s->sh) + b * s->nsh4, s->h_sh + b * s->nsh4, c * s->nsh4 * sizeof(float4),
+                              cudaMemcpyHostToDevice, st));
+      s->h2d_bytes += (int64_t)(c * (3 + s->nsh4) * sizeof(float4));
+      if (s->feat_dim) {
+        GS_CUDA(cudaMemcpyAsync(dp<uint4>(s->feat) + 4 * b, s->h_feat + 4 * b, 4 * c * sizeof(uint4),
+                                cudaMemcpyHostToDevice, st));
+        s->h2d_bytes += (int64_t)(4 * c * sizeof(uint4));
+      }
+      P.resident = true;
+    }
+    if (ranges.size() > 1 && ranges.back().y == (int)P.begin) {
+      ranges.back().y = (int)P.end;  // merge adjacent partitions
+    } else {
+      ranges.push_back(make_int4((int)P.begin, (int)P.end, total, 0));
+    }
+    total += (int)(P.end - P.begin);
+  }
+  ranges[0] = make_int4((int)ranges.size() - 1, total, 0, 0);
+  s->last_active = active;
+  return GS_OK;
+}
+
 // Record capacity the last call needed: every segment must hold its count.
 uint64_t records_capacity_needed(const Counters& c) {
   uint64_t mx = 0;
@@ -390,8 +539,10 @@ gs_status read_counters(gs_scene* s, cudaStream_t st, Counters& c) {
 // Synchronous call with the regrow rule: render, check the counters, and if the
 // workspace was too small grow it and render again.
 gs_status run_sync(gs_scene* s, const std::vector<View>& hv, uint64_t n_tiles, const GradIn* g, cudaStream_t st) {
+  std::vector<int4> ranges;
+  GS_TRY(prepare_call(s, hv, st, ranges));
   for (int attempt = 0; attempt < 4; ++attempt) {
-    GS_TRY(enqueue(s, hv, n_tiles, g, st, nullptr));
+    GS_TRY(enqueue(s, hv, ranges, n_tiles, g, st, nullptr));
     Counters c;
     GS_TRY(read_counters(s, st, c));
     if (c.error) return fail(GS_ERR_INTERNAL, "device consistency check failed");
@@ -454,17 +605,20 @@ namespace {
 gs_status run_graph(gs_scene* s, GraphCache& G, const std::vector<char>& key, const std::vector<View>& hv,
                     uint64_t n_tiles, const GradIn* g, cudaStream_t st) {
   const int n_views = (int)hv.size();
+  std::vector<int4> ranges;
+  if (G.valid && G.key == key) GS_CUDA(cudaEventSynchronize(G.done));  // previous replay read the table
+  GS_TRY(prepare_call(s, hv, st, ranges));  // uploads partitions on st before the graph runs
   if (!(G.valid && G.key == key)) {
     if (G.exec) cudaGraphExecDestroy(G.exec);
     G.exec = nullptr;
     G.valid = false;
-    if (G.host_views) cudaFreeHost(G.host_views);
-    G.host_views = nullptr;
+    if (G.host_table) cudaFreeHost(G.host_table);
+    G.host_table = nullptr;
     if (!G.done) GS_CUDA(cudaEventCreateWithFlags(&G.done, cudaEventDisableTiming));
-    GS_CUDA(cudaMallocHost(&G.host_views, (size_t)n_views * sizeof(View)));
-    std::memcpy(G.host_views, hv.data(), (size_t)n_views * sizeof(View));
+    GS_CUDA(cudaMallocHost(&G.host_table, table_bytes(s, n_views)));
+    fill_table(s, hv, ranges, G.host_table);
     GS_TRY(grow_tiles(s, n_tiles));
-    GS_TRY(ensure(s->views, (size_t)n_views * sizeof(View)));
+    GS_TRY(ensure(s->views, table_bytes(s, n_views)));
     if (g && !g->result) GS_TRY(ensure(s->result, (size_t)n_views * kResultStride * sizeof(double)));
     const uint64_t guess = std::max<uint64_t>(1u << 16, (uint64_t)s->n * n_views / 4);
     GS_TRY(grow_records(s, s->rec_cap ? s->rec_cap : guess, g != nullptr));
@@ -475,7 +629,7 @@ gs_status run_graph(gs_scene* s, GraphCache& G, const std::vector<char>& key, co
     GS_CUDA(cudaStreamSynchronize(st));
     cudaGraph_t graph = nullptr;
     GS_CUDA(cudaStreamBeginCapture(G.capture, cudaStreamCaptureModeThreadLocal));
-    const gs_status est = enqueue(s, hv, n_tiles, g, G.capture, G.host_views);
+    const gs_status est = enqueue(s, hv, ranges, n_tiles, g, G.capture, G.host_table);
     const cudaError_t ce = cudaStreamEndCapture(G.capture, &graph);
     if (est != GS_OK) {
       if (graph) cudaGraphDestroy(graph);
@@ -489,9 +643,7 @@ gs_status run_graph(gs_scene* s, GraphCache& G, const std::vector<char>& key, co
     G.n_views = n_views;
     G.valid = true;
   } else {
-    // the previous replay must have consumed the pinned view table
-    GS_CUDA(cudaEventSynchronize(G.done));
-    std::memcpy(G.host_views, hv.data(), (size_t)n_views * sizeof(View));
+    fill_table(s, hv, ranges, G.host_table);
     s->last_views = hv;
     s->last_tiles = (uint32_t)n_tiles;
   }
@@ -565,7 +717,75 @@ gs_status gs_create_scene(const gs_scene_desc* d, gs_scene** out) {
     cudaGetLastError();
     return cleanup(fail(GS_ERR_OOM, "pinned host allocation failed"));
   }
-  if (n > 0) {
+  // partitions: index ranges, bounding boxes of the means, largest scale
+  {
+    std::vector<float> hm, hs;
+    const float *m = d->means, *sc = d->scales;
+    if (n > 0 && d->device_resident) {
+      hm.resize(3 * n);
+      hs.resize(3 * n);
+      e = cudaMemcpy(hm.data(), d->means, 3 * n * sizeof(float), cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess) e = cudaMemcpy(hs.data(), d->scales, 3 * n * sizeof(float), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cleanup(fail(GS_ERR_CUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e)));
+      m = hm.data();
+      sc = hs.data();
+    }
+    for (size_t k = 0; k + 1 < parts.size(); ++k) {
+      Part P;
+      P.begin = parts[k];
+      P.end = parts[k + 1];
+      for (int a = 0; a < 3; ++a) {
+        P.lo[a] = 1e300;
+        P.hi[a] = -1e300;
+        for (int j = 0; j < kPartBoxes; ++j) {
+          P.klo[j][a] = 1e300;
+          P.khi[j][a] = -1e300;
+        }
+      }
+      for (int64_t i = P.begin; i < P.end; ++i) {
+        const double si = std::max(std::fabs((double)sc[3 * i]),
+                                   std::max(std::fabs((double)sc[3 * i + 1]), std::fabs((double)sc[3 * i + 2])));
+        P.smax = std::max(P.smax, si);
+        for (int a = 0; a < 3; ++a) {
+          const double x = m[3 * i + a];
+          P.lo[a] = std::min(P.lo[a], x);
+          P.hi[a] = std::max(P.hi[a], x);
+          for (int j = 0; j < kPartBoxes; ++j) {
+            P.klo[j][a] = std::min(P.klo[j][a], x - (double)(1 << j) * si);
+            P.khi[j][a] = std::max(P.khi[j][a], x + (double)(1 << j) * si);
+          }
+        }
+      }
+      s->parts.push_back(P);
+    }
+  }
+  s->streaming = !d->device_resident && d->n_partitions > 0 && n > 0;
+  if (s->streaming) {
+    // pack on the host into pinned memory in the device layout; partitions are
+    // uploaded on first use by a call whose views they can reach
+    if (cudaMallocHost(&s->h_pos, n * sizeof(float4)) != cudaSuccess ||
+        cudaMallocHost(&s->h_cov, 2 * n * sizeof(float4)) != cudaSuccess ||
+        cudaMallocHost(&s->h_sh, n * s->nsh4 * sizeof(float4)) != cudaSuccess ||
+        (s->feat_dim && cudaMallocHost(&s->h_feat, n * 4 * sizeof(uint4)) != cudaSuccess)) {
+      cudaGetLastError();
+      return cleanup(fail(GS_ERR_OOM, "pinned host allocation for the streamed scene failed"));
+    }
+    for (size_t i = 0; i < n; ++i) {
+      float S[6];
+      host_cov3d(d->scales + 3 * i, d->quats + 4 * i, S);
+      const float* sc = d->scales + 3 * i;
+      const float smax = std::max(sc[0], std::max(sc[1], sc[2]));
+      s->h_pos[i] = make_float4(d->means[3 * i], d->means[3 * i + 1], d->means[3 * i + 2], smax);
+      s->h_cov[2 * i] = make_float4(S[0], S[1], S[2], S[3]);
+      s->h_cov[2 * i + 1] = make_float4(S[4], S[5], d->opacities[i], 0.0f);
+      float* so = reinterpret_cast<float*>(s->h_sh + i * s->nsh4);
+      for (int k = 0; k < 4 * s->nsh4; ++k) so[k] = (k < K3) ? d->sh[i * K3 + k] : 0.0f;
+      if (s->feat_dim) std::memcpy(s->h_feat + 4 * i, d->feats_bf16 + 32 * i, 64);
+    }
+  } else {
+    for (Part& P : s->parts) P.resident = true;
+  }
+  if (n > 0 && !s->streaming) {
     const float *m = d->means, *sc = d->scales, *q = d->quats, *o = d->opacities, *sh = d->sh;
     const uint16_t* f = d->feats_bf16;
     DevBuf staging;
@@ -614,7 +834,7 @@ void gs_destroy_scene(gs_scene* s) {
   cudaDeviceSynchronize();
   for (GraphCache* G : {&s->graph, &s->graph_grad}) {
     if (G->exec) cudaGraphExecDestroy(G->exec);
-    if (G->host_views) cudaFreeHost(G->host_views);
+    if (G->host_table) cudaFreeHost(G->host_table);
     if (G->done) cudaEventDestroy(G->done);
     if (G->capture) cudaStreamDestroy(G->capture);
   }
@@ -626,6 +846,8 @@ void gs_destroy_scene(gs_scene* s) {
                     &s->tile_count, &s->tile_offset, &s->tile_cursor, &s->partials, &s->pairs, &s->pairs_tmp,
                     &s->ctr, &s->result, &s->views, &s->int_pix})
     release(*b);
+  for (void* h : {(void*)s->h_pos, (void*)s->h_cov, (void*)s->h_sh, (void*)s->h_feat})
+    if (h) cudaFreeHost(h);
   if (s->ctr_host) cudaFreeHost(s->ctr_host);
   if (s->result_host) cudaFreeHost(s->result_host);
   delete s;
@@ -662,7 +884,9 @@ gs_status gs_render_async(gs_scene* s, const gs_camera* cam, const gs_pose* pose
   std::vector<View> hv;
   uint64_t n_tiles;
   GS_TRY(build_views(s, 1, cam, pose, out, nullptr, hv, n_tiles));
-  return enqueue(s, hv, n_tiles, nullptr, (cudaStream_t)stream, nullptr);
+  std::vector<int4> ranges;
+  GS_TRY(prepare_call(s, hv, (cudaStream_t)stream, ranges));
+  return enqueue(s, hv, ranges, n_tiles, nullptr, (cudaStream_t)stream, nullptr);
 }
 
 gs_status gs_render_pose_grad(gs_scene* s, const gs_camera* cam, const gs_pose* pose, const float* target_rgb,
@@ -699,7 +923,9 @@ gs_status gs_render_pose_grad_async(gs_scene* s, const gs_camera* cam, const gs_
   std::vector<View> hv;
   uint64_t n_tiles;
   GS_TRY(build_views(s, 1, cam, pose, out, &g, hv, n_tiles));
-  return enqueue(s, hv, n_tiles, &g, (cudaStream_t)stream, nullptr);
+  std::vector<int4> ranges;
+  GS_TRY(prepare_call(s, hv, (cudaStream_t)stream, ranges));
+  return enqueue(s, hv, ranges, n_tiles, &g, (cudaStream_t)stream, nullptr);
 }
 
 gs_status gs_render_batch(gs_scene* s, int n_views, const gs_camera* cams, const gs_pose* poses,
@@ -759,6 +985,28 @@ gs_status gs_render_pose_grad_batch(gs_scene* s, int n_views, const gs_camera* c
     if (grad_out)
       for (int k = 0; k < 6; ++k) grad_out[6 * v + k] = host[(size_t)v * kResultStride + 1 + k];
   }
+  return GS_OK;
+}
+
+gs_status gs_scene_stream_stats(gs_scene* s, int64_t* h2d_bytes, int* resident_partitions,
+                                int* active_partitions) {
+  g_err.clear();
+  GS_TRY(check_scene(s));
+  int res = 0;
+  for (const Part& P : s->parts) res += P.resident ? 1 : 0;
+  if (h2d_bytes) *h2d_bytes = s->h2d_bytes;
+  if (resident_partitions) *resident_partitions = res;
+  if (active_partitions) *active_partitions = s->last_active;
+  return GS_OK;
+}
+
+gs_status gs_scene_evict(gs_scene* s) {
+  g_err.clear();
+  GS_TRY(check_scene(s));
+  if (!s->streaming) return GS_OK;
+  GS_TRY(set_device(s));
+  GS_CUDA(cudaDeviceSynchronize());
+  for (Part& P : s->parts) P.resident = false;
   return GS_OK;
 }
 

@@ -93,6 +93,9 @@ struct Work {
   Counters* ctr;
   double* partials;    // n_tiles * kPartialStride
   double* result;      // 7 doubles (loss, grad)
+  // Gaussian index ranges the projection walks (partitions in view):
+  // ranges[0] = (count, total length, 0, 0), ranges[1 + k] = (begin, end, prefix, 0)
+  const int4* ranges;
 };
 
 // launchers (return the CUDA error of the launch)

@@ -54,7 +54,8 @@ struct Layout {
   static constexpr size_t pairs_tmp = align256(pairs + P * sizeof(uint2));
   static constexpr size_t ctr = align256(pairs_tmp + P * sizeof(uint2));
   static constexpr size_t view = align256(ctr + sizeof(Counters));
-  static constexpr size_t end = align256(view + sizeof(View));
+  static constexpr size_t ranges = align256(view + sizeof(View));
+  static constexpr size_t end = align256(ranges + 2 * sizeof(int4));
 };
 static_assert(Layout::end <= GS_NOALLOC_SCRATCH_BYTES, "no-alloc limits do not fit the scratch array");
 
@@ -181,6 +182,9 @@ extern "C" gs_status gs_render_noalloc(const gs_scene_desc* d, const gs_camera* 
   w.pairs_tmp = reinterpret_cast<uint2*>(base + Layout::pairs_tmp);
   w.pair_cap = GS_NOALLOC_MAX_PAIRS;
   w.ctr = reinterpret_cast<Counters*>(base + Layout::ctr);
+  int4* dranges = reinterpret_cast<int4*>(base + Layout::ranges);
+  w.ranges = dranges;
+  const int4 hranges[2] = {make_int4(1, n, 0, 0), make_int4(0, n, 0, 0)};  // one range: every Gaussian
 
   SceneDev sc;
   sc.pos = pos;
@@ -196,6 +200,7 @@ extern "C" gs_status gs_render_noalloc(const gs_scene_desc* d, const gs_camera* 
   NA_CUDA(cudaMemsetAsync(w.tile_count, 0, (n_tiles + 1) * sizeof(uint32_t), st));
   NA_CUDA(cudaMemsetAsync(w.ctr, 0, sizeof(Counters), st));
   NA_CUDA(cudaMemcpyAsync(dview, &V, sizeof(View), cudaMemcpyHostToDevice, st));
+  NA_CUDA(cudaMemcpyAsync(dranges, hranges, sizeof(hranges), cudaMemcpyHostToDevice, st));
   NA_CUDA(launch_pack_scene(d->means, d->scales, d->quats, d->opacities, d->sh, K3, d->feats_bf16, d->feat_dim, n,
                             nsh4, pos, cov, sh, d->feat_dim ? feat : nullptr, st));
   NA_CUDA(launch_project(sc, dview, 1, w, sm_count * 8, st));

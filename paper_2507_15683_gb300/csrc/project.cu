@@ -228,9 +228,20 @@ __global__ void __launch_bounds__(256) k_project(SceneDev sc, const View* __rest
   const unsigned lt_mask = (1u << lane) - 1u;
   const int stride = gridDim.x * blockDim.x;
   const unsigned region = blockIdx.x % kRecRegions;
-  for (int base = blockIdx.x * blockDim.x; base < sc.n; base += stride) {  // warp-uniform loop
-    const int i = base + threadIdx.x;
-    const bool valid = i < sc.n;
+  const int4 hdr = w.ranges[0];  // (ranges, total length): only partitions in view are walked
+  for (int base = blockIdx.x * blockDim.x; base < hdr.y; base += stride) {  // warp-uniform loop
+    const int f = base + threadIdx.x;
+    const bool valid = f < hdr.y;
+    int i = 0;
+    if (valid) {
+      int lo = 1, hi = hdr.x;  // last range whose prefix is <= f
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (w.ranges[mid].z <= f) lo = mid; else hi = mid - 1;
+      }
+      const int4 rg = w.ranges[lo];
+      i = rg.x + (f - rg.z);
+    }
     const float4 p4 = valid ? __ldg(sc.pos + i) : make_float4(0.f, 0.f, 0.f, 0.f);
     float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = c0;
     bool have_cov = false;
@@ -509,7 +520,7 @@ cudaError_t launch_pack_scene(const float* means, const float* scales, const flo
 cudaError_t launch_project(const SceneDev& sc, const View* views, int n_views, const Work& w, int grid,
                            cudaStream_t st) {
   if (sc.n <= 0 || n_views <= 0) return cudaSuccess;
-  const int need = (sc.n + 255) / 256;
+  const int need = (sc.n + 255) / 256;  // the active ranges never exceed the scene
   const int g = need < grid ? need : grid;
   k_project<<<g, 256, 0, st>>>(sc, views, n_views, w);
   return cudaGetLastError();

@@ -79,6 +79,8 @@ def _load():
         "gs_get_records": [vp, ctypes.c_int, vp, i64, vp, vp],
         "gs_render_noalloc": [P(gs_scene_desc), P(gs_camera), P(gs_pose), P(gs_outputs), vp],
         "gs_scene_set_timing": [vp, ctypes.c_int],
+        "gs_scene_stream_stats": [vp, vp, vp, vp],
+        "gs_scene_evict": [vp],
         "gs_scene_kernel_times": [vp, vp, vp],
     }
     for name, args in sigs.items():
@@ -258,6 +260,17 @@ def gs_scene_kernel_times(h):
     return ms, n
 
 
+def gs_scene_stream_stats(h):
+    """(bytes uploaded, partitions resident, partitions walked by the last call)."""
+    b, r, a = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
+    _check(lib.gs_scene_stream_stats(h, ctypes.byref(b), ctypes.byref(r), ctypes.byref(a)))
+    return b.value, r.value, a.value
+
+
+def gs_scene_evict(h) -> None:
+    _check(lib.gs_scene_evict(h))
+
+
 def gs_version() -> str:
     return lib.gs_version().decode()
 
@@ -292,9 +305,15 @@ class Scene:
     sh_degree, optional feats_bf16 (n,32) uint16 and partition_offsets.
     """
 
-    def __init__(self, scene: dict):
+    def __init__(self, scene: dict, stream_partitions: bool = False):
+        """stream_partitions: pass host arrays and the partition table, so the
+        library keeps the scene in pinned host memory and uploads partitions on
+        demand (requires scene["partition_offsets"])."""
         import torch
         dev = torch.device("cuda", torch.cuda.current_device())
+        if stream_partitions:
+            self._init_host(scene)
+            return
 
         def t(x, dtype):
             if isinstance(x, torch.Tensor):
@@ -317,6 +336,21 @@ class Scene:
                                    None if po_np is None else po_np.ctypes.data, 1)
         torch.cuda.synchronize()
         self.handle = gs_create_scene(self._desc)
+
+    def _init_host(self, scene):
+        keep = [np.ascontiguousarray(scene[k], np.float32) for k in ("means", "scales", "quats", "opacities", "sh")]
+        f = scene.get("feats_bf16")
+        fb = None if f is None else np.ascontiguousarray(f, np.uint16)
+        po = np.ascontiguousarray(scene["partition_offsets"], np.int64)
+        self.n = int(keep[0].reshape(-1, 3).shape[0])
+        self.sh_degree = int(scene["sh_degree"])
+        self.feat_dim = 0 if fb is None else 32
+        self._desc = gs_scene_desc(self.n, self.sh_degree, self.feat_dim, *[k.ctypes.data for k in keep],
+                                   None if fb is None else fb.ctypes.data, len(po) - 1, po.ctypes.data, 0)
+        self.handle = gs_create_scene(self._desc)
+
+    def stream_stats(self):
+        return gs_scene_stream_stats(self.handle)
 
     def close(self):
         if getattr(self, "handle", None) is not None:

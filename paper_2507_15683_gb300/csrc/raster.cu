@@ -238,6 +238,26 @@ __device__ __forceinline__ bool ellipse_hits(float4 a, float C, float thr, float
   return best <= thr;
 }
 
+// Bit w set when the staged Gaussian can reach the floor in warp w's 8 x 4
+// block (ellipse_hits); a slightly widened bounding box of the ellipse rejects
+// most blocks first. Computed once per staged Gaussian by its staging thread.
+__device__ __forceinline__ uint32_t warp_hit_mask(float4 a, float C, float thr) {
+  if (!(thr > 0.0f)) return 0u;
+  const float A = a.z, B = a.w;
+  const float detq = A * C - B * B;
+  if (!(A > 0.0f) || !(C > 0.0f) || !(detq > 0.0f)) return 0xffu;
+  const float ex = sqrtf(thr * C / detq) * 1.0001f + 1e-3f, ey = sqrtf(thr * A / detq) * 1.0001f + 1e-3f;
+  uint32_t mask = 0u;
+#pragma unroll
+  for (int wv = 0; wv < kWarps; ++wv) {
+    const float x0 = (float)((wv & 1) * 8) + 0.5f, x1 = x0 + 7.0f;
+    const float y0 = (float)((wv >> 1) * 4) + 0.5f, y1 = y0 + 3.0f;
+    if (a.x + ex < x0 || a.x - ex > x1 || a.y + ey < y0 || a.y - ey > y1) continue;
+    if (ellipse_hits(a, C, thr, x0, x1, y0, y1)) mask |= 1u << wv;
+  }
+  return mask;
+}
+
 template <int FEAT>
 __global__ void __launch_bounds__(kTileThreads) k_composite(SceneDev sc, const View* __restrict__ views, int n_views,
                                                             Work w) {
@@ -248,7 +268,7 @@ __global__ void __launch_bounds__(kTileThreads) k_composite(SceneDev sc, const V
   float4* sa = reinterpret_cast<float4*>(smem_raw + kSmStage);
   float4* sb = sa + kBatchF;
   float4* scol = sb + kBatchF;
-  float* sthr = reinterpret_cast<float*>(scol + kBatchF);
+  uint32_t* smask = reinterpret_cast<uint32_t*>(scol + kBatchF);
   uint4* sf = reinterpret_cast<uint4*>(smem_raw + kSmFeat);  // FEAT: kBatchF x 4 (aliases hist)
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_tmp[kWarps];
@@ -257,7 +277,6 @@ __global__ void __launch_bounds__(kTileThreads) k_composite(SceneDev sc, const V
   int lx, ly, bxw, byw;
   warp_block(tid, lx, ly, bxw, byw);
   const float pxc = (float)lx + 0.5f, pyc = (float)ly + 0.5f;
-  const float wx0 = (float)bxw + 0.5f, wx1 = (float)bxw + 7.5f, wy0 = (float)byw + 0.5f, wy1 = (float)byw + 3.5f;
   for (;;) {
     if (tid == 0) s_tile = atomicAdd(&w.ctr->fwd_queue, 1u);
     __syncthreads();
@@ -312,7 +331,7 @@ __global__ void __launch_bounds__(kTileThreads) k_composite(SceneDev sc, const V
         sa[tid] = a;
         sb[tid] = bb;
         scol[tid] = cc;
-        sthr[tid] = floor_threshold(bb.y);
+        smask[tid] = warp_hit_mask(a, bb.x, floor_threshold(bb.y));
         if (FEAT) {
           const uint4* fp = sc.feat + (size_t)__float_as_int(bb.w) * 4;
 #pragma unroll
@@ -320,48 +339,54 @@ __global__ void __launch_bounds__(kTileThreads) k_composite(SceneDev sc, const V
         }
       }
       __syncthreads();
+      // blend one staged Gaussian (power and o exp(power) already evaluated) into
+      // this pixel; branch-free: the skip and stop decisions become predicates
+      auto blend = [&](int j, float p, float oe, float zj) {
+        const float alpha = fminf(kAlphaCap, oe);
+        const bool take = !done && !(p > 0.0f) && !(alpha < kAlphaFloor);
+        const float Tn = __fmul_rn(T, __fsub_rn(1.0f, alpha));
+        const bool stop = take && (Tn < kTCut);
+        const bool acc = take && !stop;
+        const float wgt = acc ? __fmul_rn(alpha, T) : 0.0f;
+        const float4 c = scol[j];
+        C0 = fmaf(wgt, c.x, C0);
+        C1 = fmaf(wgt, c.y, C1);
+        C2 = fmaf(wgt, c.z, C2);
+        D = fmaf(wgt, zj, D);
+        if (FEAT) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const uint4 fv = sf[j * 4 + q];
+            const uint32_t u4[4] = {fv.x, fv.y, fv.z, fv.w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              F[8 * q + 2 * h] = fmaf(wgt, __uint_as_float(u4[h] << 16), F[8 * q + 2 * h]);
+              F[8 * q + 2 * h + 1] = fmaf(wgt, __uint_as_float(u4[h] & 0xffff0000u), F[8 * q + 2 * h + 1]);
+            }
+          }
+        }
+        T = acc ? Tn : T;
+        last = acc ? (uint32_t)(bs + j + 1) : last;
+        done = done || stop;
+      };
+      const uint32_t wbit = 1u << (tid >> 5);
       bool wdone = __all_sync(0xffffffffu, done);
       for (int c0 = 0; c0 < bn && !wdone; c0 += 32) {
         const int jj = c0 + lane;
-        const bool hit = jj < bn && ellipse_hits(sa[jj], sb[jj].x, sthr[jj], wx0, wx1, wy0, wy1);
-        uint32_t m = __ballot_sync(0xffffffffu, hit);
-        while (m) {
-          const int j = c0 + __ffs(m) - 1;
+        uint32_t m = __ballot_sync(0xffffffffu, jj < bn && (smask[jj] & wbit));
+        while (m) {  // two hits per step: their exponentials overlap, blending stays in order
+          const int j1 = c0 + __ffs(m) - 1;
           m &= m - 1;
-          if (done) continue;
-          const float4 a = sa[j];
-          const float4 b = sb[j];
-          const float dx = __fsub_rn(a.x, pxc), dy = __fsub_rn(a.y, pyc);
-          const float power = gs_power(a.z, a.w, b.x, dx, dy);
-          if (power > 0.0f) continue;
-          const float oe = __fmul_rn(b.y, __expf(power));
-          const float alpha = fminf(kAlphaCap, oe);
-          if (alpha < kAlphaFloor) continue;
-          const float Tn = __fmul_rn(T, __fsub_rn(1.0f, alpha));
-          if (Tn < kTCut) {
-            done = true;
-            continue;
-          }
-          const float wgt = __fmul_rn(alpha, T);
-          const float4 c = scol[j];
-          C0 = fmaf(wgt, c.x, C0);
-          C1 = fmaf(wgt, c.y, C1);
-          C2 = fmaf(wgt, c.z, C2);
-          D = fmaf(wgt, b.z, D);
-          if (FEAT) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const uint4 fv = sf[j * 4 + q];
-              const uint32_t u4[4] = {fv.x, fv.y, fv.z, fv.w};
-#pragma unroll
-              for (int h = 0; h < 4; ++h) {
-                F[8 * q + 2 * h] = fmaf(wgt, __uint_as_float(u4[h] << 16), F[8 * q + 2 * h]);
-                F[8 * q + 2 * h + 1] = fmaf(wgt, __uint_as_float(u4[h] & 0xffff0000u), F[8 * q + 2 * h + 1]);
-              }
-            }
-          }
-          T = Tn;
-          last = (uint32_t)(bs + j + 1);
+          const bool two = m != 0u;
+          const int j2 = two ? c0 + __ffs(m) - 1 : j1;
+          if (two) m &= m - 1;
+          const float4 a1 = sa[j1], b1 = sb[j1], a2 = sa[j2], b2 = sb[j2];
+          const float p1 = gs_power(a1.z, a1.w, b1.x, __fsub_rn(a1.x, pxc), __fsub_rn(a1.y, pyc));
+          const float p2 = gs_power(a2.z, a2.w, b2.x, __fsub_rn(a2.x, pxc), __fsub_rn(a2.y, pyc));
+          const float oe1 = __fmul_rn(b1.y, __expf(p1));
+          const float oe2 = __fmul_rn(b2.y, __expf(p2));
+          blend(j1, p1, oe1, b1.z);
+          if (two) blend(j2, p2, oe2, b2.z);
         }
         wdone = __all_sync(0xffffffffu, done);
       }
@@ -397,7 +422,7 @@ __global__ void __launch_bounds__(kTileThreads) k_composite(SceneDev sc, const V
 // ---------------------------------------------------------------------------
 struct BwdSmem {
   float4 sa[kBatchB], sb[kBatchB], sc[kBatchB];
-  float sthr[kBatchB];
+  uint32_t smask[kBatchB];
   float4 sj[kBatchB * (kJacStride / 4)];
   double red[kWarps][8];
 };
@@ -413,7 +438,7 @@ __global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restric
   int lx, ly, bxw, byw;
   warp_block(tid, lx, ly, bxw, byw);
   const float pxc = (float)lx + 0.5f, pyc = (float)ly + 0.5f;
-  const float wx0 = (float)bxw + 0.5f, wx1 = (float)bxw + 7.5f, wy0 = (float)byw + 0.5f, wy1 = (float)byw + 3.5f;
+  const uint32_t wbit = 1u << wid;
   const float4* rec_j4 = reinterpret_cast<const float4*>(w.rec_j);
   for (;;) {
     if (tid == 0) s_tile = atomicAdd(&w.ctr->bwd_queue, 1u);
@@ -471,7 +496,7 @@ __global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restric
         S.sa[tid] = a;
         S.sb[tid] = bb;
         S.sc[tid] = cc;
-        S.sthr[tid] = floor_threshold(bb.y);
+        S.smask[tid] = warp_hit_mask(a, bb.x, floor_threshold(bb.y));
       }
       for (int q = tid; q < bn * (kJacStride / 4); q += kTileThreads) {
         const int jj = q / (kJacStride / 4), k = q % (kJacStride / 4);
@@ -480,58 +505,64 @@ __global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restric
       }
       __syncthreads();
       if ((uint32_t)bstart >= wm) continue;  // no pixel of this warp blended this far
-      for (int c0 = ((bn - 1) >> 5) << 5; c0 >= 0; c0 -= 32) {
-        const int jj = c0 + lane;
-        const bool hit = jj < bn && (uint32_t)(bstart + jj) < wm &&
-                         ellipse_hits(S.sa[jj], S.sb[jj].x, S.sthr[jj], wx0, wx1, wy0, wy1);
-        uint32_t m = __ballot_sync(0xffffffffu, hit);
-        while (m) {
-          const int bit = 31 - __clz(m);
-          m &= ~(1u << bit);
-          const int j = c0 + bit;
-          if (!inside || (uint32_t)(bstart + j) >= last) continue;
-          const float4 a = S.sa[j];
-          const float4 b = S.sb[j];
-          const float dx = __fsub_rn(a.x, pxc), dy = __fsub_rn(a.y, pyc);
-          const float power = gs_power(a.z, a.w, b.x, dx, dy);
-          if (power > 0.0f) continue;
-          const float oe = __fmul_rn(b.y, __expf(power));
-          const float alpha = fminf(kAlphaCap, oe);
-          if (alpha < kAlphaFloor) continue;
-          const float oma = 1.0f - alpha;
-          T = __fdividef(T, oma);  // transmittance in front of this Gaussian
-          const float wgt = alpha * T;
-          const float4 c = S.sc[j];
-          const float dLda = T * (gC0 * (c.x - acc0) + gC1 * (c.y - acc1) + gC2 * (c.z - acc2) + gD * (b.z - accD));
+      // one Gaussian, back to front: if this pixel blended it, step T and the
+      // running sums back and chain its 9 derivatives through the staged pose
+      // Jacobian (row-major 9 x 6, read as 12 float4). Branch-free: a pixel
+      // that skipped the Gaussian contributes zeros.
+      auto adjoint = [&](int j, float4 a, float4 b, float dx, float dy, float p, float oe, bool live) {
+        const float alpha = fminf(kAlphaCap, oe);
+        const bool take = live && !(p > 0.0f) && !(alpha < kAlphaFloor);
+        const float oma = 1.0f - alpha;
+        const float Tj = take ? __fdividef(T, oma) : T;  // transmittance in front of this Gaussian
+        const float wgt = take ? alpha * Tj : 0.0f;
+        const float4 c = S.sc[j];
+        const float dLda = Tj * (gC0 * (c.x - acc0) + gC1 * (c.y - acc1) + gC2 * (c.z - acc2) + gD * (b.z - accD));
+        if (take) {
           acc0 = fmaf(alpha, c.x, oma * acc0);
           acc1 = fmaf(alpha, c.y, oma * acc1);
           acc2 = fmaf(alpha, c.z, oma * acc2);
           accD = fmaf(alpha, b.z, oma * accD);
-          const float dpow = (oe < kAlphaCap) ? dLda * alpha : 0.0f;
-          const float gu = -dpow * (a.z * dx + a.w * dy);
-          const float gv = -dpow * (b.x * dy + a.w * dx);
-          const float gA = -0.5f * dpow * dx * dx;
-          const float gB = -dpow * dx * dy;
-          const float gCc = -0.5f * dpow * dy * dy;
-          const float gz = gD * wgt;
-          const float gr = gC0 * wgt, gg = gC1 * wgt, gb = gC2 * wgt;
-          const float* J = reinterpret_cast<const float*>(S.sj + j * (kJacStride / 4));
+        }
+        T = Tj;
+        const float dpow = (take && oe < kAlphaCap) ? dLda * alpha : 0.0f;
+        const float g[9] = {-dpow * (a.z * dx + a.w * dy), -dpow * (b.x * dy + a.w * dx), -0.5f * dpow * dx * dx,
+                            -dpow * dx * dy, -0.5f * dpow * dy * dy, gD * wgt, gC0 * wgt, gC1 * wgt, gC2 * wgt};
+        const float4* J4 = S.sj + j * (kJacStride / 4);
 #pragma unroll
-          for (int k = 0; k < 6; ++k) {
-            float s = xi[k];
-            s = fmaf(J[k], gu, s);
-            s = fmaf(J[6 + k], gv, s);
-            s = fmaf(J[12 + k], gA, s);
-            s = fmaf(J[18 + k], gB, s);
-            s = fmaf(J[24 + k], gCc, s);
-            s = fmaf(J[30 + k], gz, s);
-            if (k < 3) {
-              s = fmaf(J[36 + k], gr, s);
-              s = fmaf(J[39 + k], gg, s);
-              s = fmaf(J[42 + k], gb, s);
+        for (int q = 0; q < kJacStride / 4; ++q) {
+          const float4 v = J4[q];
+          const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int f = 4 * q + i;
+            if (f < 36) {
+              xi[f % 6] = fmaf(e[i], g[f / 6], xi[f % 6]);
+            } else if (f < 45) {
+              const int cf = f - 36;  // colour rows: rho only
+              xi[cf % 3] = fmaf(e[i], g[6 + cf / 3], xi[cf % 3]);
             }
-            xi[k] = s;
           }
+        }
+      };
+      for (int c0 = ((bn - 1) >> 5) << 5; c0 >= 0; c0 -= 32) {
+        const int jj = c0 + lane;
+        uint32_t m = __ballot_sync(0xffffffffu, jj < bn && (uint32_t)(bstart + jj) < wm && (S.smask[jj] & wbit));
+        while (m) {  // two hits per step, back to front
+          const int bit1 = 31 - __clz(m);
+          m &= ~(1u << bit1);
+          const bool two = m != 0u;
+          const int bit2 = two ? 31 - __clz(m) : bit1;
+          if (two) m &= ~(1u << bit2);
+          const int j1 = c0 + bit1, j2 = c0 + bit2;
+          const float4 a1 = S.sa[j1], b1 = S.sb[j1], a2 = S.sa[j2], b2 = S.sb[j2];
+          const float dx1 = __fsub_rn(a1.x, pxc), dy1 = __fsub_rn(a1.y, pyc);
+          const float dx2 = __fsub_rn(a2.x, pxc), dy2 = __fsub_rn(a2.y, pyc);
+          const float p1 = gs_power(a1.z, a1.w, b1.x, dx1, dy1);
+          const float p2 = gs_power(a2.z, a2.w, b2.x, dx2, dy2);
+          const float oe1 = __fmul_rn(b1.y, __expf(p1));
+          const float oe2 = __fmul_rn(b2.y, __expf(p2));
+          adjoint(j1, a1, b1, dx1, dy1, p1, oe1, inside && (uint32_t)(bstart + j1) < last);
+          if (two) adjoint(j2, a2, b2, dx2, dy2, p2, oe2, inside && (uint32_t)(bstart + j2) < last);
         }
       }
     }

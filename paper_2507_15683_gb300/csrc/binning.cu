@@ -50,6 +50,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(Work w) {
     w.tile_cursor[k] = (uint32_t)run;
     run += w.tile_count[k];
   }
+  // counters of the backward's chunked reduction start at zero every call
+  for (uint32_t k = threadIdx.x; k < w.n_chunks; k += kScanThreads) w.chunk_ctr[k] = 0u;
+  for (uint32_t k = threadIdx.x; k < w.n_views && w.n_chunks; k += kScanThreads) w.view_ctr[k] = 0u;
   if (threadIdx.x == kScanThreads - 1) {
     const unsigned long long total = run;
     w.tile_offset[n] = (uint32_t)total;

@@ -131,7 +131,7 @@ struct gs_scene {
   // workspace
   DevBuf rec_a, rec_b, rec_c, rec_m, rec_j;
   uint32_t rec_cap = 0, jac_cap = 0;
-  DevBuf tile_count, tile_offset, tile_cursor, partials;
+  DevBuf tile_count, tile_offset, tile_cursor, partials, chunks;
   uint32_t tile_cap = 0;
   DevBuf pairs, pairs_tmp;
   uint32_t pair_cap = 0;
@@ -189,6 +189,13 @@ Work work_of(gs_scene* s, uint32_t n_tiles) {
   w.pair_cap = s->pair_cap;
   w.ctr = dp<Counters>(s->ctr);
   w.partials = dp<double>(s->partials);
+  // chunk sums, then the chunk and view counters; one view has at least one
+  // tile, so tile_cap bounds both the chunk and the view count
+  w.chunk_part = dp<double>(s->chunks);
+  w.chunk_ctr = reinterpret_cast<uint32_t*>(w.chunk_part + (size_t)s->tile_cap * kPartialStride);
+  w.view_ctr = w.chunk_ctr + s->tile_cap;
+  w.n_chunks = 0;
+  w.n_views = 0;
   w.result = dp<double>(s->result);
   return w;
 }
@@ -227,6 +234,7 @@ gs_status grow_tiles(gs_scene* s, uint64_t n_tiles) {
     GS_TRY(ensure(s->tile_offset, cap * sizeof(uint32_t)));
     GS_TRY(ensure(s->tile_cursor, cap * sizeof(uint32_t)));
     GS_TRY(ensure(s->partials, cap * kPartialStride * sizeof(double)));
+    GS_TRY(ensure(s->chunks, cap * (kPartialStride * sizeof(double) + 2 * sizeof(uint32_t))));
     s->tile_cap = (uint32_t)cap;
   }
   return GS_OK;
@@ -254,6 +262,7 @@ gs_status build_views(gs_scene* s, int nv, const gs_camera* cams, const gs_pose*
                       const GradIn* g, std::vector<View>& hv, uint64_t& n_tiles) {
   hv.assign(nv, View{});
   n_tiles = 0;
+  uint32_t n_chunks = 0;
   uint64_t pix_total = 0;
   for (int v = 0; v < nv; ++v) {
     GS_TRY(check_cam(cams[v]));
@@ -292,7 +301,9 @@ gs_status build_views(gs_scene* s, int nv, const gs_camera* cams, const gs_pose*
     V.tiles_x = (c.width + kTile - 1) / kTile;
     V.tiles_y = (c.height + kTile - 1) / kTile;
     V.tile_base = (uint32_t)n_tiles;
+    V.chunk_base = n_chunks;
     n_tiles += (uint64_t)V.tiles_x * V.tiles_y;
+    n_chunks += (uint32_t)(((uint64_t)V.tiles_x * V.tiles_y + kChunkTiles - 1) / kChunkTiles);
     const gs_outputs o = outs ? outs[v] : gs_outputs{};
     const uint64_t P = (uint64_t)c.width * c.height;
     V.rgb = o.rgb;
@@ -357,6 +368,11 @@ gs_status enqueue(gs_scene* s, const std::vector<View>& hv, const std::vector<in
   }
   Work w = work_of(s, (uint32_t)n_tiles);
   w.ranges = dp<int4>(s->views);
+  if (g) {
+    const View& L = hv.back();
+    w.n_chunks = L.chunk_base + (uint32_t)(((uint64_t)L.tiles_x * L.tiles_y + kChunkTiles - 1) / kChunkTiles);
+    w.n_views = (uint32_t)nv;
+  }
   GS_CUDA(cudaMemsetAsync(w.tile_count, 0, (n_tiles + 1) * sizeof(uint32_t), st));
   GS_CUDA(cudaMemsetAsync(w.ctr, 0, sizeof(Counters), st));
   const SceneDev sc = scene_dev(s);
@@ -388,9 +404,7 @@ gs_status enqueue(gs_scene* s, const std::vector<View>& hv, const std::vector<in
   GS_CUDA(mark(5));
   if (g) {
     double* res = g->result ? g->result : w.result;
-    // one view: the last backward CTA reduces; several: one reduction CTA per view
-    GS_CUDA(launch_backward(dviews, nv, w, nv == 1 ? res : nullptr, s->sm_count * backward_blocks_per_sm(), st));
-    if (nv > 1) GS_CUDA(launch_reduce_views(dviews, nv, w, res, st));
+    GS_CUDA(launch_backward(dviews, nv, w, res, s->sm_count * backward_blocks_per_sm(), st));
     GS_CUDA(mark(6));
   }
   if (timed) s->ev_pending.push_back({std::move(ev), g ? GS_KERNEL_COUNT : GS_KERNEL_COUNT - 1});
@@ -843,7 +857,7 @@ void gs_destroy_scene(gs_scene* s) {
   for (auto& ev : s->ev_free)
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
   for (DevBuf* b : {&s->pos, &s->cov, &s->sh, &s->feat, &s->rec_a, &s->rec_b, &s->rec_c, &s->rec_m, &s->rec_j,
-                    &s->tile_count, &s->tile_offset, &s->tile_cursor, &s->partials, &s->pairs, &s->pairs_tmp,
+                    &s->tile_count, &s->tile_offset, &s->tile_cursor, &s->partials, &s->chunks, &s->pairs, &s->pairs_tmp,
                     &s->ctr, &s->result, &s->views, &s->int_pix})
     release(*b);
   for (void* h : {(void*)s->h_pos, (void*)s->h_cov, (void*)s->h_sh, (void*)s->h_feat})

@@ -16,6 +16,7 @@ constexpr int kBatchF = 256;       // Gaussians staged per forward batch
 constexpr int kBatchB = 128;       // Gaussians staged per backward batch
 constexpr int kJacStride = 48;     // floats per record of the pose Jacobian (45 used)
 constexpr int kPartialStride = 8;  // doubles per tile partial (loss + 6 grad + pad)
+constexpr int kChunkTiles = 64;    // tiles per first-level chunk of the fp64 pose reduction
 constexpr int kRecRegions = 64;    // record-allocation counters (block index mod 64)
 
 // Per-view parameters (device copy built on the host for every call).
@@ -30,7 +31,7 @@ struct View {
   float jb2;            // fx^2 (1 + limx^2) + fy^2 (1 + limy^2): bound on z^2 |J|_F^2
   int width, height, tiles_x, tiles_y;
   uint32_t tile_base;   // first global tile index of this view
-  uint32_t pad0;
+  uint32_t chunk_base;  // first reduction chunk (kChunkTiles tiles) of this view
   float* rgb;           // outputs (device; NULL = not written)
   float* depth;
   float* alpha;
@@ -57,9 +58,8 @@ struct Counters {
   unsigned int overflow;    // bit 0: records, bit 1: pairs, bit 2: pair count >= 2^32
   unsigned int fwd_queue;   // persistent forward tile queue
   unsigned int bwd_queue;   // persistent backward tile queue
-  unsigned int bwd_done;    // backward CTAs finished (the last one reduces)
   unsigned int error;       // device-side consistency failure
-  unsigned int pad[2];
+  unsigned int pad[3];
 };
 
 // Scene arena (device pointers).
@@ -92,6 +92,11 @@ struct Work {
   uint32_t pair_cap;
   Counters* ctr;
   double* partials;    // n_tiles * kPartialStride
+  double* chunk_part;  // n_chunks * kPartialStride: fp64 sums of kChunkTiles tile partials
+  uint32_t* chunk_ctr; // n_chunks: tiles of the chunk finished (zeroed by the scan)
+  uint32_t* view_ctr;  // n_views: chunks of the view finished (zeroed by the scan)
+  uint32_t n_chunks;
+  uint32_t n_views;
   double* result;      // 7 doubles (loss, grad)
   // Gaussian index ranges the projection walks (partitions in view):
   // ranges[0] = (count, total length, 0, 0), ranges[1 + k] = (begin, end, prefix, 0)
@@ -114,7 +119,6 @@ cudaError_t launch_composite(const SceneDev& sc, const View* views, int n_views,
                              int grid, cudaStream_t st);
 cudaError_t launch_backward(const View* views, int n_views, const Work& w, double* result, int grid,
                             cudaStream_t st);
-cudaError_t launch_reduce_views(const View* views, int n_views, const Work& w, double* result, cudaStream_t st);
 
 // occupancy-derived persistent grid sizes (per SM)
 int composite_blocks_per_sm(int feat_dim);

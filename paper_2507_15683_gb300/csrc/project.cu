@@ -496,10 +496,23 @@ __global__ void __launch_bounds__(256) k_shade(SceneDev sc, const View* __restri
         for (int k = 0; k < 3; ++k)
           jac[36 + 3 * ch + k] = clampc[ch] ? 0.0f : gp0 * R[3 * k] + gp1 * R[3 * k + 1] + gp2 * R[3 * k + 2];
       }
+      // stored tangent-major in pairs that match the adjoint's packed FMAs:
+      // per k: (du, dv), (dA, dB), (dC, dz); then per rho_k: (dr, dg); then db
+      float jt[48];
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+#pragma unroll
+        for (int r = 0; r < 6; ++r) jt[6 * k + r] = jac[6 * r + k];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        jt[36 + 2 * k] = jac[36 + k];
+        jt[37 + 2 * k] = jac[39 + k];
+        jt[42 + k] = jac[42 + k];
+      }
+      jt[45] = jt[46] = jt[47] = 0.0f;
       float4* jo = reinterpret_cast<float4*>(w.rec_j + (size_t)slot * kJacStride);
 #pragma unroll
-      for (int q = 0; q < 11; ++q) jo[q] = make_float4(jac[4 * q], jac[4 * q + 1], jac[4 * q + 2], jac[4 * q + 3]);
-      jo[11] = make_float4(jac[44], 0.f, 0.f, 0.f);
+      for (int q = 0; q < 12; ++q) jo[q] = make_float4(jt[4 * q], jt[4 * q + 1], jt[4 * q + 2], jt[4 * q + 3]);
     }
   }
 }

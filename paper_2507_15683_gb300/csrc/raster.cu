@@ -424,7 +424,7 @@ struct BwdSmem {
   float4 sa[kBatchB], sb[kBatchB], sc[kBatchB];
   uint32_t smask[kBatchB];
   float4 sj[kBatchB * (kJacStride / 4)];
-  double red[kWarps][8];
+  float red[kWarps][8];
 };
 
 __global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restrict__ views, int n_views, Work w,
@@ -433,6 +433,7 @@ __global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restric
   BwdSmem& S = *reinterpret_cast<BwdSmem*>(smem_raw);
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_max[kWarps];
+  __shared__ bool s_last;
   if (w.ctr->overflow) return;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   int lx, ly, bxw, byw;
@@ -458,7 +459,7 @@ __global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restric
 
     uint32_t last = 0;
     float T = 1.0f, gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f;
-    double loss = 0.0;
+    float loss = 0.0f;
     if (inside) {
       last = V.last_idx[p];
       T = V.final_T[p];
@@ -472,7 +473,7 @@ __global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restric
       gC1 = s3 * (float)((r1 > 0.f) - (r1 < 0.f));
       gC2 = s3 * (float)((r2 > 0.f) - (r2 < 0.f));
       gD = sd * (float)((e > 0.f) - (e < 0.f));
-      loss = (double)s3 * ((double)fabsf(r0) + (double)fabsf(r1) + (double)fabsf(r2)) + (double)sd * (double)fabsf(e);
+      loss = s3 * (fabsf(r0) + fabsf(r1) + fabsf(r2)) + sd * fabsf(e);
     }
     // longest list prefix any pixel of the tile (and of this warp) blended
     const uint32_t wm = __reduce_max_sync(0xffffffffu, last);
@@ -482,7 +483,11 @@ __global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restric
 #pragma unroll
     for (int k = 0; k < kWarps; ++k) max_last = max(max_last, s_max[k]);
 
-    float xi[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    // per-tangent partial sums: .x and .y take different Jacobian rows and are
+    // added at the end
+    float2 xi2[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) xi2[k] = make_float2(0.f, 0.f);
     float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, accD = 0.f;
     for (int bend = (int)max_last; bend > 0; bend -= kBatchB) {
       const int bstart = max(0, bend - kBatchB);
@@ -525,21 +530,31 @@ __global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restric
         }
         T = Tj;
         const float dpow = (take && oe < kAlphaCap) ? dLda * alpha : 0.0f;
-        const float g[9] = {-dpow * (a.z * dx + a.w * dy), -dpow * (b.x * dy + a.w * dx), -0.5f * dpow * dx * dx,
-                            -dpow * dx * dy, -0.5f * dpow * dy * dy, gD * wgt, gC0 * wgt, gC1 * wgt, gC2 * wgt};
+        // the nine sensitivities in pairs; each packed FMA takes one pair
+        // against the matching Jacobian pair of one tangent direction
+        const float2 g01 = make_float2(-dpow * (a.z * dx + a.w * dy), -dpow * (b.x * dy + a.w * dx));
+        const float2 g23 = make_float2(-0.5f * dpow * dx * dx, -dpow * dx * dy);
+        const float2 g45 = make_float2(-0.5f * dpow * dy * dy, gD * wgt);
+        const float2 g67 = make_float2(gC0 * wgt, gC1 * wgt);
+        const float g8 = gC2 * wgt;
         const float4* J4 = S.sj + j * (kJacStride / 4);
 #pragma unroll
         for (int q = 0; q < kJacStride / 4; ++q) {
           const float4 v = J4[q];
-          const float e[4] = {v.x, v.y, v.z, v.w};
+          const float2 e[2] = {make_float2(v.x, v.y), make_float2(v.z, v.w)};
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int f = 4 * q + i;
-            if (f < 36) {
-              xi[f % 6] = fmaf(e[i], g[f / 6], xi[f % 6]);
-            } else if (f < 45) {
-              const int cf = f - 36;  // colour rows: rho only
-              xi[cf % 3] = fmaf(e[i], g[6 + cf / 3], xi[cf % 3]);
+          for (int i = 0; i < 2; ++i) {
+            const int pr = 2 * q + i;  // pair index
+            if (pr < 18) {
+              const float2 gg = (pr % 3 == 0) ? g01 : (pr % 3 == 1) ? g23 : g45;
+              xi2[pr / 3] = __ffma2_rn(e[i], gg, xi2[pr / 3]);
+            } else if (pr < 21) {
+              xi2[pr - 18] = __ffma2_rn(e[i], g67, xi2[pr - 18]);
+            } else if (pr == 21) {  // floats 42, 43: d blue / d rho_0, rho_1
+              xi2[0].x = fmaf(e[i].x, g8, xi2[0].x);
+              xi2[1].x = fmaf(e[i].y, g8, xi2[1].x);
+            } else if (pr == 22) {  // float 44: d blue / d rho_2
+              xi2[2].x = fmaf(e[i].x, g8, xi2[2].x);
             }
           }
         }
@@ -566,8 +581,13 @@ __global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restric
         }
       }
     }
-    // fp64 reduction of (loss, xi) over the tile's pixels
-    double v[7] = {loss, (double)xi[0], (double)xi[1], (double)xi[2], (double)xi[3], (double)xi[4], (double)xi[5]};
+    // (loss, xi) of the tile in fp32: a fixed tree over each warp's lanes, then
+    // the warps in order. GB300 runs fp64 at 1/64 of the fp32 rate, so fp64
+    // starts at the tile sums.
+    float v[7];
+    v[0] = loss;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[1 + k] = xi2[k].x + xi2[k].y;
 #pragma unroll
     for (int k = 0; k < 7; ++k) {
 #pragma unroll
@@ -579,75 +599,49 @@ __global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restric
     }
     __syncthreads();
     if (tid < 7) {
-      double s = 0.0;
+      float t = S.red[0][tid];
 #pragma unroll
-      for (int k = 0; k < kWarps; ++k) s += S.red[k][tid];
-      w.partials[(size_t)tile * kPartialStride + tid] = s;
+      for (int k = 1; k < kWarps; ++k) t += S.red[k][tid];
+      w.partials[(size_t)tile * kPartialStride + tid] = (double)t;
+      __threadfence();
     }
     __syncthreads();
-  }
-  if (!result) return;  // several views: k_reduce_views sums per view
-  // The last CTA to finish sums the per-tile partials in a fixed order
-  // (deterministic): thread t takes tiles t, t + 256, ..., then a fixed tree.
-  __shared__ bool s_last;
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) s_last = atomicAdd(&w.ctr->bwd_done, 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  double v[7] = {0, 0, 0, 0, 0, 0, 0};
-  for (uint32_t t = tid; t < w.n_tiles; t += kTileThreads) {
+    // Deterministic fp64 reduction in two fixed levels, done by whichever CTA
+    // finishes the last tile of a chunk (kChunkTiles tiles of one view) and
+    // then the last chunk of the view: the order depends only on tile indices,
+    // so a view gives the same bits alone or inside a batch.
+    const uint32_t nt = (uint32_t)V.tiles_x * (uint32_t)V.tiles_y;
+    const uint32_t chunk = lt / kChunkTiles, c0 = chunk * kChunkTiles;
+    const uint32_t cn = min((uint32_t)kChunkTiles, nt - c0);
+    if (tid == 0) s_last = atomicAdd(&w.chunk_ctr[V.chunk_base + chunk], 1u) == cn - 1u;
+    __syncthreads();
+    if (!s_last) continue;
+    __threadfence();
+    if (wid < 7) {  // warp k sums component k; lanes take tiles lane and lane + 32
+      const double* src = w.partials + (size_t)(V.tile_base + c0) * kPartialStride + wid;
+      double x = (uint32_t)lane < cn ? __ldcg(src + (size_t)lane * kPartialStride) : 0.0;
+      if ((uint32_t)lane + 32u < cn) x += __ldcg(src + (size_t)(lane + 32) * kPartialStride);
 #pragma unroll
-    for (int k = 0; k < 7; ++k) v[k] += __ldcg(w.partials + (size_t)t * kPartialStride + k);
-  }
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if (lane == 0) {
+        w.chunk_part[(size_t)(V.chunk_base + chunk) * kPartialStride + wid] = x;
+        __threadfence();
+      }
+    }
+    __syncthreads();
+    const uint32_t ncv = (nt + kChunkTiles - 1) / kChunkTiles;
+    if (tid == 0) s_last = atomicAdd(&w.view_ctr[vi], 1u) == ncv - 1u;
+    __syncthreads();
+    if (!s_last) continue;
+    __threadfence();
+    if (wid < 7) {
+      double x = 0.0;
+      for (uint32_t c = lane; c < ncv; c += 32)
+        x += __ldcg(w.chunk_part + (size_t)(V.chunk_base + c) * kPartialStride + wid);
 #pragma unroll
-  for (int k = 0; k < 7; ++k) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-  }
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < 7; ++k) S.red[wid][k] = v[k];
-  }
-  __syncthreads();
-  if (tid < 7) {
-    double s = 0.0;
-#pragma unroll
-    for (int k = 0; k < kWarps; ++k) s += S.red[k][tid];
-    result[tid] = s;
-  }
-}
-
-// Per-view fp64 sums of the per-tile partials, one CTA per view, in the same
-// fixed order as the single-view reduction (so one view of a batch gives
-// bit-identical results to a single-view call). result: 8 doubles per view.
-__global__ void __launch_bounds__(kTileThreads) k_reduce_views(const View* __restrict__ views, Work w,
-                                                               double* __restrict__ result) {
-  __shared__ double red[kWarps][8];
-  const View& V = views[blockIdx.x];
-  const uint32_t nt = (uint32_t)V.tiles_x * (uint32_t)V.tiles_y;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  double v[7] = {0, 0, 0, 0, 0, 0, 0};
-  for (uint32_t t = tid; t < nt; t += kTileThreads) {
-#pragma unroll
-    for (int k = 0; k < 7; ++k) v[k] += w.partials[(size_t)(V.tile_base + t) * kPartialStride + k];
-  }
-#pragma unroll
-  for (int k = 0; k < 7; ++k) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-  }
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < 7; ++k) red[wid][k] = v[k];
-  }
-  __syncthreads();
-  if (tid < 7) {
-    double s = 0.0;
-#pragma unroll
-    for (int k = 0; k < kWarps; ++k) s += red[k][tid];
-    result[(size_t)blockIdx.x * 8 + tid] = s;
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if (lane == 0) result[(size_t)vi * kPartialStride + wid] = x;
+    }
   }
 }
 
@@ -697,11 +691,6 @@ cudaError_t launch_composite(const SceneDev& sc, const View* views, int n_views,
     composite_occ<0>();
     k_composite<0><<<g, kTileThreads, composite_smem<0>(), st>>>(sc, views, n_views, w);
   }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_reduce_views(const View* views, int n_views, const Work& w, double* result, cudaStream_t st) {
-  k_reduce_views<<<n_views, kTileThreads, 0, st>>>(views, w, result);
   return cudaGetLastError();
 }
 

@@ -305,7 +305,7 @@ def main():
     fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FMA = 2
     dom = max(per_kernel, key=per_kernel.get)
     kernels = {k: {"ms": v, "share": v / max(sum(per_kernel.values()), 1e-12)} for k, v in per_kernel.items()}
-    if dom in ("sort_composite", "backward"):
+    if dom in ("composite", "backward"):
         ach = evals * FLOPS_PER_EVAL / (per_kernel[dom] * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
                 "traffic": None, "kernel": dom,

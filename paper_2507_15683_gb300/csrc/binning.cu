@@ -128,7 +128,126 @@ __global__ void __launch_bounds__(256) k_scatter(const View* __restrict__ views,
   }
 }
 
+// Depth order of the short tile lists, one warp per tile: a bitonic network
+// over E elements per lane (element e = E lane + i sits in register i), with
+// compare-exchanges inside a lane for strides below E and across lanes by
+// shuffles above. Elements are packed as (depth bits << 32 | record), compared
+// as 64-bit integers with branch-free min/max; the record part only makes the
+// keys distinct. Runs of equal depth are then put in Gaussian-index order (the
+// tie-break of the key), which happens rarely. Lists longer than kWarpSortMax
+// are left to the compositor's block sort.
+__device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("min.u64 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("max.u64 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+
+template <int E>
+__device__ void warp_sort_list(uint2* __restrict__ list, int n, const float4* __restrict__ rec_b, int lane) {
+  uint64_t x[E];
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    const int e = lane * E + i;
+    const uint2 p = e < n ? list[e] : make_uint2(0xffffffffu, 0xffffffffu);  // pads sort last
+    x[i] = ((uint64_t)p.x << 32) | p.y;
+  }
+#pragma unroll
+  for (int size = 2; size <= 32 * E; size <<= 1) {
+#pragma unroll
+    for (int j = size >> 1; j > 0; j >>= 1) {
+      if (j >= E) {  // partner: lane ^ (j / E), same register
+        const int lj = j / E;
+        // ascending blocks: the lower element keeps the minimum
+        const bool keep_min = ((lane & lj) == 0) == (((lane * E) & size) == 0);
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+          const uint64_t o = __shfl_xor_sync(0xffffffffu, x[i], lj);
+          const uint64_t mn = umin64(x[i], o), mx = umax64(x[i], o);
+          x[i] = keep_min ? mn : mx;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+          if (i & j) continue;
+          const int q = i | j;
+          const bool up = ((lane * E + i) & size) == 0;
+          const uint64_t mn = umin64(x[i], x[q]), mx = umax64(x[i], x[q]);
+          x[i] = up ? mn : mx;
+          x[q] = up ? mx : mn;
+        }
+      }
+    }
+  }
+  uint32_t k[E];
+#pragma unroll
+  for (int i = 0; i < E; ++i) k[i] = (uint32_t)(x[i] >> 32);
+  uint32_t v[E];
+#pragma unroll
+  for (int i = 0; i < E; ++i) v[i] = (uint32_t)x[i];
+  bool tie = false;
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    const int e = lane * E + i;
+    if (e < n) list[e] = make_uint2(k[i], v[i]);
+    if (i + 1 < E) tie = tie || (e + 1 < n && k[i] == k[i + 1]);
+  }
+  const uint32_t nxt = __shfl_down_sync(0xffffffffu, k[0], 1);
+  const uint32_t prv = __shfl_up_sync(0xffffffffu, k[E - 1], 1);
+  tie = tie || (lane < 31 && lane * E + E < n && k[E - 1] == nxt);
+  if (!__any_sync(0xffffffffu, tie)) return;
+  __syncwarp();
+  // the owner of the first element of each run of equal depth puts the run in
+  // Gaussian-index order (runs are short: equal binary32 depths are rare)
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    const int e = lane * E + i;
+    const uint32_t before = i > 0 ? k[i > 0 ? i - 1 : 0] : prv;
+    const uint32_t after = i + 1 < E ? k[i + 1 < E ? i + 1 : 0] : nxt;
+    if (e + 1 < n && after == k[i] && (e == 0 || before != k[i])) {
+      int end = e + 1;
+      while (end < n && list[end].x == k[i]) ++end;
+      for (int p = e + 1; p < end; ++p) {
+        const uint2 x = list[p];
+        const int gx = __float_as_int(rec_b[x.y].w);
+        int q = p - 1;
+        while (q >= e && __float_as_int(rec_b[list[q].y].w) > gx) {
+          list[q + 1] = list[q];
+          --q;
+        }
+        list[q + 1] = x;
+      }
+    }
+  }
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(256) k_sort_tiles(Work w) {
+  if (w.ctr->overflow) return;
+  const int lane = threadIdx.x & 31;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t tile = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < w.n_tiles; tile += nw) {
+    const uint32_t start = w.tile_offset[tile];
+    const int n = (int)(w.tile_offset[tile + 1] - start);
+    if (n <= 1 || n > kWarpSortMax) continue;  // warp-uniform
+    uint2* list = w.pairs + start;
+    if (n <= 32) warp_sort_list<1>(list, n, w.rec_b, lane);
+    else if (n <= 64) warp_sort_list<2>(list, n, w.rec_b, lane);
+    else if (n <= 128) warp_sort_list<4>(list, n, w.rec_b, lane);
+    else warp_sort_list<8>(list, n, w.rec_b, lane);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_sort_tiles(const Work& w, int grid, cudaStream_t st) {
+  k_sort_tiles<<<grid, 256, 0, st>>>(w);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_scan_tiles(const Work& w, cudaStream_t st) {
   k_scan_tiles<<<1, kScanThreads, 0, st>>>(w);

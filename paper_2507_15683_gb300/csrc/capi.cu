@@ -397,15 +397,17 @@ gs_status enqueue(gs_scene* s, const std::vector<View>& hv, const std::vector<in
   GS_CUDA(mark(3));
   GS_CUDA(launch_scatter(dviews, w, s->sm_count * 8, st));
   GS_CUDA(mark(4));
+  GS_CUDA(launch_sort_tiles(w, s->sm_count * 8, st));
+  GS_CUDA(mark(5));
   bool feats = false;
   for (const View& V : hv) feats = feats || V.feats != nullptr;
   GS_CUDA(launch_composite(sc, dviews, nv, w, feats, s->sm_count * composite_blocks_per_sm(feats ? s->feat_dim : 0),
                            st));
-  GS_CUDA(mark(5));
+  GS_CUDA(mark(6));
   if (g) {
     double* res = g->result ? g->result : w.result;
     GS_CUDA(launch_backward(dviews, nv, w, res, s->sm_count * backward_blocks_per_sm(), st));
-    GS_CUDA(mark(6));
+    GS_CUDA(mark(7));
   }
   if (timed) s->ev_pending.push_back({std::move(ev), g ? GS_KERNEL_COUNT : GS_KERNEL_COUNT - 1});
   s->last_views = hv;

@@ -16,7 +16,8 @@ constexpr int kBatchF = 256;       // Gaussians staged per forward batch
 constexpr int kBatchB = 128;       // Gaussians staged per backward batch
 constexpr int kJacStride = 48;     // floats per record of the pose Jacobian (45 used)
 constexpr int kPartialStride = 8;  // doubles per tile partial (loss + 6 grad + pad)
-constexpr int kChunkTiles = 64;    // tiles per first-level chunk of the fp64 pose reduction
+constexpr int kChunkTiles = 64;
+constexpr int kWarpSortMax = 256;  // longest tile list sorted by one warp (registers)    // tiles per first-level chunk of the fp64 pose reduction
 constexpr int kRecRegions = 64;    // record-allocation counters (block index mod 64)
 
 // Per-view parameters (device copy built on the host for every call).
@@ -113,6 +114,7 @@ cudaError_t launch_project(const SceneDev& sc, const View* views, int n_views, c
 cudaError_t launch_shade(const SceneDev& sc, const View* views, const Work& w, bool grad, int grid,
                          cudaStream_t st);
 cudaError_t launch_scan_tiles(const Work& w, cudaStream_t st);
+cudaError_t launch_sort_tiles(const Work& w, int grid, cudaStream_t st);
 cudaError_t launch_scatter(const View* views, const Work& w, int grid, cudaStream_t st);
 // feats: some view writes the feature map (else the feature-free kernel runs)
 cudaError_t launch_composite(const SceneDev& sc, const View* views, int n_views, const Work& w, bool feats,

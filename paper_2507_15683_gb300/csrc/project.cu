@@ -496,13 +496,23 @@ __global__ void __launch_bounds__(256) k_shade(SceneDev sc, const View* __restri
         for (int k = 0; k < 3; ++k)
           jac[36 + 3 * ch + k] = clampc[ch] ? 0.0f : gp0 * R[3 * k] + gp1 * R[3 * k + 1] + gp2 * R[3 * k + 2];
       }
-      // stored tangent-major in pairs that match the adjoint's packed FMAs:
-      // per k: (du, dv), (dA, dB), (dC, dz); then per rho_k: (dr, dg); then db
+      // Stored tangent-major in pairs that match the adjoint's packed FMAs.
+      // With q = -dL/dpower and d = pixel - centre offset (dx, dy), the
+      // geometric part of one pixel's contribution is
+      //   q dx (A du + B dv) + q dy (B du + C dv) + q dx^2 dA/2 + q dx dy dB
+      //   + q dy^2 dC/2 + (dL/dz) dz,
+      // so per k: (A du + B dv, B du + C dv), (dA / 2, dB), (dC / 2, dz); then
+      // per rho_k: (dr, dg); then db.
       float jt[48];
 #pragma unroll
-      for (int k = 0; k < 6; ++k)
-#pragma unroll
-        for (int r = 0; r < 6; ++r) jt[6 * k + r] = jac[6 * r + k];
+      for (int k = 0; k < 6; ++k) {
+        jt[6 * k + 0] = A * jac[k] + B * jac[6 + k];
+        jt[6 * k + 1] = B * jac[k] + C * jac[6 + k];
+        jt[6 * k + 2] = 0.5f * jac[12 + k];
+        jt[6 * k + 3] = jac[18 + k];
+        jt[6 * k + 4] = 0.5f * jac[24 + k];
+        jt[6 * k + 5] = jac[30 + k];
+      }
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         jt[36 + 2 * k] = jac[36 + k];

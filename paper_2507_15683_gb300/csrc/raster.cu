@@ -289,9 +289,12 @@ __global__ void __launch_bounds__(kTileThreads) k_composite(SceneDev sc, const V
     const uint32_t start = w.tile_offset[tile];
     const int n = (int)(w.tile_offset[tile + 1] - start);
 
-    // ---- depth order of the tile's list ----
+    // ---- depth order of the tile's list (short lists: already sorted by
+    // the warp sort that ran before this kernel) ----
     const uint2* list;
-    if (n <= kSortCap) {
+    if (n <= kWarpSortMax) {
+      list = w.pairs + start;
+    } else if (n <= kSortCap) {
       for (int i = tid; i < n; i += kTileThreads) bufA[i] = w.pairs[start + i];
       __syncthreads();
       const uint2* sorted = sort_tile(bufA, bufB, n, hist, s_tmp, w.rec_b);
@@ -488,7 +491,7 @@ __global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restric
     float2 xi2[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) xi2[k] = make_float2(0.f, 0.f);
-    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, accD = 0.f;
+    float sdot = 0.f;
     for (int bend = (int)max_last; bend > 0; bend -= kBatchB) {
       const int bstart = max(0, bend - kBatchB);
       const int bn = bend - bstart;
@@ -511,30 +514,29 @@ __global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restric
       __syncthreads();
       if ((uint32_t)bstart >= wm) continue;  // no pixel of this warp blended this far
       // one Gaussian, back to front: if this pixel blended it, step T and the
-      // running sums back and chain its 9 derivatives through the staged pose
-      // Jacobian (row-major 9 x 6, read as 12 float4). Branch-free: a pixel
-      // that skipped the Gaussian contributes zeros.
+      // running sum back and chain its 9 sensitivities through the staged pose
+      // Jacobian (48 floats in tangent-major pairs, read as 12 float4).
+      // Branch-free: a pixel that skipped the Gaussian contributes zeros.
       auto adjoint = [&](int j, float4 a, float4 b, float dx, float dy, float p, float oe, bool live) {
         const float alpha = fminf(kAlphaCap, oe);
         const bool take = live && !(p > 0.0f) && !(alpha < kAlphaFloor);
-        const float oma = 1.0f - alpha;
-        const float Tj = take ? __fdividef(T, oma) : T;  // transmittance in front of this Gaussian
+        const float Tj = take ? __fdividef(T, 1.0f - alpha) : T;  // transmittance in front of this Gaussian
         const float wgt = take ? alpha * Tj : 0.0f;
         const float4 c = S.sc[j];
-        const float dLda = Tj * (gC0 * (c.x - acc0) + gC1 * (c.y - acc1) + gC2 * (c.z - acc2) + gD * (b.z - accD));
-        if (take) {
-          acc0 = fmaf(alpha, c.x, oma * acc0);
-          acc1 = fmaf(alpha, c.y, oma * acc1);
-          acc2 = fmaf(alpha, c.z, oma * acc2);
-          accD = fmaf(alpha, b.z, oma * accD);
-        }
+        // dL/dalpha = Tj (g . (c, z) - g . acc), where acc, the normalised
+        // colour and depth behind this Gaussian, follows acc <- alpha (c, z) +
+        // (1 - alpha) acc; only its projection sdot = g . acc is needed
+        const float gc = fmaf(gC0, c.x, fmaf(gC1, c.y, fmaf(gC2, c.z, gD * b.z)));
+        const float d = gc - sdot;
+        sdot = fmaf(take ? alpha : 0.0f, d, sdot);
         T = Tj;
-        const float dpow = (take && oe < kAlphaCap) ? dLda * alpha : 0.0f;
+        const float q = (take && oe < kAlphaCap) ? -(Tj * d) * alpha : 0.0f;  // -dL/dpower
+        const float dxq = q * dx, dyq = q * dy;
         // the nine sensitivities in pairs; each packed FMA takes one pair
         // against the matching Jacobian pair of one tangent direction
-        const float2 g01 = make_float2(-dpow * (a.z * dx + a.w * dy), -dpow * (b.x * dy + a.w * dx));
-        const float2 g23 = make_float2(-0.5f * dpow * dx * dx, -dpow * dx * dy);
-        const float2 g45 = make_float2(-0.5f * dpow * dy * dy, gD * wgt);
+        const float2 g01 = make_float2(dxq, dyq);
+        const float2 g23 = make_float2(dxq * dx, dxq * dy);
+        const float2 g45 = make_float2(dyq * dy, gD * wgt);
         const float2 g67 = make_float2(gC0 * wgt, gC1 * wgt);
         const float g8 = gC2 * wgt;
         const float4* J4 = S.sj + j * (kJacStride / 4);

@@ -189,3 +189,26 @@ def test_batched_pose_gradient_equals_single_views(oracle, gsr):
         assert float(res[v, 0]) == l1
         np.testing.assert_array_equal(res[v, 1:7].cpu().numpy(), g1)
     S.close()
+
+
+@pytest.mark.parametrize("n", [2, 20, 50, 100, 200, 256])
+def test_short_lists_with_equal_depths(oracle, gsr, n):
+    # n small Gaussians inside one 16 x 16 tile on three exact depth planes: the
+    # warp sort must give ascending depth bits with ties in Gaussian-index order
+    g = synth.rng(50 + n)
+    z = g.choice([4.0, 5.0, 6.5], n)
+    means = np.stack([g.uniform(-0.02, 0.02, n) * z, g.uniform(-0.02, 0.02, n) * z, z], 1)
+    scene = scene_of(means, np.full((n, 3), 0.002), opacities=g.uniform(0.05, 0.3, n), dc=g.uniform(0, 1, (n, 3)))
+    cam = synth.camera(64, 64, 300.0)
+    S = gsr.Scene(scene)
+    out = S.render(cam, np.eye(4))
+    cov = oracle.cov3d_f32(scene["scales"], scene["quats"])
+    ri, rf = oracle.project_f32(scene["means"], cov, cam, np.eye(4))
+    ts, keys, gids = oracle.bin_tiles(ri, rf, cam)
+    assert np.diff(ts).max() <= 256
+    gts, gkeys, ggids = S.tile_lists(0, cam, len(keys) + 8)
+    np.testing.assert_array_equal(gts, ts)
+    np.testing.assert_array_equal(gkeys, keys)
+    np.testing.assert_array_equal(ggids, gids)
+    compare_images(to_numpy(out, 64, 64), oracle.render(scene, cam, np.eye(4), geom64=True), oracle)
+    S.close()

@@ -305,7 +305,7 @@ def main():
     fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FMA = 2
     dom = max(per_kernel, key=per_kernel.get)
     kernels = {k: {"ms": v, "share": v / max(sum(per_kernel.values()), 1e-12)} for k, v in per_kernel.items()}
-    if dom in ("composite", "backward"):
+    if dom == "composite":
         ach = evals * FLOPS_PER_EVAL / (per_kernel[dom] * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
                 "traffic": None, "kernel": dom,
@@ -354,7 +354,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(scene, cam, T_ref, T_q, args.cpu_seconds)
 
-    launches_per_step = 6  # project, shade, scan, scatter, sort+composite, backward (+ final reduction)
+    launches_per_step = 6  # project, shade, scan, scatter, sort, composite (tangent pass + reduction)
     value = world * P / (ms_grad * 1e-3) / 1e6
     line = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,

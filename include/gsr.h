@@ -266,9 +266,10 @@ gs_status gs_scene_evict(gs_scene* scene);
 /* Kernel timing (CUDA events recorded on the call's stream around every
  * launch of every call while enabled). Kernel order of the arrays below:
  * projection (discrete layer), shading (conic, colour, centre, Jacobian),
- * tile scan, scatter, warp sort of the short tile lists, composite (with the
- * block sort of longer lists), backward (with the fp64 pose reduction). */
-#define GS_KERNEL_COUNT 7
+ * tile scan, scatter, warp sort of the short tile lists, compositing (block
+ * sort of longer lists, blending, and for the pose gradient the tangent pass
+ * with the fp64 reduction). */
+#define GS_KERNEL_COUNT 6
 gs_status gs_scene_set_timing(gs_scene* scene, int enable);
 
 /* Wait for the recorded calls and return, per kernel, the summed device time

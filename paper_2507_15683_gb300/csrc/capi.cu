@@ -138,7 +138,6 @@ struct gs_scene {
   DevBuf ctr, result, views;
   Counters* ctr_host = nullptr;
   double* result_host = nullptr;
-  DevBuf int_pix;  // internal per-pixel buffers (pose gradient without user outputs)
   // kernel timing: one set of GS_KERNEL_COUNT + 1 events per timed call
   bool timing = false;
   struct TimedCall {
@@ -256,23 +255,17 @@ gs_status check_pose(const gs_pose& p) {
   return GS_OK;
 }
 
-// Build the per-view device parameters. `pix_off` receives each view's offset
-// into the internal per-pixel buffers (used only when need_internal).
+// Build the per-view device parameters (outputs the caller did not ask for
+// are not written; the pose gradient needs none of them).
 gs_status build_views(gs_scene* s, int nv, const gs_camera* cams, const gs_pose* poses, const gs_outputs* outs,
                       const GradIn* g, std::vector<View>& hv, uint64_t& n_tiles) {
   hv.assign(nv, View{});
   n_tiles = 0;
   uint32_t n_chunks = 0;
-  uint64_t pix_total = 0;
   for (int v = 0; v < nv; ++v) {
     GS_TRY(check_cam(cams[v]));
     GS_TRY(check_pose(poses[v]));
-    pix_total += (uint64_t)cams[v].width * cams[v].height;
   }
-  const bool need_internal = g != nullptr;
-  if (need_internal) GS_TRY(ensure(s->int_pix, pix_total * 6 * sizeof(float)));
-  float* ib = dp<float>(s->int_pix);
-  uint64_t pix_off = 0;
   for (int v = 0; v < nv; ++v) {
     const gs_camera& c = cams[v];
     const double* T = poses[v].T_cw;
@@ -312,12 +305,7 @@ gs_status build_views(gs_scene* s, int nv, const gs_camera* cams, const gs_pose*
     V.final_T = o.final_T;
     V.feats = s->feat_dim ? o.feats : nullptr;
     V.last_idx = o.last_idx;
-    if (need_internal) {
-      float* base = ib + pix_off * 6;
-      if (!V.rgb) V.rgb = base;
-      if (!V.depth) V.depth = base + 3 * P;
-      if (!V.final_T) V.final_T = base + 4 * P;
-      if (!V.last_idx) V.last_idx = reinterpret_cast<uint32_t*>(base + 5 * P);
+    if (g) {
       V.target_rgb = g->target_rgb[v];
       V.target_depth = g->target_depth[v];
       V.pixel_weight = g->pixel_weight ? g->pixel_weight[v] : nullptr;
@@ -325,7 +313,6 @@ gs_status build_views(gs_scene* s, int nv, const gs_camera* cams, const gs_pose*
       V.inv_3p = (float)(1.0 / (3.0 * (double)P));
       V.inv_p = (float)(1.0 / (double)P);
     }
-    pix_off += P;
   }
   if (n_tiles >= 0x7fffffffull) return fail(GS_ERR_INVALID_ARG, "too many tiles in one call");
   return GS_OK;
@@ -401,15 +388,17 @@ gs_status enqueue(gs_scene* s, const std::vector<View>& hv, const std::vector<in
   GS_CUDA(mark(5));
   bool feats = false;
   for (const View& V : hv) feats = feats || V.feats != nullptr;
-  GS_CUDA(launch_composite(sc, dviews, nv, w, feats, s->sm_count * composite_blocks_per_sm(feats ? s->feat_dim : 0),
-                           st));
-  GS_CUDA(mark(6));
+  if (!g || feats)
+    GS_CUDA(launch_composite(sc, dviews, nv, w, feats,
+                             s->sm_count * composite_blocks_per_sm(feats ? s->feat_dim : 0, false), st));
   if (g) {
+    // the tangent pass re-renders the same values (without features) and adds
+    // the loss and its pose gradient
     double* res = g->result ? g->result : w.result;
-    GS_CUDA(launch_backward(dviews, nv, w, res, s->sm_count * backward_blocks_per_sm(), st));
-    GS_CUDA(mark(7));
+    GS_CUDA(launch_composite_tangent(sc, dviews, nv, w, res, s->sm_count * composite_blocks_per_sm(0, true), st));
   }
-  if (timed) s->ev_pending.push_back({std::move(ev), g ? GS_KERNEL_COUNT : GS_KERNEL_COUNT - 1});
+  GS_CUDA(mark(6));
+  if (timed) s->ev_pending.push_back({std::move(ev), GS_KERNEL_COUNT});
   s->last_views = hv;
   s->last_tiles = (uint32_t)n_tiles;
   return GS_OK;
@@ -838,8 +827,8 @@ gs_status gs_create_scene(const gs_scene_desc* d, gs_scene** out) {
     if (e != cudaSuccess) return cleanup(fail(GS_ERR_CUDA, std::string("pack: ") + cudaGetErrorString(e)));
   }
   // occupancy queries outside any stream capture
-  composite_blocks_per_sm(s->feat_dim);
-  backward_blocks_per_sm();
+  composite_blocks_per_sm(s->feat_dim, false);
+  composite_blocks_per_sm(0, true);
   *out = s;
   return GS_OK;
 }
@@ -860,7 +849,7 @@ void gs_destroy_scene(gs_scene* s) {
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
   for (DevBuf* b : {&s->pos, &s->cov, &s->sh, &s->feat, &s->rec_a, &s->rec_b, &s->rec_c, &s->rec_m, &s->rec_j,
                     &s->tile_count, &s->tile_offset, &s->tile_cursor, &s->partials, &s->chunks, &s->pairs, &s->pairs_tmp,
-                    &s->ctr, &s->result, &s->views, &s->int_pix})
+                    &s->ctr, &s->result, &s->views})
     release(*b);
   for (void* h : {(void*)s->h_pos, (void*)s->h_cov, (void*)s->h_sh, (void*)s->h_feat})
     if (h) cudaFreeHost(h);

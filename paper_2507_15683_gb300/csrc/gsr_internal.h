@@ -13,7 +13,7 @@ constexpr int kTile = 16;          // tile edge in pixels
 constexpr int kTileThreads = 256;  // one thread per pixel of a tile
 constexpr int kSortCap = 2048;     // (tile, Gaussian) pairs a tile sorts in shared memory
 constexpr int kBatchF = 256;       // Gaussians staged per forward batch
-constexpr int kBatchB = 128;       // Gaussians staged per backward batch
+constexpr int kBatchT = 128;       // Gaussians staged per batch in tangent (pose-gradient) mode
 constexpr int kJacStride = 48;     // floats per record of the pose Jacobian (45 used)
 constexpr int kPartialStride = 8;  // doubles per tile partial (loss + 6 grad + pad)
 constexpr int kChunkTiles = 64;
@@ -57,8 +57,8 @@ struct Counters {
   unsigned int rec_region[kRecRegions];  // records requested per segment
   unsigned int pair_total;  // pairs requested by the binning
   unsigned int overflow;    // bit 0: records, bit 1: pairs, bit 2: pair count >= 2^32
-  unsigned int fwd_queue;   // persistent forward tile queue
-  unsigned int bwd_queue;   // persistent backward tile queue
+  unsigned int fwd_queue;   // persistent tile queue of the forward render
+  unsigned int tan_queue;   // persistent tile queue of the tangent (pose-gradient) render
   unsigned int error;       // device-side consistency failure
   unsigned int pad[3];
 };
@@ -119,11 +119,12 @@ cudaError_t launch_scatter(const View* views, const Work& w, int grid, cudaStrea
 // feats: some view writes the feature map (else the feature-free kernel runs)
 cudaError_t launch_composite(const SceneDev& sc, const View* views, int n_views, const Work& w, bool feats,
                              int grid, cudaStream_t st);
-cudaError_t launch_backward(const View* views, int n_views, const Work& w, double* result, int grid,
-                            cudaStream_t st);
+// forward render plus the pose gradient (tangent mode); result: kPartialStride
+// doubles per view (loss, dL/drho, dL/dphi)
+cudaError_t launch_composite_tangent(const SceneDev& sc, const View* views, int n_views, const Work& w,
+                                     double* result, int grid, cudaStream_t st);
 
 // occupancy-derived persistent grid sizes (per SM)
-int composite_blocks_per_sm(int feat_dim);
-int backward_blocks_per_sm();
+int composite_blocks_per_sm(int feat_dim, bool tangent);
 
 }  // namespace gsr

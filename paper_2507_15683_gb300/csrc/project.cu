@@ -496,30 +496,34 @@ __global__ void __launch_bounds__(256) k_shade(SceneDev sc, const View* __restri
         for (int k = 0; k < 3; ++k)
           jac[36 + 3 * ch + k] = clampc[ch] ? 0.0f : gp0 * R[3 * k] + gp1 * R[3 * k + 1] + gp2 * R[3 * k + 2];
       }
-      // Stored tangent-major in pairs that match the adjoint's packed FMAs.
-      // With q = -dL/dpower and d = pixel - centre offset (dx, dy), the
-      // geometric part of one pixel's contribution is
-      //   q dx (A du + B dv) + q dy (B du + C dv) + q dx^2 dA/2 + q dx dy dB
-      //   + q dy^2 dC/2 + (dL/dz) dz,
-      // so per k: (A du + B dv, B du + C dv), (dA / 2, dB), (dC / 2, dz); then
-      // per rho_k: (dr, dg); then db.
+      // Stored for the compositor's packed FMAs over the direction pairs
+      // (0,1), (2,3), (4,5). With the pixel offset (dx, dy) = centre - pixel,
+      //   -dpower/dxi = dx (A du + B dv) + dy (B du + C dv) + dx^2 dA/2
+      //                 + dx dy dB + dy^2 dC/2,
+      // so pair k holds three float4: (P, Q), (dA/2, dB), (dC/2, dz), each
+      // as the two directions of the pair, with P = A du + B dv and
+      // Q = B du + C dv; then d(r, g, b)/d rho in three float4 (three
+      // directions and a zero).
       float jt[48];
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        jt[6 * k + 0] = A * jac[k] + B * jac[6 + k];
-        jt[6 * k + 1] = B * jac[k] + C * jac[6 + k];
-        jt[6 * k + 2] = 0.5f * jac[12 + k];
-        jt[6 * k + 3] = jac[18 + k];
-        jt[6 * k + 4] = 0.5f * jac[24 + k];
-        jt[6 * k + 5] = jac[30 + k];
+      for (int k = 0; k < 3; ++k) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int d = 2 * k + h;
+          jt[12 * k + h] = A * jac[d] + B * jac[6 + d];
+          jt[12 * k + 2 + h] = B * jac[d] + C * jac[6 + d];
+          jt[12 * k + 4 + h] = 0.5f * jac[12 + d];
+          jt[12 * k + 6 + h] = jac[18 + d];
+          jt[12 * k + 8 + h] = 0.5f * jac[24 + d];
+          jt[12 * k + 10 + h] = jac[30 + d];
+        }
       }
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        jt[36 + 2 * k] = jac[36 + k];
-        jt[37 + 2 * k] = jac[39 + k];
-        jt[42 + k] = jac[42 + k];
+      for (int ch = 0; ch < 3; ++ch) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) jt[36 + 4 * ch + k] = jac[36 + 3 * ch + k];
+        jt[39 + 4 * ch] = 0.0f;
       }
-      jt[45] = jt[46] = jt[47] = 0.0f;
       float4* jo = reinterpret_cast<float4*>(w.rec_j + (size_t)slot * kJacStride);
 #pragma unroll
       for (int q = 0; q < 12; ++q) jo[q] = make_float4(jt[4 * q], jt[4 * q + 1], jt[4 * q + 2], jt[4 * q + 3]);

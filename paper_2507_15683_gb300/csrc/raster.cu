@@ -1,6 +1,7 @@
-// Per-tile depth sort + front-to-back alpha compositing (forward), the adjoint
-// compositor that accumulates the se(3) pose gradient (backward), and the
-// fp64 reduction of the per-tile partial sums.
+// Front-to-back alpha compositing of the depth-sorted tile lists (with the
+// block sort of lists too long for the warp sort), optionally carrying the
+// six pose tangents through the blend to give the se(3) gradient of the L1
+// loss in the same pass, and the fp64 reduction of the per-tile sums.
 //
 // Sec. 3.1 of the paper: colour is alpha-blended over the Gaussians covering a
 // pixel, features go through the identical blending; the dense stage of
@@ -8,9 +9,9 @@
 // gradient is the analysis-by-synthesis derivative of the L1 photometric +
 // depth loss with respect to the left pose perturbation.
 //
-// Both compositing kernels are persistent: CTAs pull tiles from a global
-// queue spanning every view of the call, so views of different resolution
-// share one launch and load-balance.
+// The kernel is persistent: CTAs pull tiles from a global queue spanning
+// every view of the call, so views of different resolution share one launch
+// and load-balance.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -190,6 +191,8 @@ constexpr int kSmStage = kSmBufB;
 constexpr int kSmFwd = kSmHist + kWarps * 256 * 4;
 constexpr int kSmFeat = kSmHist;  // 16 KB of BF16 features: hist + 8 KB more
 constexpr int kSmFwdFeat = (kSmFeat + kBatchF * 64) > kSmFwd ? (kSmFeat + kBatchF * 64) : kSmFwd;
+constexpr int kSmJac = kSmFwd;  // tangent mode: the staged pose Jacobians follow the sort histogram
+constexpr int kSmTan = kSmJac + kBatchT * kJacStride * 4;
 static_assert(4 * kBatchF * 16 <= kSortCap * 8, "staging must fit in the second sort buffer");
 
 // Warp w covers the 8 x 4 pixel block at (8 (w & 1), 4 (w >> 1)) of the tile.
@@ -258,27 +261,111 @@ __device__ __forceinline__ uint32_t warp_hit_mask(float4 a, float C, float thr) 
   return mask;
 }
 
-template <int FEAT>
-__global__ void __launch_bounds__(kTileThreads) k_composite(SceneDev sc, const View* __restrict__ views, int n_views,
-                                                            Work w) {
+
+// (loss, dL/dxi) of one tile: a fixed fp32 tree over each warp's lanes, then
+// the warps in order (GB300 runs fp64 at 1/64 of the fp32 rate, so fp64 starts
+// at the tile sums). Then a deterministic fp64 reduction in two fixed levels,
+// done by whichever CTA finishes the last tile of a chunk (kChunkTiles tiles
+// of one view) and then the last chunk of the view: the order depends only on
+// tile indices, so a view gives the same bits alone or inside a batch.
+// Block-uniform control flow; ends with every thread past a barrier.
+__device__ void reduce_tile(float (&v)[7], const View& V, int vi, uint32_t lt, int tid, int lane, int wid, const Work& w,
+                            double* __restrict__ result, float (&s_red)[kWarps][8], bool& s_last) {
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 7; ++k) s_red[wid][k] = v[k];
+  }
+  __syncthreads();
+  const uint32_t tile = V.tile_base + lt;
+  if (tid < 7) {
+    float t = s_red[0][tid];
+#pragma unroll
+    for (int k = 1; k < kWarps; ++k) t += s_red[k][tid];
+    w.partials[(size_t)tile * kPartialStride + tid] = (double)t;
+    __threadfence();
+  }
+  __syncthreads();
+  const uint32_t nt = (uint32_t)V.tiles_x * (uint32_t)V.tiles_y;
+  const uint32_t chunk = lt / kChunkTiles, c0 = chunk * kChunkTiles;
+  const uint32_t cn = min((uint32_t)kChunkTiles, nt - c0);
+  if (tid == 0) s_last = atomicAdd(&w.chunk_ctr[V.chunk_base + chunk], 1u) == cn - 1u;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (wid < 7) {  // warp k sums component k; lanes take tiles lane and lane + 32
+    const double* src = w.partials + (size_t)(V.tile_base + c0) * kPartialStride + wid;
+    double x = (uint32_t)lane < cn ? __ldcg(src + (size_t)lane * kPartialStride) : 0.0;
+    if ((uint32_t)lane + 32u < cn) x += __ldcg(src + (size_t)(lane + 32) * kPartialStride);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) {
+      w.chunk_part[(size_t)(V.chunk_base + chunk) * kPartialStride + wid] = x;
+      __threadfence();
+    }
+  }
+  __syncthreads();
+  const uint32_t ncv = (nt + kChunkTiles - 1) / kChunkTiles;
+  if (tid == 0) s_last = atomicAdd(&w.view_ctr[vi], 1u) == ncv - 1u;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (wid < 7) {
+    double x = 0.0;
+    for (uint32_t c = lane; c < ncv; c += 32)
+      x += __ldcg(w.chunk_part + (size_t)(V.chunk_base + c) * kPartialStride + wid);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) result[(size_t)vi * kPartialStride + wid] = x;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Compositing, one persistent CTA per tile at a time (8 warps = 8 blocks of
+// 8 x 4 pixels). TAN = false: the forward render (colour, depth, alpha, T,
+// last index and, with FEAT = 32, the feature map). TAN = true: the same
+// forward values plus the pose gradient of the L1 loss in tangent (forward)
+// mode: along each of the six pose directions k every pixel carries
+// d(C, D, T)/d xi_k through the front-to-back recursion
+//   w = alpha T,  dw = dalpha T + alpha dT,  C += w c  -> dC += dw c + w dc,
+//   D += w z -> dD += dw z + w dz,  T' = T (1 - alpha) -> dT' = dT - dw,
+// with dalpha = alpha dpower (0 where the 0.99 cap is active) and dpower from
+// the pixel offset and the Gaussian's staged pose Jacobian. After the walk,
+// dL/dxi = sum over pixels of g . (dC, dD) with g the per-pixel L1
+// subgradient, reduced in fp32 per tile and in fp64 across tiles.
+// ---------------------------------------------------------------------------
+template <int FEAT, bool TAN>
+__global__ void __launch_bounds__(kTileThreads, (TAN || FEAT) ? 3 : 5) k_composite(SceneDev sc, const View* __restrict__ views, int n_views,
+                                                            Work w, double* __restrict__ result) {
+  static_assert(!(TAN && FEAT), "tangent mode renders without features");
+  constexpr int kB = TAN ? kBatchT : kBatchF;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint2* bufA = reinterpret_cast<uint2*>(smem_raw + kSmBufA);
   uint2* bufB = reinterpret_cast<uint2*>(smem_raw + kSmBufB);
   uint32_t* hist = reinterpret_cast<uint32_t*>(smem_raw + kSmHist);
   float4* sa = reinterpret_cast<float4*>(smem_raw + kSmStage);
-  float4* sb = sa + kBatchF;
-  float4* scol = sb + kBatchF;
-  uint32_t* smask = reinterpret_cast<uint32_t*>(scol + kBatchF);
+  float4* sb = sa + kB;
+  float4* scol = sb + kB;
+  uint32_t* smask = reinterpret_cast<uint32_t*>(scol + kB);
   uint4* sf = reinterpret_cast<uint4*>(smem_raw + kSmFeat);  // FEAT: kBatchF x 4 (aliases hist)
+  float4* sj = reinterpret_cast<float4*>(smem_raw + kSmJac);  // TAN: kBatchT x 12
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_tmp[kWarps];
+  __shared__ float s_red[kWarps][8];
+  __shared__ bool s_last;
   if (w.ctr->overflow) return;
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   int lx, ly, bxw, byw;
   warp_block(tid, lx, ly, bxw, byw);
   const float pxc = (float)lx + 0.5f, pyc = (float)ly + 0.5f;
+  const float4* rec_j4 = reinterpret_cast<const float4*>(w.rec_j);
   for (;;) {
-    if (tid == 0) s_tile = atomicAdd(&w.ctr->fwd_queue, 1u);
+    // the tangent pass keeps its own queue: it can follow a feature render
+    if (tid == 0) s_tile = atomicAdd(TAN ? &w.ctr->tan_queue : &w.ctr->fwd_queue, 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
     if (tile >= w.n_tiles) break;
@@ -321,11 +408,17 @@ __global__ void __launch_bounds__(kTileThreads) k_composite(SceneDev sc, const V
     float F[FEAT > 0 ? FEAT : 1];
 #pragma unroll
     for (int c = 0; c < (FEAT > 0 ? FEAT : 1); ++c) F[c] = 0.f;
+    // tangents, pairs over the pose directions (0,1), (2,3), (4,5)
+    float2 dC0[3], dC1[3], dC2[3], dD[3], dT[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      dC0[k] = dC1[k] = dC2[k] = dD[k] = dT[k] = make_float2(0.f, 0.f);
+    }
     uint32_t last = 0;
     bool done = !inside;
-    for (int bs = 0; bs < n; bs += kBatchF) {
+    for (int bs = 0; bs < n; bs += kB) {
       if (__syncthreads_count(done) == kTileThreads) break;
-      const int bn = min(kBatchF, n - bs);
+      const int bn = min(kB, n - bs);
       if (tid < bn) {
         const uint32_t r = list[bs + tid].y;
         const float4 cc = w.rec_c[r];
@@ -341,10 +434,16 @@ __global__ void __launch_bounds__(kTileThreads) k_composite(SceneDev sc, const V
           for (int q = 0; q < 4; ++q) sf[tid * 4 + q] = __ldg(fp + q);
         }
       }
+      if (TAN) {
+        for (int q = tid; q < bn * (kJacStride / 4); q += kTileThreads) {
+          const int jj = q / (kJacStride / 4), k = q % (kJacStride / 4);
+          sj[q] = rec_j4[(size_t)list[bs + jj].y * (kJacStride / 4) + k];
+        }
+      }
       __syncthreads();
       // blend one staged Gaussian (power and o exp(power) already evaluated) into
       // this pixel; branch-free: the skip and stop decisions become predicates
-      auto blend = [&](int j, float p, float oe, float zj) {
+      auto blend = [&](int j, float p, float oe, float zj, float dx, float dy) {
         const float alpha = fminf(kAlphaCap, oe);
         const bool take = !done && !(p > 0.0f) && !(alpha < kAlphaFloor);
         const float Tn = __fmul_rn(T, __fsub_rn(1.0f, alpha));
@@ -352,6 +451,45 @@ __global__ void __launch_bounds__(kTileThreads) k_composite(SceneDev sc, const V
         const bool acc = take && !stop;
         const float wgt = acc ? __fmul_rn(alpha, T) : 0.0f;
         const float4 c = scol[j];
+        if (TAN) {
+          // staged Jacobian: per direction pair k, (P, Q), (dA/2, dB),
+          // (dC/2, dz) with P = A du + B dv, Q = B du + C dv; then the colour
+          // rows. S_k = dx P + dy Q + dx^2 dA/2 + dx dy dB + dy^2 dC/2 is
+          // -dpower/dxi_k.
+          const float4* J4 = sj + j * (kJacStride / 4);
+          const float2 X = make_float2(dx, dx), Y = make_float2(dy, dy);
+          const float xx = dx * dx, xy = dx * dy, yy = dy * dy;
+          const float2 XX = make_float2(xx, xx), XY = make_float2(xy, xy), YY = make_float2(yy, yy);
+          const float ad = (acc && oe < kAlphaCap) ? -alpha : 0.0f;  // dalpha = -alpha S
+          const float ae = acc ? alpha : 0.0f;
+          const float2 AD = make_float2(ad, ad), AE = make_float2(ae, ae), TT = make_float2(T, T);
+          const float2 CR = make_float2(c.x, c.x), CG = make_float2(c.y, c.y), CB = make_float2(c.z, c.z);
+          const float2 ZZ = make_float2(zj, zj), WW = make_float2(wgt, wgt);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const float4 pq = J4[3 * k], ab = J4[3 * k + 1], cz = J4[3 * k + 2];
+            float2 S2 = __fmul2_rn(make_float2(pq.x, pq.y), X);
+            S2 = __ffma2_rn(make_float2(pq.z, pq.w), Y, S2);
+            S2 = __ffma2_rn(make_float2(ab.x, ab.y), XX, S2);
+            S2 = __ffma2_rn(make_float2(ab.z, ab.w), XY, S2);
+            S2 = __ffma2_rn(make_float2(cz.x, cz.y), YY, S2);
+            const float2 da = __fmul2_rn(S2, AD);
+            const float2 dw = __ffma2_rn(da, TT, __fmul2_rn(dT[k], AE));
+            dT[k] = __ffma2_rn(dw, make_float2(-1.0f, -1.0f), dT[k]);
+            dC0[k] = __ffma2_rn(dw, CR, dC0[k]);
+            dC1[k] = __ffma2_rn(dw, CG, dC1[k]);
+            dC2[k] = __ffma2_rn(dw, CB, dC2[k]);
+            dD[k] = __ffma2_rn(dw, ZZ, __ffma2_rn(make_float2(cz.z, cz.w), WW, dD[k]));
+          }
+          // colour depends on the camera centre only: rho directions 0..2
+          const float4 r0 = J4[9], r1 = J4[10], r2 = J4[11];
+          dC0[0] = __ffma2_rn(make_float2(r0.x, r0.y), WW, dC0[0]);
+          dC0[1].x = fmaf(r0.z, wgt, dC0[1].x);
+          dC1[0] = __ffma2_rn(make_float2(r1.x, r1.y), WW, dC1[0]);
+          dC1[1].x = fmaf(r1.z, wgt, dC1[1].x);
+          dC2[0] = __ffma2_rn(make_float2(r2.x, r2.y), WW, dC2[0]);
+          dC2[1].x = fmaf(r2.z, wgt, dC2[1].x);
+        }
         C0 = fmaf(wgt, c.x, C0);
         C1 = fmaf(wgt, c.y, C1);
         C2 = fmaf(wgt, c.z, C2);
@@ -372,7 +510,7 @@ __global__ void __launch_bounds__(kTileThreads) k_composite(SceneDev sc, const V
         last = acc ? (uint32_t)(bs + j + 1) : last;
         done = done || stop;
       };
-      const uint32_t wbit = 1u << (tid >> 5);
+      const uint32_t wbit = 1u << wid;
       bool wdone = __all_sync(0xffffffffu, done);
       for (int c0 = 0; c0 < bn && !wdone; c0 += 32) {
         const int jj = c0 + lane;
@@ -384,19 +522,21 @@ __global__ void __launch_bounds__(kTileThreads) k_composite(SceneDev sc, const V
           const int j2 = two ? c0 + __ffs(m) - 1 : j1;
           if (two) m &= m - 1;
           const float4 a1 = sa[j1], b1 = sb[j1], a2 = sa[j2], b2 = sb[j2];
-          const float p1 = gs_power(a1.z, a1.w, b1.x, __fsub_rn(a1.x, pxc), __fsub_rn(a1.y, pyc));
-          const float p2 = gs_power(a2.z, a2.w, b2.x, __fsub_rn(a2.x, pxc), __fsub_rn(a2.y, pyc));
+          const float dx1 = __fsub_rn(a1.x, pxc), dy1 = __fsub_rn(a1.y, pyc);
+          const float dx2 = __fsub_rn(a2.x, pxc), dy2 = __fsub_rn(a2.y, pyc);
+          const float p1 = gs_power(a1.z, a1.w, b1.x, dx1, dy1);
+          const float p2 = gs_power(a2.z, a2.w, b2.x, dx2, dy2);
           const float oe1 = __fmul_rn(b1.y, __expf(p1));
           const float oe2 = __fmul_rn(b2.y, __expf(p2));
-          blend(j1, p1, oe1, b1.z);
-          if (two) blend(j2, p2, oe2, b2.z);
+          blend(j1, p1, oe1, b1.z, dx1, dy1);
+          if (two) blend(j2, p2, oe2, b2.z, dx2, dy2);
         }
         wdone = __all_sync(0xffffffffu, done);
       }
     }
+    const size_t HW = (size_t)V.width * V.height;
+    const size_t p = (size_t)py * V.width + px;
     if (inside) {
-      const size_t HW = (size_t)V.width * V.height;
-      const size_t p = (size_t)py * V.width + px;
       if (V.rgb) {
         V.rgb[p] = C0;
         V.rgb[HW + p] = C1;
@@ -411,255 +551,51 @@ __global__ void __launch_bounds__(kTileThreads) k_composite(SceneDev sc, const V
         for (int c = 0; c < (FEAT > 0 ? FEAT : 1); ++c) V.feats[(size_t)c * HW + p] = F[c];
       }
     }
+    if (TAN) {
+      // per-pixel L1 subgradient g (sign(0) = 0) and loss
+      float v[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (inside) {
+        const float wpx = V.pixel_weight ? V.pixel_weight[p] : 1.0f;
+        const float r0 = C0 - V.target_rgb[p];
+        const float r1 = C1 - V.target_rgb[HW + p];
+        const float r2 = C2 - V.target_rgb[2 * HW + p];
+        const float e = D - V.target_depth[p];
+        const float s3 = wpx * V.inv_3p, sd = wpx * V.depth_weight * V.inv_p;
+        const float g0 = s3 * (float)((r0 > 0.f) - (r0 < 0.f));
+        const float g1 = s3 * (float)((r1 > 0.f) - (r1 < 0.f));
+        const float g2 = s3 * (float)((r2 > 0.f) - (r2 < 0.f));
+        const float gd = sd * (float)((e > 0.f) - (e < 0.f));
+        v[0] = s3 * (fabsf(r0) + fabsf(r1) + fabsf(r2)) + sd * fabsf(e);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const float2 x = __ffma2_rn(make_float2(g0, g0), dC0[k],
+                                      __ffma2_rn(make_float2(g1, g1), dC1[k],
+                                                 __ffma2_rn(make_float2(g2, g2), dC2[k],
+                                                            __fmul2_rn(make_float2(gd, gd), dD[k]))));
+          v[1 + 2 * k] = x.x;
+          v[2 + 2 * k] = x.y;
+        }
+      }
+      reduce_tile(v, V, vi, lt, tid, lane, wid, w, result, s_red, s_last);
+    }
     __syncthreads();
   }
 }
 
-// ---------------------------------------------------------------------------
-// Backward: per pixel, walk the blended Gaussians back to front recomputing
-// the transmittance from the stored final value, T_k = T_{k+1} / (1 - a_k);
-// chain dL/d(u, v, conic, z, rgb) through the per-Gaussian pose Jacobian and
-// accumulate the 6-vector per pixel (fp32); reduce across pixels in fp64.
-// The same per-warp footprint test as the forward skips pairs that no pixel of
-// the warp blended.
-// ---------------------------------------------------------------------------
-struct BwdSmem {
-  float4 sa[kBatchB], sb[kBatchB], sc[kBatchB];
-  uint32_t smask[kBatchB];
-  float4 sj[kBatchB * (kJacStride / 4)];
-  float red[kWarps][8];
-};
-
-__global__ void __launch_bounds__(kTileThreads) k_backward(const View* __restrict__ views, int n_views, Work w,
-                                                           double* __restrict__ result) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  BwdSmem& S = *reinterpret_cast<BwdSmem*>(smem_raw);
-  __shared__ uint32_t s_tile;
-  __shared__ uint32_t s_max[kWarps];
-  __shared__ bool s_last;
-  if (w.ctr->overflow) return;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  int lx, ly, bxw, byw;
-  warp_block(tid, lx, ly, bxw, byw);
-  const float pxc = (float)lx + 0.5f, pyc = (float)ly + 0.5f;
-  const uint32_t wbit = 1u << wid;
-  const float4* rec_j4 = reinterpret_cast<const float4*>(w.rec_j);
-  for (;;) {
-    if (tid == 0) s_tile = atomicAdd(&w.ctr->bwd_queue, 1u);
-    __syncthreads();
-    const uint32_t tile = s_tile;
-    if (tile >= w.n_tiles) break;
-    const int vi = find_view(views, n_views, tile);
-    const View& V = views[vi];
-    const uint32_t lt = tile - V.tile_base;
-    const int tx = (int)(lt % (uint32_t)V.tiles_x), ty = (int)(lt / (uint32_t)V.tiles_x);
-    const uint32_t start = w.tile_offset[tile];
-    const int px = tx * kTile + lx, py = ty * kTile + ly;
-    const bool inside = px < V.width && py < V.height;
-    const float X0 = (float)(tx * kTile), Y0 = (float)(ty * kTile);
-    const size_t HW = (size_t)V.width * V.height;
-    const size_t p = (size_t)py * V.width + px;
-
-    uint32_t last = 0;
-    float T = 1.0f, gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f;
-    float loss = 0.0f;
-    if (inside) {
-      last = V.last_idx[p];
-      T = V.final_T[p];
-      const float wpx = V.pixel_weight ? V.pixel_weight[p] : 1.0f;
-      const float r0 = V.rgb[p] - V.target_rgb[p];
-      const float r1 = V.rgb[HW + p] - V.target_rgb[HW + p];
-      const float r2 = V.rgb[2 * HW + p] - V.target_rgb[2 * HW + p];
-      const float e = V.depth[p] - V.target_depth[p];
-      const float s3 = wpx * V.inv_3p, sd = wpx * V.depth_weight * V.inv_p;
-      gC0 = s3 * (float)((r0 > 0.f) - (r0 < 0.f));
-      gC1 = s3 * (float)((r1 > 0.f) - (r1 < 0.f));
-      gC2 = s3 * (float)((r2 > 0.f) - (r2 < 0.f));
-      gD = sd * (float)((e > 0.f) - (e < 0.f));
-      loss = s3 * (fabsf(r0) + fabsf(r1) + fabsf(r2)) + sd * fabsf(e);
-    }
-    // longest list prefix any pixel of the tile (and of this warp) blended
-    const uint32_t wm = __reduce_max_sync(0xffffffffu, last);
-    if (lane == 0) s_max[wid] = wm;
-    __syncthreads();
-    uint32_t max_last = 0;
-#pragma unroll
-    for (int k = 0; k < kWarps; ++k) max_last = max(max_last, s_max[k]);
-
-    // per-tangent partial sums: .x and .y take different Jacobian rows and are
-    // added at the end
-    float2 xi2[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) xi2[k] = make_float2(0.f, 0.f);
-    float sdot = 0.f;
-    for (int bend = (int)max_last; bend > 0; bend -= kBatchB) {
-      const int bstart = max(0, bend - kBatchB);
-      const int bn = bend - bstart;
-      __syncthreads();
-      if (tid < bn) {
-        const uint32_t r = w.pairs[start + bstart + tid].y;
-        const float4 cc = w.rec_c[r];
-        const float4 a = tile_local(w.rec_a[r], cc.w, X0, Y0);
-        const float4 bb = w.rec_b[r];
-        S.sa[tid] = a;
-        S.sb[tid] = bb;
-        S.sc[tid] = cc;
-        S.smask[tid] = warp_hit_mask(a, bb.x, floor_threshold(bb.y));
-      }
-      for (int q = tid; q < bn * (kJacStride / 4); q += kTileThreads) {
-        const int jj = q / (kJacStride / 4), k = q % (kJacStride / 4);
-        const uint32_t r = w.pairs[start + bstart + jj].y;
-        S.sj[q] = rec_j4[(size_t)r * (kJacStride / 4) + k];
-      }
-      __syncthreads();
-      if ((uint32_t)bstart >= wm) continue;  // no pixel of this warp blended this far
-      // one Gaussian, back to front: if this pixel blended it, step T and the
-      // running sum back and chain its 9 sensitivities through the staged pose
-      // Jacobian (48 floats in tangent-major pairs, read as 12 float4).
-      // Branch-free: a pixel that skipped the Gaussian contributes zeros.
-      auto adjoint = [&](int j, float4 a, float4 b, float dx, float dy, float p, float oe, bool live) {
-        const float alpha = fminf(kAlphaCap, oe);
-        const bool take = live && !(p > 0.0f) && !(alpha < kAlphaFloor);
-        const float Tj = take ? __fdividef(T, 1.0f - alpha) : T;  // transmittance in front of this Gaussian
-        const float wgt = take ? alpha * Tj : 0.0f;
-        const float4 c = S.sc[j];
-        // dL/dalpha = Tj (g . (c, z) - g . acc), where acc, the normalised
-        // colour and depth behind this Gaussian, follows acc <- alpha (c, z) +
-        // (1 - alpha) acc; only its projection sdot = g . acc is needed
-        const float gc = fmaf(gC0, c.x, fmaf(gC1, c.y, fmaf(gC2, c.z, gD * b.z)));
-        const float d = gc - sdot;
-        sdot = fmaf(take ? alpha : 0.0f, d, sdot);
-        T = Tj;
-        const float q = (take && oe < kAlphaCap) ? -(Tj * d) * alpha : 0.0f;  // -dL/dpower
-        const float dxq = q * dx, dyq = q * dy;
-        // the nine sensitivities in pairs; each packed FMA takes one pair
-        // against the matching Jacobian pair of one tangent direction
-        const float2 g01 = make_float2(dxq, dyq);
-        const float2 g23 = make_float2(dxq * dx, dxq * dy);
-        const float2 g45 = make_float2(dyq * dy, gD * wgt);
-        const float2 g67 = make_float2(gC0 * wgt, gC1 * wgt);
-        const float g8 = gC2 * wgt;
-        const float4* J4 = S.sj + j * (kJacStride / 4);
-#pragma unroll
-        for (int q = 0; q < kJacStride / 4; ++q) {
-          const float4 v = J4[q];
-          const float2 e[2] = {make_float2(v.x, v.y), make_float2(v.z, v.w)};
-#pragma unroll
-          for (int i = 0; i < 2; ++i) {
-            const int pr = 2 * q + i;  // pair index
-            if (pr < 18) {
-              const float2 gg = (pr % 3 == 0) ? g01 : (pr % 3 == 1) ? g23 : g45;
-              xi2[pr / 3] = __ffma2_rn(e[i], gg, xi2[pr / 3]);
-            } else if (pr < 21) {
-              xi2[pr - 18] = __ffma2_rn(e[i], g67, xi2[pr - 18]);
-            } else if (pr == 21) {  // floats 42, 43: d blue / d rho_0, rho_1
-              xi2[0].x = fmaf(e[i].x, g8, xi2[0].x);
-              xi2[1].x = fmaf(e[i].y, g8, xi2[1].x);
-            } else if (pr == 22) {  // float 44: d blue / d rho_2
-              xi2[2].x = fmaf(e[i].x, g8, xi2[2].x);
-            }
-          }
-        }
-      };
-      for (int c0 = ((bn - 1) >> 5) << 5; c0 >= 0; c0 -= 32) {
-        const int jj = c0 + lane;
-        uint32_t m = __ballot_sync(0xffffffffu, jj < bn && (uint32_t)(bstart + jj) < wm && (S.smask[jj] & wbit));
-        while (m) {  // two hits per step, back to front
-          const int bit1 = 31 - __clz(m);
-          m &= ~(1u << bit1);
-          const bool two = m != 0u;
-          const int bit2 = two ? 31 - __clz(m) : bit1;
-          if (two) m &= ~(1u << bit2);
-          const int j1 = c0 + bit1, j2 = c0 + bit2;
-          const float4 a1 = S.sa[j1], b1 = S.sb[j1], a2 = S.sa[j2], b2 = S.sb[j2];
-          const float dx1 = __fsub_rn(a1.x, pxc), dy1 = __fsub_rn(a1.y, pyc);
-          const float dx2 = __fsub_rn(a2.x, pxc), dy2 = __fsub_rn(a2.y, pyc);
-          const float p1 = gs_power(a1.z, a1.w, b1.x, dx1, dy1);
-          const float p2 = gs_power(a2.z, a2.w, b2.x, dx2, dy2);
-          const float oe1 = __fmul_rn(b1.y, __expf(p1));
-          const float oe2 = __fmul_rn(b2.y, __expf(p2));
-          adjoint(j1, a1, b1, dx1, dy1, p1, oe1, inside && (uint32_t)(bstart + j1) < last);
-          if (two) adjoint(j2, a2, b2, dx2, dy2, p2, oe2, inside && (uint32_t)(bstart + j2) < last);
-        }
-      }
-    }
-    // (loss, xi) of the tile in fp32: a fixed tree over each warp's lanes, then
-    // the warps in order. GB300 runs fp64 at 1/64 of the fp32 rate, so fp64
-    // starts at the tile sums.
-    float v[7];
-    v[0] = loss;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) v[1 + k] = xi2[k].x + xi2[k].y;
-#pragma unroll
-    for (int k = 0; k < 7; ++k) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-    }
-    if (lane == 0) {
-#pragma unroll
-      for (int k = 0; k < 7; ++k) S.red[wid][k] = v[k];
-    }
-    __syncthreads();
-    if (tid < 7) {
-      float t = S.red[0][tid];
-#pragma unroll
-      for (int k = 1; k < kWarps; ++k) t += S.red[k][tid];
-      w.partials[(size_t)tile * kPartialStride + tid] = (double)t;
-      __threadfence();
-    }
-    __syncthreads();
-    // Deterministic fp64 reduction in two fixed levels, done by whichever CTA
-    // finishes the last tile of a chunk (kChunkTiles tiles of one view) and
-    // then the last chunk of the view: the order depends only on tile indices,
-    // so a view gives the same bits alone or inside a batch.
-    const uint32_t nt = (uint32_t)V.tiles_x * (uint32_t)V.tiles_y;
-    const uint32_t chunk = lt / kChunkTiles, c0 = chunk * kChunkTiles;
-    const uint32_t cn = min((uint32_t)kChunkTiles, nt - c0);
-    if (tid == 0) s_last = atomicAdd(&w.chunk_ctr[V.chunk_base + chunk], 1u) == cn - 1u;
-    __syncthreads();
-    if (!s_last) continue;
-    __threadfence();
-    if (wid < 7) {  // warp k sums component k; lanes take tiles lane and lane + 32
-      const double* src = w.partials + (size_t)(V.tile_base + c0) * kPartialStride + wid;
-      double x = (uint32_t)lane < cn ? __ldcg(src + (size_t)lane * kPartialStride) : 0.0;
-      if ((uint32_t)lane + 32u < cn) x += __ldcg(src + (size_t)(lane + 32) * kPartialStride);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-      if (lane == 0) {
-        w.chunk_part[(size_t)(V.chunk_base + chunk) * kPartialStride + wid] = x;
-        __threadfence();
-      }
-    }
-    __syncthreads();
-    const uint32_t ncv = (nt + kChunkTiles - 1) / kChunkTiles;
-    if (tid == 0) s_last = atomicAdd(&w.view_ctr[vi], 1u) == ncv - 1u;
-    __syncthreads();
-    if (!s_last) continue;
-    __threadfence();
-    if (wid < 7) {
-      double x = 0.0;
-      for (uint32_t c = lane; c < ncv; c += 32)
-        x += __ldcg(w.chunk_part + (size_t)(V.chunk_base + c) * kPartialStride + wid);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-      if (lane == 0) result[(size_t)vi * kPartialStride + wid] = x;
-    }
-  }
-}
-
-template <int FEAT>
+template <int FEAT, bool TAN>
 size_t composite_smem() {
-  return FEAT ? (size_t)kSmFwdFeat : (size_t)kSmFwd;
+  return TAN ? (size_t)kSmTan : FEAT ? (size_t)kSmFwdFeat : (size_t)kSmFwd;
 }
 
-template <int FEAT>
+template <int FEAT, bool TAN>
 int composite_occ() {
   static int occ = -1;
   if (occ < 0) {
-    cudaFuncSetAttribute(k_composite<FEAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)composite_smem<FEAT>());
+    cudaFuncSetAttribute(k_composite<FEAT, TAN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)composite_smem<FEAT, TAN>());
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_composite<FEAT>, kTileThreads, composite_smem<FEAT>()) !=
-        cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_composite<FEAT, TAN>, kTileThreads,
+                                                      composite_smem<FEAT, TAN>()) != cudaSuccess)
       b = 1;
     occ = b > 0 ? b : 1;
   }
@@ -668,18 +604,8 @@ int composite_occ() {
 
 }  // namespace
 
-int composite_blocks_per_sm(int feat_dim) { return feat_dim ? composite_occ<32>() : composite_occ<0>(); }
-
-int backward_blocks_per_sm() {
-  static int occ = -1;
-  if (occ < 0) {
-    cudaFuncSetAttribute(k_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BwdSmem));
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_backward, kTileThreads, sizeof(BwdSmem)) != cudaSuccess)
-      b = 1;
-    occ = b > 0 ? b : 1;
-  }
-  return occ;
+int composite_blocks_per_sm(int feat_dim, bool tangent) {
+  return tangent ? composite_occ<0, true>() : feat_dim ? composite_occ<32, false>() : composite_occ<0, false>();
 }
 
 cudaError_t launch_composite(const SceneDev& sc, const View* views, int n_views, const Work& w, bool feats,
@@ -687,21 +613,21 @@ cudaError_t launch_composite(const SceneDev& sc, const View* views, int n_views,
   if (w.n_tiles == 0) return cudaSuccess;
   const int g = (uint32_t)grid < w.n_tiles ? grid : (int)w.n_tiles;
   if (sc.feat_dim && feats) {
-    composite_occ<32>();
-    k_composite<32><<<g, kTileThreads, composite_smem<32>(), st>>>(sc, views, n_views, w);
+    composite_occ<32, false>();
+    k_composite<32, false><<<g, kTileThreads, composite_smem<32, false>(), st>>>(sc, views, n_views, w, nullptr);
   } else {
-    composite_occ<0>();
-    k_composite<0><<<g, kTileThreads, composite_smem<0>(), st>>>(sc, views, n_views, w);
+    composite_occ<0, false>();
+    k_composite<0, false><<<g, kTileThreads, composite_smem<0, false>(), st>>>(sc, views, n_views, w, nullptr);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_backward(const View* views, int n_views, const Work& w, double* result, int grid,
-                            cudaStream_t st) {
+cudaError_t launch_composite_tangent(const SceneDev& sc, const View* views, int n_views, const Work& w,
+                                     double* result, int grid, cudaStream_t st) {
   if (w.n_tiles == 0) return cudaSuccess;
-  backward_blocks_per_sm();
   const int g = (uint32_t)grid < w.n_tiles ? grid : (int)w.n_tiles;
-  k_backward<<<g, kTileThreads, sizeof(BwdSmem), st>>>(views, n_views, w, result);
+  composite_occ<0, true>();
+  k_composite<0, true><<<g, kTileThreads, composite_smem<0, true>(), st>>>(sc, views, n_views, w, result);
   return cudaGetLastError();
 }
 

@@ -246,7 +246,7 @@ def gs_render_noalloc(desc: gs_scene_desc, cam: gs_camera, pose: gs_pose, out: g
                                  stream))
 
 
-KERNEL_NAMES = ("project", "shade", "scan_tiles", "scatter", "sort", "composite", "backward")
+KERNEL_NAMES = ("project", "shade", "scan_tiles", "scatter", "sort", "composite")
 
 
 def gs_scene_set_timing(h, enable: bool) -> None:

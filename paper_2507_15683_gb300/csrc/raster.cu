@@ -191,8 +191,14 @@ constexpr int kSmStage = kSmBufB;
 constexpr int kSmFwd = kSmHist + kWarps * 256 * 4;
 constexpr int kSmFeat = kSmHist;  // 16 KB of BF16 features: hist + 8 KB more
 constexpr int kSmFwdFeat = (kSmFeat + kBatchF * 64) > kSmFwd ? (kSmFeat + kBatchF * 64) : kSmFwd;
-constexpr int kSmJac = kSmFwd;  // tangent mode: the staged pose Jacobians follow the sort histogram
-constexpr int kSmTan = kSmJac + kBatchT * kJacStride * 4;
+// Tangent mode reads the sorted list back from global memory, so after the
+// sort the staged pose Jacobians take the two sort buffers and the staged
+// batch takes the histogram.
+constexpr int kSmJac = 0;
+constexpr int kSmStageT = kSmHist;
+constexpr int kSmTan = kSmFwd;
+static_assert(kBatchT * kJacStride * 4 <= kSmHist, "staged Jacobians must fit in the sort buffers");
+static_assert(kSmStageT + kBatchT * 52 <= kSmTan, "tangent staging must fit in the histogram");
 static_assert(4 * kBatchF * 16 <= kSortCap * 8, "staging must fit in the second sort buffer");
 
 // Warp w covers the 8 x 4 pixel block at (8 (w & 1), 4 (w >> 1)) of the tile.
@@ -339,7 +345,7 @@ __device__ void reduce_tile(float (&v)[7], const View& V, int vi, uint32_t lt, i
 // subgradient, reduced in fp32 per tile and in fp64 across tiles.
 // ---------------------------------------------------------------------------
 template <int FEAT, bool TAN>
-__global__ void __launch_bounds__(kTileThreads, (TAN || FEAT) ? 3 : 5) k_composite(SceneDev sc, const View* __restrict__ views, int n_views,
+__global__ void __launch_bounds__(kTileThreads, TAN ? 4 : FEAT ? 3 : 5) k_composite(SceneDev sc, const View* __restrict__ views, int n_views,
                                                             Work w, double* __restrict__ result) {
   static_assert(!(TAN && FEAT), "tangent mode renders without features");
   constexpr int kB = TAN ? kBatchT : kBatchF;
@@ -347,7 +353,7 @@ __global__ void __launch_bounds__(kTileThreads, (TAN || FEAT) ? 3 : 5) k_composi
   uint2* bufA = reinterpret_cast<uint2*>(smem_raw + kSmBufA);
   uint2* bufB = reinterpret_cast<uint2*>(smem_raw + kSmBufB);
   uint32_t* hist = reinterpret_cast<uint32_t*>(smem_raw + kSmHist);
-  float4* sa = reinterpret_cast<float4*>(smem_raw + kSmStage);
+  float4* sa = reinterpret_cast<float4*>(smem_raw + (TAN ? kSmStageT : kSmStage));
   float4* sb = sa + kB;
   float4* scol = sb + kB;
   uint32_t* smask = reinterpret_cast<uint32_t*>(scol + kB);
@@ -390,7 +396,8 @@ __global__ void __launch_bounds__(kTileThreads, (TAN || FEAT) ? 3 : 5) k_composi
         __syncthreads();
       }
       for (int i = tid; i < n; i += kTileThreads) w.pairs[start + i] = bufA[i];
-      list = bufA;
+      if (TAN) __syncthreads();  // the list is read back from global memory
+      list = TAN ? w.pairs + start : bufA;
     } else {
       uint2* sorted = sort_tile(w.pairs + start, w.pairs_tmp + start, n, hist, s_tmp, w.rec_b);
       if (sorted != w.pairs + start) {
@@ -518,6 +525,13 @@ __global__ void __launch_bounds__(kTileThreads, (TAN || FEAT) ? 3 : 5) k_composi
         while (m) {  // two hits per step: their exponentials overlap, blending stays in order
           const int j1 = c0 + __ffs(m) - 1;
           m &= m - 1;
+          if (TAN) {  // one hit per step: the tangent update needs the registers
+            const float4 a1 = sa[j1], b1 = sb[j1];
+            const float dx1 = __fsub_rn(a1.x, pxc), dy1 = __fsub_rn(a1.y, pyc);
+            const float p1 = gs_power(a1.z, a1.w, b1.x, dx1, dy1);
+            blend(j1, p1, __fmul_rn(b1.y, __expf(p1)), b1.z, dx1, dy1);
+            continue;
+          }
           const bool two = m != 0u;
           const int j2 = two ? c0 + __ffs(m) - 1 : j1;
           if (two) m &= m - 1;

@@ -131,31 +131,28 @@ __global__ void __launch_bounds__(256) k_scatter(const View* __restrict__ views,
 // Depth order of the short tile lists, one warp per tile: a bitonic network
 // over E elements per lane (element e = E lane + i sits in register i), with
 // compare-exchanges inside a lane for strides below E and across lanes by
-// shuffles above. Elements are packed as (depth bits << 32 | record), compared
-// as 64-bit integers with branch-free min/max; the record part only makes the
-// keys distinct. Runs of equal depth are then put in Gaussian-index order (the
-// tie-break of the key), which happens rarely. Lists longer than kWarpSortMax
-// are left to the compositor's block sort.
-__device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) {
+// shuffles above, on distinct integer keys with branch-free min/max. When the
+// tile's depth bits span less than 2^24 the key is the 32-bit
+// (depth - smallest depth) << 8 | position, and the records wait in shared
+// memory; otherwise the 64-bit (depth << 32 | record). Runs of equal depth
+// are then put in Gaussian-index order (the tie-break of the key), which
+// happens rarely. Lists longer than kWarpSortMax are left to the compositor's
+// block sort.
+__device__ __forceinline__ uint64_t kmin(uint64_t a, uint64_t b) {
   uint64_t r;
   asm("min.u64 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
   return r;
 }
-__device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) {
+__device__ __forceinline__ uint64_t kmax(uint64_t a, uint64_t b) {
   uint64_t r;
   asm("max.u64 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
   return r;
 }
+__device__ __forceinline__ uint32_t kmin(uint32_t a, uint32_t b) { return min(a, b); }
+__device__ __forceinline__ uint32_t kmax(uint32_t a, uint32_t b) { return max(a, b); }
 
-template <int E>
-__device__ void warp_sort_list(uint2* __restrict__ list, int n, const float4* __restrict__ rec_b, int lane) {
-  uint64_t x[E];
-#pragma unroll
-  for (int i = 0; i < E; ++i) {
-    const int e = lane * E + i;
-    const uint2 p = e < n ? list[e] : make_uint2(0xffffffffu, 0xffffffffu);  // pads sort last
-    x[i] = ((uint64_t)p.x << 32) | p.y;
-  }
+template <int E, typename K>
+__device__ __forceinline__ void bitonic(K (&x)[E], int lane) {
 #pragma unroll
   for (int size = 2; size <= 32 * E; size <<= 1) {
 #pragma unroll
@@ -166,8 +163,8 @@ __device__ void warp_sort_list(uint2* __restrict__ list, int n, const float4* __
         const bool keep_min = ((lane & lj) == 0) == (((lane * E) & size) == 0);
 #pragma unroll
         for (int i = 0; i < E; ++i) {
-          const uint64_t o = __shfl_xor_sync(0xffffffffu, x[i], lj);
-          const uint64_t mn = umin64(x[i], o), mx = umax64(x[i], o);
+          const K o = __shfl_xor_sync(0xffffffffu, x[i], lj);
+          const K mn = kmin(x[i], o), mx = kmax(x[i], o);
           x[i] = keep_min ? mn : mx;
         }
       } else {
@@ -176,19 +173,60 @@ __device__ void warp_sort_list(uint2* __restrict__ list, int n, const float4* __
           if (i & j) continue;
           const int q = i | j;
           const bool up = ((lane * E + i) & size) == 0;
-          const uint64_t mn = umin64(x[i], x[q]), mx = umax64(x[i], x[q]);
+          const K mn = kmin(x[i], x[q]), mx = kmax(x[i], x[q]);
           x[i] = up ? mn : mx;
           x[q] = up ? mx : mn;
         }
       }
     }
   }
-  uint32_t k[E];
+}
+
+template <int E>
+__device__ void warp_sort_list(uint2* __restrict__ list, int n, const float4* __restrict__ rec_b, int lane,
+                               uint32_t* __restrict__ srec) {
+  uint32_t k[E], v[E];
+  uint32_t lo = 0xffffffffu, hi = 0u;
 #pragma unroll
-  for (int i = 0; i < E; ++i) k[i] = (uint32_t)(x[i] >> 32);
-  uint32_t v[E];
+  for (int i = 0; i < E; ++i) {
+    const int e = lane * E + i;
+    const uint2 p = e < n ? list[e] : make_uint2(0xffffffffu, 0xffffffffu);  // pads sort last
+    k[i] = p.x;
+    v[i] = p.y;
+    if (e < n) {
+      lo = min(lo, p.x);
+      hi = max(hi, p.x);
+      srec[e] = p.y;
+    }
+  }
+  lo = __reduce_min_sync(0xffffffffu, lo);
+  hi = __reduce_max_sync(0xffffffffu, hi);
+  if (hi - lo < (1u << 24)) {  // warp-uniform
+    uint32_t x[E];
 #pragma unroll
-  for (int i = 0; i < E; ++i) v[i] = (uint32_t)x[i];
+    for (int i = 0; i < E; ++i) {
+      const int e = lane * E + i;
+      x[i] = e < n ? ((k[i] - lo) << 8) | (uint32_t)e : 0xffffffffu;
+    }
+    bitonic<E>(x, lane);
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int e = lane * E + i;
+      k[i] = e < n ? (x[i] >> 8) + lo : 0xffffffffu;
+      v[i] = e < n ? srec[x[i] & 255u] : 0xffffffffu;
+    }
+  } else {
+    uint64_t x[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) x[i] = ((uint64_t)k[i] << 32) | v[i];
+    bitonic<E>(x, lane);
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      k[i] = (uint32_t)(x[i] >> 32);
+      v[i] = (uint32_t)x[i];
+    }
+  }
   bool tie = false;
 #pragma unroll
   for (int i = 0; i < E; ++i) {
@@ -226,19 +264,21 @@ __device__ void warp_sort_list(uint2* __restrict__ list, int n, const float4* __
   __syncwarp();
 }
 
-__global__ void __launch_bounds__(256) k_sort_tiles(Work w) {
+__global__ void __launch_bounds__(256, 4) k_sort_tiles(Work w) {
+  __shared__ uint32_t s_rec[8][kWarpSortMax];
   if (w.ctr->overflow) return;
   const int lane = threadIdx.x & 31;
+  uint32_t* srec = s_rec[threadIdx.x >> 5];
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t tile = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < w.n_tiles; tile += nw) {
     const uint32_t start = w.tile_offset[tile];
     const int n = (int)(w.tile_offset[tile + 1] - start);
     if (n <= 1 || n > kWarpSortMax) continue;  // warp-uniform
     uint2* list = w.pairs + start;
-    if (n <= 32) warp_sort_list<1>(list, n, w.rec_b, lane);
-    else if (n <= 64) warp_sort_list<2>(list, n, w.rec_b, lane);
-    else if (n <= 128) warp_sort_list<4>(list, n, w.rec_b, lane);
-    else warp_sort_list<8>(list, n, w.rec_b, lane);
+    if (n <= 32) warp_sort_list<1>(list, n, w.rec_b, lane, srec);
+    else if (n <= 64) warp_sort_list<2>(list, n, w.rec_b, lane, srec);
+    else if (n <= 128) warp_sort_list<4>(list, n, w.rec_b, lane, srec);
+    else warp_sort_list<8>(list, n, w.rec_b, lane, srec);
   }
 }
 

@@ -216,104 +216,118 @@ __device__ __forceinline__ void eval_sh_deg(int deg, const float4* shp, float x,
 }
 
 // ---------------------------------------------------------------------------
-// Projection, discrete pass: one thread per Gaussian, looping over the views
-// of the call. Decides visibility, the tile rectangle and the sort key, counts
-// pairs per tile and appends a record; the continuous quantities are filled in
-// by k_shade over the compact records (full warps instead of ~1 visible lane
-// in 6). Record fields written here: rec_m = (rect, view, depth bits),
-// rec_a = (binary32 covariance a, b, c, -), rec_b.w = Gaussian index.
+// Projection, discrete pass. Decides visibility, the tile rectangle and the
+// sort key, counts pairs per tile and appends a record; the continuous
+// quantities are filled in by k_shade over the compact records. Record fields
+// written here: rec_m = (rect, view, depth bits), rec_a = (binary32
+// covariance a, b, c, -), rec_b.w = Gaussian index.
+//
+// Two phases per block, so that the expensive binary32 layer runs on full
+// warps: a cheap conservative test (camera transform, near plane, reach of
+// the footprint) of 256 Gaussians against every view of the call appends the
+// surviving (Gaussian, view) pairs to a shared-memory queue; when the queue
+// could overflow, and at the end, the whole block drains it through the exact
+// discrete layer.
 // ---------------------------------------------------------------------------
+constexpr int kProjQ = 2048;  // (Gaussian, view) queue entries per block
+
+// camera-space position in the binary32 operation order of the oracle
+__device__ __forceinline__ void cam_xyz(const View& V, float4 p4, float& px, float& py, float& pz) {
+  px = add(add(add(mul(V.R[0], p4.x), mul(V.R[1], p4.y)), mul(V.R[2], p4.z)), V.t[0]);
+  py = add(add(add(mul(V.R[3], p4.x), mul(V.R[4], p4.y)), mul(V.R[5], p4.z)), V.t[1]);
+  pz = add(add(add(mul(V.R[6], p4.x), mul(V.R[7], p4.y)), mul(V.R[8], p4.z)), V.t[2]);
+}
+
+// Conservative reach: radius <= 3 sqrt(s_max^2 |J|_F^2 + 0.3 + sqrt(0.1)) + 1,
+// with margins for rounding; a Gaussian that fails it has an empty rectangle
+// under the exact rule, so skipping it changes nothing.
+__device__ __forceinline__ bool may_reach(const View& V, float4 p4) {
+  float px, py, pz;
+  cam_xyz(V, p4, px, py, pz);
+  if (!(pz >= 0.2f)) return false;
+  const float u = add(mul(V.fx, dvd(px, pz)), V.cx);
+  const float v = add(mul(V.fy, dvd(py, pz)), V.cy);
+  const float reach = 3.0f * sqrtf((p4.w * p4.w * V.jb2 / (pz * pz) + 0.62f) * 1.01f) + 3.0f;
+  const float wx = (float)(kTile * V.tiles_x), wy = (float)(kTile * V.tiles_y);
+  return u + reach >= -1.0f && u - reach <= wx + 1.0f && v + reach >= -1.0f && v - reach <= wy + 1.0f;
+}
+
+// The exact binary32 discrete layer (Sec. 3.1 projection, EWA footprint,
+// 3-sigma radius and tile rectangle). Returns false when the Gaussian has no
+// tile in this view.
+__device__ __forceinline__ bool discrete_layer(const View& V, float4 p4, float4 c0, float4 c1, float& pz, float& ca,
+                                               float& cb, float& cc, int& x0, int& x1, int& y0, int& y1) {
+  float px, py;
+  cam_xyz(V, p4, px, py, pz);
+  if (!(pz >= 0.2f)) return false;
+  const float ix = dvd(px, pz), iy = dvd(py, pz);
+  const float u = add(mul(V.fx, ix), V.cx);
+  const float v = add(mul(V.fy, iy), V.cy);
+  const float xh = mul(fminf(V.limx, fmaxf(-V.limx, ix)), pz);
+  const float yh = mul(fminf(V.limy, fmaxf(-V.limy, iy)), pz);
+  const float pz2 = mul(pz, pz);
+  const float j00 = dvd(V.fx, pz), j02 = -dvd(mul(V.fx, xh), pz2);
+  const float j11 = dvd(V.fy, pz), j12 = -dvd(mul(V.fy, yh), pz2);
+  float T[2][3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    T[0][k] = add(mul(j00, V.R[k]), mul(j02, V.R[6 + k]));
+    T[1][k] = add(mul(j11, V.R[3 + k]), mul(j12, V.R[6 + k]));
+  }
+  const float S[3][3] = {{c0.x, c0.y, c0.z}, {c0.y, c0.w, c1.x}, {c0.z, c1.x, c1.y}};
+  float U[2][3];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) U[a][k] = dot3(T[a][0], S[0][k], T[a][1], S[1][k], T[a][2], S[2][k]);
+  ca = add(dot3(U[0][0], T[0][0], U[0][1], T[0][1], U[0][2], T[0][2]), 0.3f);
+  cb = dot3(U[0][0], T[1][0], U[0][1], T[1][1], U[0][2], T[1][2]);
+  cc = add(dot3(U[1][0], T[1][0], U[1][1], T[1][1], U[1][2], T[1][2]), 0.3f);
+  const float det = sub(mul(ca, cc), mul(cb, cb));
+  if (!(det > 0.0f)) return false;
+  const float mid = mul(0.5f, add(ca, cc));
+  const float disc = sub(mul(mid, mid), det);
+  const float lam = add(mid, sqr(fmaxf(0.1f, disc)));
+  const float r = ceilf(mul(3.0f, sqr(lam)));
+  if (!(r > 0.0f)) return false;
+  // division by 16 is exact: multiply by 1/16
+  float fx0 = floorf(mul(sub(u, r), 0.0625f)), fx1 = floorf(mul(add(u, r), 0.0625f));
+  float fy0 = floorf(mul(sub(v, r), 0.0625f)), fy1 = floorf(mul(add(v, r), 0.0625f));
+  fx0 = fmaxf(fx0, 0.0f);
+  fy0 = fmaxf(fy0, 0.0f);
+  fx1 = fminf(fx1, (float)(V.tiles_x - 1));
+  fy1 = fminf(fy1, (float)(V.tiles_y - 1));
+  if (fx0 > fx1 || fy0 > fy1) return false;
+  x0 = (int)fx0;
+  x1 = (int)fx1;
+  y0 = (int)fy0;
+  y1 = (int)fy1;
+  return true;
+}
+
 __global__ void __launch_bounds__(256) k_project(SceneDev sc, const View* __restrict__ views, int n_views, Work w) {
-  const int lane = threadIdx.x & 31;
+  __shared__ int2 s_q[kProjQ];  // (Gaussian index, view)
+  __shared__ unsigned s_n;
+  const int tid = threadIdx.x, lane = tid & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
-  const int stride = gridDim.x * blockDim.x;
   const unsigned region = blockIdx.x % kRecRegions;
   const int4 hdr = w.ranges[0];  // (ranges, total length): only partitions in view are walked
-  for (int base = blockIdx.x * blockDim.x; base < hdr.y; base += stride) {  // warp-uniform loop
-    const int f = base + threadIdx.x;
-    const bool valid = f < hdr.y;
-    int i = 0;
-    if (valid) {
-      int lo = 1, hi = hdr.x;  // last range whose prefix is <= f
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (w.ranges[mid].z <= f) lo = mid; else hi = mid - 1;
-      }
-      const int4 rg = w.ranges[lo];
-      i = rg.x + (f - rg.z);
-    }
-    const float4 p4 = valid ? __ldg(sc.pos + i) : make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = c0;
-    bool have_cov = false;
-    for (int vi = 0; vi < n_views; ++vi) {
-      const View& V = views[vi];
+  if (tid == 0) s_n = 0u;
+  __syncthreads();
+  // exact layer over the cnt queued pairs by full warps; block-uniform
+  auto drain = [&](unsigned cnt) {
+    for (unsigned q0 = 0; q0 < cnt; q0 += 256) {
+      const unsigned q = q0 + (unsigned)tid;
       bool vis = false;
+      int i = 0, vi = 0, x0 = 0, x1 = 0, y0 = 0, y1 = 0;
       float pz = 0.f, ca = 0.f, cb = 0.f, cc = 0.f;
-      int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
-      if (valid) {
-        const float px = add(add(add(mul(V.R[0], p4.x), mul(V.R[1], p4.y)), mul(V.R[2], p4.z)), V.t[0]);
-        const float py = add(add(add(mul(V.R[3], p4.x), mul(V.R[4], p4.y)), mul(V.R[5], p4.z)), V.t[1]);
-        pz = add(add(add(mul(V.R[6], p4.x), mul(V.R[7], p4.y)), mul(V.R[8], p4.z)), V.t[2]);
-        if (pz >= 0.2f) {
-          const float ix = dvd(px, pz), iy = dvd(py, pz);
-          const float u = add(mul(V.fx, ix), V.cx);
-          const float v = add(mul(V.fy, iy), V.cy);
-          // Conservative reach: radius <= 3 sqrt(s_max^2 |J|_F^2 + 0.3 + sqrt(0.1)) + 1,
-          // with margins for rounding; a Gaussian that cannot reach the image has an
-          // empty rectangle under the exact rule, so skipping it changes nothing.
-          const float reach = 3.0f * sqrtf((p4.w * p4.w * V.jb2 / (pz * pz) + 0.62f) * 1.01f) + 3.0f;
-          const float wx = (float)(kTile * V.tiles_x), wy = (float)(kTile * V.tiles_y);
-          if (u + reach >= -1.0f && u - reach <= wx + 1.0f && v + reach >= -1.0f && v - reach <= wy + 1.0f) {
-            if (!have_cov) {
-              c0 = __ldg(sc.cov + 2 * i);
-              c1 = __ldg(sc.cov + 2 * i + 1);
-              have_cov = true;
-            }
-            const float xh = mul(fminf(V.limx, fmaxf(-V.limx, ix)), pz);
-            const float yh = mul(fminf(V.limy, fmaxf(-V.limy, iy)), pz);
-            const float pz2 = mul(pz, pz);
-            const float j00 = dvd(V.fx, pz), j02 = -dvd(mul(V.fx, xh), pz2);
-            const float j11 = dvd(V.fy, pz), j12 = -dvd(mul(V.fy, yh), pz2);
-            float T[2][3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-              T[0][k] = add(mul(j00, V.R[k]), mul(j02, V.R[6 + k]));
-              T[1][k] = add(mul(j11, V.R[3 + k]), mul(j12, V.R[6 + k]));
-            }
-            const float S[3][3] = {{c0.x, c0.y, c0.z}, {c0.y, c0.w, c1.x}, {c0.z, c1.x, c1.y}};
-            float U[2][3];
-#pragma unroll
-            for (int a = 0; a < 2; ++a)
-#pragma unroll
-              for (int k = 0; k < 3; ++k) U[a][k] = dot3(T[a][0], S[0][k], T[a][1], S[1][k], T[a][2], S[2][k]);
-            ca = add(dot3(U[0][0], T[0][0], U[0][1], T[0][1], U[0][2], T[0][2]), 0.3f);
-            cb = dot3(U[0][0], T[1][0], U[0][1], T[1][1], U[0][2], T[1][2]);
-            cc = add(dot3(U[1][0], T[1][0], U[1][1], T[1][1], U[1][2], T[1][2]), 0.3f);
-            const float det = sub(mul(ca, cc), mul(cb, cb));
-            if (det > 0.0f) {
-              const float mid = mul(0.5f, add(ca, cc));
-              const float disc = sub(mul(mid, mid), det);
-              const float lam = add(mid, sqr(fmaxf(0.1f, disc)));
-              const float r = ceilf(mul(3.0f, sqr(lam)));
-              if (r > 0.0f) {
-                // division by 16 is exact: multiply by 1/16
-                float fx0 = floorf(mul(sub(u, r), 0.0625f)), fx1 = floorf(mul(add(u, r), 0.0625f));
-                float fy0 = floorf(mul(sub(v, r), 0.0625f)), fy1 = floorf(mul(add(v, r), 0.0625f));
-                fx0 = fmaxf(fx0, 0.0f);
-                fy0 = fmaxf(fy0, 0.0f);
-                fx1 = fminf(fx1, (float)(V.tiles_x - 1));
-                fy1 = fminf(fy1, (float)(V.tiles_y - 1));
-                if (!(fx0 > fx1 || fy0 > fy1)) {
-                  vis = true;
-                  x0 = (int)fx0;
-                  x1 = (int)fx1;
-                  y0 = (int)fy0;
-                  y1 = (int)fy1;
-                }
-              }
-            }
-          }
-        }
+      if (q < cnt) {
+        const int2 e = s_q[q];
+        i = e.x;
+        vi = e.y;
+        const float4 p4 = __ldg(sc.pos + i);
+        const float4 c0 = __ldg(sc.cov + 2 * i), c1 = __ldg(sc.cov + 2 * i + 1);
+        vis = discrete_layer(views[vi], p4, c0, c1, pz, ca, cb, cc, x0, x1, y0, y1);
       }
       const unsigned vmask = __ballot_sync(0xffffffffu, vis);
       if (vmask == 0u) continue;
@@ -333,10 +347,48 @@ __global__ void __launch_bounds__(256) k_project(SceneDev sc, const View* __rest
       w.rec_b[slot] = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(i));
       w.rec_m[slot] = make_uint4((unsigned)x0 | ((unsigned)x1 << 16), (unsigned)y0 | ((unsigned)y1 << 16),
                                  (unsigned)vi, __float_as_uint(pz));
+      const View& V = views[vi];
       for (int ty = y0; ty <= y1; ++ty)
         for (int tx = x0; tx <= x1; ++tx) atomicAdd(&w.tile_count[V.tile_base + ty * V.tiles_x + tx], 1u);
     }
+    __syncthreads();
+    if (tid == 0) s_n = 0u;
+    __syncthreads();
+  };
+  for (int base = blockIdx.x * 256; base < hdr.y; base += gridDim.x * 256) {  // block-uniform loop
+    const int f = base + tid;
+    const bool valid = f < hdr.y;
+    int i = 0;
+    if (valid) {
+      int lo = 1, hi = hdr.x;  // last range whose prefix is <= f
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (w.ranges[mid].z <= f) lo = mid; else hi = mid - 1;
+      }
+      const int4 rg = w.ranges[lo];
+      i = rg.x + (f - rg.z);
+    }
+    const float4 p4 = valid ? __ldg(sc.pos + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int vi = 0; vi < n_views; ++vi) {
+      const bool pass = valid && may_reach(views[vi], p4);
+      const unsigned pm = __ballot_sync(0xffffffffu, pass);
+      if (pm) {  // warp-aggregated append to the queue
+        unsigned q0 = 0;
+        const int leader = __ffs(pm) - 1;
+        if (lane == leader) q0 = atomicAdd(&s_n, (unsigned)__popc(pm));
+        q0 = __shfl_sync(0xffffffffu, q0, leader);
+        if (pass) s_q[q0 + __popc(pm & lt_mask)] = make_int2(i, vi);
+      }
+      __syncthreads();
+      const unsigned queued = s_n;
+      __syncthreads();  // read by all before the next appends
+      if (queued + 256u > (unsigned)kProjQ) drain(queued);  // room for the next 256 entries
+    }
   }
+  __syncthreads();
+  const unsigned queued = s_n;
+  __syncthreads();
+  drain(queued);
 }
 
 // ---------------------------------------------------------------------------
@@ -344,7 +396,7 @@ __global__ void __launch_bounds__(256) k_project(SceneDev sc, const View* __rest
 // blending centre and, for the pose gradient, the per-record pose Jacobian.
 // ---------------------------------------------------------------------------
 template <bool GRAD>
-__global__ void __launch_bounds__(256) k_shade(SceneDev sc, const View* __restrict__ views, Work w) {
+__global__ void __launch_bounds__(256, 3) k_shade(SceneDev sc, const View* __restrict__ views, Work w) {
   if (w.ctr->overflow) return;
   for (uint32_t slot = blockIdx.x * blockDim.x + threadIdx.x; slot < w.rec_cap; slot += gridDim.x * blockDim.x) {
     const uint32_t reg = slot / w.rec_seg, loc = slot - reg * w.rec_seg;

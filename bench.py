@@ -32,13 +32,23 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Mpix/s fwd and pose-grad iters/s, 1M Gaussians @1080p; batched vs single-pose"
-WORKLOAD = "aerial 1M Gaussians SH3, 1920x1080 f=1400, pose-gradient step (fwd + L1 rgb/depth loss + se(3) adjoint)"
+WORKLOAD = ("aerial 1M Gaussians SH3, 1920x1080 f=1400, pose-gradient step (fwd + L1 rgb/depth loss + se(3) "
+            "gradient)")
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 256 << 20
 # fp32 operations of one (pixel, Gaussian) evaluation on the skip path:
 # dx, dy, dx^2, dy^2, A dx^2, C dy^2 (+), x(-1/2), dx dy, B dx dy (+), o e^p, min, 2 compares
 FLOPS_PER_EVAL = 14
+# additional fp32 operations of a blended evaluation in the tangent pass (FMA = 2):
+# blend 12 (1 - a, T', w = a T, C, D += w (c, z)); tangent 168: -dpower/dxi over 6
+# directions (5 FMA each) 60, dalpha 6, dw = dalpha T + a dT 18, dT 6, dC 36,
+# colour rows (3 x 3 FMA) 18, dD 24
+FLOPS_PER_BLEND = 180
+# DRAM bytes (read + write) of one tangent-pass launch on this workload, from
+# one ncu capture of this kernel (dram__bytes_read.sum + dram__bytes_write.sum);
+# None whenever the kernel has changed since that capture
+COMPOSITE_DRAM_BYTES = None
 
 
 def parse():
@@ -175,15 +185,11 @@ def run_reference(args):
     ref = O.render(scene, cam, T_ref, geom64=True, n_threads=n_thr)
     trgb = ref["rgb"].T.reshape(3, H, W).astype(np.float32)
     tdep = ref["depth"].reshape(H, W).astype(np.float32)
-    n_pix = 8192
-    g = np.random.default_rng(1)
+    n_pix = H * W  # the whole frame per step, as the GPU arm (about 0.75 s on 16 cores)
 
     def step():
-        pix = np.sort(g.choice(H * W, n_pix, replace=False))
-        w = np.zeros((H, W), np.float32)
-        w.reshape(-1)[pix] = 1.0
-        O.render(scene, cam, T_q, geom64=True, want_grad=True, pixels=pix, target_rgb=trgb, target_depth=tdep,
-                 pixel_weight=w, n_threads=n_thr)
+        O.render(scene, cam, T_q, geom64=True, want_grad=True, target_rgb=trgb, target_depth=tdep,
+                 n_threads=n_thr)
 
     for _ in range(args.warmup):
         step()
@@ -198,7 +204,9 @@ def run_reference(args):
             "config": {"workload": WORKLOAD, "gaussians": 1_000_000, "width": W, "height": H, "sh_degree": 3,
                        "sample_pixels": n_pix},
             "cpu_baseline": {"value": v, "unit": "Mpix/s", "cores": n_thr, "kind": "oracle",
-                             "sample": "fp64 oracle pose-gradient step on %d random pixels per step" % n_pix},
+                             "sample": "fp64 oracle pose-gradient step (projection of all 1M Gaussians, binning, "
+                                       "fp64 compositing + forward-mode se(3) gradient) on the whole %dx%d frame "
+                                       "per step" % (W, H)},
             "e2e": {"value": v, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -305,11 +313,14 @@ def main():
     fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FMA = 2
     dom = max(per_kernel, key=per_kernel.get)
     kernels = {k: {"ms": v, "share": v / max(sum(per_kernel.values()), 1e-12)} for k, v in per_kernel.items()}
+    blends = gsr.gs_scene_blend_count(S.handle)
     if dom == "composite":
-        ach = evals * FLOPS_PER_EVAL / (per_kernel[dom] * 1e-3) / 1e12
+        flops = evals * FLOPS_PER_EVAL + blends * FLOPS_PER_BLEND
+        ach = flops / (per_kernel[dom] * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
-                "traffic": None, "kernel": dom,
-                "work": "%d (pixel, Gaussian) evaluations x %d fp32 ops (skip path)" % (evals, FLOPS_PER_EVAL),
+                "traffic": COMPOSITE_DRAM_BYTES, "kernel": "composite (tangent pass)",
+                "work": "%d (pixel, Gaussian) evaluations x %d fp32 ops (skip path) + %d blended pairs x %d "
+                        "(blend + six-direction tangent update)" % (evals, FLOPS_PER_EVAL, blends, FLOPS_PER_BLEND),
                 "peak_source": "%d SMs x 128 fp32 lanes x 2 x %.0f MHz (%s max clock)" % (n_sm, sm_max, pk_src)}
     else:
         nsh = 48
@@ -361,7 +372,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_grad, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "gaussians": 1_000_000, "width": W, "height": H, "sh_degree": 3,
-                   "records": int(n_rec), "pairs": int(n_pairs), "evaluations": evals,
+                   "records": int(n_rec), "pairs": int(n_pairs), "evaluations": evals, "blended": int(blends),
                    "l2": "flushed (256 MB write) between timed steps, outside the timed events",
                    "parallelism": "replicas" if world > 1 else "single"},
         "pose_grad_iters_per_s": world / (ms_grad * 1e-3),

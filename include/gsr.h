@@ -278,6 +278,13 @@ gs_status gs_scene_set_timing(gs_scene* scene, int enable);
  * then reset the sums. Errors: INVALID_ARG, CUDA. */
 gs_status gs_scene_kernel_times(gs_scene* scene, double* total_ms, int64_t* launches);
 
+/* Number of (pixel, Gaussian) pairs that the last pose-gradient call blended
+ * (alpha accumulated into a pixel before its transmittance cutoff), summed
+ * over its views: the work unit of the tangent pass, for roofline accounting.
+ * 0 after a forward-only call. Waits for `stream`. `blended` is a host
+ * pointer. Errors: INVALID_ARG, CUDA. */
+gs_status gs_scene_blend_count(gs_scene* scene, void* stream, int64_t* blended);
+
 /* gs_render_noalloc -- the forward render of gs_render that allocates
  * nothing (the paper has no counterpart).
  *

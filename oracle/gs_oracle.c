@@ -546,7 +546,7 @@ static void prep_gauss(const prep_ctx* cx, int64_t g, gprep* o) {
 
 typedef struct {
   double rgb[3][ORC_ND], depth[ORC_ND], T[ORC_ND];
-  int32_t last_idx, n_eval;
+  int32_t last_idx, n_eval, n_blend;
   uint8_t flags;
   uint64_t hash;
 } pix_result;
@@ -632,6 +632,7 @@ static void composite_pixel(const gprep* prep, const int32_t* vis, const uint32_
     r->T[0] = Tn;
     for (int k = 1; k < nd; ++k) r->T[k] = dT[k];
     r->last_idx = (int32_t)(j + 1);
+    r->n_blend += 1;
     r->hash = mix64(r->hash, ((uint64_t)gid << 3) | 4 | (capped ? 8 : 0));
   }
 }
@@ -735,6 +736,7 @@ static void* render_worker(void* arg) {
       if (out->final_T) out->final_T[i] = r.T[0];
       if (out->last_idx) out->last_idx[i] = r.last_idx;
       if (out->n_eval) out->n_eval[i] = r.n_eval;
+      if (out->n_blend) out->n_blend[i] = r.n_blend;
       if (out->flags) out->flags[i] = flags;
       if (out->feats && fd)
         for (int c = 0; c < fd; ++c) out->feats[i * fd + c] = fbuf[c];

@@ -82,6 +82,7 @@ typedef struct {
   double* final_T;    /* n_pix, or NULL */
   int32_t* last_idx;  /* n_pix: 1 + list position of the last blended Gaussian (0 = none) */
   int32_t* n_eval;    /* n_pix: list entries examined, or NULL */
+  int32_t* n_blend;   /* n_pix: Gaussians blended (accumulated before the cutoff), or NULL */
   uint8_t* flags;     /* n_pix: ORC_TIE_* bits, or NULL */
   double* feats;      /* n_pix x feat_dim, or NULL */
   double* loss;       /* 1, or NULL */

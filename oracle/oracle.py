@@ -75,7 +75,7 @@ class _Opts(ctypes.Structure):
 
 class _Out(ctypes.Structure):
     _fields_ = [(name, ctypes.c_void_p) for name in
-                ("rgb", "depth", "alpha", "final_T", "last_idx", "n_eval", "flags", "feats",
+                ("rgb", "depth", "alpha", "final_T", "last_idx", "n_eval", "n_blend", "flags", "feats",
                  "loss", "grad", "signature", "n_pairs")]
 
 
@@ -197,7 +197,8 @@ def render(scene, cam, T, *, geom64=False, want_grad=False, n_threads=1, pixels=
 
     Returns a dict of per-pixel arrays in the order of ``pixels`` (or row-major
     for the full frame): rgb (n,3), depth, alpha, final_T, last_idx, n_eval,
-    flags, feats (n,feat_dim) and, with targets, loss and grad (rho, phi).
+    n_blend, flags, feats (n,feat_dim) and, with targets, loss and grad (rho,
+    phi).
     """
     sc = scene if isinstance(scene, OracleScene) else OracleScene(scene)
     W, H = int(cam["width"]), int(cam["height"])
@@ -215,6 +216,7 @@ def render(scene, cam, T, *, geom64=False, want_grad=False, n_threads=1, pixels=
         "final_T": np.zeros(npx, np.float64),
         "last_idx": np.zeros(npx, np.int32),
         "n_eval": np.zeros(npx, np.int32),
+        "n_blend": np.zeros(npx, np.int32),
         "flags": np.zeros(npx, np.uint8),
         "loss": np.zeros(1, np.float64),
         "grad": np.zeros(6, np.float64),
@@ -223,8 +225,8 @@ def render(scene, cam, T, *, geom64=False, want_grad=False, n_threads=1, pixels=
     }
     if sc.feat_dim and want_feats:
         res["feats"] = np.zeros((npx, sc.feat_dim), np.float64)
-    out = _Out(*[_p(res.get(k)) for k in ("rgb", "depth", "alpha", "final_T", "last_idx", "n_eval", "flags",
-                                           "feats", "loss", "grad", "signature", "n_pairs")])
+    out = _Out(*[_p(res.get(k)) for k in ("rgb", "depth", "alpha", "final_T", "last_idx", "n_eval", "n_blend",
+                                           "flags", "feats", "loss", "grad", "signature", "n_pairs")])
     cc = _cam(cam)
     Tp = _pose(T)
     fn = lib().orc_render_brute if brute else lib().orc_render

@@ -1047,6 +1047,17 @@ gs_status gs_scene_kernel_times(gs_scene* s, double* total_ms, int64_t* launches
   return GS_OK;
 }
 
+gs_status gs_scene_blend_count(gs_scene* s, void* stream, int64_t* blended) {
+  g_err.clear();
+  GS_TRY(check_scene(s));
+  if (!blended) return fail(GS_ERR_INVALID_ARG, "blended is required");
+  GS_TRY(set_device(s));
+  Counters c;
+  GS_TRY(read_counters(s, (cudaStream_t)stream, c));
+  *blended = (int64_t)c.blends;
+  return GS_OK;
+}
+
 gs_status gs_scene_status(gs_scene* s, void* stream, int64_t* needed_records, int64_t* needed_pairs) {
   g_err.clear();
   GS_TRY(check_scene(s));

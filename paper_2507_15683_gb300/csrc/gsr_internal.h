@@ -60,7 +60,8 @@ struct Counters {
   unsigned int fwd_queue;   // persistent tile queue of the forward render
   unsigned int tan_queue;   // persistent tile queue of the tangent (pose-gradient) render
   unsigned int error;       // device-side consistency failure
-  unsigned int pad[3];
+  unsigned int pad;
+  unsigned long long blends;  // (pixel, Gaussian) pairs blended by the tangent pass
 };
 
 // Scene arena (device pointers).

@@ -369,12 +369,19 @@ __global__ void __launch_bounds__(kTileThreads, TAN ? 4 : FEAT ? 3 : 5) k_compos
   warp_block(tid, lx, ly, bxw, byw);
   const float pxc = (float)lx + 0.5f, pyc = (float)ly + 0.5f;
   const float4* rec_j4 = reinterpret_cast<const float4*>(w.rec_j);
+  uint32_t n_blend = 0;  // tangent pass: blended (pixel, Gaussian) pairs of this thread
   for (;;) {
     // the tangent pass keeps its own queue: it can follow a feature render
     if (tid == 0) s_tile = atomicAdd(TAN ? &w.ctr->tan_queue : &w.ctr->fwd_queue, 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
-    if (tile >= w.n_tiles) break;
+    if (tile >= w.n_tiles) {
+      if (TAN) {
+        const uint32_t nb = __reduce_add_sync(0xffffffffu, n_blend);
+        if (lane == 0 && nb) atomicAdd(&w.ctr->blends, (unsigned long long)nb);
+      }
+      break;
+    }
     const int vi = find_view(views, n_views, tile);
     const View& V = views[vi];
     const uint32_t lt = tile - V.tile_base;
@@ -513,6 +520,7 @@ __global__ void __launch_bounds__(kTileThreads, TAN ? 4 : FEAT ? 3 : 5) k_compos
             }
           }
         }
+        if (TAN) n_blend += acc ? 1u : 0u;
         T = acc ? Tn : T;
         last = acc ? (uint32_t)(bs + j + 1) : last;
         done = done || stop;

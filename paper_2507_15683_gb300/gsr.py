@@ -82,6 +82,7 @@ def _load():
         "gs_scene_stream_stats": [vp, vp, vp, vp],
         "gs_scene_evict": [vp],
         "gs_scene_kernel_times": [vp, vp, vp],
+        "gs_scene_blend_count": [vp, vp, vp],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -258,6 +259,13 @@ def gs_scene_kernel_times(h):
     n = np.zeros(len(KERNEL_NAMES), np.int64)
     _check(lib.gs_scene_kernel_times(h, ms.ctypes.data, n.ctypes.data))
     return ms, n
+
+
+def gs_scene_blend_count(h, stream=None):
+    """(pixel, Gaussian) pairs blended by the last pose-gradient call."""
+    b = ctypes.c_int64()
+    _check(lib.gs_scene_blend_count(h, _stream() if stream is None else stream, ctypes.byref(b)))
+    return b.value
 
 
 def gs_scene_stream_stats(h):

@@ -104,3 +104,24 @@ def test_autograd_function_and_fp32_finite_differences(oracle, gsr):
     print("fp32 FD", fd, "analytic", grad, "block rel", block_rel_err(fd, grad))
     assert max(block_rel_err(fd, grad)) < 0.2
     S.close()
+
+
+def test_blend_count_matches_oracle(oracle, gsr):
+    # the tangent pass counts the (pixel, Gaussian) pairs it blends; the oracle
+    # counts the same pairs per pixel; pixels with a near-tie decision may differ
+    scene, cam, T_gt = _small_aerial(33)
+    T_q = synth.perturb_pose(T_gt, synth.rng(33), 1.0, 1.0)
+    trgb, tdep = _targets(oracle, scene, cam, T_gt)
+    orc = oracle.render(scene, cam, T_q, geom64=True, target_rgb=trgb, target_depth=tdep, n_threads=16)
+    S = gsr.Scene(scene)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    S.render_pose_grad(cam, T_q, t(trgb), t(tdep))
+    n_gpu = gsr.gs_scene_blend_count(S.handle)
+    S.render(cam, T_q)
+    assert gsr.gs_scene_blend_count(S.handle) == 0  # forward-only calls count nothing
+    S.close()
+    flagged = orc["flags"] != 0
+    n_orc = int(orc["n_blend"].sum())
+    slack = int(orc["n_eval"][flagged].sum())
+    print("blended: gpu", n_gpu, "oracle", n_orc, "flagged-pixel slack", slack)
+    assert n_orc > 0 and abs(n_gpu - n_orc) <= slack

@@ -133,6 +133,8 @@ def test_two_stacked_gaussians(oracle):
     np.testing.assert_allclose(r["rgb"], expect, atol=1e-12)
     np.testing.assert_allclose(r["depth"], 5 * a_front + 6 * (1 - a_front) * a_back, atol=1e-12)
     np.testing.assert_allclose(r["final_T"], (1 - a_front) * (1 - a_back), atol=1e-12)
+    # blended count: one per Gaussian whose alpha reaches the floor at the pixel
+    np.testing.assert_array_equal(r["n_blend"], (a_front >= 1 / 255).astype(int) + (a_back >= 1 / 255).astype(int))
 
 
 def test_separated_gaussians_are_independent(oracle):
@@ -172,7 +174,7 @@ def test_alpha_cap_and_transmittance_cutoff(oracle):
     p = 64 * 128 + 64
     c1, c2 = 0.5 + Y00 * dc[0].astype(np.float64), 0.5 + Y00 * dc[1].astype(np.float64)
     np.testing.assert_allclose(r["rgb"][p], 0.99 * c1 + (1 - 0.99) * 0.99 * c2, rtol=1e-14)
-    assert r["last_idx"][p] == 2 and r["n_eval"][p] == 3
+    assert r["last_idx"][p] == 2 and r["n_eval"][p] == 3 and r["n_blend"][p] == 2
     assert r["final_T"][p] == pytest.approx((1 - 0.99) ** 2, rel=1e-12)
     assert r["flags"][p] & oracle.TIE_T_CUTOFF  # T after two is within rounding of the cutoff
 
@@ -193,6 +195,9 @@ def test_weights_telescope(oracle, seed):
     assert r["final_T"].min() >= 1e-4 and r["final_T"].max() <= 1.0
     assert r["alpha"].min() >= 0.0 and r["alpha"].max() < 1.0
     assert np.all(r["last_idx"] <= r["n_eval"])
+    # blended Gaussians: never more than the examined prefix, none exactly when nothing was blended
+    assert np.all(r["n_blend"] <= r["last_idx"])
+    np.testing.assert_array_equal(r["n_blend"] == 0, r["last_idx"] == 0)
 
 
 def test_features_identical_blending(oracle):
@@ -222,7 +227,7 @@ def test_binned_equals_brute_force(oracle, seed, w, h, deg):
     for geom64 in (False, True):
         a = oracle.render(sc, c, np.eye(4), geom64=geom64)
         b = oracle.render(sc, c, np.eye(4), geom64=geom64, brute=True)
-        for k in ("rgb", "depth", "final_T", "last_idx", "n_eval"):
+        for k in ("rgb", "depth", "final_T", "last_idx", "n_eval", "n_blend"):
             np.testing.assert_array_equal(a[k], b[k])
 
 

@@ -355,20 +355,26 @@ __global__ void __launch_bounds__(256) k_project(SceneDev sc, const View* __rest
     if (tid == 0) s_n = 0u;
     __syncthreads();
   };
-  for (int base = blockIdx.x * 256; base < hdr.y; base += gridDim.x * 256) {  // block-uniform loop
-    const int f = base + tid;
-    const bool valid = f < hdr.y;
-    int i = 0;
-    if (valid) {
-      int lo = 1, hi = hdr.x;  // last range whose prefix is <= f
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (w.ranges[mid].z <= f) lo = mid; else hi = mid - 1;
-      }
-      const int4 rg = w.ranges[lo];
-      i = rg.x + (f - rg.z);
+  // Gaussian index of flat position f over the active ranges, or -1
+  auto gaussian_of = [&](int f) -> int {
+    if (f >= hdr.y) return -1;
+    int lo = 1, hi = hdr.x;  // last range whose prefix is <= f
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (w.ranges[mid].z <= f) lo = mid; else hi = mid - 1;
     }
-    const float4 p4 = valid ? __ldg(sc.pos + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int4 rg = w.ranges[lo];
+    return rg.x + (f - rg.z);
+  };
+  // the next block of means is loaded before the current one is tested
+  int i_next = gaussian_of(blockIdx.x * 256 + tid);
+  float4 p_next = i_next >= 0 ? __ldg(sc.pos + i_next) : make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int base = blockIdx.x * 256; base < hdr.y; base += gridDim.x * 256) {  // block-uniform loop
+    const int i = i_next;
+    const bool valid = i >= 0;
+    const float4 p4 = p_next;
+    i_next = gaussian_of(base + gridDim.x * 256 + tid);
+    if (i_next >= 0) p_next = __ldg(sc.pos + i_next);
     for (int vi = 0; vi < n_views; ++vi) {
       const bool pass = valid && may_reach(views[vi], p4);
       const unsigned pm = __ballot_sync(0xffffffffu, pass);

@@ -48,7 +48,7 @@ FLOPS_PER_BLEND = 180
 # DRAM bytes (read + write) of one tangent-pass launch on this workload, from
 # one ncu capture of this kernel (dram__bytes_read.sum + dram__bytes_write.sum);
 # None whenever the kernel has changed since that capture
-COMPOSITE_DRAM_BYTES = 83_365_376  # 80,574,464 read + 2,790,912 written
+COMPOSITE_DRAM_BYTES = None
 
 
 def parse():

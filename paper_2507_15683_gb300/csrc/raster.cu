@@ -471,29 +471,32 @@ __global__ void __launch_bounds__(kTileThreads, TAN ? 4 : FEAT ? 3 : 5) k_compos
           // rows. S_k = dx P + dy Q + dx^2 dA/2 + dx dy dB + dy^2 dC/2 is
           // -dpower/dxi_k.
           const float4* J4 = sj + j * (kJacStride / 4);
-          const float2 X = make_float2(dx, dx), Y = make_float2(dy, dy);
-          const float xx = dx * dx, xy = dx * dy, yy = dy * dy;
-          const float2 XX = make_float2(xx, xx), XY = make_float2(xy, xy), YY = make_float2(yy, yy);
-          const float ad = (acc && oe < kAlphaCap) ? -alpha : 0.0f;  // dalpha = -alpha S
+          // T dalpha = -alpha T S (0 where the 0.99 cap is active); -alpha T
+          // is folded into the monomials of the pixel offset
+          const float nat = (acc && oe < kAlphaCap) ? -alpha * T : 0.0f;
+          const float qx = nat * dx, qy = nat * dy;
+          const float qxx = qx * dx, qxy = qx * dy, qyy = qy * dy;
+          const float2 X = make_float2(qx, qx), Y = make_float2(qy, qy);
+          const float2 XX = make_float2(qxx, qxx), XY = make_float2(qxy, qxy), YY = make_float2(qyy, qyy);
           const float ae = acc ? alpha : 0.0f;
-          const float2 AD = make_float2(ad, ad), AE = make_float2(ae, ae), TT = make_float2(T, T);
+          const float2 AE = make_float2(ae, ae);
           const float2 CR = make_float2(c.x, c.x), CG = make_float2(c.y, c.y), CB = make_float2(c.z, c.z);
           const float2 ZZ = make_float2(zj, zj), WW = make_float2(wgt, wgt);
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
             const float4 pq = J4[3 * k], ab = J4[3 * k + 1], cz = J4[3 * k + 2];
-            float2 S2 = __fmul2_rn(make_float2(pq.x, pq.y), X);
-            S2 = __ffma2_rn(make_float2(pq.z, pq.w), Y, S2);
-            S2 = __ffma2_rn(make_float2(ab.x, ab.y), XX, S2);
-            S2 = __ffma2_rn(make_float2(ab.z, ab.w), XY, S2);
-            S2 = __ffma2_rn(make_float2(cz.x, cz.y), YY, S2);
-            const float2 da = __fmul2_rn(S2, AD);
-            const float2 dw = __ffma2_rn(da, TT, __fmul2_rn(dT[k], AE));
+            float2 tda = __fmul2_rn(make_float2(pq.x, pq.y), X);  // T dalpha
+            tda = __ffma2_rn(make_float2(pq.z, pq.w), Y, tda);
+            tda = __ffma2_rn(make_float2(ab.x, ab.y), XX, tda);
+            tda = __ffma2_rn(make_float2(ab.z, ab.w), XY, tda);
+            tda = __ffma2_rn(make_float2(cz.x, cz.y), YY, tda);
+            const float2 dw = __ffma2_rn(dT[k], AE, tda);
             dT[k] = __ffma2_rn(dw, make_float2(-1.0f, -1.0f), dT[k]);
             dC0[k] = __ffma2_rn(dw, CR, dC0[k]);
             dC1[k] = __ffma2_rn(dw, CG, dC1[k]);
             dC2[k] = __ffma2_rn(dw, CB, dC2[k]);
-            dD[k] = __ffma2_rn(dw, ZZ, __ffma2_rn(make_float2(cz.z, cz.w), WW, dD[k]));
+            // dz/drho_0 = dz/drho_1 = 0: the first pair has no w dz term
+            dD[k] = __ffma2_rn(dw, ZZ, k == 0 ? dD[k] : __ffma2_rn(make_float2(cz.z, cz.w), WW, dD[k]));
           }
           // colour depends on the camera centre only: rho directions 0..2
           const float4 r0 = J4[9], r1 = J4[10], r2 = J4[11];

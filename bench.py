@@ -332,13 +332,9 @@ def main():
     # end to end through the public API: pinned host targets -> device, synchronous call, result to host
     h_rgb = trgb.cpu().pin_memory()
     h_dep = tdep.cpu().pin_memory()
-    d_rgb = torch.empty_like(trgb)
-    d_dep = torch.empty_like(tdep)
 
-    def e2e_step():
-        d_rgb.copy_(h_rgb, non_blocking=True)
-        d_dep.copy_(h_dep, non_blocking=True)
-        return S.render_pose_grad(cam, T_q, d_rgb, d_dep)
+    def e2e_step():  # host targets in, (loss, gradient) out; the upload overlaps projection and binning
+        return S.render_pose_grad_host(cam, T_q, h_rgb, h_dep)
 
     for _ in range(args.warmup):
         e2e_step()

@@ -133,17 +133,32 @@ gs_status gs_render_async(gs_scene* scene, const gs_camera* cam, const gs_pose* 
 /* Render one view and the gradient of
  *   L = 1/(3P) sum_px,c w_px |C - C*| + depth_weight * 1/P sum_px w_px |D - D*|
  * (P = W * H, w_px = pixel_weight or 1, sign(0) = 0) with respect to the pose
- * tangent xi = (rho, phi). The per-pixel transmittance is recomputed from the
- * stored final transmittance; the per-pixel sums are reduced across pixels in
- * fp64. target_rgb (3 x H x W), target_depth (H x W) and pixel_weight (H x W or
+ * tangent xi = (rho, phi) (left perturbation, T(xi) = Exp(xi^) T_cw). One
+ * compositing pass carries the six pose derivatives of colour, depth and
+ * transmittance through the front-to-back blend; the per-pixel terms are
+ * summed in fp32 per tile and in fp64 across tiles, in a fixed order.
+ * target_rgb (3 x H x W), target_depth (H x W) and pixel_weight (H x W or
  * NULL) are device pointers. loss_out (1) and grad_xi_out (6) are host
  * pointers written before return (synchronous, with the same regrow rule as
- * gs_render). out may be NULL or have NULL members; the forward outputs are
- * then kept internally. Errors: INVALID_ARG, OOM, CUDA. */
+ * gs_render). out may be NULL or have NULL members (those outputs are not
+ * written). Errors: INVALID_ARG, OOM, CUDA. */
 gs_status gs_render_pose_grad(gs_scene* scene, const gs_camera* cam, const gs_pose* pose,
                               const float* target_rgb, const float* target_depth, const float* pixel_weight,
                               float depth_weight, const gs_outputs* out, double* loss_out,
                               double* grad_xi_out, void* stream);
+
+/* gs_render_pose_grad with the loss inputs in host memory: target_rgb
+ * (3 x H x W), target_depth (H x W) and pixel_weight (H x W or NULL) are host
+ * pointers, copied into a scene-owned device buffer on a side stream that runs
+ * beside the projection and binning kernels; only the compositing pass waits
+ * for the copies. Page-locked (pinned) host memory makes the copies
+ * asynchronous; pageable memory works but is copied before the kernels start.
+ * The host buffers may be reused once the call returns. Everything else as
+ * gs_render_pose_grad. Errors: INVALID_ARG, OOM, CUDA. */
+gs_status gs_render_pose_grad_host(gs_scene* scene, const gs_camera* cam, const gs_pose* pose,
+                                   const float* target_rgb, const float* target_depth, const float* pixel_weight,
+                                   float depth_weight, const gs_outputs* out, double* loss_out,
+                                   double* grad_xi_out, void* stream);
 
 /* Asynchronous form of gs_render_pose_grad: result_dev (device, 7 doubles)
  * receives (loss, grad rho_x, rho_y, rho_z, phi_x, phi_y, phi_z). Capacity

@@ -138,6 +138,11 @@ struct gs_scene {
   DevBuf ctr, result, views;
   Counters* ctr_host = nullptr;
   double* result_host = nullptr;
+  // loss targets uploaded from host memory (gs_render_pose_grad_host) on a side
+  // stream that overlaps the projection and binning kernels
+  DevBuf targets;
+  cudaStream_t copy_st = nullptr;
+  cudaEvent_t ev_call = nullptr, ev_targets = nullptr;
   // kernel timing: one set of GS_KERNEL_COUNT + 1 events per timed call
   bool timing = false;
   struct TimedCall {
@@ -332,7 +337,7 @@ void fill_table(const gs_scene* s, const std::vector<View>& hv, const std::vecto
 }
 
 gs_status enqueue(gs_scene* s, const std::vector<View>& hv, const std::vector<int4>& ranges, uint64_t n_tiles,
-                  const GradIn* g, cudaStream_t st, const char* upload_src) {
+                  const GradIn* g, cudaStream_t st, const char* upload_src, cudaEvent_t targets_ready = nullptr) {
   const int nv = (int)hv.size();
   GS_TRY(grow_tiles(s, n_tiles));
   GS_TRY(ensure(s->views, table_bytes(s, nv)));
@@ -395,6 +400,7 @@ gs_status enqueue(gs_scene* s, const std::vector<View>& hv, const std::vector<in
     // the tangent pass re-renders the same values (without features) and adds
     // the loss and its pose gradient
     double* res = g->result ? g->result : w.result;
+    if (targets_ready) GS_CUDA(cudaStreamWaitEvent(st, targets_ready, 0));  // only this pass reads the targets
     GS_CUDA(launch_composite_tangent(sc, dviews, nv, w, res, s->sm_count * composite_blocks_per_sm(0, true), st));
   }
   GS_CUDA(mark(6));
@@ -543,13 +549,19 @@ gs_status read_counters(gs_scene* s, cudaStream_t st, Counters& c) {
 
 // Synchronous call with the regrow rule: render, check the counters, and if the
 // workspace was too small grow it and render again.
-gs_status run_sync(gs_scene* s, const std::vector<View>& hv, uint64_t n_tiles, const GradIn* g, cudaStream_t st) {
+// With a pose gradient the (loss, gradient) of the first view are copied to
+// s->result_host in the same round trip as the counters.
+gs_status run_sync(gs_scene* s, const std::vector<View>& hv, uint64_t n_tiles, const GradIn* g, cudaStream_t st,
+                   cudaEvent_t targets_ready = nullptr) {
   std::vector<int4> ranges;
   GS_TRY(prepare_call(s, hv, st, ranges));
   for (int attempt = 0; attempt < 4; ++attempt) {
-    GS_TRY(enqueue(s, hv, ranges, n_tiles, g, st, nullptr));
-    Counters c;
-    GS_TRY(read_counters(s, st, c));
+    GS_TRY(enqueue(s, hv, ranges, n_tiles, g, st, nullptr, targets_ready));
+    GS_CUDA(cudaMemcpyAsync(s->ctr_host, s->ctr.p, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    if (g && !g->result)
+      GS_CUDA(cudaMemcpyAsync(s->result_host, s->result.p, 7 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    GS_CUDA(cudaStreamSynchronize(st));
+    const Counters c = *s->ctr_host;
     if (c.error) return fail(GS_ERR_INTERNAL, "device consistency check failed");
     if (!c.overflow) return GS_OK;
     if (c.overflow & 4u) return fail(GS_ERR_CAPACITY, "more than 2^32 (tile, Gaussian) pairs in one call");
@@ -855,6 +867,10 @@ void gs_destroy_scene(gs_scene* s) {
     if (h) cudaFreeHost(h);
   if (s->ctr_host) cudaFreeHost(s->ctr_host);
   if (s->result_host) cudaFreeHost(s->result_host);
+  release(s->targets);
+  if (s->copy_st) cudaStreamDestroy(s->copy_st);
+  if (s->ev_call) cudaEventDestroy(s->ev_call);
+  if (s->ev_targets) cudaEventDestroy(s->ev_targets);
   delete s;
 }
 
@@ -908,8 +924,47 @@ gs_status gs_render_pose_grad(gs_scene* s, const gs_camera* cam, const gs_pose* 
   GS_TRY(build_views(s, 1, cam, pose, out, &g, hv, n_tiles));
   const cudaStream_t st = (cudaStream_t)stream;
   GS_TRY(run_sync(s, hv, n_tiles, &g, st));
-  GS_CUDA(cudaMemcpyAsync(s->result_host, s->result.p, 7 * sizeof(double), cudaMemcpyDeviceToHost, st));
-  GS_CUDA(cudaStreamSynchronize(st));
+  if (loss_out) *loss_out = s->result_host[0];
+  if (grad_xi_out)
+    for (int k = 0; k < 6; ++k) grad_xi_out[k] = s->result_host[1 + k];
+  return GS_OK;
+}
+
+gs_status gs_render_pose_grad_host(gs_scene* s, const gs_camera* cam, const gs_pose* pose,
+                                   const float* target_rgb, const float* target_depth, const float* pixel_weight,
+                                   float depth_weight, const gs_outputs* out, double* loss_out, double* grad_xi_out,
+                                   void* stream) {
+  g_err.clear();
+  GS_TRY(check_scene(s));
+  if (!cam || !pose) return fail(GS_ERR_INVALID_ARG, "cam and pose are required");
+  GS_TRY(check_grad_args(target_rgb, target_depth, depth_weight));
+  GS_TRY(set_device(s));
+  GS_TRY(check_cam(*cam));
+  const cudaStream_t st = (cudaStream_t)stream;
+  const size_t P = (size_t)cam->width * cam->height;
+  GS_TRY(ensure(s->targets, (pixel_weight ? 5 : 4) * P * sizeof(float)));
+  if (!s->copy_st) GS_CUDA(cudaStreamCreateWithFlags(&s->copy_st, cudaStreamNonBlocking));
+  if (!s->ev_call) GS_CUDA(cudaEventCreateWithFlags(&s->ev_call, cudaEventDisableTiming));
+  if (!s->ev_targets) GS_CUDA(cudaEventCreateWithFlags(&s->ev_targets, cudaEventDisableTiming));
+  float* d_rgb = dp<float>(s->targets);
+  float* d_dep = d_rgb + 3 * P;
+  float* d_w = pixel_weight ? d_rgb + 4 * P : nullptr;
+  // the uploads start after the work already on the caller's stream (which may
+  // still read the buffers) and run beside this call's projection and binning
+  GS_CUDA(cudaEventRecord(s->ev_call, st));
+  GS_CUDA(cudaStreamWaitEvent(s->copy_st, s->ev_call, 0));
+  GS_CUDA(cudaMemcpyAsync(d_rgb, target_rgb, 3 * P * sizeof(float), cudaMemcpyHostToDevice, s->copy_st));
+  GS_CUDA(cudaMemcpyAsync(d_dep, target_depth, P * sizeof(float), cudaMemcpyHostToDevice, s->copy_st));
+  if (d_w) GS_CUDA(cudaMemcpyAsync(d_w, pixel_weight, P * sizeof(float), cudaMemcpyHostToDevice, s->copy_st));
+  GS_CUDA(cudaEventRecord(s->ev_targets, s->copy_st));
+  const float* tr = d_rgb;
+  const float* td = d_dep;
+  const float* tw = d_w;
+  GradIn g{&tr, &td, &tw, depth_weight, nullptr};
+  std::vector<View> hv;
+  uint64_t n_tiles;
+  GS_TRY(build_views(s, 1, cam, pose, out, &g, hv, n_tiles));
+  GS_TRY(run_sync(s, hv, n_tiles, &g, st, s->ev_targets));
   if (loss_out) *loss_out = s->result_host[0];
   if (grad_xi_out)
     for (int k = 0; k < 6; ++k) grad_xi_out[k] = s->result_host[1 + k];

@@ -71,6 +71,8 @@ def _load():
         "gs_render_pose_grad": [vp, P(gs_camera), P(gs_pose), vp, vp, vp, ctypes.c_float, P(gs_outputs), vp, vp, vp],
         "gs_render_pose_grad_async": [vp, P(gs_camera), P(gs_pose), vp, vp, vp, ctypes.c_float, P(gs_outputs), vp,
                                       vp],
+        "gs_render_pose_grad_host": [vp, P(gs_camera), P(gs_pose), vp, vp, vp, ctypes.c_float, P(gs_outputs), vp,
+                                     vp, vp],
         "gs_render_batch": [vp, ctypes.c_int, P(gs_camera), P(gs_pose), P(gs_outputs), ctypes.c_uint, vp],
         "gs_render_pose_grad_batch": [vp, ctypes.c_int, P(gs_camera), P(gs_pose), vp, vp, vp, ctypes.c_float,
                                       vp, vp, vp, vp, ctypes.c_uint, vp],
@@ -142,6 +144,18 @@ def gs_render_pose_grad(h, cam, pose, target_rgb: int, target_depth: int, pixel_
     _check(lib.gs_render_pose_grad(h, ctypes.byref(cam), ctypes.byref(pose), target_rgb, target_depth,
                                    pixel_weight, float(depth_weight), ctypes.byref(out) if out is not None else None,
                                    ctypes.byref(loss), grad, stream))
+    return loss.value, np.array(grad[:], np.float64)
+
+
+def gs_render_pose_grad_host(h, cam, pose, target_rgb: int, target_depth: int, pixel_weight, depth_weight: float,
+                             out, stream: int):
+    """As gs_render_pose_grad with the targets as host addresses (pinned for overlap)."""
+    loss = ctypes.c_double()
+    grad = (ctypes.c_double * 6)()
+    _check(lib.gs_render_pose_grad_host(h, ctypes.byref(cam), ctypes.byref(pose), target_rgb, target_depth,
+                                        pixel_weight, float(depth_weight),
+                                        ctypes.byref(out) if out is not None else None, ctypes.byref(loss), grad,
+                                        stream))
     return loss.value, np.array(grad[:], np.float64)
 
 
@@ -400,6 +414,24 @@ class Scene:
         return gs_render_pose_grad(self.handle, camera(cam), pose(T), _ptr(target_rgb), _ptr(target_depth),
                                    _ptr(pixel_weight) or None, depth_weight,
                                    self.outputs_struct(out) if out is not None else None, _stream())
+
+    def render_pose_grad_host(self, cam, T, target_rgb, target_depth, pixel_weight=None, depth_weight=0.1,
+                              out=None):
+        """Pose gradient with host-memory targets: contiguous float32 numpy arrays or
+        CPU torch tensors (pinned tensors let the upload overlap the projection)."""
+        def hptr(a):
+            if a is None:
+                return None
+            if hasattr(a, "data_ptr"):
+                if a.is_cuda or a.dtype != __import__("torch").float32 or not a.is_contiguous():
+                    raise ValueError("host targets must be contiguous float32 CPU tensors")
+                return a.data_ptr()
+            if a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
+                raise ValueError("host targets must be contiguous float32 arrays")
+            return a.ctypes.data
+        return gs_render_pose_grad_host(self.handle, camera(cam), pose(T), hptr(target_rgb), hptr(target_depth),
+                                        hptr(pixel_weight), depth_weight,
+                                        self.outputs_struct(out) if out is not None else None, _stream())
 
     def render_pose_grad_batch(self, cams, poses, target_rgb, target_depth, pixel_weight=None, depth_weight=0.1,
                                outs=None, results=None, graph=False):

@@ -125,3 +125,26 @@ def test_blend_count_matches_oracle(oracle, gsr):
     slack = int(orc["n_eval"][flagged].sum())
     print("blended: gpu", n_gpu, "oracle", n_orc, "flagged-pixel slack", slack)
     assert n_orc > 0 and abs(n_gpu - n_orc) <= slack
+
+
+def test_host_targets_equal_device_targets(oracle, gsr):
+    # gs_render_pose_grad_host uploads the targets itself (beside the projection
+    # and binning kernels): same loss and gradient bits as the device-pointer call
+    scene, cam, T_gt = _small_aerial(34)
+    T_q = synth.perturb_pose(T_gt, synth.rng(34), 1.0, 1.0)
+    trgb, tdep = _targets(oracle, scene, cam, T_gt)
+    w = synth.rng(35).uniform(0.0, 1.0, (cam["height"], cam["width"])).astype(np.float32)
+    S = gsr.Scene(scene)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    for weight in (None, w):
+        ld, gd = S.render_pose_grad(cam, T_q, t(trgb), t(tdep), None if weight is None else t(weight))
+        lh, gh = S.render_pose_grad_host(cam, T_q, np.ascontiguousarray(trgb), np.ascontiguousarray(tdep), weight)
+        assert lh == ld
+        np.testing.assert_array_equal(gh, gd)
+        pr = torch.from_numpy(np.ascontiguousarray(trgb)).pin_memory()
+        pd = torch.from_numpy(np.ascontiguousarray(tdep)).pin_memory()
+        pw = None if weight is None else torch.from_numpy(weight).pin_memory()
+        lp, gp = S.render_pose_grad_host(cam, T_q, pr, pd, pw)
+        assert lp == ld
+        np.testing.assert_array_equal(gp, gd)
+    S.close()

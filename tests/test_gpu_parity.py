@@ -108,3 +108,70 @@ def test_full_size_aerial_1080p(oracle, gsr):
     orc = oracle.render(scene, cam, T, pixels=pix, geom64=True, n_threads=16)
     compare_images(gpu, orc, oracle, pixels=pix)
     S.close()
+
+
+def test_full_size_batched_84_views(oracle, gsr):
+    """The 84-view mixed-resolution batch (2,000,000 Gaussians in 4 partitions,
+    32 BF16 feature channels) in the graph launch the benchmark times: one view
+    of each resolution against the oracle on sampled pixels, features included,
+    and every view bit-identical to its single-view render."""
+    import torch
+    scene = synth.partitioned_scene(4, 2, 2, 500_000, sh_degree=3, feat_dim=32)
+    cams, poses = synth.batched_views()
+    S = gsr.Scene(scene)
+    outs = [S.alloc_outputs(c, feat_dim=32) for c in cams]
+    S.render_batch(cams, poses, outs)  # sizes the workspace
+    _, n_rec, n_pairs = S.status()
+    S.reserve(int(n_rec * 1.2) + 1024, int(n_pairs * 1.2) + 4096)
+    S.render_batch(cams, poses, outs, graph=True)
+    assert S.status()[0] == 0
+    for v in (0, 64, 80):  # 480x270, 960x540, 1920x1080
+        cam, T = cams[v], poses[v]
+        H, W = cam["height"], cam["width"]
+        gpu = to_numpy(outs[v], H, W)
+        pix = np.sort(synth.rng(90 + v).choice(W * H, min(W * H, 6000), replace=False))
+        orc = oracle.render(scene, cam, T, pixels=pix, geom64=True, n_threads=16)
+        errs = compare_images(gpu, orc, oracle, pixels=pix)
+        assert "feats" in errs
+        single = S.alloc_outputs(cam, feat_dim=32)
+        S.render_batch([cam], [T], [single])
+        for k in single:
+            torch.testing.assert_close(single[k], outs[v][k], rtol=0, atol=0)
+    S.close()
+
+
+def test_full_size_pose_gradient_1080p(oracle, gsr):
+    """The benchmark's pose-gradient step (1,000,000 Gaussians, 1920x1080, query
+    2 deg / 5 m from the reference) on 20,000 sampled pixels: the loss and
+    gradient restricted to those pixels (weight 1 there, 0 elsewhere) against the
+    oracle's; near-tie pixels get weight 0 on both sides."""
+    import torch
+    from tests.gpu_helpers import GRAD_TOL, block_rel_err
+    scene = synth.aerial_scene(2, 1_000_000)
+    cam = synth.aerial_camera()
+    T_ref = synth.aerial_pose()
+    T_q = synth.perturb_pose(T_ref, synth.rng(100), 2.0, 5.0)
+    H, W = cam["height"], cam["width"]
+    pix = np.sort(synth.rng(7).choice(W * H, 20000, replace=False))
+    ref = oracle.render(scene, cam, T_ref, pixels=pix, geom64=True, n_threads=16)
+    trgb = np.zeros((3, H * W), np.float32)
+    tdep = np.zeros(H * W, np.float32)
+    trgb[:, pix] = ref["rgb"].T
+    tdep[pix] = ref["depth"]
+    trgb, tdep = trgb.reshape(3, H, W), tdep.reshape(H, W)
+    w = np.zeros(H * W, np.float32)
+    w[pix] = 1.0
+    probe = oracle.render(scene, cam, T_q, pixels=pix, geom64=True, target_rgb=trgb, target_depth=tdep,
+                          pixel_weight=w.reshape(H, W), n_threads=16)
+    w[pix] *= (probe["flags"] == 0)
+    w = w.reshape(H, W)
+    orc = oracle.render(scene, cam, T_q, pixels=pix, geom64=True, want_grad=True, target_rgb=trgb,
+                        target_depth=tdep, pixel_weight=w, n_threads=16)
+    S = gsr.Scene(scene)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    loss, grad = S.render_pose_grad(cam, T_q, t(trgb), t(tdep), t(w))
+    S.close()
+    assert loss == pytest.approx(orc["loss"], rel=1e-4)
+    errs = block_rel_err(grad, orc["grad"])
+    print("loss", loss, orc["loss"], "grad", grad, orc["grad"], "block rel err", errs)
+    assert max(errs) <= GRAD_TOL

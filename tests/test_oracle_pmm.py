@@ -1,0 +1,132 @@
+"""Pins of the PMM oracle (Sec. 3.4, Eq. 11) against closed forms, invariants
+and brute force; no GPU."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import pmm
+
+R = pmm.RATIO
+
+
+def _blocks_to_map(cells, Hc, Wc, ratio=R, jitter=None):
+    """Fine map (C, Hc*ratio, Wc*ratio) whose block (cy, cx) holds the vector cells[cy*Wc+cx] everywhere
+    (plus optional per-pixel jitter)."""
+    C = cells.shape[1]
+    F = np.repeat(np.repeat(cells.T.reshape(C, Hc, Wc), ratio, axis=1), ratio, axis=2).astype(np.float32)
+    if jitter is not None:
+        F = (F + jitter).astype(np.float32)
+    return F
+
+
+def test_coarse_codes_match_binary32_brute_force():
+    # plain loops over np.float32 scalars in the stated order give the same bits
+    g = np.random.default_rng(0)
+    F = g.standard_normal((4, 16, 24)).astype(np.float32)
+    codes = pmm.coarse_codes(F)
+    C, H, W = F.shape
+    for cy in range(H // R):
+        for cx in range(W // R):
+            m = []
+            for c in range(C):
+                s = np.float32(0.0)
+                for dy in range(R):
+                    for dx in range(R):
+                        s = np.float32(s + F[c, cy * R + dy, cx * R + dx])
+                m.append(np.float32(s * np.float32(1.0 / 64)))
+            ss = np.float32(0.0)
+            for v in m:
+                ss = np.float32(ss + np.float32(v * v))
+            n = np.float32(math.sqrt(float(ss)))  # sqrt of a float32 value, correctly rounded to float32
+            u = np.array([np.float32(v / n) for v in m], np.float32)
+            np.testing.assert_array_equal(codes[cy * (W // R) + cx], pmm._bf16_round_bits(u))
+
+
+def test_coarse_codes_are_rounded_unit_means():
+    g = np.random.default_rng(1)
+    F = g.standard_normal((32, 40, 64)).astype(np.float32)
+    codes = pmm.bf16_to_f64(pmm.coarse_codes(F))
+    mean = F.astype(np.float64).reshape(32, 5, 8, 8, 8).mean(axis=(2, 4)).reshape(32, -1).T
+    unit = mean / np.linalg.norm(mean, axis=1, keepdims=True)
+    np.testing.assert_allclose(codes, unit, rtol=2 ** -8, atol=1e-6)  # bf16 keeps 8 significant bits
+    # zero map: zero codes; constant map: one code everywhere
+    assert not pmm.coarse_codes(np.zeros((32, 16, 16), np.float32)).any()
+    const = np.broadcast_to(g.standard_normal((32, 1, 1)).astype(np.float32), (32, 16, 16))
+    cc = pmm.coarse_codes(const)
+    assert (cc == cc[0]).all()
+
+
+def test_dual_softmax_is_product_of_row_and_column_softmax():
+    g = np.random.default_rng(2)
+    M = g.uniform(-1, 1, (5, 7))
+    logP, r, c = pmm.log_dual_softmax(M, 0.1)
+    for i in range(5):
+        for j in range(7):
+            row = math.exp(M[i, j] / 0.1) / sum(math.exp(M[i, k] / 0.1) for k in range(7))
+            col = math.exp(M[i, j] / 0.1) / sum(math.exp(M[k, j] / 0.1) for k in range(5))
+            assert logP[i, j] == pytest.approx(math.log(row * col), rel=1e-12)
+    np.testing.assert_allclose(np.exp(M / 0.1 - r[:, None]).sum(axis=1), 1.0, rtol=1e-12)
+    np.testing.assert_allclose(np.exp(M / 0.1 - c[None, :]).sum(axis=0), 1.0, rtol=1e-12)
+
+
+def test_orthonormal_codes_closed_form():
+    # cells carry distinct unit basis vectors (exact in bf16): M = I, so every cell matches
+    # itself with P = e^{2/tau} / (e^{1/tau} + N - 1)^2 and off-diagonal 1 / (e^{1/tau} + N - 1)^2
+    Hc, Wc, C = 3, 4, 32
+    N = Hc * Wc
+    cells = np.eye(C)[:N] * 0.7
+    F = _blocks_to_map(cells, Hc, Wc)
+    out = pmm.coarse_pmm(F, F)
+    np.testing.assert_array_equal(out["M"], np.eye(N))
+    np.testing.assert_array_equal(out["matches"], np.stack([np.arange(N)] * 2, 1))
+    z = math.exp(1 / pmm.TAU) + N - 1
+    np.testing.assert_allclose(out["prob"], math.exp(2 / pmm.TAU) / z ** 2, rtol=1e-12)
+    logP, _, _ = pmm.log_dual_softmax(out["M"])
+    np.testing.assert_allclose(np.exp(logP[0, 1]), 1 / z ** 2, rtol=1e-12)
+
+
+def test_mnn_brute_force():
+    g = np.random.default_rng(3)
+    for _ in range(20):
+        L = g.standard_normal((6, 9))
+        m = pmm.mnn(L)
+        exp = []
+        for i in range(6):
+            j = max(range(9), key=lambda k: (L[i, k], -k))
+            ib = max(range(6), key=lambda k: (L[k, j], -k))
+            if ib == i:
+                exp.append((i, j))
+        np.testing.assert_array_equal(m["matches"], np.asarray(exp, np.int64).reshape(-1, 2))
+
+
+def test_permuting_rendered_cells_permutes_matches():
+    g = np.random.default_rng(4)
+    Hc, Wc, C = 4, 5, 32
+    cells = g.standard_normal((Hc * Wc, C))
+    Fq = _blocks_to_map(cells, Hc, Wc, jitter=0.05 * g.standard_normal((C, Hc * R, Wc * R)))
+    perm = g.permutation(Hc * Wc)
+    Fr = _blocks_to_map(cells[perm], Hc, Wc, jitter=0.05 * g.standard_normal((C, Hc * R, Wc * R)))
+    out = pmm.coarse_pmm(Fq, Fr)
+    # rendered cell k holds query cell perm[k]: every query cell i matches inv[i]
+    inv = np.argsort(perm)
+    assert len(out["matches"]) == Hc * Wc
+    np.testing.assert_array_equal(out["matches"][:, 1], inv[out["matches"][:, 0]])
+
+
+def test_fine_windows_match_themselves():
+    g = np.random.default_rng(5)
+    C, Hc, Wc = 32, 2, 3
+    F = g.standard_normal((C, Hc * R, Wc * R)).astype(np.float32)
+    coarse = np.stack([np.arange(Hc * Wc)] * 2, 1)
+    fine = pmm.fine_pmm(F, F, coarse)
+    assert len(fine["matches"]) == Hc * Wc * R * R
+    np.testing.assert_array_equal(fine["matches"][:, 1], fine["matches"][:, 2])
+    assert not fine["flag"].any()
+    # a shifted rendered window still pairs pixels by content
+    Fr = np.roll(F, 1, axis=2)  # rendered pixel x holds query pixel x - 1
+    fine2 = pmm.fine_pmm(F, Fr, np.array([[0, 0]]))
+    W = Wc * R
+    q, r = fine2["matches"][:, 1], fine2["matches"][:, 2]
+    inner = (q % W) < R - 1  # query pixels whose shifted copy stays inside the window
+    np.testing.assert_array_equal(r[inner], q[inner] + 1)

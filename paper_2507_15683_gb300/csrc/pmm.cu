@@ -1,0 +1,765 @@
+// Probabilistic mutual matching (PMM) of a query and a rendered feature map,
+// coarse to fine: Hi^2-GSLoc Sec. 3.4, Eq. 11.
+//
+// Coarse level. Each 8 x 8 block of the fine maps becomes one coarse cell: its
+// mean, L2-normalised and rounded to bfloat16 (k_pmm_codes, binary32 in a fixed
+// operation order). The cosine matrix M of all query cells against all
+// rendered cells is a 32-deep contraction, computed tile by tile on the 5th
+// generation tensor cores (tcgen05.mma, bf16 operands in shared memory, fp32
+// accumulator in tensor memory) and never stored. Two passes over the tiles:
+//   1. row and column sums of exp((M - 1) / tau), hence the row and column
+//      log-sum-exps r_i, c_j of M / tau (|M| <= 1 makes 1 / tau a fixed
+//      shift, so one exponential serves the row and the column);
+//   2. per row i the first argmax over j of log P_M + r_i = 2 M / tau - c_j,
+//      per column j the first argmax over i of 2 M / tau - r_i.
+// Partial results per tile row / column are reduced in a fixed order, and a
+// query cell i matches rendered cell j when each is the other's argmax (MNN).
+//
+// Fine level. For every coarse match the 64 fine query vectors of cell i and
+// the 64 rendered vectors of cell j (normalised in fp32) give a 64 x 64 cosine
+// matrix; the same dual softmax and MNN inside the window pair give the fine
+// matches (one CTA per coarse match).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+
+#include "gsr_pmm.h"
+
+namespace gsr {
+void set_last_error(const std::string& msg);
+}
+
+namespace {
+
+constexpr int kC = 32;         // channels
+constexpr int kRatio = 8;      // H_f / H_c
+constexpr int kTile = 128;     // cells per tile side (MMA M = N = 128)
+constexpr int kThreads = 128;  // 4 warps; warp w reads tensor-memory lanes 32 w .. 32 w + 31
+constexpr uint32_t kTmemCols = 128;
+constexpr int kWaitLimit = 1 << 22;  // polls of an mbarrier before giving up (far beyond a 2-MMA tile)
+constexpr int kMaxCells = 1 << 18;
+constexpr int kScanThreads = 1024;
+constexpr int kWin = kRatio * kRatio;  // fine vectors per window
+
+// ---------------------------------------------------------------------------
+// coarse codes: one warp per cell, lane = channel
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_pmm_codes(const float* __restrict__ F, int H, int W, int Wc, int n_cells,
+                                                   __nv_bfloat16* __restrict__ codes) {
+  const int lane = threadIdx.x & 31;
+  const int cell = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (cell >= n_cells) return;  // warp-uniform
+  const int cy = cell / Wc, cx = cell - cy * Wc;
+  const float* base = F + (size_t)lane * H * W + (size_t)(cy * kRatio) * W + cx * kRatio;
+  float s = 0.0f;  // block sum in row-major order
+#pragma unroll
+  for (int dy = 0; dy < kRatio; ++dy) {
+    const float4 a = *reinterpret_cast<const float4*>(base + (size_t)dy * W);
+    const float4 b = *reinterpret_cast<const float4*>(base + (size_t)dy * W + 4);
+    s = __fadd_rn(s, a.x);
+    s = __fadd_rn(s, a.y);
+    s = __fadd_rn(s, a.z);
+    s = __fadd_rn(s, a.w);
+    s = __fadd_rn(s, b.x);
+    s = __fadd_rn(s, b.y);
+    s = __fadd_rn(s, b.z);
+    s = __fadd_rn(s, b.w);
+  }
+  const float m = __fmul_rn(s, 1.0f / (kRatio * kRatio));  // exact scaling
+  const float m2 = __fmul_rn(m, m);
+  float ss = 0.0f;  // squares summed over channels in channel order
+#pragma unroll
+  for (int c = 0; c < kC; ++c) ss = __fadd_rn(ss, __shfl_sync(0xffffffffu, m2, c));
+  const float n = __fsqrt_rn(ss);
+  const float u = n > 0.0f ? __fdiv_rn(m, n) : 0.0f;
+  codes[(size_t)cell * kC + lane] = __float2bfloat16_rn(u);
+}
+
+// ---------------------------------------------------------------------------
+// tcgen05 helpers (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: K-major, no swizzle. The operand is stored
+// as 8 x 16-byte core matrices; adjacent core matrices along K are `lbo` bytes
+// apart and adjacent 8-row groups `sbo` bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version field (0b001)
+  return d;                 // base offset 0, relative LBO, no swizzle
+}
+
+// Instruction descriptor of tcgen05.mma kind::f16: fp32 accumulator, bf16 A and
+// B, both K-major, N = M = 128.
+constexpr uint32_t kIdesc = (1u << 4)                         // D format: f32
+                            | (1u << 7)                       // A format: bf16
+                            | (1u << 10)                      // B format: bf16
+                            | ((uint32_t)(kTile >> 3) << 17)  // N >> 3
+                            | ((uint32_t)(kTile >> 4) << 24);  // M >> 4
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// bounded wait for the phase `parity` of an mbarrier; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int it = 0; it < kWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 consecutive fp32 accumulator columns of this thread's lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+// ---------------------------------------------------------------------------
+// similarity tiles (both passes)
+// ---------------------------------------------------------------------------
+struct TileSmem {
+  uint4 a[kTile * kC * 2 / 16];  // query codes, core-matrix layout (8 KB)
+  uint4 b[kTile * kC * 2 / 16];  // rendered codes (8 KB)
+  float colv[4][kTile];          // per-warp column partials
+  int coli[4][kTile];            // pass 2: their row index
+  float lse_c[kTile];            // pass 2: c_j of the tile's columns
+  unsigned long long bar;
+  uint32_t tmem;
+  int fail;
+};
+// one CTA uses 128 of the 512 tensor-memory columns of an SM; the dynamic
+// shared-memory request keeps at most 4 CTAs on an SM so allocation never waits
+constexpr size_t kTileSmemBytes = 48 * 1024;
+static_assert(sizeof(TileSmem) <= kTileSmemBytes, "tile shared memory");
+
+// byte offset of the 16-byte chunk (row r, k-chunk c) in the core-matrix layout:
+// core matrix (r / 8, c) is 128 bytes, k-chunks of a row group are adjacent
+__device__ __forceinline__ int core_off(int r, int c) { return ((r >> 3) * 4 + c) * 128 + (r & 7) * 16; }
+
+// lane l ends with v[0] = sum over the warp's lanes of v[l] (l < 16 values: the
+// columns of one half-chunk are summed over the lane pairs l, l ^ 16 too)
+__device__ __forceinline__ float reduce_scatter16(float (&v)[16], int lane) {
+#pragma unroll
+  for (int s = 8; s >= 1; s >>= 1) {
+    const bool up = (lane & s) != 0;
+#pragma unroll
+    for (int i = 0; i < s; ++i) {
+      const float send = up ? v[i] : v[i + s];
+      const float keep = up ? v[i + s] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
+}
+
+// argmax form: larger value wins, equal values go to the smaller index
+__device__ __forceinline__ bool better(float v, int i, float bv, int bi) { return v > bv || (v == bv && i < bi); }
+
+__device__ __forceinline__ void reduce_scatter16_max(float (&v)[16], int (&ix)[16], int lane, float& out_v,
+                                                     int& out_i) {
+#pragma unroll
+  for (int s = 8; s >= 1; s >>= 1) {
+    const bool up = (lane & s) != 0;
+#pragma unroll
+    for (int i = 0; i < s; ++i) {
+      const float sv = up ? v[i] : v[i + s];
+      const int si = up ? ix[i] : ix[i + s];
+      const float kv = up ? v[i + s] : v[i];
+      const int ki = up ? ix[i + s] : ix[i];
+      const float rv = __shfl_xor_sync(0xffffffffu, sv, s);
+      const int ri = __shfl_xor_sync(0xffffffffu, si, s);
+      const bool take = better(rv, ri, kv, ki);
+      v[i] = take ? rv : kv;
+      ix[i] = take ? ri : ki;
+    }
+  }
+  const float rv = __shfl_xor_sync(0xffffffffu, v[0], 16);
+  const int ri = __shfl_xor_sync(0xffffffffu, ix[0], 16);
+  const bool take = better(rv, ri, v[0], ix[0]);
+  out_v = take ? rv : v[0];
+  out_i = take ? ri : ix[0];
+}
+
+// PASS 1: prow_v[rb n + i] = sum over the tile's columns of exp((M - 1) / tau),
+//         pcol_v[qb n + j] = the same over the tile's rows.
+// PASS 2: prow_v / prow_i = best 2 M / tau - c_j of row i within the tile,
+//         pcol_v / pcol_i = best 2 M / tau - r_i of column j within the tile.
+template <int PASS>
+__global__ void __launch_bounds__(kThreads) k_pmm_tiles(const uint4* __restrict__ cq, const uint4* __restrict__ cr,
+                                                        int n, int nb, float s_exp, float s_two,
+                                                        const float* __restrict__ lse_row,
+                                                        const float* __restrict__ lse_col, float* __restrict__ prow_v,
+                                                        int* __restrict__ prow_i, float* __restrict__ pcol_v,
+                                                        int* __restrict__ pcol_i, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  TileSmem& S = *reinterpret_cast<TileSmem*>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t bar = smem_u32(&S.bar);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    S.fail = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = S.tmem;
+  const uint32_t tlane = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's 32 lanes
+  const uint32_t sa = smem_u32(S.a), sb = smem_u32(S.b);
+  uint32_t phase = 0;
+  const int n_tiles = nb * nb;
+  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {  // block-uniform
+    const int qb = t / nb, rb = t - qb * nb;
+    const int qrow = qb * kTile + tid, rrow = rb * kTile + tid;
+    // stage the two 128 x 32 bf16 operands (rows past n are zero)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+      const uint4 av = qrow < n ? cq[(size_t)qrow * 4 + c] : z;
+      const uint4 bv = rrow < n ? cr[(size_t)rrow * 4 + c] : z;
+      *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(S.a) + core_off(tid, c)) = av;
+      *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(S.b) + core_off(tid, c)) = bv;
+    }
+    if (PASS == 2) S.lse_c[tid] = rrow < n ? lse_col[rrow] : 0.0f;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // operands visible to the tensor core
+    tc_fence_before();  // previous tile's accumulator reads are done
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      // K = 32 as two K = 16 steps: k-chunks (0, 1), then (2, 3) at +256 bytes
+      mma_bf16(tmem, smem_desc(sa, 128, 512), smem_desc(sb, 128, 512), 0u);
+      mma_bf16(tmem, smem_desc(sa + 256, 128, 512), smem_desc(sb + 256, 128, 512), 1u);
+      mma_commit(bar);
+    }
+    const bool done = mbar_wait(bar, phase);
+    phase ^= 1u;
+    if (__syncthreads_or(!done)) {  // the accumulator never arrived: report, drain, stop
+      if (tid == 0) {
+        atomicExch(err, 1);
+        S.fail = 1;
+      }
+      mbar_wait(bar, phase ^ 1u);
+      break;
+    }
+    tc_fence_after();
+
+    const bool row_ok = qrow < n;
+    if (PASS == 1) {
+      float rsum = 0.0f;
+#pragma unroll 1
+      for (int ch = 0; ch < kTile / 16; ++ch) {
+        float v[16];
+        tmem_ld16(tlane + (uint32_t)(ch * 16), v);
+        const int col0 = rb * kTile + ch * 16;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const float e = exp2f((v[k] - 1.0f) * s_exp);
+          v[k] = (row_ok && col0 + k < n) ? e : 0.0f;
+          rsum += v[k];
+        }
+        const float cs = reduce_scatter16(v, lane);
+        if (lane < 16) S.colv[warp][ch * 16 + lane] = cs;
+      }
+      if (row_ok) prow_v[(size_t)rb * n + qrow] = rsum;
+    } else {
+      const float rq = row_ok ? lse_row[qrow] : 0.0f;
+      float best = -INFINITY;
+      int bidx = 0x7fffffff;
+#pragma unroll 1
+      for (int ch = 0; ch < kTile / 16; ++ch) {
+        float v[16];
+        tmem_ld16(tlane + (uint32_t)(ch * 16), v);
+        const int col0 = rb * kTile + ch * 16;
+        float cv[16];
+        int ci[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const bool ok = row_ok && col0 + k < n;
+          const float m2 = v[k] * s_two;
+          const float rv = m2 - S.lse_c[ch * 16 + k];
+          if (ok && rv > best) {  // columns in ascending order: the first maximum stays
+            best = rv;
+            bidx = col0 + k;
+          }
+          cv[k] = ok ? m2 - rq : -INFINITY;
+          ci[k] = ok ? qrow : 0x7fffffff;
+        }
+        float ov;
+        int oi;
+        reduce_scatter16_max(cv, ci, lane, ov, oi);
+        if (lane < 16) {
+          S.colv[warp][ch * 16 + lane] = ov;
+          S.coli[warp][ch * 16 + lane] = oi;
+        }
+      }
+      if (row_ok) {
+        prow_v[(size_t)rb * n + qrow] = best;
+        prow_i[(size_t)rb * n + qrow] = bidx;
+      }
+    }
+    __syncthreads();
+    if (rrow < n) {  // thread t owns column t of the tile: warps (rows 0-31, 32-63, ...) in order
+      if (PASS == 1) {
+        const float s = ((S.colv[0][tid] + S.colv[1][tid]) + S.colv[2][tid]) + S.colv[3][tid];
+        pcol_v[(size_t)qb * n + rrow] = s;
+      } else {
+        float bv = S.colv[0][tid];
+        int bi = S.coli[0][tid];
+#pragma unroll
+        for (int w = 1; w < 4; ++w)
+          if (better(S.colv[w][tid], S.coli[w][tid], bv, bi)) {
+            bv = S.colv[w][tid];
+            bi = S.coli[w][tid];
+          }
+        pcol_v[(size_t)qb * n + rrow] = bv;
+        pcol_i[(size_t)qb * n + rrow] = bi;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+// fixed-order reductions of the per-tile partials (thread per row / column)
+__global__ void k_pmm_lse(const float* __restrict__ part, int nb, int n, float inv_tau, float* __restrict__ lse) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float s = 0.0f;
+  for (int b = 0; b < nb; ++b) s += part[(size_t)b * n + i];
+  lse[i] = inv_tau + logf(s);  // log sum exp(M / tau) = 1 / tau + log sum exp((M - 1) / tau)
+}
+
+__global__ void k_pmm_best(const float* __restrict__ pv, const int* __restrict__ pi, int nb, int n,
+                           int* __restrict__ best) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float bv = -INFINITY;
+  int bi = 0x7fffffff;
+  for (int b = 0; b < nb; ++b) {
+    const float v = pv[(size_t)b * n + i];
+    const int x = pi[(size_t)b * n + i];
+    if (better(v, x, bv, bi)) {
+      bv = v;
+      bi = x;
+    }
+  }
+  best[i] = bi;
+}
+
+__device__ __forceinline__ float dot_codes(const __nv_bfloat16* a, const __nv_bfloat16* b) {
+  float s = 0.0f;
+#pragma unroll
+  for (int k = 0; k < kC; ++k) s = fmaf(__bfloat162float(a[k]), __bfloat162float(b[k]), s);
+  return s;
+}
+
+// exclusive scan of one value per thread over kScanThreads threads
+__device__ uint32_t scan_block(uint32_t v, uint32_t* tmp) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) tmp[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    const uint32_t x = tmp[lane];
+    uint32_t y = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) y += t;
+    }
+    tmp[lane] = y - x;
+  }
+  __syncthreads();
+  return tmp[wid] + incl - v;
+}
+
+// mutual nearest neighbours, compacted in ascending query order (one CTA)
+__global__ void __launch_bounds__(kScanThreads) k_pmm_mnn(int n, const int* __restrict__ row_best,
+                                                          const int* __restrict__ col_best,
+                                                          const __nv_bfloat16* __restrict__ cq,
+                                                          const __nv_bfloat16* __restrict__ cr,
+                                                          const float* __restrict__ lse_row,
+                                                          const float* __restrict__ lse_col, float s_two,
+                                                          int* __restrict__ coarse, float* __restrict__ prob,
+                                                          int* __restrict__ n_out) {
+  __shared__ uint32_t tmp[32];
+  const int per = (n + kScanThreads - 1) / kScanThreads;
+  const int b = threadIdx.x * per, e = min(n, b + per);
+  // an argmax left at its sentinel (non-finite features) matches nothing
+  auto mutual = [&](int i, int j) { return j >= 0 && j < n && col_best[j] == i; };
+  uint32_t cnt = 0;
+  for (int i = b; i < e; ++i) cnt += mutual(i, row_best[i]) ? 1u : 0u;
+  uint32_t pos = scan_block(cnt, tmp);
+  for (int i = b; i < e; ++i) {
+    const int j = row_best[i];
+    if (!mutual(i, j)) continue;
+    coarse[2 * pos] = i;
+    coarse[2 * pos + 1] = j;
+    const float m = dot_codes(cq + (size_t)i * kC, cr + (size_t)j * kC);
+    prob[pos] = expf(m * s_two - lse_row[i] - lse_col[j]);
+    ++pos;
+  }
+  if (threadIdx.x == kScanThreads - 1) *n_out = (int)pos;
+}
+
+// ---------------------------------------------------------------------------
+// fine level: one CTA of 64 threads per coarse match
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kWin) k_pmm_fine(const float* __restrict__ Fq, const float* __restrict__ Fr, int H,
+                                                   int W, int Wc, const int* __restrict__ coarse, float inv_tau,
+                                                   float s_exp, float s_two, int* __restrict__ slot_r,
+                                                   float* __restrict__ slot_p, int* __restrict__ win_count) {
+  __shared__ float uq[kWin][kC + 1], ur[kWin][kC + 1];
+  __shared__ float Mf[kWin][kWin + 1];
+  __shared__ float lr[kWin], lc[kWin];
+  __shared__ int rbest[kWin], cbest[kWin];
+  const int k = blockIdx.x, a = threadIdx.x;
+  const int ci = coarse[2 * k], cj = coarse[2 * k + 1];
+  const size_t HW = (size_t)H * W;
+  const int qy = (ci / Wc) * kRatio + a / kRatio, qx = (ci % Wc) * kRatio + a % kRatio;
+  const int ry = (cj / Wc) * kRatio + a / kRatio, rx = (cj % Wc) * kRatio + a % kRatio;
+  {  // normalised fine vectors (fp32, channel order)
+    float vq[kC], vr[kC];
+    float sq = 0.0f, sr = 0.0f;
+#pragma unroll
+    for (int c = 0; c < kC; ++c) {
+      vq[c] = Fq[c * HW + (size_t)qy * W + qx];
+      vr[c] = Fr[c * HW + (size_t)ry * W + rx];
+      sq = fmaf(vq[c], vq[c], sq);
+      sr = fmaf(vr[c], vr[c], sr);
+    }
+    const float iq = sq > 0.0f ? 1.0f / sqrtf(sq) : 0.0f, ir = sr > 0.0f ? 1.0f / sqrtf(sr) : 0.0f;
+#pragma unroll
+    for (int c = 0; c < kC; ++c) {
+      uq[a][c] = vq[c] * iq;
+      ur[a][c] = vr[c] * ir;
+    }
+  }
+  __syncthreads();
+  float rs = 0.0f;  // row a: similarities and exp sum
+  for (int b = 0; b < kWin; ++b) {
+    float m = 0.0f;
+#pragma unroll
+    for (int c = 0; c < kC; ++c) m = fmaf(uq[a][c], ur[b][c], m);
+    Mf[a][b] = m;
+    rs += exp2f((m - 1.0f) * s_exp);
+  }
+  lr[a] = inv_tau + logf(rs);
+  __syncthreads();
+  float cs = 0.0f;  // column a
+  for (int i = 0; i < kWin; ++i) cs += exp2f((Mf[i][a] - 1.0f) * s_exp);
+  lc[a] = inv_tau + logf(cs);
+  __syncthreads();
+  {
+    float bv = -INFINITY;
+    int bi = 0;
+    for (int b = 0; b < kWin; ++b) {
+      const float v = Mf[a][b] * s_two - lc[b];
+      if (v > bv) {
+        bv = v;
+        bi = b;
+      }
+    }
+    rbest[a] = bi;
+    bv = -INFINITY;
+    bi = 0;
+    for (int i = 0; i < kWin; ++i) {
+      const float v = Mf[i][a] * s_two - lr[i];
+      if (v > bv) {
+        bv = v;
+        bi = i;
+      }
+    }
+    cbest[a] = bi;
+  }
+  __syncthreads();
+  const int b = rbest[a];
+  const bool mutual = cbest[b] == a;
+  const int by = (cj / Wc) * kRatio + b / kRatio, bx = (cj % Wc) * kRatio + b % kRatio;
+  slot_r[(size_t)k * kWin + a] = mutual ? by * W + bx : -1;
+  slot_p[(size_t)k * kWin + a] = mutual ? expf(Mf[a][b] * s_two - lr[a] - lc[b]) : 0.0f;
+  const unsigned bal = __ballot_sync(0xffffffffu, mutual);
+  if ((a & 31) == 0) rbest[a] = __popc(bal);  // rows are no longer read: reuse for the two warp counts
+  __syncthreads();
+  if (a == 0) win_count[k] = rbest[0] + rbest[32];
+}
+
+// exclusive scan of the per-window match counts (one CTA): window offsets and
+// the total
+__global__ void __launch_bounds__(kScanThreads) k_pmm_scan_windows(int n_win, const int* __restrict__ cnt,
+                                                                   int* __restrict__ off, int* __restrict__ total) {
+  __shared__ uint32_t tmp[32];
+  const int per = (n_win + kScanThreads - 1) / kScanThreads;
+  const int b = threadIdx.x * per, e = min(n_win, b + per);
+  uint32_t c = 0;
+  for (int k = b; k < e; ++k) c += (uint32_t)cnt[k];
+  uint32_t pos = scan_block(c, tmp);
+  for (int k = b; k < e; ++k) {
+    off[k] = (int)pos;
+    pos += (uint32_t)cnt[k];
+  }
+  if (threadIdx.x == kScanThreads - 1) *total = (int)pos;
+}
+
+// fine matches of window k at its offset, in query-pixel order (64 threads)
+__global__ void __launch_bounds__(kWin) k_pmm_fine_scatter(int W, int Wc, const int* __restrict__ coarse,
+                                                           const int* __restrict__ slot_r,
+                                                           const float* __restrict__ slot_p,
+                                                           const int* __restrict__ off, int* __restrict__ fine,
+                                                           float* __restrict__ prob) {
+  __shared__ int w0;
+  const int k = blockIdx.x, a = threadIdx.x;
+  const int r = slot_r[(size_t)k * kWin + a];
+  const unsigned bal = __ballot_sync(0xffffffffu, r >= 0);
+  if (a == 0) w0 = __popc(bal);
+  __syncthreads();
+  if (r < 0) return;
+  const int pos = off[k] + (a >= 32 ? w0 : 0) + __popc(bal & ((1u << (a & 31)) - 1u));
+  const int ci = coarse[2 * k];
+  const int qy = (ci / Wc) * kRatio + a / kRatio, qx = (ci % Wc) * kRatio + a % kRatio;
+  fine[3 * pos] = k;
+  fine[3 * pos + 1] = qy * W + qx;
+  fine[3 * pos + 2] = r;
+  prob[pos] = slot_p[(size_t)k * kWin + a];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+struct gs_pmm {
+  int device = 0, sm_count = 1;
+  int C = 0, H = 0, W = 0, Hc = 0, Wc = 0, n = 0, nb = 0;
+  void* arena = nullptr;
+  __nv_bfloat16 *codes_q = nullptr, *codes_r = nullptr;
+  float *prow_v = nullptr, *pcol_v = nullptr, *lse_row = nullptr, *lse_col = nullptr;
+  int *prow_i = nullptr, *pcol_i = nullptr, *row_best = nullptr, *col_best = nullptr;
+  int *coarse = nullptr, *fine = nullptr, *slot_r = nullptr, *counters = nullptr, *win_cnt = nullptr,
+      *win_off = nullptr;
+  float *coarse_p = nullptr, *fine_p = nullptr, *slot_p = nullptr;
+  int* host = nullptr;  // pinned: counts and error flag
+};
+
+namespace {
+
+gs_status pmm_fail(gs_status st, const std::string& msg) {
+  gsr::set_last_error(msg);
+  return st;
+}
+
+#define PMM_CUDA(x)                                                                    \
+  do {                                                                                 \
+    const cudaError_t e_ = (x);                                                        \
+    if (e_ != cudaSuccess) return pmm_fail(GS_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" {
+
+gs_status gs_pmm_create(int channels, int height, int width, gs_pmm** out) {
+  if (!out) return pmm_fail(GS_ERR_INVALID_ARG, "out is required");
+  *out = nullptr;
+  if (channels != kC) return pmm_fail(GS_ERR_INVALID_ARG, "PMM needs 32 feature channels");
+  if (height < kRatio || width < kRatio || height % kRatio || width % kRatio || height > 8192 || width > 8192)
+    return pmm_fail(GS_ERR_INVALID_ARG, "feature maps must be 8..8192 pixels, multiples of 8");
+  const int Hc = height / kRatio, Wc = width / kRatio, n = Hc * Wc;
+  if (n > kMaxCells) return pmm_fail(GS_ERR_INVALID_ARG, "more than 2^18 coarse cells");
+  gs_pmm* m = new gs_pmm();
+  m->C = channels;
+  m->H = height;
+  m->W = width;
+  m->Hc = Hc;
+  m->Wc = Wc;
+  m->n = n;
+  m->nb = (n + kTile - 1) / kTile;
+  cudaError_t e = cudaGetDevice(&m->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&m->sm_count, cudaDevAttrMultiProcessorCount, m->device);
+  const size_t nn = (size_t)n, part = (size_t)m->nb * nn;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes);
+    return o;
+  };
+  const size_t o_cq = take(nn * kC * 2), o_cr = take(nn * kC * 2);
+  const size_t o_prv = take(part * 4), o_pri = take(part * 4), o_pcv = take(part * 4), o_pci = take(part * 4);
+  const size_t o_lr = take(nn * 4), o_lc = take(nn * 4), o_rb = take(nn * 4), o_cb = take(nn * 4);
+  const size_t o_co = take(nn * 8), o_cp = take(nn * 4);
+  const size_t o_sr = take(nn * kWin * 4), o_sp = take(nn * kWin * 4);
+  const size_t o_fi = take(nn * kWin * 12), o_fp = take(nn * kWin * 4);
+  const size_t o_wc = take(nn * 4), o_wo = take(nn * 4);
+  const size_t o_ct = take(4 * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&m->arena, off);
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&m->host), 4 * sizeof(int));
+  if (e != cudaSuccess) {
+    gs_pmm_destroy(m);
+    return pmm_fail(e == cudaErrorMemoryAllocation ? GS_ERR_OOM : GS_ERR_CUDA,
+                    std::string("gs_pmm_create: ") + cudaGetErrorString(e));
+  }
+  char* base = static_cast<char*>(m->arena);
+  m->codes_q = reinterpret_cast<__nv_bfloat16*>(base + o_cq);
+  m->codes_r = reinterpret_cast<__nv_bfloat16*>(base + o_cr);
+  m->prow_v = reinterpret_cast<float*>(base + o_prv);
+  m->prow_i = reinterpret_cast<int*>(base + o_pri);
+  m->pcol_v = reinterpret_cast<float*>(base + o_pcv);
+  m->pcol_i = reinterpret_cast<int*>(base + o_pci);
+  m->lse_row = reinterpret_cast<float*>(base + o_lr);
+  m->lse_col = reinterpret_cast<float*>(base + o_lc);
+  m->row_best = reinterpret_cast<int*>(base + o_rb);
+  m->col_best = reinterpret_cast<int*>(base + o_cb);
+  m->coarse = reinterpret_cast<int*>(base + o_co);
+  m->coarse_p = reinterpret_cast<float*>(base + o_cp);
+  m->slot_r = reinterpret_cast<int*>(base + o_sr);
+  m->slot_p = reinterpret_cast<float*>(base + o_sp);
+  m->fine = reinterpret_cast<int*>(base + o_fi);
+  m->fine_p = reinterpret_cast<float*>(base + o_fp);
+  m->win_cnt = reinterpret_cast<int*>(base + o_wc);
+  m->win_off = reinterpret_cast<int*>(base + o_wo);
+  m->counters = reinterpret_cast<int*>(base + o_ct);
+  *out = m;
+  return GS_OK;
+}
+
+void gs_pmm_destroy(gs_pmm* m) {
+  if (!m) return;
+  cudaSetDevice(m->device);
+  if (m->arena) {
+    cudaDeviceSynchronize();
+    cudaFree(m->arena);
+  }
+  if (m->host) cudaFreeHost(m->host);
+  delete m;
+}
+
+gs_status gs_pmm_match(gs_pmm* m, const float* feat_query, const float* feat_render, float tau,
+                       gs_pmm_result* out, void* stream) {
+  gsr::set_last_error("");
+  if (!m || !feat_query || !feat_render || !out) return pmm_fail(GS_ERR_INVALID_ARG, "matcher, maps and out are required");
+  if (((uintptr_t)feat_query | (uintptr_t)feat_render) & 15u)
+    return pmm_fail(GS_ERR_INVALID_ARG, "feature maps must be 16-byte aligned");
+  if (!(tau >= 0.025f) || !std::isfinite(tau)) return pmm_fail(GS_ERR_INVALID_ARG, "tau must be finite and >= 0.025");
+  PMM_CUDA(cudaSetDevice(m->device));
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int n = m->n, nb = m->nb;
+  const float inv_tau = 1.0f / tau;
+  const float s_exp = 1.4426950408889634f * inv_tau;  // exp(x / tau) = exp2(x log2(e) / tau)
+  const float s_two = 2.0f * inv_tau;
+  PMM_CUDA(cudaMemsetAsync(m->counters, 0, 4 * sizeof(int), st));
+  const int cb = (n * 32 + 255) / 256;
+  k_pmm_codes<<<cb, 256, 0, st>>>(feat_query, m->H, m->W, m->Wc, n, m->codes_q);
+  k_pmm_codes<<<cb, 256, 0, st>>>(feat_render, m->H, m->W, m->Wc, n, m->codes_r);
+  PMM_CUDA(cudaGetLastError());
+  static bool attr = false;
+  if (!attr) {
+    PMM_CUDA(cudaFuncSetAttribute(k_pmm_tiles<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes));
+    PMM_CUDA(cudaFuncSetAttribute(k_pmm_tiles<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes));
+    attr = true;
+  }
+  const int tiles = nb * nb;
+  const int grid = tiles < 4 * m->sm_count ? tiles : 4 * m->sm_count;
+  const uint4* cq = reinterpret_cast<const uint4*>(m->codes_q);
+  const uint4* cr = reinterpret_cast<const uint4*>(m->codes_r);
+  int* err = m->counters + 3;
+  k_pmm_tiles<1><<<grid, kThreads, kTileSmemBytes, st>>>(cq, cr, n, nb, s_exp, s_two, nullptr, nullptr, m->prow_v,
+                                                         nullptr, m->pcol_v, nullptr, err);
+  PMM_CUDA(cudaGetLastError());
+  const int rg = (n + 255) / 256;
+  k_pmm_lse<<<rg, 256, 0, st>>>(m->prow_v, nb, n, inv_tau, m->lse_row);
+  k_pmm_lse<<<rg, 256, 0, st>>>(m->pcol_v, nb, n, inv_tau, m->lse_col);
+  k_pmm_tiles<2><<<grid, kThreads, kTileSmemBytes, st>>>(cq, cr, n, nb, s_exp, s_two, m->lse_row, m->lse_col,
+                                                         m->prow_v, m->prow_i, m->pcol_v, m->pcol_i, err);
+  PMM_CUDA(cudaGetLastError());
+  k_pmm_best<<<rg, 256, 0, st>>>(m->prow_v, m->prow_i, nb, n, m->row_best);
+  k_pmm_best<<<rg, 256, 0, st>>>(m->pcol_v, m->pcol_i, nb, n, m->col_best);
+  k_pmm_mnn<<<1, kScanThreads, 0, st>>>(n, m->row_best, m->col_best, m->codes_q, m->codes_r, m->lse_row, m->lse_col,
+                                        s_two, m->coarse, m->coarse_p, m->counters);
+  PMM_CUDA(cudaGetLastError());
+  PMM_CUDA(cudaMemcpyAsync(m->host, m->counters, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  PMM_CUDA(cudaStreamSynchronize(st));
+  if (m->host[3]) return pmm_fail(GS_ERR_INTERNAL, "tensor-core completion wait timed out");
+  const int n_coarse = m->host[0];
+  if (n_coarse > 0) {
+    k_pmm_fine<<<n_coarse, kWin, 0, st>>>(feat_query, feat_render, m->H, m->W, m->Wc, m->coarse, inv_tau, s_exp,
+                                          s_two, m->slot_r, m->slot_p, m->win_cnt);
+    k_pmm_scan_windows<<<1, kScanThreads, 0, st>>>(n_coarse, m->win_cnt, m->win_off, m->counters + 1);
+    k_pmm_fine_scatter<<<n_coarse, kWin, 0, st>>>(m->W, m->Wc, m->coarse, m->slot_r, m->slot_p, m->win_off, m->fine,
+                                                  m->fine_p);
+    PMM_CUDA(cudaGetLastError());
+    PMM_CUDA(cudaMemcpyAsync(m->host + 1, m->counters + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PMM_CUDA(cudaStreamSynchronize(st));
+  } else {
+    m->host[1] = 0;
+  }
+  out->n_cells = n;
+  out->codes_q = reinterpret_cast<const uint16_t*>(m->codes_q);
+  out->codes_r = reinterpret_cast<const uint16_t*>(m->codes_r);
+  out->lse_row = m->lse_row;
+  out->lse_col = m->lse_col;
+  out->row_best = m->row_best;
+  out->col_best = m->col_best;
+  out->n_coarse = n_coarse;
+  out->coarse = m->coarse;
+  out->coarse_prob = m->coarse_p;
+  out->n_fine = m->host[1];
+  out->fine = m->fine;
+  out->fine_prob = m->fine_p;
+  return GS_OK;
+}
+
+}  // extern "C"

@@ -57,6 +57,14 @@ class gs_outputs(ctypes.Structure):
                 ("final_T", ctypes.c_void_p), ("feats", ctypes.c_void_p), ("last_idx", ctypes.c_void_p)]
 
 
+class gs_pmm_result(ctypes.Structure):
+    _fields_ = [("n_cells", ctypes.c_int32), ("codes_q", ctypes.c_void_p), ("codes_r", ctypes.c_void_p),
+                ("lse_row", ctypes.c_void_p), ("lse_col", ctypes.c_void_p), ("row_best", ctypes.c_void_p),
+                ("col_best", ctypes.c_void_p), ("n_coarse", ctypes.c_int64), ("coarse", ctypes.c_void_p),
+                ("coarse_prob", ctypes.c_void_p), ("n_fine", ctypes.c_int64), ("fine", ctypes.c_void_p),
+                ("fine_prob", ctypes.c_void_p)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError("libgsr.so is not built (run: python -m paper_2507_15683_gb300.build)")
@@ -85,6 +93,8 @@ def _load():
         "gs_scene_evict": [vp],
         "gs_scene_kernel_times": [vp, vp, vp],
         "gs_scene_blend_count": [vp, vp, vp],
+        "gs_pmm_create": [st, st, st, P(vp)],
+        "gs_pmm_match": [vp, vp, vp, ctypes.c_float, P(gs_pmm_result), vp],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -99,6 +109,8 @@ def _load():
     L.gs_refine_defaults.restype = gs_refine_opts
     L.gs_destroy_scene.argtypes = [vp]
     L.gs_destroy_scene.restype = None
+    L.gs_pmm_destroy.argtypes = [vp]
+    L.gs_pmm_destroy.restype = None
     L.gs_last_error.argtypes = []
     L.gs_last_error.restype = ctypes.c_char_p
     L.gs_version.argtypes = []
@@ -482,3 +494,63 @@ def pose_loss_function():
             return g * grad, None, None, None, None, None, None, None
 
     return PoseLoss
+
+
+# ---- probabilistic mutual matching (Sec. 3.4, Eq. 11) ---------------------------------------------
+def gs_pmm_create(channels: int, height: int, width: int):
+    h = ctypes.c_void_p()
+    _check(lib.gs_pmm_create(int(channels), int(height), int(width), ctypes.byref(h)))
+    return h
+
+
+def gs_pmm_destroy(h) -> None:
+    lib.gs_pmm_destroy(h)
+
+
+def gs_pmm_match(h, feat_query: int, feat_render: int, tau: float, stream: int) -> gs_pmm_result:
+    r = gs_pmm_result()
+    _check(lib.gs_pmm_match(h, feat_query, feat_render, float(tau), ctypes.byref(r), stream))
+    return r
+
+
+class _DevView:
+    """A device array of the library, seen by torch without a copy."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(int(x) for x in shape), "typestr": typestr,
+                                         "data": (int(ptr or 0), False), "version": 3, "strides": None}
+
+
+class Matcher:
+    """PMM of two (32, H, W) fp32 CUDA feature maps; ``match`` returns copies of the results."""
+
+    def __init__(self, height: int, width: int, channels: int = 32):
+        self.H, self.W = int(height), int(width)
+        self.handle = gs_pmm_create(channels, self.H, self.W)
+
+    def close(self):
+        if self.handle:
+            gs_pmm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def match(self, feat_query, feat_render, tau: float = 0.1) -> dict:
+        import torch
+        for f in (feat_query, feat_render):
+            if not (f.is_cuda and f.dtype == torch.float32 and f.is_contiguous() and f.shape[1:] == (self.H, self.W)):
+                raise ValueError("feature maps must be contiguous float32 CUDA tensors of shape (32, H, W)")
+        r = gs_pmm_match(self.handle, feat_query.data_ptr(), feat_render.data_ptr(), tau, _stream())
+        n, nc, nf = r.n_cells, r.n_coarse, r.n_fine
+        v = lambda p, shape, t: torch.as_tensor(_DevView(p, shape, t), device="cuda").clone()
+        return {"codes_q": v(r.codes_q, (n, 32), "<u2"), "codes_r": v(r.codes_r, (n, 32), "<u2"),
+                "lse_row": v(r.lse_row, (n,), "<f4"), "lse_col": v(r.lse_col, (n,), "<f4"),
+                "row_best": v(r.row_best, (n,), "<i4"), "col_best": v(r.col_best, (n,), "<i4"),
+                "coarse": v(r.coarse, (nc, 2), "<i4") if nc else torch.zeros((0, 2), dtype=torch.int32, device="cuda"),
+                "coarse_prob": v(r.coarse_prob, (nc,), "<f4") if nc else torch.zeros(0, device="cuda"),
+                "fine": v(r.fine, (nf, 3), "<i4") if nf else torch.zeros((0, 3), dtype=torch.int32, device="cuda"),
+                "fine_prob": v(r.fine_prob, (nf,), "<f4") if nf else torch.zeros(0, device="cuda")}

@@ -1,5 +1,5 @@
 """The C-ABI library builds, loads without a GPU and exports every entry point
-declared in include/gsr.h (no compute call is made here)."""
+declared in include/*.h (no compute call is made here)."""
 import ctypes
 import os
 import re
@@ -8,7 +8,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_functions():
-    text = open(os.path.join(ROOT, "include", "gsr.h")).read()
+    inc = os.path.join(ROOT, "include")
+    text = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"^\s*(?:gs_status|void|const char\s*\*|gs_refine_opts)\s*(gs_\w+)\s*\(", text,
                                  flags=re.M)))
@@ -18,7 +19,7 @@ def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("gs_create_scene", "gs_destroy_scene", "gs_render", "gs_render_pose_grad", "gs_render_batch",
                      "gs_render_pose_grad_batch", "gs_refine_pose", "gs_refine_poses_batch", "gs_refine_defaults",
-                     "gs_last_error"):
+                     "gs_last_error", "gs_pmm_create", "gs_pmm_match", "gs_pmm_destroy"):
         assert required in names
 
 
@@ -38,3 +39,12 @@ def test_invalid_arguments_fail_without_a_gpu(libgsr_path):
     assert b"required" in lib.gs_last_error()
     lib.gs_render.argtypes = [ctypes.c_void_p] * 5
     assert lib.gs_render(None, None, None, None, None) == 1
+
+
+def test_pmm_create_rejects_bad_sizes_without_a_gpu(libgsr_path):
+    lib = ctypes.CDLL(libgsr_path)
+    lib.gs_pmm_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+    h = ctypes.c_void_p()
+    assert lib.gs_pmm_create(31, 64, 64, ctypes.byref(h)) == 1  # 32 channels only
+    assert lib.gs_pmm_create(32, 60, 64, ctypes.byref(h)) == 1  # multiples of 8
+    assert not h.value

@@ -1,0 +1,131 @@
+"""GPU probabilistic mutual matching (Sec. 3.4, Eq. 11) against the oracle,
+through the C ABI (gs_pmm_*).
+
+Inputs are feature maps rendered by the oracle (32 channels, fp32) at a
+reference and a perturbed pose. The bf16 coarse codes must be bit-identical;
+the row / column log-sum-exps agree to 1e-5; every argmax decision and coarse
+or fine match whose margin is not within rounding of a tie (oracle flag) must
+be identical.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import pmm as OP
+from paper_2507_15683_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _maps(oracle, seed, w, h, f, n=20000, angle=2.0, move=2.0):
+    scene = synth.aerial_scene(seed, n, extent=(0.0, 200.0, 0.0, 200.0), n_clusters=20, feat_dim=32)
+    cam = synth.camera(w, h, f)
+    T = synth.look_pose((100.0, 40.0, 60.0), 0.0, math.radians(30.0))
+    Tq = synth.perturb_pose(T, synth.rng(seed + 1), angle, move)
+    out = []
+    for pose in (T, Tq):
+        r = oracle.render(scene, cam, pose, geom64=True, n_threads=16)
+        out.append(np.ascontiguousarray(r["feats"].T.reshape(32, h, w).astype(np.float32)))
+    return out
+
+
+def _gpu(gsr, Fq, Fr, tau=OP.TAU):
+    m = gsr.Matcher(Fq.shape[1], Fq.shape[2])
+    res = m.match(torch.from_numpy(Fq).cuda(), torch.from_numpy(Fr).cuda(), tau)
+    m.close()
+    return {k: v.cpu().numpy() for k, v in res.items()}
+
+
+def _check_coarse(g, o):
+    np.testing.assert_array_equal(g["codes_q"], o["codes_q"])
+    np.testing.assert_array_equal(g["codes_r"], o["codes_r"])
+    np.testing.assert_allclose(g["lse_row"], o["lse_row"], rtol=1e-5)
+    np.testing.assert_allclose(g["lse_col"], o["lse_col"], rtol=1e-5)
+    rok, cok = ~o["row_flag"], ~o["col_flag"]
+    assert rok.mean() > 0.5 and cok.mean() > 0.5
+    np.testing.assert_array_equal(g["row_best"][rok], o["row_best"][rok])
+    np.testing.assert_array_equal(g["col_best"][cok], o["col_best"][cok])
+    # coarse matches: identical wherever both decisions of the pair are clear of ties
+    gm = {tuple(x) for x in g["coarse"].tolist()}
+    om = {tuple(x) for x in o["matches"].tolist()}
+    clear = lambda ij: rok[ij[0]] and cok[ij[1]]
+    assert {x for x in gm if clear(x)} == {x for x in om if clear(x)}
+    assert len(om) > 0
+    # probabilities of the common pairs
+    gp = dict(zip(map(tuple, g["coarse"].tolist()), g["coarse_prob"]))
+    for (i, j), p in zip(o["matches"].tolist(), o["prob"]):
+        if (i, j) in gp:
+            assert gp[(i, j)] == pytest.approx(p, rel=1e-3, abs=1e-7)
+    # ascending query cells
+    assert np.all(np.diff(g["coarse"][:, 0]) > 0)
+
+
+def _check_fine(g, o_coarse, Fq, Fr):
+    """Every coarse pair found by both sides: the window's fine matches agree on
+    each query pixel whose row decision and partner-column decision are clear."""
+    W = Fq.shape[2]
+    Wc = W // OP.RATIO
+    win = lambda pix: ((pix // W) % OP.RATIO) * OP.RATIO + (pix % W) % OP.RATIO
+    gby = {}
+    for (k, q, r), p in zip(g["fine"].tolist(), g["fine_prob"]):
+        gby.setdefault(int(g["coarse"][k, 0]), {})[win(q)] = (win(r), float(p))
+    common = {tuple(x) for x in g["coarse"].tolist()} & {tuple(x) for x in o_coarse["matches"].tolist()}
+    checked = 0
+    for i, j in sorted(common):
+        logP, _, _ = OP.log_dual_softmax(OP._window(Fq, i, Wc, OP.RATIO) @ OP._window(Fr, j, Wc, OP.RATIO).T)
+        m = OP.mnn(logP)
+        opair = {int(a): int(b) for a, b in m["matches"]}
+        gw = gby.get(i, {})
+        for a in range(OP.RATIO * OP.RATIO):
+            if m["row_flag"][a] or m["col_flag"][m["row_best"][a]]:
+                continue
+            if a in opair:
+                assert a in gw and gw[a][0] == opair[a], (i, j, a)
+                assert gw[a][1] == pytest.approx(math.exp(logP[a, opair[a]]), rel=1e-3, abs=1e-7)
+            else:
+                assert a not in gw, (i, j, a)
+            checked += 1
+    assert checked > 0
+
+
+def test_pmm_small_aerial(oracle, gsr):
+    Fq, Fr = _maps(oracle, 61, 240, 136, 175.0)  # 30 x 17 = 510 cells: 4 x 4 tiles, the last ragged
+    o = OP.coarse_pmm(Fq, Fr)
+    g = _gpu(gsr, Fq, Fr)
+    _check_coarse(g, o)
+    _check_fine(g, o, Fq, Fr)
+
+
+def test_pmm_multi_tile(oracle, gsr):
+    Fq, Fr = _maps(oracle, 62, 512, 520, 380.0, n=40000)  # 64 x 65 = 4160 cells: 33 x 33 tiles
+    o = OP.coarse_pmm(Fq, Fr)
+    g = _gpu(gsr, Fq, Fr)
+    _check_coarse(g, o)
+
+
+def test_pmm_self_match_and_one_cell(oracle, gsr):
+    g = np.random.default_rng(6)
+    F = g.standard_normal((32, 64, 80)).astype(np.float32)  # 8 x 10 cells of distinct random vectors
+    res = _gpu(gsr, F, F)
+    n = 80
+    np.testing.assert_array_equal(res["coarse"], np.stack([np.arange(n)] * 2, 1))
+    assert len(res["fine"]) == n * 64
+    np.testing.assert_array_equal(res["fine"][:, 1], res["fine"][:, 2])
+    one = g.standard_normal((32, 8, 8)).astype(np.float32)
+    r1 = _gpu(gsr, one, one)
+    np.testing.assert_array_equal(r1["coarse"], [[0, 0]])
+    assert r1["coarse_prob"][0] == pytest.approx(1.0, rel=1e-6)
+
+
+def test_pmm_arguments(gsr):
+    with pytest.raises(gsr.GsError) as e:
+        gsr.Matcher(100, 64)  # not a multiple of 8
+    assert e.value.status == gsr.GS_ERR_INVALID_ARG
+    m = gsr.Matcher(16, 16)
+    x = torch.zeros((32, 16, 16), device="cuda")
+    with pytest.raises(gsr.GsError) as e:
+        m.match(x, x, tau=0.01)
+    assert e.value.status == gsr.GS_ERR_INVALID_ARG
+    m.close()

@@ -159,3 +159,55 @@ def fine_pmm(Fq: np.ndarray, Fr: np.ndarray, coarse_matches: np.ndarray, tau: fl
             flags.append(bool(m["row_flag"][a] or m["col_flag"][b]))
     return {"matches": np.asarray(rows, np.int64).reshape(-1, 3), "prob": np.asarray(probs, np.float64),
             "flag": np.asarray(flags, bool)}
+
+
+def coarse_pmm_chunked(Fq: np.ndarray, Fr: np.ndarray, tau: float = TAU, ratio: int = RATIO,
+                       chunk: int = 2048, tie_gap: float = TIE_GAP) -> dict:
+    """coarse_pmm for maps whose full similarity matrix does not fit in memory:
+    the same formulas over blocks of query rows (M is never stored whole).
+    Returns the same keys except "M"."""
+    cq = coarse_codes(Fq, ratio)
+    cr = coarse_codes(Fr, ratio)
+    Q, R = bf16_to_f64(cq), bf16_to_f64(cr)
+    n_q, n_r = Q.shape[0], R.shape[0]
+    # pass 1: row log-sum-exps; column log-sum-exps from per-block maxima and sums
+    r = np.empty(n_q)
+    cmax = np.full(n_r, -np.inf)
+    for s in range(0, n_q, chunk):
+        A = (Q[s:s + chunk] @ R.T) / tau
+        m = A.max(axis=1, keepdims=True)
+        r[s:s + chunk] = (m + np.log(np.exp(A - m).sum(axis=1, keepdims=True)))[:, 0]
+        cmax = np.maximum(cmax, A.max(axis=0))
+    csum = np.zeros(n_r)
+    for s in range(0, n_q, chunk):
+        A = (Q[s:s + chunk] @ R.T) / tau
+        csum += np.exp(A - cmax[None, :]).sum(axis=0)
+    c = cmax + np.log(csum)
+    # pass 2: best and runner-up of rows and columns of log P_M
+    rb = np.empty(n_q, np.int64)
+    rgap = np.empty(n_q)
+    ctop = np.full(n_r, -np.inf)
+    csec = np.full(n_r, -np.inf)
+    cb = np.zeros(n_r, np.int64)
+    for s in range(0, n_q, chunk):
+        L = 2.0 * (Q[s:s + chunk] @ R.T) / tau - r[s:s + chunk, None] - c[None, :]
+        b, gap = _best_and_gap(L, 1)
+        rb[s:s + chunk], rgap[s:s + chunk] = b, gap
+        # columns: merge this block's top two into the running top two (first index kept on ties)
+        bi = np.argmax(L, axis=0)
+        bt = L[bi, np.arange(n_r)]
+        L2 = L.copy()
+        L2[bi, np.arange(n_r)] = -np.inf
+        bs = L2.max(axis=0) if L.shape[0] > 1 else np.full(n_r, -np.inf)
+        new_top = bt > ctop
+        csec = np.where(new_top, np.maximum(ctop, bs), np.maximum(csec, bt))
+        cb = np.where(new_top, s + bi, cb)
+        ctop = np.where(new_top, bt, ctop)
+    cgap = ctop - csec
+    i = np.arange(n_q)
+    mutual = cb[rb] == i
+    mi, mj = i[mutual], rb[mutual]
+    prob = np.exp(2.0 * np.einsum("ij,ij->i", Q[mi], R[mj]) / tau - r[mi] - c[mj])
+    return {"row_best": rb, "col_best": cb, "row_gap": rgap, "col_gap": cgap, "row_flag": rgap < tie_gap,
+            "col_flag": cgap < tie_gap, "matches": np.stack([mi, mj], 1).astype(np.int64), "prob": prob,
+            "codes_q": cq, "codes_r": cr, "lse_row": r, "lse_col": c}

@@ -129,3 +129,28 @@ def test_pmm_arguments(gsr):
         m.match(x, x, tau=0.01)
     assert e.value.status == gsr.GS_ERR_INVALID_ARG
     m.close()
+
+
+def test_pmm_full_size_1080p(oracle, gsr):
+    """1920 x 1080 feature maps (32,400 coarse cells, a 32,400 x 32,400 similarity
+    matrix) rendered by the oracle from 1,000,000 Gaussians with 32 feature
+    channels, reference pose against a query 2 deg / 5 m away: every coarse code
+    bit for bit, every clear decision, and the fine matches of 300 coarse pairs."""
+    scene = synth.aerial_scene(2, 1_000_000, feat_dim=32)
+    cam = synth.aerial_camera()
+    T_ref = synth.aerial_pose()
+    T_q = synth.perturb_pose(T_ref, synth.rng(100), 2.0, 5.0)
+    H, W = cam["height"], cam["width"]
+    maps = []
+    for T in (T_q, T_ref):
+        r = oracle.render(scene, cam, T, geom64=True, n_threads=16)
+        maps.append(np.ascontiguousarray(r["feats"].T.reshape(32, H, W).astype(np.float32)))
+    Fq, Fr = maps
+    o = OP.coarse_pmm_chunked(Fq, Fr)
+    g = _gpu(gsr, Fq, Fr)
+    _check_coarse(g, o)
+    sub = o["matches"][np.sort(synth.rng(8).choice(len(o["matches"]), 300, replace=False))]
+    keep = np.isin(g["coarse"][:, 0], sub[:, 0])
+    gsub = {"coarse": g["coarse"], "fine": g["fine"][np.isin(g["fine"][:, 0], np.nonzero(keep)[0])],
+            "fine_prob": g["fine_prob"][np.isin(g["fine"][:, 0], np.nonzero(keep)[0])]}
+    _check_fine(gsub, {"matches": sub}, Fq, Fr)

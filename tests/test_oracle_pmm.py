@@ -130,3 +130,17 @@ def test_fine_windows_match_themselves():
     q, r = fine2["matches"][:, 1], fine2["matches"][:, 2]
     inner = (q % W) < R - 1  # query pixels whose shifted copy stays inside the window
     np.testing.assert_array_equal(r[inner], q[inner] + 1)
+
+
+def test_chunked_equals_dense():
+    # the blocked form used at full image size gives the dense form's results
+    g = np.random.default_rng(7)
+    cells = g.standard_normal((9 * 11, 32))
+    Fq = _blocks_to_map(cells, 9, 11, jitter=0.3 * g.standard_normal((32, 72, 88)))
+    Fr = _blocks_to_map(cells[g.permutation(99)], 9, 11, jitter=0.3 * g.standard_normal((32, 72, 88)))
+    d = pmm.coarse_pmm(Fq, Fr)
+    c = pmm.coarse_pmm_chunked(Fq, Fr, chunk=16)
+    for k in ("row_best", "col_best", "matches"):
+        np.testing.assert_array_equal(c[k], d[k])
+    for k in ("lse_row", "lse_col", "row_gap", "col_gap", "prob"):
+        np.testing.assert_allclose(c[k], d[k], rtol=1e-12, atol=1e-12)

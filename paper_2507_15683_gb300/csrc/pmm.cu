@@ -38,7 +38,6 @@ namespace {
 constexpr int kC = 32;         // channels
 constexpr int kRatio = 8;      // H_f / H_c
 constexpr int kTile = 128;     // cells per tile side (MMA M = N = 128)
-constexpr int kThreads = 128;  // 4 warps; warp w reads tensor-memory lanes 32 w .. 32 w + 31
 constexpr uint32_t kTmemCols = 128;
 constexpr int kWaitLimit = 1 << 22;  // polls of an mbarrier before giving up (far beyond a 2-MMA tile)
 constexpr int kMaxCells = 1 << 18;
@@ -46,37 +45,54 @@ constexpr int kScanThreads = 1024;
 constexpr int kWin = kRatio * kRatio;  // fine vectors per window
 
 // ---------------------------------------------------------------------------
-// coarse codes: one warp per cell, lane = channel
+// coarse codes: a CTA takes 32 horizontally adjacent cells; warp c sums channel c
+// of each cell (lane = cell: the 32 lanes read one contiguous row of 256
+// pixels), warp 0 forms the norms, and the codes leave as one contiguous block
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_pmm_codes(const float* __restrict__ F, int H, int W, int Wc, int n_cells,
-                                                   __nv_bfloat16* __restrict__ codes) {
-  const int lane = threadIdx.x & 31;
-  const int cell = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  if (cell >= n_cells) return;  // warp-uniform
-  const int cy = cell / Wc, cx = cell - cy * Wc;
-  const float* base = F + (size_t)lane * H * W + (size_t)(cy * kRatio) * W + cx * kRatio;
-  float s = 0.0f;  // block sum in row-major order
+__global__ void __launch_bounds__(1024) k_pmm_codes(const float* __restrict__ F, int H, int W, int Wc, int n_cells,
+                                                    unsigned short* __restrict__ codes) {
+  __shared__ float m_s[kC][32];
+  __shared__ float inv_s[32];
+  __shared__ unsigned short u_s[32][kC];
+  const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cy = blockIdx.y, cx = blockIdx.x * 32 + lane;
+  const bool ok = cx < Wc;
+  float m = 0.0f;
+  if (ok) {
+    const float* base = F + (size_t)c * H * W + (size_t)(cy * kRatio) * W + cx * kRatio;
+    float s = 0.0f;  // block sum in row-major order
 #pragma unroll
-  for (int dy = 0; dy < kRatio; ++dy) {
-    const float4 a = *reinterpret_cast<const float4*>(base + (size_t)dy * W);
-    const float4 b = *reinterpret_cast<const float4*>(base + (size_t)dy * W + 4);
-    s = __fadd_rn(s, a.x);
-    s = __fadd_rn(s, a.y);
-    s = __fadd_rn(s, a.z);
-    s = __fadd_rn(s, a.w);
-    s = __fadd_rn(s, b.x);
-    s = __fadd_rn(s, b.y);
-    s = __fadd_rn(s, b.z);
-    s = __fadd_rn(s, b.w);
+    for (int dy = 0; dy < kRatio; ++dy) {
+      const float4 a = *reinterpret_cast<const float4*>(base + (size_t)dy * W);
+      const float4 b = *reinterpret_cast<const float4*>(base + (size_t)dy * W + 4);
+      s = __fadd_rn(s, a.x);
+      s = __fadd_rn(s, a.y);
+      s = __fadd_rn(s, a.z);
+      s = __fadd_rn(s, a.w);
+      s = __fadd_rn(s, b.x);
+      s = __fadd_rn(s, b.y);
+      s = __fadd_rn(s, b.z);
+      s = __fadd_rn(s, b.w);
+    }
+    m = __fmul_rn(s, 1.0f / (kRatio * kRatio));  // exact scaling
   }
-  const float m = __fmul_rn(s, 1.0f / (kRatio * kRatio));  // exact scaling
-  const float m2 = __fmul_rn(m, m);
-  float ss = 0.0f;  // squares summed over channels in channel order
+  m_s[c][lane] = m;
+  __syncthreads();
+  if (c == 0) {  // squares summed over channels in channel order
+    float ss = 0.0f;
 #pragma unroll
-  for (int c = 0; c < kC; ++c) ss = __fadd_rn(ss, __shfl_sync(0xffffffffu, m2, c));
-  const float n = __fsqrt_rn(ss);
+    for (int k = 0; k < kC; ++k) ss = __fadd_rn(ss, __fmul_rn(m_s[k][lane], m_s[k][lane]));
+    inv_s[lane] = __fsqrt_rn(ss);
+  }
+  __syncthreads();
+  const float n = inv_s[lane];
   const float u = n > 0.0f ? __fdiv_rn(m, n) : 0.0f;
-  codes[(size_t)cell * kC + lane] = __float2bfloat16_rn(u);
+  u_s[lane][c] = __bfloat16_as_ushort(__float2bfloat16_rn(u));
+  __syncthreads();
+  const int cell0 = cy * Wc + blockIdx.x * 32;
+  const int ncell = min(32, Wc - blockIdx.x * 32);
+  const int t = threadIdx.x;  // 32 cells x 32 channels, contiguous in the output
+  if (t < ncell * kC) codes[(size_t)cell0 * kC + t] = u_s[t / kC][t % kC];
 }
 
 // ---------------------------------------------------------------------------
@@ -152,17 +168,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 }
 
 // ---------------------------------------------------------------------------
-// similarity tiles (both passes)
+// similarity tiles
 // ---------------------------------------------------------------------------
+constexpr int kTileThreads = 256;  // warp w: tensor-memory lanes 32 (w % 4) .. +31, columns 64 (w / 4) .. +63
+
 struct TileSmem {
-  uint4 a[kTile * kC * 2 / 16];  // query codes, core-matrix layout (8 KB)
-  uint4 b[kTile * kC * 2 / 16];  // rendered codes (8 KB)
-  float colv[4][kTile];          // per-warp column partials
-  int coli[4][kTile];            // pass 2: their row index
-  float lse_c[kTile];            // pass 2: c_j of the tile's columns
+  uint4 a[kTile * kC * 2 / 16];  // A codes (rows of M), core-matrix layout (8 KB)
+  uint4 b[kTile * kC * 2 / 16];  // B codes (columns of M) (8 KB)
+  float colv[4][kTile];          // pass 1: column partials per row quarter
+  float rowv[2][kTile];          // row partials per column half
+  int rowi[2][kTile];            // pass 2: their column index
+  float lse_c[kTile];            // pass 2: log-sum-exp of the tile's columns
   unsigned long long bar;
   uint32_t tmem;
-  int fail;
 };
 // one CTA uses 128 of the 512 tensor-memory columns of an SM; the dynamic
 // shared-memory request keeps at most 4 CTAs on an SM so allocation never waits
@@ -173,8 +191,8 @@ static_assert(sizeof(TileSmem) <= kTileSmemBytes, "tile shared memory");
 // core matrix (r / 8, c) is 128 bytes, k-chunks of a row group are adjacent
 __device__ __forceinline__ int core_off(int r, int c) { return ((r >> 3) * 4 + c) * 128 + (r & 7) * 16; }
 
-// lane l ends with v[0] = sum over the warp's lanes of v[l] (l < 16 values: the
-// columns of one half-chunk are summed over the lane pairs l, l ^ 16 too)
+// lane l ends with the sum over the warp's lanes of v[l & 15] (the 16 columns of
+// a chunk, each summed over the warp's 32 rows)
 __device__ __forceinline__ float reduce_scatter16(float (&v)[16], int lane) {
 #pragma unroll
   for (int s = 8; s >= 1; s >>= 1) {
@@ -189,48 +207,36 @@ __device__ __forceinline__ float reduce_scatter16(float (&v)[16], int lane) {
   return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
 }
 
-// argmax form: larger value wins, equal values go to the smaller index
-__device__ __forceinline__ bool better(float v, int i, float bv, int bi) { return v > bv || (v == bv && i < bi); }
-
-__device__ __forceinline__ void reduce_scatter16_max(float (&v)[16], int (&ix)[16], int lane, float& out_v,
-                                                     int& out_i) {
-#pragma unroll
-  for (int s = 8; s >= 1; s >>= 1) {
-    const bool up = (lane & s) != 0;
-#pragma unroll
-    for (int i = 0; i < s; ++i) {
-      const float sv = up ? v[i] : v[i + s];
-      const int si = up ? ix[i] : ix[i + s];
-      const float kv = up ? v[i + s] : v[i];
-      const int ki = up ? ix[i + s] : ix[i];
-      const float rv = __shfl_xor_sync(0xffffffffu, sv, s);
-      const int ri = __shfl_xor_sync(0xffffffffu, si, s);
-      const bool take = better(rv, ri, kv, ki);
-      v[i] = take ? rv : kv;
-      ix[i] = take ? ri : ki;
-    }
-  }
-  const float rv = __shfl_xor_sync(0xffffffffu, v[0], 16);
-  const int ri = __shfl_xor_sync(0xffffffffu, ix[0], 16);
-  const bool take = better(rv, ri, v[0], ix[0]);
-  out_v = take ? rv : v[0];
-  out_i = take ? ri : ix[0];
+// 2^x for x in [-120, 1]: the results stay normal binary32 numbers, so the
+// flush-to-zero form of the hardware approximation is exact enough here
+__device__ __forceinline__ float ex2_ftz(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
-// PASS 1: prow_v[rb n + i] = sum over the tile's columns of exp((M - 1) / tau),
-//         pcol_v[qb n + j] = the same over the tile's rows.
-// PASS 2: prow_v / prow_i = best 2 M / tau - c_j of row i within the tile,
-//         pcol_v / pcol_i = best 2 M / tau - r_i of column j within the tile.
+// argmax order: larger value wins, equal values go to the smaller index
+__device__ __forceinline__ bool better(float v, int i, float bv, int bi) { return v > bv || (v == bv && i < bi); }
+
+// Tiles of M = A B^T (A, B: n x 32 bf16 codes), 128 x 128 each, persistent.
+// PASS 1: prow_v[cb n + i] = sum over the tile's columns j of exp((M_ij - 1) / tau)
+//         and pcol_v[rb n + j] = the same over the tile's rows (row block rb,
+//         column block cb).
+// PASS 2: prow_v / prow_i = the best 2 M_ij / tau - lse_c[j] of row i within the
+//         tile and its column (the first on ties). With A = query, B = rendered
+//         and lse_c = column log-sum-exps this is the row argmax of log P_M; with
+//         the operands swapped and the row log-sum-exps, its column argmax.
 template <int PASS>
-__global__ void __launch_bounds__(kThreads) k_pmm_tiles(const uint4* __restrict__ cq, const uint4* __restrict__ cr,
-                                                        int n, int nb, float s_exp, float s_two,
-                                                        const float* __restrict__ lse_row,
-                                                        const float* __restrict__ lse_col, float* __restrict__ prow_v,
-                                                        int* __restrict__ prow_i, float* __restrict__ pcol_v,
-                                                        int* __restrict__ pcol_i, int* __restrict__ err) {
+__global__ void __launch_bounds__(kTileThreads) k_pmm_tiles(const uint4* __restrict__ ca, const uint4* __restrict__ cb,
+                                                            int n, int nb, float s_exp, float s_two,
+                                                            const float* __restrict__ lse_c,
+                                                            float* __restrict__ prow_v, int* __restrict__ prow_i,
+                                                            float* __restrict__ pcol_v, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   TileSmem& S = *reinterpret_cast<TileSmem*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int quarter = warp & 3, half = warp >> 2;
+  const int lrow = quarter * 32 + lane;  // this thread's row of the tile
   const uint32_t bar = smem_u32(&S.bar);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem)),
@@ -241,31 +247,42 @@ __global__ void __launch_bounds__(kThreads) k_pmm_tiles(const uint4* __restrict_
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    S.fail = 0;
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = S.tmem;
-  const uint32_t tlane = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's 32 lanes
+  const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 64);
   const uint32_t sa = smem_u32(S.a), sb = smem_u32(S.b);
+  unsigned char* pa = reinterpret_cast<unsigned char*>(S.a);
+  unsigned char* pb = reinterpret_cast<unsigned char*>(S.b);
+  // operand staging: thread t moves k-chunks 2 (t / 128) and 2 (t / 128) + 1 of row t % 128
+  const int srow = tid & (kTile - 1), sc0 = (tid >> 7) * 2;
+  auto load_ops = [&](int t, uint4 (&ra)[2], uint4 (&rb)[2]) {
+    const int rb_ = t / nb, cb_ = t - rb_ * nb;
+    const int ar = rb_ * kTile + srow, br = cb_ * kTile + srow;
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      ra[c] = ar < n ? ca[(size_t)ar * 4 + sc0 + c] : z;
+      rb[c] = br < n ? cb[(size_t)br * 4 + sc0 + c] : z;
+    }
+  };
   uint32_t phase = 0;
   const int n_tiles = nb * nb;
+  uint4 ra[2], rbv[2];
+  if ((int)blockIdx.x < n_tiles) load_ops(blockIdx.x, ra, rbv);
   for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {  // block-uniform
-    const int qb = t / nb, rb = t - qb * nb;
-    const int qrow = qb * kTile + tid, rrow = rb * kTile + tid;
-    // stage the two 128 x 32 bf16 operands (rows past n are zero)
+    const int rb_ = t / nb, cb_ = t - rb_ * nb;
+    const int grow = rb_ * kTile + lrow;  // global row (A index) of this thread
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-      const uint4 av = qrow < n ? cq[(size_t)qrow * 4 + c] : z;
-      const uint4 bv = rrow < n ? cr[(size_t)rrow * 4 + c] : z;
-      *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(S.a) + core_off(tid, c)) = av;
-      *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(S.b) + core_off(tid, c)) = bv;
+    for (int c = 0; c < 2; ++c) {
+      *reinterpret_cast<uint4*>(pa + core_off(srow, sc0 + c)) = ra[c];
+      *reinterpret_cast<uint4*>(pb + core_off(srow, sc0 + c)) = rbv[c];
     }
-    if (PASS == 2) S.lse_c[tid] = rrow < n ? lse_col[rrow] : 0.0f;
+    if (PASS == 2 && tid < kTile) S.lse_c[tid] = cb_ * kTile + tid < n ? lse_c[cb_ * kTile + tid] : 0.0f;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // operands visible to the tensor core
-    tc_fence_before();  // previous tile's accumulator reads are done
+    tc_fence_before();  // the previous tile's accumulator reads are done
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
@@ -274,89 +291,91 @@ __global__ void __launch_bounds__(kThreads) k_pmm_tiles(const uint4* __restrict_
       mma_bf16(tmem, smem_desc(sa + 256, 128, 512), smem_desc(sb + 256, 128, 512), 1u);
       mma_commit(bar);
     }
+    if (t + (int)gridDim.x < n_tiles) load_ops(t + gridDim.x, ra, rbv);  // next operands, during the MMA
     const bool done = mbar_wait(bar, phase);
     phase ^= 1u;
     if (__syncthreads_or(!done)) {  // the accumulator never arrived: report, drain, stop
-      if (tid == 0) {
-        atomicExch(err, 1);
-        S.fail = 1;
-      }
+      if (tid == 0) atomicExch(err, 1);
       mbar_wait(bar, phase ^ 1u);
       break;
     }
     tc_fence_after();
-
-    const bool row_ok = qrow < n;
+    const bool row_ok = grow < n;
+    // interior tiles (every row and column below n) take the unmasked path
+    const bool interior = (rb_ + 1) * kTile <= n && (cb_ + 1) * kTile <= n;
     if (PASS == 1) {
       float rsum = 0.0f;
-#pragma unroll 1
-      for (int ch = 0; ch < kTile / 16; ++ch) {
+#pragma unroll 2
+      for (int ch = 0; ch < 4; ++ch) {
         float v[16];
-        tmem_ld16(tlane + (uint32_t)(ch * 16), v);
-        const int col0 = rb * kTile + ch * 16;
+        tmem_ld16(tbase + (uint32_t)(ch * 16), v);
+        if (interior) {
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const float e = exp2f((v[k] - 1.0f) * s_exp);
-          v[k] = (row_ok && col0 + k < n) ? e : 0.0f;
-          rsum += v[k];
+          for (int k = 0; k < 16; ++k) {
+            v[k] = ex2_ftz(fmaf(v[k], s_exp, -s_exp));  // exp((M - 1) / tau)
+            rsum += v[k];
+          }
+        } else {
+          const int col0 = cb_ * kTile + half * 64 + ch * 16;
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            const float e = ex2_ftz(fmaf(v[k], s_exp, -s_exp));
+            v[k] = (row_ok && col0 + k < n) ? e : 0.0f;
+            rsum += v[k];
+          }
         }
         const float cs = reduce_scatter16(v, lane);
-        if (lane < 16) S.colv[warp][ch * 16 + lane] = cs;
+        if (lane < 16) S.colv[quarter][half * 64 + ch * 16 + lane] = cs;
       }
-      if (row_ok) prow_v[(size_t)rb * n + qrow] = rsum;
+      S.rowv[half][lrow] = rsum;
     } else {
-      const float rq = row_ok ? lse_row[qrow] : 0.0f;
       float best = -INFINITY;
       int bidx = 0x7fffffff;
-#pragma unroll 1
-      for (int ch = 0; ch < kTile / 16; ++ch) {
+#pragma unroll 2
+      for (int ch = 0; ch < 4; ++ch) {
         float v[16];
-        tmem_ld16(tlane + (uint32_t)(ch * 16), v);
-        const int col0 = rb * kTile + ch * 16;
-        float cv[16];
-        int ci[16];
+        tmem_ld16(tbase + (uint32_t)(ch * 16), v);
+        const int l0 = half * 64 + ch * 16;
+        const float4* lc4 = reinterpret_cast<const float4*>(S.lse_c + l0);
+        float lc[16];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 x = lc4[q];
+          lc[4 * q] = x.x;
+          lc[4 * q + 1] = x.y;
+          lc[4 * q + 2] = x.z;
+          lc[4 * q + 3] = x.w;
+        }
+        const int col0 = cb_ * kTile + l0;
+        const int lim = interior ? 16 : (row_ok ? min(16, n - col0) : 0);
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
-          const bool ok = row_ok && col0 + k < n;
-          const float m2 = v[k] * s_two;
-          const float rv = m2 - S.lse_c[ch * 16 + k];
-          if (ok && rv > best) {  // columns in ascending order: the first maximum stays
+          const float rv = fmaf(v[k], s_two, -lc[k]);
+          if (k < lim && rv > best) {  // ascending columns: the first maximum stays
             best = rv;
             bidx = col0 + k;
           }
-          cv[k] = ok ? m2 - rq : -INFINITY;
-          ci[k] = ok ? qrow : 0x7fffffff;
-        }
-        float ov;
-        int oi;
-        reduce_scatter16_max(cv, ci, lane, ov, oi);
-        if (lane < 16) {
-          S.colv[warp][ch * 16 + lane] = ov;
-          S.coli[warp][ch * 16 + lane] = oi;
         }
       }
-      if (row_ok) {
-        prow_v[(size_t)rb * n + qrow] = best;
-        prow_i[(size_t)rb * n + qrow] = bidx;
-      }
+      S.rowv[half][lrow] = best;
+      S.rowi[half][lrow] = bidx;
     }
+    tc_fence_before();
     __syncthreads();
-    if (rrow < n) {  // thread t owns column t of the tile: warps (rows 0-31, 32-63, ...) in order
-      if (PASS == 1) {
-        const float s = ((S.colv[0][tid] + S.colv[1][tid]) + S.colv[2][tid]) + S.colv[3][tid];
-        pcol_v[(size_t)qb * n + rrow] = s;
-      } else {
-        float bv = S.colv[0][tid];
-        int bi = S.coli[0][tid];
-#pragma unroll
-        for (int w = 1; w < 4; ++w)
-          if (better(S.colv[w][tid], S.coli[w][tid], bv, bi)) {
-            bv = S.colv[w][tid];
-            bi = S.coli[w][tid];
-          }
-        pcol_v[(size_t)qb * n + rrow] = bv;
-        pcol_i[(size_t)qb * n + rrow] = bi;
+    if (tid < kTile) {  // rows: the two column halves in order
+      const int r = rb_ * kTile + tid;
+      if (r < n) {
+        if (PASS == 1) {
+          prow_v[(size_t)cb_ * n + r] = S.rowv[0][tid] + S.rowv[1][tid];
+        } else {
+          const bool h1 = better(S.rowv[1][tid], S.rowi[1][tid], S.rowv[0][tid], S.rowi[0][tid]);
+          prow_v[(size_t)cb_ * n + r] = h1 ? S.rowv[1][tid] : S.rowv[0][tid];
+          prow_i[(size_t)cb_ * n + r] = h1 ? S.rowi[1][tid] : S.rowi[0][tid];
+        }
       }
+    } else if (PASS == 1) {  // columns: the four row quarters in order
+      const int l = tid - kTile, col = cb_ * kTile + l;
+      if (col < n) pcol_v[(size_t)rb_ * n + col] = ((S.colv[0][l] + S.colv[1][l]) + S.colv[2][l]) + S.colv[3][l];
     }
   }
   tc_fence_before();
@@ -425,33 +444,31 @@ __device__ uint32_t scan_block(uint32_t v, uint32_t* tmp) {
   return tmp[wid] + incl - v;
 }
 
-// mutual nearest neighbours, compacted in ascending query order (one CTA)
-__global__ void __launch_bounds__(kScanThreads) k_pmm_mnn(int n, const int* __restrict__ row_best,
-                                                          const int* __restrict__ col_best,
-                                                          const __nv_bfloat16* __restrict__ cq,
-                                                          const __nv_bfloat16* __restrict__ cr,
-                                                          const float* __restrict__ lse_row,
-                                                          const float* __restrict__ lse_col, float s_two,
-                                                          int* __restrict__ coarse, float* __restrict__ prob,
-                                                          int* __restrict__ n_out) {
-  __shared__ uint32_t tmp[32];
-  const int per = (n + kScanThreads - 1) / kScanThreads;
-  const int b = threadIdx.x * per, e = min(n, b + per);
-  // an argmax left at its sentinel (non-finite features) matches nothing
-  auto mutual = [&](int i, int j) { return j >= 0 && j < n && col_best[j] == i; };
-  uint32_t cnt = 0;
-  for (int i = b; i < e; ++i) cnt += mutual(i, row_best[i]) ? 1u : 0u;
-  uint32_t pos = scan_block(cnt, tmp);
-  for (int i = b; i < e; ++i) {
-    const int j = row_best[i];
-    if (!mutual(i, j)) continue;
-    coarse[2 * pos] = i;
-    coarse[2 * pos + 1] = j;
-    const float m = dot_codes(cq + (size_t)i * kC, cr + (size_t)j * kC);
-    prob[pos] = expf(m * s_two - lse_row[i] - lse_col[j]);
-    ++pos;
-  }
-  if (threadIdx.x == kScanThreads - 1) *n_out = (int)pos;
+// mutual nearest neighbours: flag[i] = 1 when query cell i and rendered cell
+// row_best[i] are each other's argmax, with P_M of the pair (an argmax left at
+// its sentinel by non-finite features matches nothing)
+__global__ void k_pmm_mnn(int n, const int* __restrict__ row_best, const int* __restrict__ col_best,
+                          const __nv_bfloat16* __restrict__ cq, const __nv_bfloat16* __restrict__ cr,
+                          const float* __restrict__ lse_row, const float* __restrict__ lse_col, float s_two,
+                          int* __restrict__ flag, float* __restrict__ prob) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int j = row_best[i];
+  const bool mutual = j >= 0 && j < n && col_best[j] == i;
+  flag[i] = mutual ? 1 : 0;
+  if (mutual) prob[i] = expf(dot_codes(cq + (size_t)i * kC, cr + (size_t)j * kC) * s_two - lse_row[i] - lse_col[j]);
+}
+
+// the matches at their scanned positions, in ascending query order
+__global__ void k_pmm_mnn_scatter(int n, const int* __restrict__ row_best, const int* __restrict__ flag,
+                                  const int* __restrict__ off, const float* __restrict__ prob_in,
+                                  int* __restrict__ coarse, float* __restrict__ prob) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || !flag[i]) return;
+  const int pos = off[i];
+  coarse[2 * pos] = i;
+  coarse[2 * pos + 1] = row_best[i];
+  prob[pos] = prob_in[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -461,7 +478,7 @@ __global__ void __launch_bounds__(kWin) k_pmm_fine(const float* __restrict__ Fq,
                                                    int W, int Wc, const int* __restrict__ coarse, float inv_tau,
                                                    float s_exp, float s_two, int* __restrict__ slot_r,
                                                    float* __restrict__ slot_p, int* __restrict__ win_count) {
-  __shared__ float uq[kWin][kC + 1], ur[kWin][kC + 1];
+  __shared__ __align__(16) float ur[kWin][kC];  // rendered unit vectors (read as float4 broadcasts)
   __shared__ float Mf[kWin][kWin + 1];
   __shared__ float lr[kWin], lc[kWin];
   __shared__ int rbest[kWin], cbest[kWin];
@@ -470,29 +487,37 @@ __global__ void __launch_bounds__(kWin) k_pmm_fine(const float* __restrict__ Fq,
   const size_t HW = (size_t)H * W;
   const int qy = (ci / Wc) * kRatio + a / kRatio, qx = (ci % Wc) * kRatio + a % kRatio;
   const int ry = (cj / Wc) * kRatio + a / kRatio, rx = (cj % Wc) * kRatio + a % kRatio;
-  {  // normalised fine vectors (fp32, channel order)
-    float vq[kC], vr[kC];
+  float uq[kC];  // this thread's query unit vector (fp32, channel order)
+  {
+    float vr[kC];
     float sq = 0.0f, sr = 0.0f;
 #pragma unroll
     for (int c = 0; c < kC; ++c) {
-      vq[c] = Fq[c * HW + (size_t)qy * W + qx];
+      uq[c] = Fq[c * HW + (size_t)qy * W + qx];
       vr[c] = Fr[c * HW + (size_t)ry * W + rx];
-      sq = fmaf(vq[c], vq[c], sq);
+      sq = fmaf(uq[c], uq[c], sq);
       sr = fmaf(vr[c], vr[c], sr);
     }
     const float iq = sq > 0.0f ? 1.0f / sqrtf(sq) : 0.0f, ir = sr > 0.0f ? 1.0f / sqrtf(sr) : 0.0f;
 #pragma unroll
     for (int c = 0; c < kC; ++c) {
-      uq[a][c] = vq[c] * iq;
+      uq[c] *= iq;
       ur[a][c] = vr[c] * ir;
     }
   }
   __syncthreads();
   float rs = 0.0f;  // row a: similarities and exp sum
   for (int b = 0; b < kWin; ++b) {
+    const float4* rb4 = reinterpret_cast<const float4*>(ur[b]);
     float m = 0.0f;
 #pragma unroll
-    for (int c = 0; c < kC; ++c) m = fmaf(uq[a][c], ur[b][c], m);
+    for (int q = 0; q < kC / 4; ++q) {
+      const float4 x = rb4[q];
+      m = fmaf(uq[4 * q], x.x, m);
+      m = fmaf(uq[4 * q + 1], x.y, m);
+      m = fmaf(uq[4 * q + 2], x.z, m);
+      m = fmaf(uq[4 * q + 3], x.w, m);
+    }
     Mf[a][b] = m;
     rs += exp2f((m - 1.0f) * s_exp);
   }
@@ -536,10 +561,9 @@ __global__ void __launch_bounds__(kWin) k_pmm_fine(const float* __restrict__ Fq,
   if (a == 0) win_count[k] = rbest[0] + rbest[32];
 }
 
-// exclusive scan of the per-window match counts (one CTA): window offsets and
-// the total
-__global__ void __launch_bounds__(kScanThreads) k_pmm_scan_windows(int n_win, const int* __restrict__ cnt,
-                                                                   int* __restrict__ off, int* __restrict__ total) {
+// exclusive scan of n_win counts (one CTA): offsets and the total
+__global__ void __launch_bounds__(kScanThreads) k_pmm_scan(int n_win, const int* __restrict__ cnt,
+                                                           int* __restrict__ off, int* __restrict__ total) {
   __shared__ uint32_t tmp[32];
   const int per = (n_win + kScanThreads - 1) / kScanThreads;
   const int b = threadIdx.x * per, e = min(n_win, b + per);
@@ -701,9 +725,11 @@ gs_status gs_pmm_match(gs_pmm* m, const float* feat_query, const float* feat_ren
   const float s_exp = 1.4426950408889634f * inv_tau;  // exp(x / tau) = exp2(x log2(e) / tau)
   const float s_two = 2.0f * inv_tau;
   PMM_CUDA(cudaMemsetAsync(m->counters, 0, 4 * sizeof(int), st));
-  const int cb = (n * 32 + 255) / 256;
-  k_pmm_codes<<<cb, 256, 0, st>>>(feat_query, m->H, m->W, m->Wc, n, m->codes_q);
-  k_pmm_codes<<<cb, 256, 0, st>>>(feat_render, m->H, m->W, m->Wc, n, m->codes_r);
+  const dim3 cgrid((unsigned)((m->Wc + 31) / 32), (unsigned)m->Hc);
+  unsigned short* cq16 = reinterpret_cast<unsigned short*>(m->codes_q);
+  unsigned short* cr16 = reinterpret_cast<unsigned short*>(m->codes_r);
+  k_pmm_codes<<<cgrid, 1024, 0, st>>>(feat_query, m->H, m->W, m->Wc, n, cq16);
+  k_pmm_codes<<<cgrid, 1024, 0, st>>>(feat_render, m->H, m->W, m->Wc, n, cr16);
   PMM_CUDA(cudaGetLastError());
   static bool attr = false;
   if (!attr) {
@@ -716,19 +742,26 @@ gs_status gs_pmm_match(gs_pmm* m, const float* feat_query, const float* feat_ren
   const uint4* cq = reinterpret_cast<const uint4*>(m->codes_q);
   const uint4* cr = reinterpret_cast<const uint4*>(m->codes_r);
   int* err = m->counters + 3;
-  k_pmm_tiles<1><<<grid, kThreads, kTileSmemBytes, st>>>(cq, cr, n, nb, s_exp, s_two, nullptr, nullptr, m->prow_v,
-                                                         nullptr, m->pcol_v, nullptr, err);
-  PMM_CUDA(cudaGetLastError());
   const int rg = (n + 255) / 256;
+  // pass 1: row and column exp sums, then the log-sum-exps
+  k_pmm_tiles<1><<<grid, kTileThreads, kTileSmemBytes, st>>>(cq, cr, n, nb, s_exp, s_two, nullptr, m->prow_v,
+                                                             nullptr, m->pcol_v, err);
+  PMM_CUDA(cudaGetLastError());
   k_pmm_lse<<<rg, 256, 0, st>>>(m->prow_v, nb, n, inv_tau, m->lse_row);
   k_pmm_lse<<<rg, 256, 0, st>>>(m->pcol_v, nb, n, inv_tau, m->lse_col);
-  k_pmm_tiles<2><<<grid, kThreads, kTileSmemBytes, st>>>(cq, cr, n, nb, s_exp, s_two, m->lse_row, m->lse_col,
-                                                         m->prow_v, m->prow_i, m->pcol_v, m->pcol_i, err);
-  PMM_CUDA(cudaGetLastError());
+  // pass 2: row argmax of log P_M, then (operands swapped) its column argmax
+  k_pmm_tiles<2><<<grid, kTileThreads, kTileSmemBytes, st>>>(cq, cr, n, nb, s_exp, s_two, m->lse_col, m->prow_v,
+                                                             m->prow_i, nullptr, err);
   k_pmm_best<<<rg, 256, 0, st>>>(m->prow_v, m->prow_i, nb, n, m->row_best);
-  k_pmm_best<<<rg, 256, 0, st>>>(m->pcol_v, m->pcol_i, nb, n, m->col_best);
-  k_pmm_mnn<<<1, kScanThreads, 0, st>>>(n, m->row_best, m->col_best, m->codes_q, m->codes_r, m->lse_row, m->lse_col,
-                                        s_two, m->coarse, m->coarse_p, m->counters);
+  k_pmm_tiles<2><<<grid, kTileThreads, kTileSmemBytes, st>>>(cr, cq, n, nb, s_exp, s_two, m->lse_row, m->prow_v,
+                                                             m->prow_i, nullptr, err);
+  k_pmm_best<<<rg, 256, 0, st>>>(m->prow_v, m->prow_i, nb, n, m->col_best);
+  PMM_CUDA(cudaGetLastError());
+  // mutual nearest neighbours in ascending query order
+  k_pmm_mnn<<<rg, 256, 0, st>>>(n, m->row_best, m->col_best, m->codes_q, m->codes_r, m->lse_row, m->lse_col, s_two,
+                                m->win_cnt, m->slot_p);
+  k_pmm_scan<<<1, kScanThreads, 0, st>>>(n, m->win_cnt, m->win_off, m->counters);
+  k_pmm_mnn_scatter<<<rg, 256, 0, st>>>(n, m->row_best, m->win_cnt, m->win_off, m->slot_p, m->coarse, m->coarse_p);
   PMM_CUDA(cudaGetLastError());
   PMM_CUDA(cudaMemcpyAsync(m->host, m->counters, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
   PMM_CUDA(cudaStreamSynchronize(st));
@@ -737,7 +770,7 @@ gs_status gs_pmm_match(gs_pmm* m, const float* feat_query, const float* feat_ren
   if (n_coarse > 0) {
     k_pmm_fine<<<n_coarse, kWin, 0, st>>>(feat_query, feat_render, m->H, m->W, m->Wc, m->coarse, inv_tau, s_exp,
                                           s_two, m->slot_r, m->slot_p, m->win_cnt);
-    k_pmm_scan_windows<<<1, kScanThreads, 0, st>>>(n_coarse, m->win_cnt, m->win_off, m->counters + 1);
+    k_pmm_scan<<<1, kScanThreads, 0, st>>>(n_coarse, m->win_cnt, m->win_off, m->counters + 1);
     k_pmm_fine_scatter<<<n_coarse, kWin, 0, st>>>(m->W, m->Wc, m->coarse, m->slot_r, m->slot_p, m->win_off, m->fine,
                                                   m->fine_p);
     PMM_CUDA(cudaGetLastError());

@@ -347,13 +347,24 @@ __global__ void __launch_bounds__(kTileThreads) k_pmm_tiles(const uint4* __restr
           lc[4 * q + 3] = x.w;
         }
         const int col0 = cb_ * kTile + l0;
-        const int lim = interior ? 16 : (row_ok ? min(16, n - col0) : 0);
+        if (interior) {
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const float rv = fmaf(v[k], s_two, -lc[k]);
-          if (k < lim && rv > best) {  // ascending columns: the first maximum stays
-            best = rv;
-            bidx = col0 + k;
+          for (int k = 0; k < 16; ++k) {
+            const float rv = fmaf(v[k], s_two, -lc[k]);
+            if (rv > best) {  // ascending columns: the first maximum stays
+              best = rv;
+              bidx = col0 + k;
+            }
+          }
+        } else {
+          const int lim = row_ok ? min(16, n - col0) : 0;
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            const float rv = fmaf(v[k], s_two, -lc[k]);
+            if (k < lim && rv > best) {
+              best = rv;
+              bidx = col0 + k;
+            }
           }
         }
       }
@@ -391,6 +402,7 @@ __global__ void k_pmm_lse(const float* __restrict__ part, int nb, int n, float i
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float s = 0.0f;
+#pragma unroll 8
   for (int b = 0; b < nb; ++b) s += part[(size_t)b * n + i];
   lse[i] = inv_tau + logf(s);  // log sum exp(M / tau) = 1 / tau + log sum exp((M - 1) / tau)
 }
@@ -401,6 +413,7 @@ __global__ void k_pmm_best(const float* __restrict__ pv, const int* __restrict__
   if (i >= n) return;
   float bv = -INFINITY;
   int bi = 0x7fffffff;
+#pragma unroll 8
   for (int b = 0; b < nb; ++b) {
     const float v = pv[(size_t)b * n + i];
     const int x = pi[(size_t)b * n + i];
@@ -419,30 +432,6 @@ __device__ __forceinline__ float dot_codes(const __nv_bfloat16* a, const __nv_bf
   return s;
 }
 
-// exclusive scan of one value per thread over kScanThreads threads
-__device__ uint32_t scan_block(uint32_t v, uint32_t* tmp) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint32_t incl = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
-  }
-  if (lane == 31) tmp[wid] = incl;
-  __syncthreads();
-  if (wid == 0) {
-    const uint32_t x = tmp[lane];
-    uint32_t y = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t t = __shfl_up_sync(0xffffffffu, y, o);
-      if (lane >= o) y += t;
-    }
-    tmp[lane] = y - x;
-  }
-  __syncthreads();
-  return tmp[wid] + incl - v;
-}
 
 // mutual nearest neighbours: flag[i] = 1 when query cell i and rendered cell
 // row_best[i] are each other's argmax, with P_M of the pair (an argmax left at
@@ -506,20 +495,25 @@ __global__ void __launch_bounds__(kWin) k_pmm_fine(const float* __restrict__ Fq,
     }
   }
   __syncthreads();
-  float rs = 0.0f;  // row a: similarities and exp sum
-  for (int b = 0; b < kWin; ++b) {
-    const float4* rb4 = reinterpret_cast<const float4*>(ur[b]);
-    float m = 0.0f;
+  float rs = 0.0f;  // row a: similarities and exp sum, four columns at a time (independent chains)
+  for (int b = 0; b < kWin; b += 4) {
+    float m[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int q = 0; q < kC / 4; ++q) {
-      const float4 x = rb4[q];
-      m = fmaf(uq[4 * q], x.x, m);
-      m = fmaf(uq[4 * q + 1], x.y, m);
-      m = fmaf(uq[4 * q + 2], x.z, m);
-      m = fmaf(uq[4 * q + 3], x.w, m);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float4 x = reinterpret_cast<const float4*>(ur[b + u])[q];
+        m[u] = fmaf(uq[4 * q], x.x, m[u]);
+        m[u] = fmaf(uq[4 * q + 1], x.y, m[u]);
+        m[u] = fmaf(uq[4 * q + 2], x.z, m[u]);
+        m[u] = fmaf(uq[4 * q + 3], x.w, m[u]);
+      }
     }
-    Mf[a][b] = m;
-    rs += exp2f((m - 1.0f) * s_exp);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      Mf[a][b + u] = m[u];
+      rs += exp2f((m[u] - 1.0f) * s_exp);
+    }
   }
   lr[a] = inv_tau + logf(rs);
   __syncthreads();
@@ -564,17 +558,40 @@ __global__ void __launch_bounds__(kWin) k_pmm_fine(const float* __restrict__ Fq,
 // exclusive scan of n_win counts (one CTA): offsets and the total
 __global__ void __launch_bounds__(kScanThreads) k_pmm_scan(int n_win, const int* __restrict__ cnt,
                                                            int* __restrict__ off, int* __restrict__ total) {
-  __shared__ uint32_t tmp[32];
-  const int per = (n_win + kScanThreads - 1) / kScanThreads;
-  const int b = threadIdx.x * per, e = min(n_win, b + per);
-  uint32_t c = 0;
-  for (int k = b; k < e; ++k) c += (uint32_t)cnt[k];
-  uint32_t pos = scan_block(c, tmp);
-  for (int k = b; k < e; ++k) {
-    off[k] = (int)pos;
-    pos += (uint32_t)cnt[k];
+  __shared__ uint32_t wsum[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int per = (n_win + 31) / 32;  // a contiguous chunk per warp, read in coalesced steps of 32
+  const int b = w * per, e = min(n_win, b + per);
+  uint32_t s = 0;
+  for (int k = b + lane; k < e; k += 32) s += (uint32_t)cnt[k];
+  s = __reduce_add_sync(0xffffffffu, s);
+  if (lane == 0) wsum[w] = s;
+  __syncthreads();
+  if (w == 0) {
+    const uint32_t x = wsum[lane];
+    uint32_t y = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) y += t;
+    }
+    wsum[lane] = y - x;
+    if (lane == 31) *total = (int)y;
   }
-  if (threadIdx.x == kScanThreads - 1) *total = (int)pos;
+  __syncthreads();
+  uint32_t run = wsum[w];
+  for (int k0 = b; k0 < e; k0 += 32) {
+    const int k = k0 + lane;
+    const uint32_t c = k < e ? (uint32_t)cnt[k] : 0u;
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (k < e) off[k] = (int)(run + incl - c);
+    run += __shfl_sync(0xffffffffu, incl, 31);
+  }
 }
 
 // fine matches of window k at its offset, in query-pixel order (64 threads)

@@ -341,6 +341,7 @@ typedef struct {
   const float* rec_f;
   int geom64, nd;
   double tie_rel;
+  int64_t mean_gid;  /* >= 0: tangents along this Gaussian's mean only */
 } prep_ctx;
 
 /* colour from SH at dir = normalize(mean - camera centre) [R: +0.5, clamp >= 0] */
@@ -397,6 +398,12 @@ static void prep_gauss(const prep_ctx* cx, int64_t g, gprep* o) {
   double dd[6][3]; /* tangent of (mu - c_w) = R^T rho */
   for (int k = 0; k < 6; ++k)
     for (int a = 0; a < 3; ++a) dd[k][a] = (k < 3) ? R[k][a] : 0.0;
+  /* mean tangents (Algorithm 1): d (mu - c_w) / d mu_k = e_k for the chosen Gaussian, 0 for the rest */
+  const int mean_mode = cx->mean_gid >= 0;
+  const int own = mean_mode && cx->mean_gid == g;
+  if (mean_mode)
+    for (int k = 0; k < 6; ++k)
+      for (int a = 0; a < 3; ++a) dd[k][a] = (own && k < 3 && a == k) ? 1.0 : 0.0;
 
   if (!cx->geom64) {
     const float* of = cx->rec_f + ORC_NF * g;
@@ -417,7 +424,9 @@ static void prep_gauss(const prep_ctx* cx, int64_t g, gprep* o) {
   for (int a = 0; a < 3; ++a) p[a] = R[a][0] * mu[0] + R[a][1] * mu[1] + R[a][2] * mu[2] + t[a];
   double dp[6][3];
   for (int k = 0; k < 6; ++k) {
-    if (k < 3) {
+    if (mean_mode) {  /* d p / d mu_k = R e_k for the chosen Gaussian */
+      for (int a = 0; a < 3; ++a) dp[k][a] = (own && k < 3) ? R[a][k] : 0.0;
+    } else if (k < 3) {
       for (int a = 0; a < 3; ++a) dp[k][a] = (a == k) ? 1.0 : 0.0;
     } else {
       double w[3] = {0, 0, 0};
@@ -453,7 +462,7 @@ static void prep_gauss(const prep_ctx* cx, int64_t g, gprep* o) {
   mat3_mul(tmp, RT, Sc);
   double dSc[6][3][3];
   for (int k = 0; k < 6; ++k) {
-    if (k < 3) {
+    if (k < 3 || mean_mode) {  /* the covariance does not depend on the mean */
       memset(dSc[k], 0, sizeof(dSc[k]));
       continue;
     }
@@ -712,7 +721,12 @@ static void* render_worker(void* arg) {
       for (int64_t j = 0; j < r.n_eval; ++j) flags |= jb->prep[jb->vis[list[j]]].tie;
       uint64_t h = r.hash;
       for (int64_t j = 0; j < r.n_eval; ++j) h = mix64(h, jb->prep[jb->vis[list[j]]].clamp_bits);
-      if (op->target_rgb) {
+      if (op->mean_tangent_gid >= 0) {  /* Algorithm 1: sum of the rendered colours */
+        for (int ch = 0; ch < 3; ++ch) {
+          closs += r.rgb[ch][0];
+          for (int k = 1; k < jb->nd; ++k) cgrad[k - 1] += r.rgb[ch][k];
+        }
+      } else if (op->target_rgb) {
         const double wpx = op->pixel_weight ? (double)op->pixel_weight[lin] : 1.0;
         for (int ch = 0; ch < 3; ++ch) {
           const double res = r.rgb[ch][0] - (double)op->target_rgb[(int64_t)ch * W * H + lin];
@@ -781,7 +795,8 @@ static int render_impl(const orc_scene* sc, const orc_camera* cam, const double*
   int64_t n_vis = 0;
   for (int64_t i = 0; i < n; ++i) vis[i] = (rec_i[ORC_NI * i] == ORC_VISIBLE) ? (int32_t)n_vis++ : -1;
   gprep* prep = (gprep*)malloc(sizeof(gprep) * (size_t)(n_vis > 0 ? n_vis : 1));
-  prep_ctx pc = {sc, cam, T_cw, rec_i, rec_f, op->geom64, op->want_grad ? ORC_ND : 1, op->tie_rel};
+  prep_ctx pc = {sc, cam, T_cw, rec_i, rec_f, op->geom64, op->want_grad ? ORC_ND : 1, op->tie_rel,
+                 op->mean_tangent_gid};
   for (int64_t i = 0; i < n; ++i)
     if (vis[i] >= 0) prep_gauss(&pc, i, prep + vis[i]);
 

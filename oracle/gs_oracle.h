@@ -72,6 +72,9 @@ typedef struct {
   double depth_weight;      /* lambda_d of the loss */
   double tie_rel;           /* relative margin for near-tie flags (alpha floor, cap) */
   double tie_rel_T;         /* relative margin for the transmittance cutoff */
+  int64_t mean_tangent_gid; /* >= 0: tangents 1..3 are d/d(mean x, y, z) of this Gaussian alone, and
+                               loss / grad are sum_px,c C and its tangents (Algorithm 1's RGB.sum());
+                               -1: pose tangents and the L1 loss of the targets */
 } orc_opts;
 
 typedef struct {

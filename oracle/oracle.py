@@ -70,7 +70,8 @@ class _Opts(ctypes.Structure):
                 ("pixels", ctypes.c_void_p), ("n_pixels", ctypes.c_int64),
                 ("target_rgb", ctypes.c_void_p), ("target_depth", ctypes.c_void_p),
                 ("pixel_weight", ctypes.c_void_p), ("depth_weight", ctypes.c_double),
-                ("tie_rel", ctypes.c_double), ("tie_rel_T", ctypes.c_double)]
+                ("tie_rel", ctypes.c_double), ("tie_rel_T", ctypes.c_double),
+                ("mean_tangent_gid", ctypes.c_int64)]
 
 
 class _Out(ctypes.Structure):
@@ -192,7 +193,7 @@ class OracleScene:
 
 def render(scene, cam, T, *, geom64=False, want_grad=False, n_threads=1, pixels=None,
            target_rgb=None, target_depth=None, pixel_weight=None, depth_weight=0.1,
-           tie_rel=1e-4, tie_rel_T=2e-4, brute=False, want_feats=True):
+           tie_rel=1e-4, tie_rel_T=2e-4, brute=False, want_feats=True, mean_tangent_gid=-1):
     """Full oracle render (Sec. 3.1 alpha blending; Algorithm 1 projection).
 
     Returns a dict of per-pixel arrays in the order of ``pixels`` (or row-major
@@ -208,7 +209,7 @@ def render(scene, cam, T, *, geom64=False, want_grad=False, n_threads=1, pixels=
     tdep = None if target_depth is None else _f32(target_depth).reshape(H, W)
     pw = None if pixel_weight is None else _f32(pixel_weight).reshape(H, W)
     opts = _Opts(int(geom64), int(want_grad), int(n_threads), _p(pix), npx, _p(trgb), _p(tdep), _p(pw),
-                 float(depth_weight), float(tie_rel), float(tie_rel_T))
+                 float(depth_weight), float(tie_rel), float(tie_rel_T), int(mean_tangent_gid))
     res = {
         "rgb": np.zeros((npx, 3), np.float64),
         "depth": np.zeros(npx, np.float64),
@@ -237,6 +238,63 @@ def render(scene, cam, T, *, geom64=False, want_grad=False, n_threads=1, pixels=
     res["signature"] = int(res["signature"][0])
     res["n_pairs"] = int(res["n_pairs"][0])
     return res
+
+
+def mean_gradient(scene, cam, T, gid: int, pixels=None, n_threads=1) -> dict:
+    """Algorithm 1's RGB.sum().backward() for one Gaussian: the gradient of the
+    sum of the rendered colours with respect to the mean of Gaussian `gid`,
+    by forward differentiation in binary64 along its three mean coordinates
+    (every other Gaussian held fixed). `pixels` may restrict the sum to a
+    superset of the pixels the Gaussian can touch (its tile rectangle).
+    Returns dict: grad (3), sum (of the colours over the pixels), flags (per
+    pixel), signature."""
+    r = render(scene, cam, T, geom64=True, want_grad=True, pixels=pixels, n_threads=n_threads,
+               mean_tangent_gid=int(gid), want_feats=False)
+    return {"grad": np.asarray(r["grad"][:3], np.float64), "sum": r["loss"], "flags": r["flags"],
+            "signature": r["signature"]}
+
+
+def visibility(scene, cam, T, n_threads=1, gids=None, grad_tie=1e-9, edge_tie=1e-6) -> dict:
+    """Algorithm 1 (render-gradient visibility check with projection filtering).
+
+    M^r[j] = |grad_mean_j sum RGB| > 0 (mean_gradient over the pixels of the
+    tiles Gaussian j covers), M^i[j] = the projection (u, v) = K (p / z) lies in
+    [0, W) x [0, H), M = M^i and M^r. Evaluated for every Gaussian, or for
+    `gids`. Returns dict over those Gaussians: gids, grad (n, 3), M_r, M_i, M,
+    uv (n, 2), flag (a decision within rounding: a gradient below grad_tie
+    relative to the largest, a zero gradient with a near-tie pixel in its
+    rectangle, or (u, v) within edge_tie of an image edge)."""
+    cov = cov3d_f32(scene["scales"], scene["quats"])
+    ri, rf = project_f32(scene["means"], cov, cam, T)
+    W, H = int(cam["width"]), int(cam["height"])
+    n = ri.shape[0]
+    gids = np.arange(n) if gids is None else np.asarray(gids, np.int64)
+    Tm = np.asarray(T, np.float64)
+    p = np.asarray(scene["means"], np.float64)[gids] @ Tm[:3, :3].T + Tm[:3, 3]
+    fx, fy, cx, cy = (float(np.float32(cam[k])) for k in ("fx", "fy", "cx", "cy"))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        u = fx * p[:, 0] / p[:, 2] + cx
+        v = fy * p[:, 1] / p[:, 2] + cy
+    M_i = (u >= 0) & (u < W) & (v >= 0) & (v < H)
+    grad = np.zeros((len(gids), 3))
+    tie_px = np.zeros(len(gids), bool)
+    for k, g in enumerate(gids):
+        if ri[g, I_STATUS] != VISIBLE:
+            continue
+        x0, x1, y0, y1 = (int(ri[g, c]) for c in (I_X0, I_X1, I_Y0, I_Y1))
+        ys, xs = np.mgrid[y0 * TILE:min(H, (y1 + 1) * TILE), x0 * TILE:min(W, (x1 + 1) * TILE)]
+        pix = (ys * W + xs).reshape(-1).astype(np.int64)
+        r = mean_gradient(scene, cam, T, int(g), pixels=pix, n_threads=n_threads)
+        grad[k] = r["grad"]
+        tie_px[k] = bool((r["flags"] & TIE_IMAGE).any())
+    norm = np.linalg.norm(grad, axis=1)
+    M_r = norm > 0
+    big = norm.max() if len(norm) else 0.0
+    edge = (np.abs(u) <= edge_tie * W) | (np.abs(u - W) <= edge_tie * W) | (np.abs(v) <= edge_tie * H) | \
+        (np.abs(v - H) <= edge_tie * H)
+    flag = ((norm > 0) & (norm <= grad_tie * big)) | ((norm == 0) & tie_px) | edge
+    return {"gids": gids, "grad": grad, "M_r": M_r, "M_i": M_i, "M": M_r & M_i,
+            "uv": np.stack([u, v], 1), "flag": flag}
 
 
 def se3_exp_left(xi, T) -> np.ndarray:

@@ -300,6 +300,35 @@ gs_status gs_scene_kernel_times(gs_scene* scene, double* total_ms, int64_t* laun
  * pointer. Errors: INVALID_ARG, CUDA. */
 gs_status gs_scene_blend_count(gs_scene* scene, void* stream, int64_t* blended);
 
+/* Render-gradient visibility check with projection filtering (Sec. 3.2,
+ * Algorithm 1) of every Gaussian of the scene from one pose.
+ *
+ * M^r[j] = the gradient of the summed rendered colours (sum over pixels and
+ * channels of RGB, Sec. 3.1 rasterisation) with respect to Gaussian j's mean
+ * is non-zero, i.e. j contributed to some pixel; M^i[j] = its projected centre
+ * (U, V) = K (R X + t) / z lies in [0, W) x [0, H) (no depth test);
+ * M = M^r and M^i. The gradient comes from one forward render, one reverse
+ * pass over the same tile lists and a chain rule per Gaussian; it is fp32 and
+ * its summation order varies between calls (the zero / non-zero test does
+ * not, up to rounding of sums that cancel to within fp32 precision).
+ *
+ * Device outputs (n = the scene's Gaussian count):
+ *   mask         required, n bytes: bit 0 = M, bit 1 = M^r, bit 2 = M^i
+ *   uv           NULL or n x 2 floats (8-byte aligned): (U, V) of every Gaussian
+ *   grad_mean    NULL or n x 3 floats: d sum(RGB) / d mean (0 for Gaussians
+ *                that reach no tile)
+ *   visible_ids  NULL or capacity n int32 (4-byte aligned): the Gaussians with
+ *                M set, ascending -- the selection (U', V') = (U, V)[:, M]
+ *   visible_uv   NULL or capacity n x 2 floats (8-byte aligned): their (U, V)
+ * n_visible: host pointer or NULL, receives the number of Gaussians with M.
+ * A streamed scene (partitions uploaded on demand) is made fully resident
+ * first: the in-image test covers every Gaussian. Synchronous (waits for
+ * `stream`). Errors: INVALID_ARG (NULL cam, pose or mask, misaligned array,
+ * camera out of range, non-finite pose), OOM, CAPACITY, CUDA. */
+gs_status gs_visibility(gs_scene* scene, const gs_camera* cam, const gs_pose* pose, uint8_t* mask, float* uv,
+                        float* grad_mean, int32_t* visible_ids, float* visible_uv, int64_t* n_visible,
+                        void* stream);
+
 /* gs_render_noalloc -- the forward render of gs_render that allocates
  * nothing (the paper has no counterpart).
  *

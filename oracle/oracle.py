@@ -254,7 +254,7 @@ def mean_gradient(scene, cam, T, gid: int, pixels=None, n_threads=1) -> dict:
             "signature": r["signature"]}
 
 
-def visibility(scene, cam, T, n_threads=1, gids=None, grad_tie=1e-9, edge_tie=1e-6) -> dict:
+def visibility(scene, cam, T, n_threads=1, gids=None, grad_tie=1e-9, edge_tie=1e-6, want_grad=True) -> dict:
     """Algorithm 1 (render-gradient visibility check with projection filtering).
 
     M^r[j] = |grad_mean_j sum RGB| > 0 (mean_gradient over the pixels of the
@@ -263,7 +263,8 @@ def visibility(scene, cam, T, n_threads=1, gids=None, grad_tie=1e-9, edge_tie=1e
     `gids`. Returns dict over those Gaussians: gids, grad (n, 3), M_r, M_i, M,
     uv (n, 2), flag (a decision within rounding: a gradient below grad_tie
     relative to the largest, a zero gradient with a near-tie pixel in its
-    rectangle, or (u, v) within edge_tie of an image edge)."""
+    rectangle, or (u, v) within edge_tie of an image edge). want_grad=False
+    evaluates the projection part only (grad, M_r and M are then all zero)."""
     cov = cov3d_f32(scene["scales"], scene["quats"])
     ri, rf = project_f32(scene["means"], cov, cam, T)
     W, H = int(cam["width"]), int(cam["height"])
@@ -279,7 +280,7 @@ def visibility(scene, cam, T, n_threads=1, gids=None, grad_tie=1e-9, edge_tie=1e
     grad = np.zeros((len(gids), 3))
     tie_px = np.zeros(len(gids), bool)
     for k, g in enumerate(gids):
-        if ri[g, I_STATUS] != VISIBLE:
+        if not want_grad or ri[g, I_STATUS] != VISIBLE:
             continue
         x0, x1, y0, y1 = (int(ri[g, c]) for c in (I_X0, I_X1, I_Y0, I_Y1))
         ys, xs = np.mgrid[y0 * TILE:min(H, (y1 + 1) * TILE), x0 * TILE:min(W, (x1 + 1) * TILE)]

@@ -84,6 +84,16 @@ struct GradIn {
 
 constexpr int kResultStride = 8;  // (loss, grad rho, grad phi, pad) per view
 
+// Outputs of a visibility-check call (device pointers; uv is never NULL: the
+// caller's array or the scene's scratch).
+struct VisOut {
+  uint8_t* mask;
+  float2* uv;
+  float* grad;
+  int32_t* vis_gid;
+  float2* vis_uv;
+};
+
 // A captured batch: replayed while everything but the poses is unchanged.
 struct GraphCache {
   bool valid = false;
@@ -141,6 +151,9 @@ struct gs_scene {
   // loss targets uploaded from host memory (gs_render_pose_grad_host) on a side
   // stream that overlaps the projection and binning kernels
   DevBuf targets;
+  // visibility check: final transmittance and last index of its forward
+  // render, per-record accumulators, (U, V) scratch, compaction counters
+  DevBuf vis_T, vis_last, vis_acc, vis_uv, vis_blk;
   cudaStream_t copy_st = nullptr;
   cudaEvent_t ev_call = nullptr, ev_targets = nullptr;
   // kernel timing: one set of GS_KERNEL_COUNT + 1 events per timed call
@@ -337,19 +350,25 @@ void fill_table(const gs_scene* s, const std::vector<View>& hv, const std::vecto
 }
 
 gs_status enqueue(gs_scene* s, const std::vector<View>& hv, const std::vector<int4>& ranges, uint64_t n_tiles,
-                  const GradIn* g, cudaStream_t st, const char* upload_src, cudaEvent_t targets_ready = nullptr) {
+                  const GradIn* g, cudaStream_t st, const char* upload_src, cudaEvent_t targets_ready = nullptr,
+                  const VisOut* vis = nullptr) {
   const int nv = (int)hv.size();
+  const bool jac = g != nullptr || vis != nullptr;  // per-record pose Jacobian
   GS_TRY(grow_tiles(s, n_tiles));
   GS_TRY(ensure(s->views, table_bytes(s, nv)));
   if (g && !g->result) GS_TRY(ensure(s->result, (size_t)nv * kResultStride * sizeof(double)));
   if (s->rec_cap == 0) {
     const uint64_t guess = std::max<uint64_t>(1u << 16, (uint64_t)s->n * nv / 4);
-    GS_TRY(grow_records(s, guess, g != nullptr));
+    GS_TRY(grow_records(s, guess, jac));
     GS_TRY(grow_pairs(s, guess * 8));
   } else {
-    GS_TRY(grow_records(s, s->rec_cap, g != nullptr));
+    GS_TRY(grow_records(s, s->rec_cap, jac));
   }
   if (s->pair_cap == 0) GS_TRY(grow_pairs(s, (uint64_t)s->rec_cap * 8));
+  if (vis) {
+    GS_TRY(ensure(s->vis_acc, (size_t)s->rec_cap * kVisAcc * sizeof(float)));
+    GS_TRY(ensure(s->vis_blk, ((size_t)s->n / kVisBlock + 1) * sizeof(uint32_t)));
+  }
   View* dviews = reinterpret_cast<View*>(static_cast<char*>(s->views.p) + table_ranges_bytes(s));
   if (upload_src) {
     GS_CUDA(cudaMemcpyAsync(s->views.p, upload_src, table_bytes(s, nv), cudaMemcpyHostToDevice, st));
@@ -383,7 +402,7 @@ gs_status enqueue(gs_scene* s, const std::vector<View>& hv, const std::vector<in
   GS_CUDA(mark(0));
   GS_CUDA(launch_project(sc, dviews, nv, w, s->sm_count * 8, st));
   GS_CUDA(mark(1));
-  GS_CUDA(launch_shade(sc, dviews, w, g != nullptr, s->sm_count * 8, st));
+  GS_CUDA(launch_shade(sc, dviews, w, jac, s->sm_count * 8, st));
   GS_CUDA(mark(2));
   GS_CUDA(launch_scan_tiles(w, st));
   GS_CUDA(mark(3));
@@ -402,6 +421,16 @@ gs_status enqueue(gs_scene* s, const std::vector<View>& hv, const std::vector<in
     double* res = g->result ? g->result : w.result;
     if (targets_ready) GS_CUDA(cudaStreamWaitEvent(st, targets_ready, 0));  // only this pass reads the targets
     GS_CUDA(launch_composite_tangent(sc, dviews, nv, w, res, s->sm_count * composite_blocks_per_sm(0, true), st));
+  }
+  if (vis) {
+    // Algorithm 1: reverse pass of sum RGB, then the per-Gaussian tests
+    float* acc = dp<float>(s->vis_acc);
+    GS_CUDA(cudaMemsetAsync(acc, 0, (size_t)s->rec_cap * kVisAcc * sizeof(float), st));
+    GS_CUDA(launch_vis_backward(dviews, nv, w, acc, s->sm_count * 4, st));
+    GS_CUDA(launch_vis_inimage(sc, dviews, vis->mask, vis->uv, vis->grad, s->sm_count * 8, st));
+    GS_CUDA(launch_vis_chain(dviews, w, acc, vis->mask, vis->grad, s->sm_count * 8, st));
+    GS_CUDA(launch_vis_compact(vis->mask, vis->uv, (int)s->n, dp<uint32_t>(s->vis_blk), vis->vis_gid, vis->vis_uv,
+                               st));
   }
   GS_CUDA(mark(6));
   if (timed) s->ev_pending.push_back({std::move(ev), GS_KERNEL_COUNT});
@@ -485,6 +514,25 @@ bool part_in_view(const Part& P, const View& V) {
   return !(out_near || out_l || out_r || out_t || out_b);
 }
 
+// Upload a streamed partition that is not on the device yet (no-op otherwise).
+gs_status make_resident(gs_scene* s, Part& P, cudaStream_t st) {
+  if (!s->streaming || P.resident || P.end <= P.begin) return GS_OK;
+  const size_t b = (size_t)P.begin, c = (size_t)(P.end - P.begin);
+  GS_CUDA(cudaMemcpyAsync(dp<float4>(s->pos) + b, s->h_pos + b, c * sizeof(float4), cudaMemcpyHostToDevice, st));
+  GS_CUDA(cudaMemcpyAsync(dp<float4>(s->cov) + 2 * b, s->h_cov + 2 * b, 2 * c * sizeof(float4),
+                          cudaMemcpyHostToDevice, st));
+  GS_CUDA(cudaMemcpyAsync(dp<float4>(s->sh) + b * s->nsh4, s->h_sh + b * s->nsh4, c * s->nsh4 * sizeof(float4),
+                          cudaMemcpyHostToDevice, st));
+  s->h2d_bytes += (int64_t)(c * (3 + s->nsh4) * sizeof(float4));
+  if (s->feat_dim) {
+    GS_CUDA(cudaMemcpyAsync(dp<uint4>(s->feat) + 4 * b, s->h_feat + 4 * b, 4 * c * sizeof(uint4),
+                            cudaMemcpyHostToDevice, st));
+    s->h2d_bytes += (int64_t)(4 * c * sizeof(uint4));
+  }
+  P.resident = true;
+  return GS_OK;
+}
+
 // Partitions in view of any view of the call: uploads the non-resident ones
 // (streaming scenes) on the stream and returns the index ranges the
 // projection walks, in ascending order (header entry first).
@@ -497,21 +545,7 @@ gs_status prepare_call(gs_scene* s, const std::vector<View>& hv, cudaStream_t st
     for (const View& V : hv) need = need || part_in_view(P, V);
     if (!need) continue;
     ++active;
-    if (s->streaming && !P.resident) {
-      const size_t b = (size_t)P.begin, c = (size_t)(P.end - P.begin);
-      GS_CUDA(cudaMemcpyAsync(dp<float4>(s->pos) + b, s->h_pos + b, c * sizeof(float4), cudaMemcpyHostToDevice, st));
-      GS_CUDA(cudaMemcpyAsync(dp<float4>(s->cov) + 2 * b, s->h_cov + 2 * b, 2 * c * sizeof(float4),
-                              cudaMemcpyHostToDevice, st));
-      GS_CUDA(cudaMemcpyAsync(dp<float4>(s->sh) + b * s->nsh4, s->h_sh + b * s->nsh4, c * s->nsh4 * sizeof(float4),
-                              cudaMemcpyHostToDevice, st));
-      s->h2d_bytes += (int64_t)(c * (3 + s->nsh4) * sizeof(float4));
-      if (s->feat_dim) {
-        GS_CUDA(cudaMemcpyAsync(dp<uint4>(s->feat) + 4 * b, s->h_feat + 4 * b, 4 * c * sizeof(uint4),
-                                cudaMemcpyHostToDevice, st));
-        s->h2d_bytes += (int64_t)(4 * c * sizeof(uint4));
-      }
-      P.resident = true;
-    }
+    GS_TRY(make_resident(s, P, st));
     if (ranges.size() > 1 && ranges.back().y == (int)P.begin) {
       ranges.back().y = (int)P.end;  // merge adjacent partitions
     } else {
@@ -552,11 +586,11 @@ gs_status read_counters(gs_scene* s, cudaStream_t st, Counters& c) {
 // With a pose gradient the (loss, gradient) of the first view are copied to
 // s->result_host in the same round trip as the counters.
 gs_status run_sync(gs_scene* s, const std::vector<View>& hv, uint64_t n_tiles, const GradIn* g, cudaStream_t st,
-                   cudaEvent_t targets_ready = nullptr) {
+                   cudaEvent_t targets_ready = nullptr, const VisOut* vis = nullptr) {
   std::vector<int4> ranges;
   GS_TRY(prepare_call(s, hv, st, ranges));
   for (int attempt = 0; attempt < 4; ++attempt) {
-    GS_TRY(enqueue(s, hv, ranges, n_tiles, g, st, nullptr, targets_ready));
+    GS_TRY(enqueue(s, hv, ranges, n_tiles, g, st, nullptr, targets_ready, vis));
     GS_CUDA(cudaMemcpyAsync(s->ctr_host, s->ctr.p, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     if (g && !g->result)
       GS_CUDA(cudaMemcpyAsync(s->result_host, s->result.p, 7 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -571,7 +605,7 @@ gs_status run_sync(gs_scene* s, const std::vector<View>& hv, uint64_t n_tiles, c
     if (c.overflow & 1u)  // pair count is incomplete when records overflowed
       need_pair = std::max<uint64_t>(need_pair, (uint64_t)s->pair_cap * (need_rec / std::max<uint32_t>(1, s->rec_cap) + 1));
     GS_CUDA(cudaStreamSynchronize(st));
-    GS_TRY(grow_records(s, need_rec, g != nullptr));
+    GS_TRY(grow_records(s, need_rec, g != nullptr || vis != nullptr));
     GS_TRY(grow_pairs(s, need_pair));
   }
   return fail(GS_ERR_CAPACITY, "workspace did not converge");
@@ -861,7 +895,7 @@ void gs_destroy_scene(gs_scene* s) {
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
   for (DevBuf* b : {&s->pos, &s->cov, &s->sh, &s->feat, &s->rec_a, &s->rec_b, &s->rec_c, &s->rec_m, &s->rec_j,
                     &s->tile_count, &s->tile_offset, &s->tile_cursor, &s->partials, &s->chunks, &s->pairs, &s->pairs_tmp,
-                    &s->ctr, &s->result, &s->views})
+                    &s->ctr, &s->result, &s->views, &s->vis_T, &s->vis_last, &s->vis_acc, &s->vis_uv, &s->vis_blk})
     release(*b);
   for (void* h : {(void*)s->h_pos, (void*)s->h_cov, (void*)s->h_sh, (void*)s->h_feat})
     if (h) cudaFreeHost(h);
@@ -1099,6 +1133,38 @@ gs_status gs_scene_kernel_times(gs_scene* s, double* total_ms, int64_t* launches
     s->kt_ms[k] = 0.0;
     s->kt_n[k] = 0;
   }
+  return GS_OK;
+}
+
+gs_status gs_visibility(gs_scene* s, const gs_camera* cam, const gs_pose* pose, uint8_t* mask, float* uv,
+                        float* grad_mean, int32_t* visible_ids, float* visible_uv, int64_t* n_visible,
+                        void* stream) {
+  g_err.clear();
+  GS_TRY(check_scene(s));
+  if (!cam || !pose || !mask) return fail(GS_ERR_INVALID_ARG, "cam, pose and mask are required");
+  for (const void* q : {(const void*)uv, (const void*)visible_uv})
+    if (reinterpret_cast<uintptr_t>(q) % 8) return fail(GS_ERR_INVALID_ARG, "uv arrays must be 8-byte aligned");
+  if (reinterpret_cast<uintptr_t>(grad_mean) % 4 || reinterpret_cast<uintptr_t>(visible_ids) % 4)
+    return fail(GS_ERR_INVALID_ARG, "grad_mean and visible_ids must be 4-byte aligned");
+  GS_TRY(set_device(s));
+  GS_TRY(check_cam(*cam));
+  const cudaStream_t st = (cudaStream_t)stream;
+  const size_t P = (size_t)cam->width * cam->height;
+  GS_TRY(ensure(s->vis_T, P * sizeof(float)));
+  GS_TRY(ensure(s->vis_last, P * sizeof(uint32_t)));
+  if (!uv) GS_TRY(ensure(s->vis_uv, (size_t)std::max<int64_t>(s->n, 1) * sizeof(float2)));
+  // the in-image test covers every Gaussian: a streamed scene becomes resident
+  for (Part& Pt : s->parts) GS_TRY(make_resident(s, Pt, st));
+  gs_outputs o{};
+  o.final_T = dp<float>(s->vis_T);
+  o.last_idx = dp<uint32_t>(s->vis_last);
+  std::vector<View> hv;
+  uint64_t n_tiles;
+  GS_TRY(build_views(s, 1, cam, pose, &o, nullptr, hv, n_tiles));
+  const VisOut vo{mask, uv ? reinterpret_cast<float2*>(uv) : dp<float2>(s->vis_uv), grad_mean, visible_ids,
+                  reinterpret_cast<float2*>(visible_uv)};
+  GS_TRY(run_sync(s, hv, n_tiles, nullptr, st, nullptr, &vo));
+  if (n_visible) *n_visible = (int64_t)s->ctr_host->vis_count;
   return GS_OK;
 }
 

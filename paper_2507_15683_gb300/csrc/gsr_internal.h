@@ -16,8 +16,10 @@ constexpr int kBatchF = 256;       // Gaussians staged per forward batch
 constexpr int kBatchT = 128;       // Gaussians staged per batch in tangent (pose-gradient) mode
 constexpr int kJacStride = 48;     // floats per record of the pose Jacobian (45 used)
 constexpr int kPartialStride = 8;  // doubles per tile partial (loss + 6 grad + pad)
-constexpr int kChunkTiles = 64;
-constexpr int kWarpSortMax = 256;  // longest tile list sorted by one warp (registers)    // tiles per first-level chunk of the fp64 pose reduction
+constexpr int kChunkTiles = 64;    // tiles per first-level chunk of the fp64 pose reduction
+constexpr int kWarpSortMax = 256;  // longest tile list sorted by one warp (registers)
+constexpr int kVisAcc = 8;         // floats per record of the visibility check's accumulator
+constexpr int kVisBlock = 2048;    // Gaussians per block of the visibility compaction
 constexpr int kRecRegions = 64;    // record-allocation counters (block index mod 64)
 
 // Per-view parameters (device copy built on the host for every call).
@@ -60,7 +62,7 @@ struct Counters {
   unsigned int fwd_queue;   // persistent tile queue of the forward render
   unsigned int tan_queue;   // persistent tile queue of the tangent (pose-gradient) render
   unsigned int error;       // device-side consistency failure
-  unsigned int pad;
+  unsigned int vis_count;   // Gaussians the visibility check keeps (M = M^r and M^i)
   unsigned long long blends;  // (pixel, Gaussian) pairs blended by the tangent pass
 };
 
@@ -124,6 +126,21 @@ cudaError_t launch_composite(const SceneDev& sc, const View* views, int n_views,
 // doubles per view (loss, dL/drho, dL/dphi)
 cudaError_t launch_composite_tangent(const SceneDev& sc, const View* views, int n_views, const Work& w,
                                      double* result, int grid, cudaStream_t st);
+
+// Algorithm 1 visibility check, after a forward render of one view that wrote
+// final_T and last_idx and a shading pass that wrote the pose Jacobian:
+// reverse pass into acc (kVisAcc floats per record, zeroed by the caller)
+cudaError_t launch_vis_backward(const View* views, int n_views, const Work& w, float* acc, int grid,
+                                cudaStream_t st);
+// every Gaussian: projected centre (U, V) and M^i (mask bit 2); zeroes grad
+cudaError_t launch_vis_inimage(const SceneDev& sc, const View* views, uint8_t* mask, float2* uv, float* grad,
+                               int grid, cudaStream_t st);
+// every record: mean gradient of sum RGB, M^r (bit 1), M (bit 0), count
+cudaError_t launch_vis_chain(const View* views, const Work& w, const float* acc, uint8_t* mask, float* grad,
+                             int grid, cudaStream_t st);
+// kept Gaussians in ascending order: ids and (U, V); blk holds n / kVisBlock + 1 counters
+cudaError_t launch_vis_compact(const uint8_t* mask, const float2* uv, int n, uint32_t* blk, int32_t* vis_gid,
+                               float2* vis_uv, cudaStream_t st);
 
 // occupancy-derived persistent grid sizes (per SM)
 int composite_blocks_per_sm(int feat_dim, bool tangent);

@@ -589,6 +589,178 @@ __global__ void __launch_bounds__(256, 3) k_shade(SceneDev sc, const View* __res
   }
 }
 
+// ---------------------------------------------------------------------------
+// Algorithm 1 (render-gradient visibility check), per-Gaussian parts.
+//
+// In-image test: (U, V) = K (p / z) with p = R X + t in float-float (the
+// blending centre's arithmetic), M^i = U in [0, W) and V in [0, H). No depth
+// test: the algorithm has none, and M^r is false behind the near plane.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_vis_inimage(SceneDev sc, const View* __restrict__ views,
+                                                     uint8_t* __restrict__ mask, float2* __restrict__ uv,
+                                                     float* __restrict__ grad) {
+  const View& V = views[0];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < sc.n; i += gridDim.x * blockDim.x) {
+    const float4 p4 = __ldg(sc.pos + i);
+    const ff fpx = ff_row(V.R, V.Rl, V.t[0], V.tl[0], p4.x, p4.y, p4.z);
+    const ff fpy = ff_row(V.R + 3, V.Rl + 3, V.t[1], V.tl[1], p4.x, p4.y, p4.z);
+    const ff fpz = ff_row(V.R + 6, V.Rl + 6, V.t[2], V.tl[2], p4.x, p4.y, p4.z);
+    const float u = ff_project(fpx, fpz, V.fx, V.cx).hi;
+    const float v = ff_project(fpy, fpz, V.fy, V.cy).hi;
+    const bool in = u >= 0.0f && u < (float)V.width && v >= 0.0f && v < (float)V.height;
+    mask[i] = in ? 4u : 0u;
+    uv[i] = make_float2(u, v);
+    if (grad) {
+      grad[3 * (size_t)i] = 0.0f;
+      grad[3 * (size_t)i + 1] = 0.0f;
+      grad[3 * (size_t)i + 2] = 0.0f;
+    }
+  }
+}
+
+// Chain rule from the reverse pass's per-record sums to the mean. Moving the
+// mean by d moves the camera-frame centre by R d exactly as a translation
+// rho = R d of the pose does, and the view direction by d exactly as that
+// translation does (d(X - c) = R^T rho), while the camera-frame covariance is
+// unchanged in both; so dL/dX = R^T dL/drho restricted to this Gaussian, and
+// dL/drho_k = -(P_k s_x + Q_k s_y + dA_k/2 s_xx + dB_k s_xy + dC_k/2 s_yy)
+//             + (dr_k + dg_k + db_k) s_w
+// with the record's pose Jacobian rows and accumulated sums. M^r = some
+// component of the gradient is non-zero; M = M^r and M^i (bit 2 set by
+// k_vis_inimage).
+__global__ void __launch_bounds__(256) k_vis_chain(const View* __restrict__ views, Work w,
+                                                   const float* __restrict__ acc, uint8_t* __restrict__ mask,
+                                                   float* __restrict__ grad) {
+  if (w.ctr->overflow) return;
+  const View& V = views[0];
+  const int lane = threadIdx.x & 31;
+  for (uint32_t base = blockIdx.x * blockDim.x; base < w.rec_cap; base += gridDim.x * blockDim.x) {
+    const uint32_t slot = base + threadIdx.x;
+    bool keep = false;
+    if (slot < w.rec_cap) {
+      const uint32_t reg = slot / w.rec_seg, loc = slot - reg * w.rec_seg;
+      if (loc < min(w.ctr->rec_region[reg], w.rec_seg)) {
+        const float4 a0 = reinterpret_cast<const float4*>(acc)[2 * (size_t)slot];
+        const float4 a1 = reinterpret_cast<const float4*>(acc)[2 * (size_t)slot + 1];
+        if (a0.x != 0.0f || a0.y != 0.0f || a0.z != 0.0f || a0.w != 0.0f || a1.x != 0.0f || a1.y != 0.0f) {
+          const float* J = w.rec_j + (size_t)slot * kJacStride;
+          float gr[3];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            const int o = 12 * (d >> 1) + (d & 1);  // direction d of pair d / 2
+            const float sp = J[o] * a0.x + J[o + 2] * a0.y + J[o + 4] * a0.z + J[o + 6] * a0.w + J[o + 8] * a1.x;
+            gr[d] = (J[36 + d] + J[40 + d] + J[44 + d]) * a1.y - sp;
+          }
+          float g[3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) g[a] = V.R[a] * gr[0] + V.R[3 + a] * gr[1] + V.R[6 + a] * gr[2];
+          const int i = __float_as_int(w.rec_b[slot].w);
+          if (grad) {
+            grad[3 * (size_t)i] = g[0];
+            grad[3 * (size_t)i + 1] = g[1];
+            grad[3 * (size_t)i + 2] = g[2];
+          }
+          if (g[0] != 0.0f || g[1] != 0.0f || g[2] != 0.0f) {
+            const uint8_t m = mask[i];
+            keep = (m & 4u) != 0;
+            mask[i] = (uint8_t)(m | 2u | (keep ? 1u : 0u));
+          }
+        }
+      }
+    }
+    const unsigned km = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0 && km) atomicAdd(&w.ctr->vis_count, (unsigned)__popc(km));
+  }
+}
+
+// Order-preserving compaction of the kept Gaussians: per-block counts, one
+// scan block, scatter (blocks of kVisBlock Gaussians, 256 threads).
+__global__ void __launch_bounds__(256) k_vis_count(const uint8_t* __restrict__ mask, int n,
+                                                   uint32_t* __restrict__ blk) {
+  __shared__ uint32_t s_w[8];
+  const int base = blockIdx.x * kVisBlock;
+  uint32_t c = 0;
+#pragma unroll
+  for (int k = 0; k < kVisBlock / 256; ++k) {
+    const int i = base + k * 256 + threadIdx.x;
+    c += (i < n && (mask[i] & 1u)) ? 1u : 0u;
+  }
+  c = __reduce_add_sync(0xffffffffu, c);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int k = 0; k < 8; ++k) t += s_w[k];
+    blk[blockIdx.x] = t;
+  }
+}
+
+// exclusive scan of nb counters in place (one block of 1024 threads)
+__global__ void __launch_bounds__(1024) k_vis_scan(uint32_t* __restrict__ blk, int nb) {
+  __shared__ uint32_t s_w[32];
+  __shared__ uint32_t s_carry;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) s_carry = 0;
+  __syncthreads();
+  for (int b0 = 0; b0 < nb; b0 += 1024) {
+    const int i = b0 + tid;
+    const uint32_t x = i < nb ? blk[i] : 0u;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_w[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+      uint32_t t = s_w[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      s_w[lane] = t;  // inclusive over warps
+    }
+    __syncthreads();
+    const uint32_t carry = s_carry;
+    const uint32_t excl = carry + (wid ? s_w[wid - 1] : 0u) + inc - x;
+    if (i < nb) blk[i] = excl;
+    __syncthreads();
+    if (tid == 0) s_carry = carry + s_w[31];
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256) k_vis_scatter(const uint8_t* __restrict__ mask, const float2* __restrict__ uv,
+                                                     int n, const uint32_t* __restrict__ blk,
+                                                     int32_t* __restrict__ vis_gid, float2* __restrict__ vis_uv) {
+  __shared__ uint32_t s_w[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int base = blockIdx.x * kVisBlock;
+  uint32_t off = blk[blockIdx.x];
+  for (int k = 0; k < kVisBlock / 256; ++k) {
+    const int i = base + k * 256 + threadIdx.x;
+    const bool m = i < n && (mask[i] & 1u);
+    const unsigned b = __ballot_sync(0xffffffffu, m);
+    if (lane == 0) s_w[wid] = (uint32_t)__popc(b);
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      before += q < wid ? s_w[q] : 0u;
+      total += s_w[q];
+    }
+    if (m) {
+      const uint32_t o = off + before + (uint32_t)__popc(b & ((1u << lane) - 1u));
+      if (vis_gid) vis_gid[o] = i;
+      if (vis_uv) vis_uv[o] = uv[i];
+    }
+    off += total;
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_pack_scene(const float* means, const float* scales, const float* quats,
@@ -620,6 +792,36 @@ cudaError_t launch_shade(const SceneDev& sc, const View* views, const Work& w, b
     k_shade<true><<<g, 256, 0, st>>>(sc, views, w);
   else
     k_shade<false><<<g, 256, 0, st>>>(sc, views, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vis_inimage(const SceneDev& sc, const View* views, uint8_t* mask, float2* uv, float* grad,
+                               int grid, cudaStream_t st) {
+  if (sc.n <= 0) return cudaSuccess;
+  const int need = (sc.n + 255) / 256;
+  k_vis_inimage<<<need < grid ? need : grid, 256, 0, st>>>(sc, views, mask, uv, grad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vis_chain(const View* views, const Work& w, const float* acc, uint8_t* mask, float* grad,
+                             int grid, cudaStream_t st) {
+  if (w.rec_cap == 0) return cudaSuccess;
+  const int need = (int)((w.rec_cap + 255) / 256);
+  k_vis_chain<<<need < grid ? need : grid, 256, 0, st>>>(views, w, acc, mask, grad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vis_compact(const uint8_t* mask, const float2* uv, int n, uint32_t* blk, int32_t* vis_gid,
+                               float2* vis_uv, cudaStream_t st) {
+  if (n <= 0 || (!vis_gid && !vis_uv)) return cudaSuccess;
+  const int nb = (n + kVisBlock - 1) / kVisBlock;
+  k_vis_count<<<nb, 256, 0, st>>>(mask, n, blk);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_vis_scan<<<1, 1024, 0, st>>>(blk, nb);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_vis_scatter<<<nb, 256, 0, st>>>(mask, uv, n, blk, vis_gid, vis_uv);
   return cudaGetLastError();
 }
 

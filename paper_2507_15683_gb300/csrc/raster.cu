@@ -607,6 +607,120 @@ __global__ void __launch_bounds__(kTileThreads, TAN ? 4 : FEAT ? 3 : 5) k_compos
   }
 }
 
+// ---------------------------------------------------------------------------
+// Algorithm 1 (render-gradient visibility check): reverse walk of every pixel
+// for L = sum of the rendered colours (dL/dC = 1 per channel), from the final
+// transmittance and last blended index of a forward render. Walking back,
+// with s the channel sum of the normalised colour behind the current
+// Gaussian, dL/dalpha_j = T_j (r_j + g_j + b_j - s) and dL/dc_j = alpha_j T_j
+// per channel. Per blended pair the record accumulates
+//   (e dx, e dy, e dx^2, e dx dy, e dy^2, alpha T, 0, 0),  e = dL/dpower,
+// (dx, dy) = centre - pixel: the pose Jacobian's rows contract these with
+// (P, Q, dA/2, dB, dC/2) to dL/dxi (see the tangent pass). The eight values
+// are summed over the warp (lane l ends with the total of value l / 4) and
+// added to the record's accumulator; a Gaussian nobody blended keeps an exact
+// zero. The order of the atomic additions varies, so the sums are not
+// bit-reproducible; the test the algorithm makes (gradient != 0) is.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTileThreads) k_vis_backward(const View* __restrict__ views, int n_views, Work w,
+                                                               float* __restrict__ acc) {
+  __shared__ float4 sa[kBatchT], sb[kBatchT], sc[kBatchT];
+  __shared__ uint32_t smask[kBatchT], srec[kBatchT];
+  __shared__ uint32_t s_tile, s_max[kWarps];
+  if (w.ctr->overflow) return;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  int lx, ly, bxw, byw;
+  warp_block(tid, lx, ly, bxw, byw);
+  const float pxc = (float)lx + 0.5f, pyc = (float)ly + 0.5f;
+  const uint32_t wbit = 1u << wid;
+  for (;;) {
+    if (tid == 0) s_tile = atomicAdd(&w.ctr->tan_queue, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= w.n_tiles) break;
+    const int vi = find_view(views, n_views, tile);
+    const View& V = views[vi];
+    const uint32_t lt = tile - V.tile_base;
+    const int tx = (int)(lt % (uint32_t)V.tiles_x), ty = (int)(lt / (uint32_t)V.tiles_x);
+    const uint32_t start = w.tile_offset[tile];
+    const int px = tx * kTile + lx, py = ty * kTile + ly;
+    const bool inside = px < V.width && py < V.height;
+    const float X0 = (float)(tx * kTile), Y0 = (float)(ty * kTile);
+    const size_t p = (size_t)py * V.width + px;
+    uint32_t last = 0;
+    float T = 1.0f;
+    if (inside) {
+      last = V.last_idx[p];
+      T = V.final_T[p];
+    }
+    const uint32_t wm = __reduce_max_sync(0xffffffffu, last);
+    if (lane == 0) s_max[wid] = wm;
+    __syncthreads();
+    uint32_t max_last = 0;
+#pragma unroll
+    for (int k = 0; k < kWarps; ++k) max_last = max(max_last, s_max[k]);
+    float sdot = 0.0f;  // sum over channels of the normalised colour behind
+    for (int bend = (int)max_last; bend > 0; bend -= kBatchT) {
+      const int bstart = max(0, bend - kBatchT);
+      const int bn = bend - bstart;
+      __syncthreads();
+      if (tid < bn) {
+        const uint32_t r = w.pairs[start + bstart + tid].y;
+        const float4 cc = w.rec_c[r];
+        const float4 a = tile_local(w.rec_a[r], cc.w, X0, Y0);
+        const float4 bb = w.rec_b[r];
+        sa[tid] = a;
+        sb[tid] = bb;
+        sc[tid] = cc;
+        srec[tid] = r;
+        smask[tid] = warp_hit_mask(a, bb.x, floor_threshold(bb.y));
+      }
+      __syncthreads();
+      if ((uint32_t)bstart >= wm) continue;
+      for (int c0 = ((bn - 1) >> 5) << 5; c0 >= 0; c0 -= 32) {
+        const int jj = c0 + lane;
+        uint32_t m = __ballot_sync(0xffffffffu, jj < bn && (uint32_t)(bstart + jj) < wm && (smask[jj] & wbit));
+        while (m) {  // back to front
+          const int bit = 31 - __clz(m);
+          m &= ~(1u << bit);
+          const int j = c0 + bit;
+          const float4 a = sa[j], b = sb[j], c = sc[j];
+          const float dx = __fsub_rn(a.x, pxc), dy = __fsub_rn(a.y, pyc);
+          const float pw = gs_power(a.z, a.w, b.x, dx, dy);
+          const float oe = __fmul_rn(b.y, __expf(pw));
+          const float alpha = fminf(kAlphaCap, oe);
+          const bool take = inside && (uint32_t)(bstart + j) < last && !(pw > 0.0f) && !(alpha < kAlphaFloor);
+          if (!__any_sync(0xffffffffu, take)) continue;  // nobody in the warp blended it
+          const float Tj = take ? __fdividef(T, 1.0f - alpha) : T;
+          const float wgt = take ? alpha * Tj : 0.0f;
+          const float d = (c.x + c.y + c.z) - sdot;  // dL/dalpha = Tj d
+          sdot = fmaf(take ? alpha : 0.0f, d, sdot);
+          T = Tj;
+          const float e = (take && oe < kAlphaCap) ? (Tj * d) * alpha : 0.0f;  // dalpha/dpower = alpha
+          const float ex = e * dx, ey = e * dy;
+          float g[8] = {ex, ey, ex * dx, ex * dy, ey * dy, wgt, 0.0f, 0.0f};
+          // reduce over the warp's pixels: halve the value set across lane bits 4, 3, 2, then
+          // sum over bits 1, 0; lane l ends with the total of value (l >> 2)
+#pragma unroll
+          for (int s = 4, bitv = 16; s >= 1; s >>= 1, bitv >>= 1) {
+            const bool up = (lane & bitv) != 0;
+#pragma unroll
+            for (int i = 0; i < s; ++i) {
+              const float send = up ? g[i] : g[i + s];
+              const float keep = up ? g[i + s] : g[i];
+              g[i] = keep + __shfl_xor_sync(0xffffffffu, send, bitv);
+            }
+          }
+          float tot = g[0] + __shfl_xor_sync(0xffffffffu, g[0], 2);
+          tot += __shfl_xor_sync(0xffffffffu, tot, 1);
+          if ((lane & 3) == 0 && tot != 0.0f) atomicAdd(acc + (size_t)srec[j] * kVisAcc + (lane >> 2), tot);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 template <int FEAT, bool TAN>
 size_t composite_smem() {
   return TAN ? (size_t)kSmTan : FEAT ? (size_t)kSmFwdFeat : (size_t)kSmFwd;
@@ -644,6 +758,14 @@ cudaError_t launch_composite(const SceneDev& sc, const View* views, int n_views,
     composite_occ<0, false>();
     k_composite<0, false><<<g, kTileThreads, composite_smem<0, false>(), st>>>(sc, views, n_views, w, nullptr);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vis_backward(const View* views, int n_views, const Work& w, float* acc, int grid,
+                                cudaStream_t st) {
+  if (w.n_tiles == 0) return cudaSuccess;
+  const int g = (uint32_t)grid < w.n_tiles ? grid : (int)w.n_tiles;
+  k_vis_backward<<<g, kTileThreads, 0, st>>>(views, n_views, w, acc);
   return cudaGetLastError();
 }
 

@@ -93,6 +93,7 @@ def _load():
         "gs_scene_evict": [vp],
         "gs_scene_kernel_times": [vp, vp, vp],
         "gs_scene_blend_count": [vp, vp, vp],
+        "gs_visibility": [vp, P(gs_camera), P(gs_pose), vp, vp, vp, vp, vp, vp, vp],
         "gs_pmm_create": [st, st, st, P(vp)],
         "gs_pmm_match": [vp, vp, vp, ctypes.c_float, P(gs_pmm_result), vp],
     }
@@ -294,6 +295,16 @@ def gs_scene_blend_count(h, stream=None):
     return b.value
 
 
+def gs_visibility(h, cam: gs_camera, pose_: gs_pose, mask: int, uv, grad_mean, visible_ids, visible_uv,
+                  stream: int) -> int:
+    """Algorithm 1 visibility check; device pointers (all but mask may be None).
+    Returns the number of Gaussians kept."""
+    n = ctypes.c_int64()
+    _check(lib.gs_visibility(h, ctypes.byref(cam), ctypes.byref(pose_), mask, uv, grad_mean, visible_ids,
+                             visible_uv, ctypes.byref(n), stream))
+    return n.value
+
+
 def gs_scene_stream_stats(h):
     """(bytes uploaded, partitions resident, partitions walked by the last call)."""
     b, r, a = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
@@ -459,6 +470,24 @@ class Scene:
         gs_render_batch(self.handle, [camera(c) for c in cams], [pose(T) for T in poses],
                         [self.outputs_struct(o) for o in outs], GS_BATCH_GRAPH if graph else 0, _stream())
         return outs
+
+    def visibility(self, cam, T, grad=True, compact=True):
+        """Algorithm 1 from pose T: dict of device tensors mask (n uint8: bit 0 M,
+        bit 1 M^r, bit 2 M^i), uv (n, 2), grad (n, 3) or None, ids (K,) and
+        uv_visible (K, 2) of the kept Gaussians (compact=True), and n_visible."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        mask = torch.empty(max(self.n, 1), dtype=torch.uint8, device=dev)
+        uv = torch.empty((max(self.n, 1), 2), dtype=torch.float32, device=dev)
+        g = torch.empty((max(self.n, 1), 3), dtype=torch.float32, device=dev) if grad else None
+        ids = torch.empty(max(self.n, 1), dtype=torch.int32, device=dev) if compact else None
+        uvv = torch.empty((max(self.n, 1), 2), dtype=torch.float32, device=dev) if compact else None
+        k = gs_visibility(self.handle, camera(cam), pose(T), _ptr(mask), _ptr(uv), _ptr(g), _ptr(ids), _ptr(uvv),
+                          _stream())
+        n = self.n
+        return {"mask": mask[:n], "uv": uv[:n], "grad": None if g is None else g[:n],
+                "ids": None if ids is None else ids[:k], "uv_visible": None if uvv is None else uvv[:k],
+                "n_visible": k}
 
     def status(self):
         return gs_scene_status(self.handle, _stream())

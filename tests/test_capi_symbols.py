@@ -19,7 +19,7 @@ def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("gs_create_scene", "gs_destroy_scene", "gs_render", "gs_render_pose_grad", "gs_render_batch",
                      "gs_render_pose_grad_batch", "gs_refine_pose", "gs_refine_poses_batch", "gs_refine_defaults",
-                     "gs_last_error", "gs_pmm_create", "gs_pmm_match", "gs_pmm_destroy"):
+                     "gs_last_error", "gs_pmm_create", "gs_pmm_match", "gs_pmm_destroy", "gs_visibility"):
         assert required in names
 
 
@@ -39,6 +39,8 @@ def test_invalid_arguments_fail_without_a_gpu(libgsr_path):
     assert b"required" in lib.gs_last_error()
     lib.gs_render.argtypes = [ctypes.c_void_p] * 5
     assert lib.gs_render(None, None, None, None, None) == 1
+    lib.gs_visibility.argtypes = [ctypes.c_void_p] * 10
+    assert lib.gs_visibility(*([None] * 10)) == 1
 
 
 def test_pmm_create_rejects_bad_sizes_without_a_gpu(libgsr_path):

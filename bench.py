@@ -49,6 +49,13 @@ FLOPS_PER_BLEND = 180
 # one ncu capture of this kernel (dram__bytes_read.sum + dram__bytes_write.sum);
 # None whenever the kernel has changed since that capture
 COMPOSITE_DRAM_BYTES = 83_501_056  # 80,544,000 read + 2,957,056 written
+# Visibility reverse pass (Algorithm 1): a (pixel, Gaussian) evaluation shares
+# the forward's FLOPS_PER_EVAL; a blended pair adds the transmittance
+# division, weight, colour sum and running sum (8), dL/dpower and the five
+# monomials (7) and their share of the per-record sums over pixels (6).
+FLOPS_PER_VIS_BLEND = 21
+# DRAM bytes of one reverse-pass launch (ncu, same kernel): 37,470,720 read + 20,480 written
+VIS_BACKWARD_DRAM_BYTES = 37_491_200
 
 
 def parse():
@@ -61,6 +68,7 @@ def parse():
     p.add_argument("--no-refine", action="store_true")
     p.add_argument("--no-large", action="store_true")
     p.add_argument("--no-pmm", action="store_true")
+    p.add_argument("--no-vis", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     return p.parse_args()
@@ -301,7 +309,7 @@ def main():
     timed(grad_step, args.steps)
     kms, kn = gsr.gs_scene_kernel_times(S.handle)
     gsr.gs_scene_set_timing(S.handle, False)
-    per_kernel = {name: (kms[i] / kn[i] if kn[i] else 0.0) for i, name in enumerate(gsr.KERNEL_NAMES)}
+    per_kernel = {name: kms[i] / kn[i] for i, name in enumerate(gsr.KERNEL_NAMES) if kn[i]}
     ts, _, _ = S.tile_lists(0, cam, n_pairs + 16)
     counts = np.diff(ts)
     tx, ty = (W + 15) // 16, (H + 15) // 16
@@ -358,6 +366,11 @@ def main():
     large = None if args.no_large else bench_large(gsr, synth, torch)
     # dense matching of rendered feature maps (PMM, Eq. 11) at 1920x1080: 32,400 x 32,400 similarities
     pmm = None if args.no_pmm else bench_pmm(gsr, synth, torch, pk_for_pmm(), max(3, args.steps // 4), args.warmup)
+    # Algorithm 1 visibility check of all 1M Gaussians from the query pose
+    vis = None
+    if not args.no_vis:
+        vis = bench_visibility(gsr, torch, S, scene, cam, T_q, flush, max(3, args.steps // 2), args.warmup,
+                               with_oracle=rank == 0 and world == 1 and not args.no_cpu)
     clk = clocks.stop()
 
     cpu = None
@@ -381,7 +394,7 @@ def main():
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 7 * 8},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roof, "kernels": kernels,
-        "refine": refine, "batched": batched, "large": large, "pmm": pmm, "cpu_baseline": cpu,
+        "refine": refine, "batched": batched, "large": large, "pmm": pmm, "visibility": vis, "cpu_baseline": cpu,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -552,6 +565,70 @@ def bench_pmm(gsr, synth, torch, pk_src, steps, warmup):
                        "note": "K = 32: the contraction is small; the epilogue (exp, reductions, argmax) bounds"},
             "exp": {"count": int(sims), "achieved_per_s": sims / (ms * 1e-3), "mufu_peak_per_s": mufu_peak,
                     "frac": sims / (ms * 1e-3) / mufu_peak}}
+
+
+def bench_visibility(gsr, torch, S, scene, cam, T, flush, steps, warmup, with_oracle):
+    """Render-gradient visibility check (Sec. 3.2, Algorithm 1) of every Gaussian
+    of the headline scene from the query pose, through gs_visibility."""
+    n = S.n
+    for _ in range(warmup):
+        r = S.visibility(cam, T)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for a, b in ev:
+        flush.zero_()
+        a.record()
+        r = S.visibility(cam, T)
+        b.record()
+    torch.cuda.synchronize()
+    wall_ms = (time.perf_counter() - t0) * 1e3 / steps
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    gsr.gs_scene_set_timing(S.handle, True)
+    gsr.gs_scene_kernel_times(S.handle)
+    for _ in range(steps):
+        flush.zero_()
+        S.visibility(cam, T)
+    kms, kn = gsr.gs_scene_kernel_times(S.handle)
+    gsr.gs_scene_set_timing(S.handle, False)
+    per_kernel = {name: kms[i] / kn[i] for i, name in enumerate(gsr.KERNEL_NAMES) if kn[i]}
+    blends, evals = gsr.gs_scene_work_counts(S.handle)
+    pk, pk_src = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12
+    t_bw = per_kernel["vis_backward"]
+    flops = evals * FLOPS_PER_EVAL + blends * FLOPS_PER_VIS_BLEND
+    ach = flops / (t_bw * 1e-3) / 1e12
+    mask = r["mask"].cpu().numpy()
+    out = {"workload": "Algorithm 1 visibility of all 1M Gaussians (aerial SH3) at 1920x1080 from the query pose: "
+                       "forward render, reverse pass of sum(RGB), mean gradients, in-image test, compaction",
+           "gaussians": n, "kept": int(r["n_visible"]), "m_r": int(((mask & 2) != 0).sum()),
+           "m_i": int(((mask & 4) != 0).sum()), "ms": ms, "wall_ms": wall_ms,
+           "gaussians_per_s": n / (ms * 1e-3),
+           "kernels": {k: {"ms": v, "share": v / max(sum(per_kernel.values()), 1e-12)} for k, v in per_kernel.items()},
+           "roofline": {"bound": "alu", "kernel": "vis_backward (reverse pass, accumulator zeroing included)",
+                        "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
+                        "traffic": VIS_BACKWARD_DRAM_BYTES,
+                        "work": "%d (pixel, Gaussian) evaluations x %d + %d blended pairs x %d (reverse blend, "
+                                "monomial sums, warp reduction)" % (evals, FLOPS_PER_EVAL, blends,
+                                                                    FLOPS_PER_VIS_BLEND),
+                        "peak_source": "%d SMs x 128 fp32 lanes x 2 x %.0f MHz (%s max clock)"
+                                       % (n_sm, sm_max, pk_src)},
+           "l2": "flushed (256 MB write) between timed calls, outside the timed events"}
+    if with_oracle:
+        from oracle import oracle as O
+        O.build()
+        n_thr = os.cpu_count() or 1
+        keep = np.nonzero(mask & 2)[0]
+        sample = np.sort(np.random.default_rng(1).choice(keep, min(16, len(keep)), replace=False))
+        t0 = time.perf_counter()
+        O.visibility(scene, cam, T, n_threads=n_thr, gids=sample)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": len(sample) / dt, "unit": "Gaussians/s", "cores": n_thr, "kind": "oracle",
+                               "sample": "fp64 oracle mean gradient (forward mode, one Gaussian at a time over its "
+                                         "tile rectangle) of %d Gaussians with M^r, %.2f s" % (len(sample), dt)}
+    return out
 
 
 def bench_batched(gsr, synth, torch, flush, steps, warmup):

@@ -283,8 +283,10 @@ gs_status gs_scene_evict(gs_scene* scene);
  * projection (discrete layer), shading (conic, colour, centre, Jacobian),
  * tile scan, scatter, warp sort of the short tile lists, compositing (block
  * sort of longer lists, blending, and for the pose gradient the tangent pass
- * with the fp64 reduction). */
-#define GS_KERNEL_COUNT 6
+ * with the fp64 reduction); then, in gs_visibility calls only, the reverse
+ * pass (with the zeroing of its accumulators) and the per-Gaussian selection
+ * (in-image test, chain rule, compaction). */
+#define GS_KERNEL_COUNT 8
 gs_status gs_scene_set_timing(gs_scene* scene, int enable);
 
 /* Wait for the recorded calls and return, per kernel, the summed device time
@@ -299,6 +301,15 @@ gs_status gs_scene_kernel_times(gs_scene* scene, double* total_ms, int64_t* laun
  * 0 after a forward-only call. Waits for `stream`. `blended` is a host
  * pointer. Errors: INVALID_ARG, CUDA. */
 gs_status gs_scene_blend_count(gs_scene* scene, void* stream, int64_t* blended);
+
+/* Work units of the last call's backward walk, for roofline accounting:
+ * blended = (pixel, Gaussian) pairs blended (as gs_scene_blend_count; after a
+ * gs_visibility call, the pairs its reverse pass walked back through), and
+ * evaluated = (pixel, Gaussian) pairs whose footprint the visibility reverse
+ * pass evaluated (a pair before the pixel's last blended Gaussian whose tile
+ * entry hits the pixel's 8 x 4 block; 0 after any other call). Waits for
+ * `stream`; host pointers, either may be NULL. Errors: INVALID_ARG, CUDA. */
+gs_status gs_scene_work_counts(gs_scene* scene, void* stream, int64_t* blended, int64_t* evaluated);
 
 /* Render-gradient visibility check with projection filtering (Sec. 3.2,
  * Algorithm 1) of every Gaussian of the scene from one pose.

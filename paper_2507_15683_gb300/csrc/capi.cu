@@ -422,18 +422,20 @@ gs_status enqueue(gs_scene* s, const std::vector<View>& hv, const std::vector<in
     if (targets_ready) GS_CUDA(cudaStreamWaitEvent(st, targets_ready, 0));  // only this pass reads the targets
     GS_CUDA(launch_composite_tangent(sc, dviews, nv, w, res, s->sm_count * composite_blocks_per_sm(0, true), st));
   }
+  GS_CUDA(mark(6));
   if (vis) {
     // Algorithm 1: reverse pass of sum RGB, then the per-Gaussian tests
     float* acc = dp<float>(s->vis_acc);
     GS_CUDA(cudaMemsetAsync(acc, 0, (size_t)s->rec_cap * kVisAcc * sizeof(float), st));
-    GS_CUDA(launch_vis_backward(dviews, nv, w, acc, s->sm_count * 4, st));
+    GS_CUDA(launch_vis_backward(dviews, nv, w, acc, s->sm_count, st));
+    GS_CUDA(mark(7));
     GS_CUDA(launch_vis_inimage(sc, dviews, vis->mask, vis->uv, vis->grad, s->sm_count * 8, st));
     GS_CUDA(launch_vis_chain(dviews, w, acc, vis->mask, vis->grad, s->sm_count * 8, st));
     GS_CUDA(launch_vis_compact(vis->mask, vis->uv, (int)s->n, dp<uint32_t>(s->vis_blk), vis->vis_gid, vis->vis_uv,
                                st));
+    GS_CUDA(mark(8));
   }
-  GS_CUDA(mark(6));
-  if (timed) s->ev_pending.push_back({std::move(ev), GS_KERNEL_COUNT});
+  if (timed) s->ev_pending.push_back({std::move(ev), vis ? 8 : 6});
   s->last_views = hv;
   s->last_tiles = (uint32_t)n_tiles;
   return GS_OK;
@@ -1176,6 +1178,17 @@ gs_status gs_scene_blend_count(gs_scene* s, void* stream, int64_t* blended) {
   Counters c;
   GS_TRY(read_counters(s, (cudaStream_t)stream, c));
   *blended = (int64_t)c.blends;
+  return GS_OK;
+}
+
+gs_status gs_scene_work_counts(gs_scene* s, void* stream, int64_t* blended, int64_t* evaluated) {
+  g_err.clear();
+  GS_TRY(check_scene(s));
+  GS_TRY(set_device(s));
+  Counters c;
+  GS_TRY(read_counters(s, (cudaStream_t)stream, c));
+  if (blended) *blended = (int64_t)c.blends;
+  if (evaluated) *evaluated = (int64_t)c.evals;
   return GS_OK;
 }
 

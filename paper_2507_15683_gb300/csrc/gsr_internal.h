@@ -63,7 +63,8 @@ struct Counters {
   unsigned int tan_queue;   // persistent tile queue of the tangent (pose-gradient) render
   unsigned int error;       // device-side consistency failure
   unsigned int vis_count;   // Gaussians the visibility check keeps (M = M^r and M^i)
-  unsigned long long blends;  // (pixel, Gaussian) pairs blended by the tangent pass
+  unsigned long long blends;  // (pixel, Gaussian) pairs blended by the tangent or visibility reverse pass
+  unsigned long long evals;   // (pixel, Gaussian) pairs the visibility reverse pass evaluated
 };
 
 // Scene arena (device pointers).
@@ -129,8 +130,9 @@ cudaError_t launch_composite_tangent(const SceneDev& sc, const View* views, int 
 
 // Algorithm 1 visibility check, after a forward render of one view that wrote
 // final_T and last_idx and a shading pass that wrote the pose Jacobian:
-// reverse pass into acc (kVisAcc floats per record, zeroed by the caller)
-cudaError_t launch_vis_backward(const View* views, int n_views, const Work& w, float* acc, int grid,
+// reverse pass into acc (kVisAcc floats per record, zeroed by the caller);
+// persistent grid of the resident blocks on sm_count SMs
+cudaError_t launch_vis_backward(const View* views, int n_views, const Work& w, float* acc, int sm_count,
                                 cudaStream_t st);
 // every Gaussian: projected centre (U, V) and M^i (mask bit 2); zeroes grad
 cudaError_t launch_vis_inimage(const SceneDev& sc, const View* views, uint8_t* mask, float2* uv, float* grad,

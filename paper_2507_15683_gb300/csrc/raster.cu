@@ -618,14 +618,20 @@ __global__ void __launch_bounds__(kTileThreads, TAN ? 4 : FEAT ? 3 : 5) k_compos
 // (dx, dy) = centre - pixel: the pose Jacobian's rows contract these with
 // (P, Q, dA/2, dB, dC/2) to dL/dxi (see the tangent pass). The eight values
 // are summed over the warp (lane l ends with the total of value l / 4) and
-// added to the record's accumulator; a Gaussian nobody blended keeps an exact
-// zero. The order of the atomic additions varies, so the sums are not
+// added to the record's accumulator, or, when few lanes blended, added by
+// those lanes; a Gaussian nobody blended keeps an exact zero. The order of the atomic additions varies, so the sums are not
 // bit-reproducible; the test the algorithm makes (gradient != 0) is.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kTileThreads) k_vis_backward(const View* __restrict__ views, int n_views, Work w,
+constexpr int kBatchV = kTileThreads;  // entries staged per batch of the reverse pass
+constexpr int kVisDirect = 12;         // at most this many blending lanes add without the warp reduction
+
+__global__ void __launch_bounds__(kTileThreads, 7) k_vis_backward(const View* __restrict__ views, int n_views, Work w,
                                                                float* __restrict__ acc) {
-  __shared__ float4 sa[kBatchT], sb[kBatchT], sc[kBatchT];
-  __shared__ uint32_t smask[kBatchT], srec[kBatchT];
+  // staged per entry: centre and conic A, B; (C, opacity); channel sum of the colour
+  __shared__ float4 sa[kBatchV];
+  __shared__ float2 sb[kBatchV];
+  __shared__ float sg[kBatchV];
+  __shared__ uint32_t smask[kBatchV], srec[kBatchV];
   __shared__ uint32_t s_tile, s_max[kWarps];
   if (w.ctr->overflow) return;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -633,11 +639,17 @@ __global__ void __launch_bounds__(kTileThreads) k_vis_backward(const View* __res
   warp_block(tid, lx, ly, bxw, byw);
   const float pxc = (float)lx + 0.5f, pyc = (float)ly + 0.5f;
   const uint32_t wbit = 1u << wid;
+  uint32_t n_eval = 0, n_take = 0;  // (pixel, Gaussian) pairs evaluated / blended by this thread
   for (;;) {
     if (tid == 0) s_tile = atomicAdd(&w.ctr->tan_queue, 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
-    if (tile >= w.n_tiles) break;
+    if (tile >= w.n_tiles) {
+      const uint32_t ne = __reduce_add_sync(0xffffffffu, n_eval), nt = __reduce_add_sync(0xffffffffu, n_take);
+      if (lane == 0 && ne) atomicAdd(&w.ctr->evals, (unsigned long long)ne);
+      if (lane == 0 && nt) atomicAdd(&w.ctr->blends, (unsigned long long)nt);
+      break;
+    }
     const int vi = find_view(views, n_views, tile);
     const View& V = views[vi];
     const uint32_t lt = tile - V.tile_base;
@@ -660,8 +672,8 @@ __global__ void __launch_bounds__(kTileThreads) k_vis_backward(const View* __res
 #pragma unroll
     for (int k = 0; k < kWarps; ++k) max_last = max(max_last, s_max[k]);
     float sdot = 0.0f;  // sum over channels of the normalised colour behind
-    for (int bend = (int)max_last; bend > 0; bend -= kBatchT) {
-      const int bstart = max(0, bend - kBatchT);
+    for (int bend = (int)max_last; bend > 0; bend -= kBatchV) {
+      const int bstart = max(0, bend - kBatchV);
       const int bn = bend - bstart;
       __syncthreads();
       if (tid < bn) {
@@ -670,8 +682,8 @@ __global__ void __launch_bounds__(kTileThreads) k_vis_backward(const View* __res
         const float4 a = tile_local(w.rec_a[r], cc.w, X0, Y0);
         const float4 bb = w.rec_b[r];
         sa[tid] = a;
-        sb[tid] = bb;
-        sc[tid] = cc;
+        sb[tid] = make_float2(bb.x, bb.y);
+        sg[tid] = cc.x + cc.y + cc.z;
         srec[tid] = r;
         smask[tid] = warp_hit_mask(a, bb.x, floor_threshold(bb.y));
       }
@@ -684,21 +696,34 @@ __global__ void __launch_bounds__(kTileThreads) k_vis_backward(const View* __res
           const int bit = 31 - __clz(m);
           m &= ~(1u << bit);
           const int j = c0 + bit;
-          const float4 a = sa[j], b = sb[j], c = sc[j];
+          const float4 a = sa[j];
+          const float2 b = sb[j];
           const float dx = __fsub_rn(a.x, pxc), dy = __fsub_rn(a.y, pyc);
           const float pw = gs_power(a.z, a.w, b.x, dx, dy);
           const float oe = __fmul_rn(b.y, __expf(pw));
           const float alpha = fminf(kAlphaCap, oe);
-          const bool take = inside && (uint32_t)(bstart + j) < last && !(pw > 0.0f) && !(alpha < kAlphaFloor);
-          if (!__any_sync(0xffffffffu, take)) continue;  // nobody in the warp blended it
+          const bool before = inside && (uint32_t)(bstart + j) < last;
+          const bool take = before && !(pw > 0.0f) && !(alpha < kAlphaFloor);
+          n_eval += before ? 1u : 0u;
+          n_take += take ? 1u : 0u;
+          const unsigned tb = __ballot_sync(0xffffffffu, take);
+          if (!tb) continue;  // nobody in the warp blended it
           const float Tj = take ? __fdividef(T, 1.0f - alpha) : T;
           const float wgt = take ? alpha * Tj : 0.0f;
-          const float d = (c.x + c.y + c.z) - sdot;  // dL/dalpha = Tj d
+          const float d = sg[j] - sdot;  // dL/dalpha = Tj d
           sdot = fmaf(take ? alpha : 0.0f, d, sdot);
           T = Tj;
           const float e = (take && oe < kAlphaCap) ? (Tj * d) * alpha : 0.0f;  // dalpha/dpower = alpha
           const float ex = e * dx, ey = e * dy;
           float g[8] = {ex, ey, ex * dx, ex * dy, ey * dy, wgt, 0.0f, 0.0f};
+          if (__popc(tb) <= kVisDirect) {  // few pixels: their own additions beat the reduction
+            if (take) {
+              float* ap = acc + (size_t)srec[j] * kVisAcc;
+#pragma unroll
+              for (int k = 0; k < 6; ++k) atomicAdd(ap + k, g[k]);
+            }
+            continue;
+          }
           // reduce over the warp's pixels: halve the value set across lane bits 4, 3, 2, then
           // sum over bits 1, 0; lane l ends with the total of value (l >> 2)
 #pragma unroll
@@ -761,9 +786,17 @@ cudaError_t launch_composite(const SceneDev& sc, const View* views, int n_views,
   return cudaGetLastError();
 }
 
-cudaError_t launch_vis_backward(const View* views, int n_views, const Work& w, float* acc, int grid,
+cudaError_t launch_vis_backward(const View* views, int n_views, const Work& w, float* acc, int sm_count,
                                 cudaStream_t st) {
   if (w.n_tiles == 0) return cudaSuccess;
+  static int per_sm = 0;  // resident blocks per SM (persistent grid)
+  if (per_sm == 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_vis_backward, kTileThreads, 0) != cudaSuccess || b < 1)
+      b = 4;
+    per_sm = b;
+  }
+  const int grid = sm_count * per_sm;
   const int g = (uint32_t)grid < w.n_tiles ? grid : (int)w.n_tiles;
   k_vis_backward<<<g, kTileThreads, 0, st>>>(views, n_views, w, acc);
   return cudaGetLastError();

@@ -93,6 +93,7 @@ def _load():
         "gs_scene_evict": [vp],
         "gs_scene_kernel_times": [vp, vp, vp],
         "gs_scene_blend_count": [vp, vp, vp],
+        "gs_scene_work_counts": [vp, vp, vp, vp],
         "gs_visibility": [vp, P(gs_camera), P(gs_pose), vp, vp, vp, vp, vp, vp, vp],
         "gs_pmm_create": [st, st, st, P(vp)],
         "gs_pmm_match": [vp, vp, vp, ctypes.c_float, P(gs_pmm_result), vp],
@@ -274,7 +275,7 @@ def gs_render_noalloc(desc: gs_scene_desc, cam: gs_camera, pose: gs_pose, out: g
                                  stream))
 
 
-KERNEL_NAMES = ("project", "shade", "scan_tiles", "scatter", "sort", "composite")
+KERNEL_NAMES = ("project", "shade", "scan_tiles", "scatter", "sort", "composite", "vis_backward", "vis_select")
 
 
 def gs_scene_set_timing(h, enable: bool) -> None:
@@ -303,6 +304,13 @@ def gs_visibility(h, cam: gs_camera, pose_: gs_pose, mask: int, uv, grad_mean, v
     _check(lib.gs_visibility(h, ctypes.byref(cam), ctypes.byref(pose_), mask, uv, grad_mean, visible_ids,
                              visible_uv, ctypes.byref(n), stream))
     return n.value
+
+
+def gs_scene_work_counts(h, stream=None):
+    """(blended, evaluated) pairs of the last call's backward walk."""
+    b, e = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib.gs_scene_work_counts(h, _stream() if stream is None else stream, ctypes.byref(b), ctypes.byref(e)))
+    return b.value, e.value
 
 
 def gs_scene_stream_stats(h):

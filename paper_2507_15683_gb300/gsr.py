@@ -65,6 +65,18 @@ class gs_pmm_result(ctypes.Structure):
                 ("fine_prob", ctypes.c_void_p)]
 
 
+class gs_pnp_opts(ctypes.Structure):
+    _fields_ = [("tau_px", ctypes.c_float), ("min_alpha", ctypes.c_float), ("refine_iters", ctypes.c_int)]
+
+
+class gs_pnp_result(ctypes.Structure):
+    _fields_ = [("T_cw", ctypes.c_double * 16), ("n_valid", ctypes.c_int64), ("n_inliers", ctypes.c_int64),
+                ("best_hypothesis", ctypes.c_int32), ("best_solution", ctypes.c_int32),
+                ("best_count", ctypes.c_int64), ("refine_steps", ctypes.c_int32), ("inlier", ctypes.c_void_p),
+                ("valid_index", ctypes.c_void_p), ("points", ctypes.c_void_p), ("hyp_counts", ctypes.c_void_p),
+                ("hyp_poses", ctypes.c_void_p)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError("libgsr.so is not built (run: python -m paper_2507_15683_gb300.build)")
@@ -97,6 +109,8 @@ def _load():
         "gs_visibility": [vp, P(gs_camera), P(gs_pose), vp, vp, vp, vp, vp, vp, vp],
         "gs_pmm_create": [st, st, st, P(vp)],
         "gs_pmm_match": [vp, vp, vp, ctypes.c_float, P(gs_pmm_result), vp],
+        "gs_pnp_create": [i64, st, P(vp)],
+        "gs_pnp_solve": [vp, P(gs_camera), P(gs_pose), vp, vp, vp, i64, vp, st, P(gs_pnp_opts), P(gs_pnp_result), vp],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -113,6 +127,10 @@ def _load():
     L.gs_destroy_scene.restype = None
     L.gs_pmm_destroy.argtypes = [vp]
     L.gs_pmm_destroy.restype = None
+    L.gs_pnp_destroy.argtypes = [vp]
+    L.gs_pnp_destroy.restype = None
+    L.gs_pnp_defaults.argtypes = []
+    L.gs_pnp_defaults.restype = gs_pnp_opts
     L.gs_last_error.argtypes = []
     L.gs_last_error.restype = ctypes.c_char_p
     L.gs_version.argtypes = []
@@ -591,3 +609,71 @@ class Matcher:
                 "coarse_prob": v(r.coarse_prob, (nc,), "<f4") if nc else torch.zeros(0, device="cuda"),
                 "fine": v(r.fine, (nf, 3), "<i4") if nf else torch.zeros((0, 3), dtype=torch.int32, device="cuda"),
                 "fine_prob": v(r.fine_prob, (nf,), "<f4") if nf else torch.zeros(0, device="cuda")}
+
+
+# ---- dense PnP + RANSAC (Sec. 3.4, Eq. 10) ------------------------------------------------------
+def gs_pnp_defaults() -> gs_pnp_opts:
+    return lib.gs_pnp_defaults()
+
+
+def gs_pnp_create(max_matches: int, max_hypotheses: int):
+    h = ctypes.c_void_p()
+    _check(lib.gs_pnp_create(max_matches, max_hypotheses, ctypes.byref(h)))
+    return h
+
+
+def gs_pnp_destroy(h) -> None:
+    lib.gs_pnp_destroy(h)
+
+
+def gs_pnp_solve(h, cam: gs_camera, T_render: gs_pose, depth: int, alpha: int, matches: int, n_matches: int,
+                 words: int, n_hypotheses: int, opts: gs_pnp_opts, stream: int) -> gs_pnp_result:
+    r = gs_pnp_result()
+    _check(lib.gs_pnp_solve(h, ctypes.byref(cam), ctypes.byref(T_render), depth, alpha, matches, n_matches, words,
+                            n_hypotheses, ctypes.byref(opts), ctypes.byref(r), stream))
+    return r
+
+
+class PnP:
+    """Dense PnP + RANSAC on rendered depth; ``solve`` returns the pose and copies
+    of the device results."""
+
+    def __init__(self, max_matches: int, max_hypotheses: int = 256):
+        self.handle = gs_pnp_create(max_matches, max_hypotheses)
+
+    def close(self):
+        if self.handle:
+            gs_pnp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, cam, T_render, depth, alpha, matches, words, tau=2.0, min_alpha=0.5, refine_iters=10) -> dict:
+        """depth, alpha: (H, W) float32 CUDA tensors rendered at T_render; matches:
+        (K, 3) int32 CUDA tensor (PMM fine layout); words: (n_hyp, 3) int32 or
+        uint32-bits CUDA tensor of random words."""
+        import torch
+        for t, dt in ((depth, torch.float32), (alpha, torch.float32), (matches, torch.int32)):
+            if not (t.is_cuda and t.dtype == dt and t.is_contiguous()):
+                raise ValueError("depth / alpha (float32) and matches (int32) must be contiguous CUDA tensors")
+        if not (words.is_cuda and words.is_contiguous() and words.element_size() == 4):
+            raise ValueError("words must be a contiguous 32-bit CUDA tensor")
+        o = gs_pnp_opts(tau, min_alpha, refine_iters)
+        K, nh = int(matches.shape[0]), int(words.shape[0])
+        r = gs_pnp_solve(self.handle, camera(cam), pose(T_render), depth.data_ptr(), alpha.data_ptr(),
+                         matches.data_ptr() if K else None, K, words.data_ptr() if nh else None, nh, o, _stream())
+        nv = r.n_valid
+        v = lambda p, shape, t: torch.as_tensor(_DevView(p, shape, t), device="cuda").clone()
+        empty = lambda shape, dt: torch.zeros(shape, dtype=dt, device="cuda")
+        return {"T": np.array(r.T_cw[:], np.float64).reshape(4, 4), "n_valid": nv, "n_inliers": r.n_inliers,
+                "best": (r.best_hypothesis, r.best_solution), "best_count": r.best_count,
+                "refine_steps": r.refine_steps,
+                "inlier": v(r.inlier, (K,), "|u1") if K else empty((0,), torch.uint8),
+                "valid_index": v(r.valid_index, (nv,), "<i4") if nv else empty((0,), torch.int32),
+                "points": v(r.points, (nv, 3), "<f8") if nv else empty((0, 3), torch.float64),
+                "hyp_counts": v(r.hyp_counts, (nh, 4), "<i4") if nh else empty((0, 4), torch.int32),
+                "hyp_poses": v(r.hyp_poses, (nh, 4, 12), "<f8") if nh else empty((0, 4, 12), torch.float64)}

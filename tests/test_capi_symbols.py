@@ -11,7 +11,7 @@ def declared_functions():
     inc = os.path.join(ROOT, "include")
     text = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:gs_status|void|const char\s*\*|gs_refine_opts)\s*(gs_\w+)\s*\(", text,
+    return sorted(set(re.findall(r"^\s*(?:gs_status|void|const char\s*\*|gs_\w+_opts)\s*(gs_\w+)\s*\(", text,
                                  flags=re.M)))
 
 
@@ -19,7 +19,8 @@ def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("gs_create_scene", "gs_destroy_scene", "gs_render", "gs_render_pose_grad", "gs_render_batch",
                      "gs_render_pose_grad_batch", "gs_refine_pose", "gs_refine_poses_batch", "gs_refine_defaults",
-                     "gs_last_error", "gs_pmm_create", "gs_pmm_match", "gs_pmm_destroy", "gs_visibility"):
+                     "gs_last_error", "gs_pmm_create", "gs_pmm_match", "gs_pmm_destroy", "gs_visibility",
+                     "gs_pnp_create", "gs_pnp_solve", "gs_pnp_destroy", "gs_pnp_defaults"):
         assert required in names
 
 
@@ -50,3 +51,14 @@ def test_pmm_create_rejects_bad_sizes_without_a_gpu(libgsr_path):
     assert lib.gs_pmm_create(31, 64, 64, ctypes.byref(h)) == 1  # 32 channels only
     assert lib.gs_pmm_create(32, 60, 64, ctypes.byref(h)) == 1  # multiples of 8
     assert not h.value
+
+
+def test_pnp_create_rejects_bad_sizes_without_a_gpu(libgsr_path):
+    lib = ctypes.CDLL(libgsr_path)
+    lib.gs_pnp_create.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]
+    h = ctypes.c_void_p()
+    assert lib.gs_pnp_create(0, 16, ctypes.byref(h)) == 1
+    assert lib.gs_pnp_create(100, 0, ctypes.byref(h)) == 1
+    assert not h.value
+    lib.gs_pnp_solve.argtypes = [ctypes.c_void_p] * 12
+    assert lib.gs_pnp_solve(*([None] * 12)) == 1

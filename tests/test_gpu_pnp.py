@@ -1,0 +1,208 @@
+"""GPU dense PnP + RANSAC (Sec. 3.4, Eq. 10) against the oracle, through the C
+ABI (gs_pnp_*).
+
+Inputs are either synthetic (a depth / alpha map and matches made by
+projecting lifted points with a known query pose, plus outliers) or the whole
+dense stage of the oracle (oracle renders of features, depth and alpha, oracle
+PMM fine matches). Bars:
+* the matches with depth and their world points: identical indices, points
+  to 1e-9 relative (fp64 on both sides);
+* per RANSAC hypothesis: the same solutions unless the oracle flags a
+  near-double root, poses to 1e-6 (deg, relative translation) for all but 1 %
+  of them (ill-conditioned samples) and to 1e-3 for all; inlier counts within
+  the number of matches the oracle finds within 1e-3 px of the threshold;
+* the RANSAC winner: the oracle's when its count leads every other solution by
+  more than that band, else a solution whose count is within the band of the
+  oracle's best;
+* the refined pose: within 2e-5 deg and 2e-4 m (+ 1e-6 of the camera
+  distance) of the oracle's; the final inlier mask identical on matches clear
+  of the threshold.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import pnp as OP
+from paper_2507_15683_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _rot_deg(Ra, Rb):
+    """Angle of Ra Rb^T in degrees, from its skew part (accurate near zero,
+    where the arccos of the trace loses half the digits)."""
+    M = Ra @ Rb.T
+    s = 0.5 * np.linalg.norm([M[2, 1] - M[1, 2], M[0, 2] - M[2, 0], M[1, 0] - M[0, 1]])
+    c = 0.5 * (np.trace(M) - 1.0)
+    return math.degrees(math.atan2(s, c))
+
+
+def _synthetic(seed, W=320, H=240, f=300.0, n=20000, out_frac=0.3, alpha_lo=0.2):
+    """Depth / alpha maps at a render pose, matches whose query pixel is the
+    projection (pixel containing it) of the lifted point under a true pose, and
+    random outliers."""
+    g = np.random.default_rng(seed)
+    cam = synth.camera(W, H, f)
+    T_true = synth.look_pose((100.0, 40.0, 60.0), 0.3, math.radians(30.0))
+    T_r = synth.perturb_pose(T_true, g, 2.0, 3.0)
+    yy, xx = np.mgrid[0:H, 0:W]
+    z = 60.0 + 20.0 * np.sin(xx / 37.0) + 15.0 * np.cos(yy / 23.0) + g.uniform(0, 2, (H, W))
+    alpha = g.uniform(alpha_lo, 1.0, (H, W)).astype(np.float32)
+    depth = (alpha * z).astype(np.float32)
+    r = g.choice(W * H, n, replace=False)
+    X, _, valid = OP.lift(depth, alpha, cam, T_r, np.stack([np.zeros(n, np.int64), r, r], 1))
+    pc = X @ T_true[:3, :3].T + T_true[:3, 3]
+    u = cam["fx"] * pc[:, 0] / pc[:, 2] + cam["cx"]
+    v = cam["fy"] * pc[:, 1] / pc[:, 2] + cam["cy"]
+    inside = (pc[:, 2] > 0) & (u >= 0) & (u < W) & (v >= 0) & (v < H)
+    q = np.where(inside, np.floor(v).clip(0, H - 1) * W + np.floor(u).clip(0, W - 1), g.integers(0, W * H, n))
+    n_out = int(out_frac * n)
+    q[:n_out] = g.integers(0, W * H, n_out)
+    matches = np.stack([np.arange(n), q, r], 1).astype(np.int32)
+    return cam, T_true, T_r, depth, alpha, matches
+
+
+def _words(seed, n):
+    return np.random.default_rng(seed).integers(0, 2 ** 32, (n, 3), dtype=np.uint64).astype(np.uint32)
+
+
+def _gpu(gsr, cam, T_r, depth, alpha, matches, words, **kw):
+    S = gsr.PnP(max(1, len(matches)), max(1, len(words)))
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    r = S.solve(cam, T_r, t(depth), t(alpha), t(matches), t(words.view(np.int32)), **kw)
+    S.close()
+    return {k: (v.cpu().numpy() if torch.is_tensor(v) else v) for k, v in r.items()}
+
+
+def _check(g, o, cam, tau):
+    # lifting
+    valid_idx = np.nonzero(o["valid"])[0]
+    assert g["n_valid"] == len(valid_idx)
+    np.testing.assert_array_equal(g["valid_index"], valid_idx)
+    np.testing.assert_allclose(g["points"], o["X"], rtol=1e-9, atol=1e-9)
+    rs = o["ransac"]
+    n_hyp = len(rs["hyps"])
+    # hypotheses
+    compared, loose = 0, 0
+    for h in range(n_hyp):
+        sols = rs["hyps"][h]
+        gc = g["hyp_counts"][h]
+        if rs["near_root"][h]:
+            continue
+        assert int((gc >= 0).sum()) == len(sols), (h, gc, len(sols))
+        for s, (R, t, _) in enumerate(sols):
+            P = g["hyp_poses"][h, s]
+            dr = _rot_deg(P[:9].reshape(3, 3), R)
+            dt = np.linalg.norm(P[9:] - t) / (1 + np.linalg.norm(t))
+            # an ill-conditioned sample amplifies the 1e-16 differences of the lifted points
+            assert dr < 1e-3 and dt < 1e-3, (h, s, dr, dt)
+            loose += not (dr < 1e-6 and dt < 1e-6)
+            assert abs(int(gc[s]) - rs["counts"][h][s]) <= rs["ambiguous"][h][s], (h, s, gc[s], rs["counts"][h][s])
+            compared += 1
+    assert compared > 0 and loose <= max(1, compared // 100), (loose, compared)
+    # winner
+    flat = [(c, a, h, s) for h in range(n_hyp) for s, (c, a) in enumerate(zip(rs["counts"][h], rs["ambiguous"][h]))]
+    ob = rs["best"]
+    ob_c = rs["best_count"]
+    ob_a = rs["ambiguous"][ob[0]][ob[1]]
+    others = [c + a for c, a, h, s in flat if (h, s) != ob]
+    clear = not others or ob_c - ob_a > max(others)
+    gb = g["best"]
+    if clear:
+        assert gb == ob, (gb, ob)
+    else:
+        gh, gs_ = gb
+        assert abs(rs["counts"][gh][gs_] - ob_c) <= ob_a + rs["ambiguous"][gh][gs_]
+    # refined pose and inliers
+    Tg, To = g["T"], o["T"]
+    rot, tr = _rot_deg(Tg[:3, :3], To[:3, :3]), float(np.linalg.norm(Tg[:3, 3] - To[:3, 3]))
+    dist = float(np.linalg.norm(To[:3, :3].T @ To[:3, 3]))
+    print("pnp: %d matches, %d with depth, %d inliers (oracle %d); pose diff %.3g deg %.3g m; steps %d"
+          % (len(g["inlier"]), g["n_valid"], g["n_inliers"], o["n_inliers"], rot, tr, g["refine_steps"]))
+    assert rot < 2e-5 and tr < 2e-4 + 1e-6 * dist
+    assert g["refine_steps"] == len(o["history"]) or o["history"][-1] < 3
+    ok = ~o["tie"]
+    gin = g["inlier"][valid_idx].astype(bool)
+    np.testing.assert_array_equal(gin[ok], o["inlier"][ok])
+    assert not np.any(g["inlier"][~o["valid"]])
+    assert abs(g["n_inliers"] - o["n_inliers"]) <= int(o["tie"].sum())
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_pnp_synthetic(gsr, seed):
+    cam, T_true, T_r, depth, alpha, matches = _synthetic(seed)
+    words = _words(100 + seed, 96)
+    o = OP.pnp_ransac(depth, alpha, cam, T_r, matches, words, tau=2.0, refine_iters=10)
+    g = _gpu(gsr, cam, T_r, depth, alpha, matches, words, tau=2.0, refine_iters=10)
+    _check(g, o, cam, 2.0)
+    # the solution explains the planted correspondences: close to the true pose
+    assert _rot_deg(g["T"][:3, :3], T_true[:3, :3]) < 0.05 and np.linalg.norm(g["T"][:3, 3] - T_true[:3, 3]) < 0.2
+
+
+def test_pnp_dense_stage_of_the_oracle(oracle, gsr):
+    """Query features rendered at a pose 2 deg / 3 m from the render pose; the
+    oracle's PMM fine matches, depth and alpha feed both PnP solvers."""
+    from oracle import pmm as PM
+    scene = synth.aerial_scene(71, 30000, extent=(0.0, 200.0, 0.0, 200.0), n_clusters=20, feat_dim=32)
+    cam = synth.camera(240, 136, 175.0)
+    T_q = synth.look_pose((100.0, 40.0, 60.0), 0.0, math.radians(30.0))
+    T_r = synth.perturb_pose(T_q, synth.rng(72), 2.0, 3.0)
+    H, W = cam["height"], cam["width"]
+    rq = oracle.render(scene, cam, T_q, geom64=True, n_threads=16)
+    rr = oracle.render(scene, cam, T_r, geom64=True, n_threads=16)
+    Fq = np.ascontiguousarray(rq["feats"].T.reshape(32, H, W).astype(np.float32))
+    Fr = np.ascontiguousarray(rr["feats"].T.reshape(32, H, W).astype(np.float32))
+    coarse = PM.coarse_pmm(Fq, Fr)
+    fine = PM.fine_pmm(Fq, Fr, coarse["matches"])
+    matches = fine["matches"].astype(np.int32)
+    depth = rr["depth"].reshape(H, W).astype(np.float32)
+    alpha = rr["alpha"].reshape(H, W).astype(np.float32)
+    words = _words(7, 128)
+    o = OP.pnp_ransac(depth, alpha, cam, T_r, matches, words)
+    g = _gpu(gsr, cam, T_r, depth, alpha, matches, words)
+    _check(g, o, cam, 2.0)
+    assert g["n_inliers"] > 0.3 * g["n_valid"]
+
+
+def test_pnp_edge_cases(gsr):
+    cam, T_true, T_r, depth, alpha, matches = _synthetic(3, n=400)
+    words = _words(9, 16)
+    # no matches; no hypotheses; nothing with depth: the render pose comes back
+    for m, w in ((matches[:0], words), (matches, words[:0])):
+        g = _gpu(gsr, cam, T_r, depth, alpha, m, w)
+        assert g["best"] == (-1, -1) and g["refine_steps"] == 0
+        np.testing.assert_allclose(g["T"], T_r, rtol=0, atol=0)
+    g = _gpu(gsr, cam, T_r, depth, np.zeros_like(alpha), matches, words)
+    assert g["n_valid"] == 0 and g["best"] == (-1, -1) and not g["inlier"].any()
+    # repeated indices: hypotheses without solutions
+    rep = np.zeros((4, 3), np.uint32)
+    g = _gpu(gsr, cam, T_r, depth, alpha, matches, rep)
+    assert np.all(g["hyp_counts"] == -1) and g["best"] == (-1, -1)
+    # two matches with depth: no sample of three
+    g = _gpu(gsr, cam, T_r, depth, alpha, matches[:2], words)
+    assert g["best"] == (-1, -1)
+    # a pixel outside the image is an argument error, and nothing reads it
+    bad = matches.copy()
+    bad[5, 2] = cam["width"] * cam["height"]
+    with pytest.raises(gsr.GsError) as e:
+        _gpu(gsr, cam, T_r, depth, alpha, bad, words)
+    assert e.value.status == gsr.GS_ERR_INVALID_ARG
+    S = gsr.PnP(10, 4)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    with pytest.raises(gsr.GsError):  # above the solver's capacity
+        S.solve(cam, T_r, t(depth), t(alpha), t(matches[:11]), t(words[:4].view(np.int32)))
+    with pytest.raises(gsr.GsError):
+        S.solve(cam, T_r, t(depth), t(alpha), t(matches[:10]), t(words[:4].view(np.int32)), tau=0.0)
+    S.close()
+
+
+def test_pnp_full_size_1080p(gsr):
+    """1920 x 1080 maps, 1,000,000 matches (30 % outliers), 128 hypotheses: the
+    size of the dense stage's fine matches at full resolution."""
+    cam, T_true, T_r, depth, alpha, matches = _synthetic(4, W=1920, H=1080, f=1400.0, n=1_000_000)
+    words = _words(11, 128)
+    o = OP.pnp_ransac(depth, alpha, cam, T_r, matches, words)
+    g = _gpu(gsr, cam, T_r, depth, alpha, matches, words)
+    _check(g, o, cam, 2.0)

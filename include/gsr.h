@@ -278,6 +278,10 @@ gs_status gs_scene_stream_stats(gs_scene* scene, int64_t* h2d_bytes, int* reside
                                 int* active_partitions);
 gs_status gs_scene_evict(gs_scene* scene);
 
+/* Gaussian count, SH degree and feature channels of a scene (host pointers,
+ * each may be NULL). Errors: INVALID_ARG (NULL scene). */
+gs_status gs_scene_shape(const gs_scene* scene, int64_t* n, int* sh_degree, int* feat_dim);
+
 /* Kernel timing (CUDA events recorded on the call's stream around every
  * launch of every call while enabled). Kernel order of the arrays below:
  * projection (discrete layer), shading (conic, colour, centre, Jacobian),

@@ -37,6 +37,10 @@ typedef struct gs_pmm gs_pmm;
 gs_status gs_pmm_create(int channels, int height, int width, gs_pmm** out);
 void gs_pmm_destroy(gs_pmm* matcher);
 
+/* The feature-map shape the matcher was created for (host pointers, each may
+ * be NULL). Errors: INVALID_ARG (NULL matcher). */
+gs_status gs_pmm_shape(const gs_pmm* matcher, int* channels, int* height, int* width);
+
 /* Results of the last gs_pmm_match; the device arrays belong to the matcher
  * and stay valid until its next call or destruction. A cell is a coarse
  * position, index cy * (W / 8) + cx; a pixel is y * W + x. */

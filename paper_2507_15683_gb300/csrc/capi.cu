@@ -1096,6 +1096,15 @@ gs_status gs_scene_stream_stats(gs_scene* s, int64_t* h2d_bytes, int* resident_p
   return GS_OK;
 }
 
+gs_status gs_scene_shape(const gs_scene* s, int64_t* n, int* sh_degree, int* feat_dim) {
+  g_err.clear();
+  GS_TRY(check_scene(s));
+  if (n) *n = s->n;
+  if (sh_degree) *sh_degree = s->sh_degree;
+  if (feat_dim) *feat_dim = s->feat_dim;
+  return GS_OK;
+}
+
 gs_status gs_scene_evict(gs_scene* s) {
   g_err.clear();
   GS_TRY(check_scene(s));

@@ -717,6 +717,14 @@ gs_status gs_pmm_create(int channels, int height, int width, gs_pmm** out) {
   return GS_OK;
 }
 
+gs_status gs_pmm_shape(const gs_pmm* m, int* channels, int* height, int* width) {
+  if (!m) return pmm_fail(GS_ERR_INVALID_ARG, "matcher is NULL");
+  if (channels) *channels = m->C;
+  if (height) *height = m->H;
+  if (width) *width = m->W;
+  return GS_OK;
+}
+
 void gs_pmm_destroy(gs_pmm* m) {
   if (!m) return;
   cudaSetDevice(m->device);

@@ -77,6 +77,23 @@ class gs_pnp_result(ctypes.Structure):
                 ("hyp_poses", ctypes.c_void_p)]
 
 
+GS_LOCALIZE_MAX_ROUNDS = 8
+
+
+class gs_localize_opts(ctypes.Structure):
+    _fields_ = [("n_rounds", ctypes.c_int), ("pmm_tau", ctypes.c_float), ("max_angle_deg", ctypes.c_double),
+                ("n_hypotheses", ctypes.c_int), ("pnp", gs_pnp_opts)]
+
+
+class gs_localize_result(ctypes.Structure):
+    _fields_ = [("T_cw", ctypes.c_double * 16), ("reliable", ctypes.c_int), ("n_rounds", ctypes.c_int),
+                ("round_T", (ctypes.c_double * 16) * GS_LOCALIZE_MAX_ROUNDS),
+                ("angle_deg", ctypes.c_double * GS_LOCALIZE_MAX_ROUNDS),
+                ("trans", ctypes.c_double * GS_LOCALIZE_MAX_ROUNDS),
+                ("n_matches", ctypes.c_int64 * GS_LOCALIZE_MAX_ROUNDS),
+                ("n_inliers", ctypes.c_int64 * GS_LOCALIZE_MAX_ROUNDS)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError("libgsr.so is not built (run: python -m paper_2507_15683_gb300.build)")
@@ -110,6 +127,11 @@ def _load():
         "gs_pmm_create": [st, st, st, P(vp)],
         "gs_pmm_match": [vp, vp, vp, ctypes.c_float, P(gs_pmm_result), vp],
         "gs_pnp_create": [i64, st, P(vp)],
+        "gs_pose_difference": [P(gs_pose), P(gs_pose), P(ctypes.c_double), P(ctypes.c_double)],
+        "gs_dense_localize": [vp, vp, vp, P(gs_camera), P(gs_pose), vp, vp, P(gs_localize_opts),
+                              P(gs_localize_result), vp],
+        "gs_scene_shape": [vp, vp, vp, vp],
+        "gs_pmm_shape": [vp, vp, vp, vp],
         "gs_pnp_solve": [vp, P(gs_camera), P(gs_pose), vp, vp, vp, i64, vp, st, P(gs_pnp_opts), P(gs_pnp_result), vp],
     }
     for name, args in sigs.items():
@@ -131,6 +153,8 @@ def _load():
     L.gs_pnp_destroy.restype = None
     L.gs_pnp_defaults.argtypes = []
     L.gs_pnp_defaults.restype = gs_pnp_opts
+    L.gs_localize_defaults.argtypes = []
+    L.gs_localize_defaults.restype = gs_localize_opts
     L.gs_last_error.argtypes = []
     L.gs_last_error.restype = ctypes.c_char_p
     L.gs_version.argtypes = []
@@ -677,3 +701,37 @@ class PnP:
                 "points": v(r.points, (nv, 3), "<f8") if nv else empty((0, 3), torch.float64),
                 "hyp_counts": v(r.hyp_counts, (nh, 4), "<i4") if nh else empty((0, 4), torch.int32),
                 "hyp_poses": v(r.hyp_poses, (nh, 4, 12), "<f8") if nh else empty((0, 4, 12), torch.float64)}
+
+
+# ---- dense stage with Algorithm 2's consistency check ------------------------------------------
+def gs_pose_difference(T1, T2):
+    """Algorithm 2's Psi: (angle in degrees, translation distance)."""
+    a, d = ctypes.c_double(), ctypes.c_double()
+    _check(lib.gs_pose_difference(ctypes.byref(pose(T1)), ctypes.byref(pose(T2)), ctypes.byref(a), ctypes.byref(d)))
+    return a.value, d.value
+
+
+def gs_localize_defaults() -> gs_localize_opts:
+    return lib.gs_localize_defaults()
+
+
+def dense_localize(scene, matcher, solver, cam, T_init, feat_query, words, n_rounds=3, n_hypotheses=None,
+                   pmm_tau=0.1, max_angle_deg=20.0, tau=2.0, min_alpha=0.5, refine_iters=10) -> dict:
+    """Algorithm 2 around n rounds of render -> PMM -> PnP. feat_query: (32, H, W)
+    float32 CUDA tensor; words: (n_rounds, n_hypotheses, 3) 32-bit CUDA tensor."""
+    import torch
+    if not (feat_query.is_cuda and feat_query.dtype == torch.float32 and feat_query.is_contiguous()):
+        raise ValueError("feat_query must be a contiguous float32 CUDA tensor")
+    if not (words.is_cuda and words.is_contiguous() and words.element_size() == 4 and words.dim() == 3):
+        raise ValueError("words must be a contiguous 32-bit CUDA tensor (rounds, hypotheses, 3)")
+    nh = int(words.shape[1]) if n_hypotheses is None else int(n_hypotheses)
+    o = gs_localize_opts(n_rounds, pmm_tau, max_angle_deg, nh, gs_pnp_opts(tau, min_alpha, refine_iters))
+    r = gs_localize_result()
+    _check(lib.gs_dense_localize(scene.handle, matcher.handle, solver.handle, ctypes.byref(camera(cam)),
+                                 ctypes.byref(pose(T_init)), feat_query.data_ptr(), words.data_ptr(),
+                                 ctypes.byref(o), ctypes.byref(r), _stream()))
+    n = r.n_rounds
+    return {"T": np.array(r.T_cw[:], np.float64).reshape(4, 4), "reliable": bool(r.reliable), "n_rounds": n,
+            "round_T": [np.array(r.round_T[i][:], np.float64).reshape(4, 4) for i in range(n)],
+            "angle_deg": list(r.angle_deg[:max(0, n - 1)]), "trans": list(r.trans[:max(0, n - 1)]),
+            "n_matches": list(r.n_matches[:n]), "n_inliers": list(r.n_inliers[:n])}

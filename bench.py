@@ -56,6 +56,10 @@ COMPOSITE_DRAM_BYTES = 83_501_056  # 80,544,000 read + 2,957,056 written
 FLOPS_PER_VIS_BLEND = 21
 # DRAM bytes of one reverse-pass launch (ncu, same kernel): 37,470,720 read + 20,480 written
 VIS_BACKWARD_DRAM_BYTES = 37_491_200
+# PnP scoring (Eq. 10 RANSAC): one (solution, match) pair is p = R X + t (9 FMA),
+# x - a z, y - b z (2 FMA), the scaled squares (2 mul + 1 FMA), tau z twice (2 mul),
+# the threshold difference (1 FMA) and 2 compares: 33 fp32 operations (FMA = 2)
+FLOPS_PER_PNP_PAIR = 33
 
 
 def parse():
@@ -69,6 +73,7 @@ def parse():
     p.add_argument("--no-large", action="store_true")
     p.add_argument("--no-pmm", action="store_true")
     p.add_argument("--no-vis", action="store_true")
+    p.add_argument("--no-dense", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     return p.parse_args()
@@ -371,6 +376,11 @@ def main():
     if not args.no_vis:
         vis = bench_visibility(gsr, torch, S, scene, cam, T_q, flush, max(3, args.steps // 2), args.warmup,
                                with_oracle=rank == 0 and world == 1 and not args.no_cpu)
+    # dense stage at 1080p: PMM -> PnP + RANSAC (Eq. 10), and three rounds with Algorithm 2
+    dense = None
+    if not args.no_dense:
+        dense = bench_dense(gsr, synth, torch, max(3, args.steps // 2), args.warmup, pk_for_pmm(),
+                            with_oracle=rank == 0 and world == 1 and not args.no_cpu)
     clk = clocks.stop()
 
     cpu = None
@@ -394,7 +404,8 @@ def main():
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 7 * 8},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roof, "kernels": kernels,
-        "refine": refine, "batched": batched, "large": large, "pmm": pmm, "visibility": vis, "cpu_baseline": cpu,
+        "refine": refine, "batched": batched, "large": large, "pmm": pmm, "visibility": vis, "dense": dense,
+        "cpu_baseline": cpu,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -628,6 +639,102 @@ def bench_visibility(gsr, torch, S, scene, cam, T, flush, steps, warmup, with_or
         out["cpu_baseline"] = {"value": len(sample) / dt, "unit": "Gaussians/s", "cores": n_thr, "kind": "oracle",
                                "sample": "fp64 oracle mean gradient (forward mode, one Gaussian at a time over its "
                                          "tile rectangle) of %d Gaussians with M^r, %.2f s" % (len(sample), dt)}
+    return out
+
+
+def bench_dense(gsr, synth, torch, steps, warmup, pk_src, with_oracle):
+    """The dense stage of Sec. 3.4 at 1920x1080 on 1M Gaussians with 32 BF16
+    features. The query image's feature map is the library's render at the
+    query pose; the render pose is 2 deg / 5 m away. One round: PMM of the
+    query features against the render's, PnP + RANSAC (128 P3P samples) on the
+    fine matches lifted through the rendered depth. Then gs_dense_localize: three
+    such rounds from the render pose and Algorithm 2's check."""
+    pk, src = pk_src
+    scene = synth.aerial_scene(2, 1_000_000, feat_dim=32)
+    cam = synth.aerial_camera()
+    T_r = synth.aerial_pose()
+    T_q = synth.perturb_pose(T_r, synth.rng(100), 2.0, 5.0)
+    H, W = cam["height"], cam["width"]
+    S = gsr.Scene(scene)
+    oq = S.alloc_outputs(cam, feat_dim=32, last_idx=False)
+    S.render(cam, T_q, oq)
+    Fq = oq["feats"].contiguous()
+    orr = S.alloc_outputs(cam, feat_dim=32, last_idx=False)
+    S.render(cam, T_r, orr)
+    M = gsr.Matcher(H, W)
+    res = M.match(Fq, orr["feats"].contiguous())
+    fine = res["fine"].contiguous()
+    n_hyp = 128
+    words_np = np.random.default_rng(5).integers(0, 2 ** 32, (3, n_hyp, 3), dtype=np.uint64).astype(np.uint32)
+    words = torch.from_numpy(words_np.view(np.int32)).cuda()
+    P = gsr.PnP(H * W, n_hyp)
+    depth, alpha = orr["depth"].contiguous(), orr["alpha"].contiguous()
+    for _ in range(warmup):
+        r = P.solve(cam, T_r, depth, alpha, fine, words[0])
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for a, b in ev:
+        a.record()
+        r = P.solve(cam, T_r, depth, alpha, fine, words[0])
+        b.record()
+    torch.cuda.synchronize()
+    ms_pnp = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    gsr.gs_pnp_set_timing(P.handle, True)
+    gsr.gs_pnp_phase_times(P.handle)
+    for _ in range(steps):
+        P.solve(cam, T_r, depth, alpha, fine, words[0])
+    ph_ms, ph_n = gsr.gs_pnp_phase_times(P.handle)
+    gsr.gs_pnp_set_timing(P.handle, False)
+    phases = {k: float(ph_ms[i] / max(ph_n, 1)) for i, k in enumerate(gsr.PNP_PHASES)}
+    n_sol = int((r["hyp_counts"] >= 0).sum().item())
+    pairs = n_sol * int(r["n_valid"])
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12
+    ach = pairs * FLOPS_PER_PNP_PAIR / (phases["score"] * 1e-3) / 1e12
+    err = _pose_errors(r["T"], T_q)
+    # Algorithm 2: three rounds from the render pose
+    loc = gsr.dense_localize(S, M, P, cam, T_r, Fq, words)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(max(2, steps // 2)):
+        loc = gsr.dense_localize(S, M, P, cam, T_r, Fq, words)
+    torch.cuda.synchronize()
+    ms_loc = (time.perf_counter() - t0) * 1e3 / max(2, steps // 2)
+    out = {"workload": "dense stage at 1920x1080, 1M Gaussians with 32-channel BF16 features; query features "
+                       "rendered at a pose 2 deg / 5 m from the render pose; PMM fine matches -> PnP + RANSAC "
+                       "(128 P3P samples, tau 2 px, 5 Gauss-Newton steps); Algorithm 2 over 3 rounds",
+           "fine_matches": int(fine.shape[0]), "with_depth": int(r["n_valid"]), "inliers": int(r["n_inliers"]),
+           "solutions": n_sol, "pnp_ms": ms_pnp, "pnp_phases_ms": phases,
+           "pose_error_after_one_round": {"rot_deg": err[0], "centre_m": err[1]},
+           "start_error": dict(zip(("rot_deg", "centre_m"), _pose_errors(T_r, T_q))),
+           "roofline": {"bound": "alu", "kernel": "k_pnp_score (every P3P solution against every match)",
+                        "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
+                        "traffic": None,
+                        "work": "%d solutions x %d matches x %d fp32 ops" % (n_sol, int(r["n_valid"]),
+                                                                         FLOPS_PER_PNP_PAIR),
+                        "peak_source": "%d SMs x 128 fp32 lanes x 2 x %.0f MHz (%s max clock)"
+                                       % (n_sm, sm_max, src)},
+           "algorithm2": {"ms_per_localisation": ms_loc, "rounds": loc["n_rounds"], "reliable": loc["reliable"],
+                          "angles_deg": loc["angle_deg"], "matches": loc["n_matches"], "inliers": loc["n_inliers"],
+                          "final_error": dict(zip(("rot_deg", "centre_m"), _pose_errors(loc["T"], T_q)))}}
+    if with_oracle:
+        from oracle import oracle as O
+        from oracle import pnp as OPn
+        O.build()
+        m_np = fine.cpu().numpy()
+        d_np, a_np = depth.cpu().numpy(), alpha.cpu().numpy()
+        n_s = 8
+        t0 = time.perf_counter()
+        OPn.pnp_ransac(d_np, a_np, cam, T_r, m_np, words_np[0][:n_s], refine_iters=2)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": n_s / dt, "unit": "hypotheses/s (lift + P3P + scoring, 2 GN steps)",
+                               "cores": os.cpu_count() or 1, "kind": "oracle",
+                               "sample": "fp64 oracle PnP + RANSAC with %d of the 128 samples on all %d fine matches, "
+                                         "%.2f s" % (n_s, int(fine.shape[0]), dt)}
+    P.close()
+    M.close()
+    S.close()
     return out
 
 

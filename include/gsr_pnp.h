@@ -47,7 +47,7 @@ typedef struct {
   int refine_iters;  /* Gauss-Newton steps after RANSAC, 0 .. 100 */
 } gs_pnp_opts;
 
-/* Defaults: tau 2 px, min_alpha 0.5, 10 refinement steps. */
+/* Defaults: tau 2 px, min_alpha 0.5, 5 refinement steps. */
 gs_pnp_opts gs_pnp_defaults(void);
 
 /* A solver for up to max_matches matches and max_hypotheses RANSAC samples.
@@ -90,6 +90,16 @@ typedef struct {
 gs_status gs_pnp_solve(gs_pnp* solver, const gs_camera* cam, const gs_pose* T_render, const float* depth,
                        const float* alpha, const int32_t* matches, int64_t n_matches, const uint32_t* words,
                        int n_hypotheses, const gs_pnp_opts* opts, gs_pnp_result* out, void* stream);
+
+/* Phase timing: while enabled, every gs_pnp_solve records CUDA events on its
+ * stream around its GS_PNP_PHASES phases -- lifting (flags, scan, lift), P3P,
+ * scoring, RANSAC argmax, Gauss-Newton refinement (all steps), final inliers --
+ * and adds their durations. gs_pnp_phase_times returns the sums (ms, host
+ * array of GS_PNP_PHASES) and the number of timed calls (may be NULL), then
+ * resets them. Errors: INVALID_ARG, CUDA. */
+#define GS_PNP_PHASES 6
+gs_status gs_pnp_set_timing(gs_pnp* solver, int enable);
+gs_status gs_pnp_phase_times(gs_pnp* solver, double* total_ms, int64_t* calls);
 
 #ifdef __cplusplus
 }

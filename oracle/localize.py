@@ -36,7 +36,7 @@ def consistency(poses, max_angle_deg=20.0):
 
 
 def dense_round(scene, cam, T, feat_query, words, pmm_tau=PM.TAU, tau=2.0, min_alpha=OP.MIN_ALPHA,
-                refine_iters=10, n_threads=16):
+                refine_iters=5, n_threads=16):
     """One render -> PMM -> PnP round from pose T. Returns (pose, fine matches, pnp record)."""
     H, W = int(cam["height"]), int(cam["width"])
     r = O.render(scene, cam, T, geom64=True, n_threads=n_threads)

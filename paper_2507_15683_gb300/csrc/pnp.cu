@@ -4,8 +4,8 @@
 //      the world point R_r^T (z K^-1 (x + .5, y + .5, 1) - t_r), z = depth /
 //      alpha (fp64), compacted in match order;
 //   2. hypotheses: one thread per RANSAC sample solves P3P in fp64 (Grunert's
-//      quartic in v = s3 / s1, real roots isolated between the roots of its
-//      derivatives and bisected to full precision, triad absolute orientation);
+//      quartic in v = s3 / s1, Ferrari's closed form polished by Newton,
+//      triad absolute orientation);
 //   3. scoring: every solution against every lifted match, packed fp32
 //      (__ffma2_rn on pairs of matches), inlier counts per solution;
 //   4. the RANSAC argmax (most inliers, lowest index on ties);
@@ -40,6 +40,7 @@ constexpr int kGnBlocks = 304;    // accumulation blocks (fixed, so the summatio
 
 struct Cam {
   double fx, fy, cx, cy;
+  double ifx, ify;  // 1 / fx, 1 / fy
   int W, H;
 };
 
@@ -165,9 +166,15 @@ __global__ void __launch_bounds__(kThreads) k_pnp_lift(const int32_t* __restrict
     if (v) {
       const unsigned o = off + before + (unsigned)__popc(b & ((1u << lane) - 1u));
       const int qp = m[3 * i + 1], rp = m[3 * i + 2];
-      const double z = (double)depth[rp] / (double)alpha[rp];
-      const double xc = z * (((double)(rp % cam.W) + 0.5 - cam.cx) / cam.fx);
-      const double yc = z * (((double)(rp / cam.W) + 0.5 - cam.cy) / cam.fy);
+      // z = depth / alpha in fp64 without a division: the binary32 reciprocal
+      // refined by one Newton step (48 bits), then one correction of the quotient
+      const double A = alpha[rp], D = depth[rp];
+      double rcp = (double)(1.0f / alpha[rp]);
+      rcp = rcp * (2.0 - A * rcp);
+      double z = D * rcp;
+      z = fma(rcp, fma(-z, A, D), z);
+      const double xc = z * (((double)(rp % cam.W) + 0.5 - cam.cx) * cam.ifx);
+      const double yc = z * (((double)(rp / cam.W) + 0.5 - cam.cy) * cam.ify);
       const double d0 = xc - Tr.v[9], d1 = yc - Tr.v[10], d2 = z - Tr.v[11];
       const double* R = Tr.v;
       const double X = R[0] * d0 + R[3] * d1 + R[6] * d2;  // R^T d
@@ -179,7 +186,7 @@ __global__ void __launch_bounds__(kThreads) k_pnp_lift(const int32_t* __restrict
       X32[o] = make_float4((float)X, (float)Y, (float)Z, 0.0f);
       const double px = (double)(qp % cam.W) + 0.5, py = (double)(qp / cam.W) + 0.5;
       pix[o] = make_float2((float)px, (float)py);
-      nab[o] = make_float2((float)(-(px - cam.cx) / cam.fx), (float)(-(py - cam.cy) / cam.fy));
+      nab[o] = make_float2((float)(-(px - cam.cx) * cam.ifx), (float)(-(py - cam.cy) * cam.ify));
       vidx[o] = (int32_t)i;
     }
     off += total;
@@ -188,81 +195,87 @@ __global__ void __launch_bounds__(kThreads) k_pnp_lift(const int32_t* __restrict
 }
 
 // ------------------------------------------------------------------ P3P (fp64)
-// Real polynomial c[0] + c[1] x + ... + c[deg] x^deg.
-__device__ double peval(const double* c, int deg, double x) {
-  double s = c[deg];
-  for (int k = deg - 1; k >= 0; --k) s = s * x + c[k];
-  return s;
-}
-
-// Roots of c (degree deg) in the open interval (lo, hi], one per sign change
-// between consecutive points of lo < crit[...] < hi (crit sorted: the roots of
-// the derivative), each bisected until the bracket cannot shrink. Returns the
-// count; roots ascending.
-__device__ int roots_between(const double* c, int deg, const double* crit, int ncrit, double lo, double hi,
-                             double* out) {
-  double pts[6];
-  int np = 0;
-  pts[np++] = lo;
-  for (int k = 0; k < ncrit; ++k)
-    if (crit[k] > lo && crit[k] < hi) pts[np++] = crit[k];
-  pts[np++] = hi;
-  int nr = 0;
-  for (int k = 0; k + 1 < np; ++k) {
-    double a = pts[k], b = pts[k + 1];
-    double fa = peval(c, deg, a), fb = peval(c, deg, b);
-    if (fb == 0.0) {  // a root exactly at a point: taken as the right end of its interval
-      if (b > lo) out[nr++] = b;
-      continue;
-    }
-    if (fa == 0.0 || (fa < 0.0) == (fb < 0.0)) continue;
-    for (int it = 0; it < 2100; ++it) {
-      const double mid = 0.5 * (a + b);
-      if (!(mid > a && mid < b)) break;
-      const double fm = peval(c, deg, mid);
-      if (fm == 0.0) {
-        a = b = mid;
-        break;
-      }
-      if ((fm < 0.0) == (fa < 0.0)) {
-        a = mid;
-        fa = fm;
-      } else {
-        b = mid;
-        fb = fm;
-      }
-    }
-    out[nr++] = fabs(fa) <= fabs(fb) ? a : b;
-  }
-  return nr;
-}
-
-// Positive real roots of the quartic q (q[4] != 0), ascending.
-__device__ int quartic_positive_roots(const double* q, double* out) {
-  double mx = 0.0;
-  for (int k = 0; k < 4; ++k) mx = fmax(mx, fabs(q[k] / q[4]));
-  const double B = 1.0 + mx;  // Cauchy bound on |root|
-  // derivative cubic and its derivative quadratic
-  const double c3[4] = {q[1], 2.0 * q[2], 3.0 * q[3], 4.0 * q[4]};
-  const double a2 = 3.0 * c3[3], a1 = 2.0 * c3[2], a0 = c3[1];
-  double qr[2];
-  int nq = 0;
-  const double disc = a1 * a1 - 4.0 * a2 * a0;
-  if (disc >= 0.0) {
+// Real roots of the monic quartic x^4 + a x^3 + b x^2 + c x + d by Ferrari's
+// method in fp64: with x = y - a/4 the depressed quartic y^4 + p y^2 + q y + r
+// equals (y^2 + m)^2 - (s y - q / (2 s))^2, s^2 = 2 m - p, for the largest root
+// m of the resolvent cubic 8 m^3 - 4 p m^2 - 8 r m + 4 p r - q^2 (Cardano or the
+// trigonometric form, then Newton-polished); y solves y^2 +- s y + m -+ q/(2 s)
+// = 0 (for q = 0: y^2 = the roots of z^2 + p z + r). The closed form runs in a
+// few hundred fp64 operations, against thousands for bracketing: fp64 is slow
+// on this part. Each real root is then polished by two Newton steps on the
+// original quartic. Returns the count; roots ascending.
+__device__ int quartic_real_roots(const double* q4, double* out) {
+  const double a = q4[3] / q4[4], b = q4[2] / q4[4], c = q4[1] / q4[4], d = q4[0] / q4[4];
+  const double a2 = a * a;
+  const double p = b - 0.375 * a2;
+  const double q = c - 0.5 * a * b + 0.125 * a2 * a;
+  const double r = d - 0.25 * a * c + 0.0625 * a2 * b - (3.0 / 256.0) * a2 * a2;
+  // resolvent m^3 + A m^2 + B m + C, A = -p/2, B = -r, C = (4 p r - q^2) / 8
+  const double A = -0.5 * p, B = -r, C = 0.125 * (4.0 * p * r - q * q);
+  const double P3 = B - A * A / 3.0, Q3 = 2.0 * A * A * A / 27.0 - A * B / 3.0 + C;
+  const double disc = 0.25 * Q3 * Q3 + P3 * P3 * P3 / 27.0;
+  double t;
+  if (disc > 0.0) {  // one real root
     const double sq = sqrt(disc);
-    const double h = -0.5 * (a1 + (a1 >= 0.0 ? sq : -sq));
-    double r1 = h / a2, r2 = (h != 0.0) ? a0 / h : r1;
-    if (r1 > r2) {
-      const double t = r1;
-      r1 = r2;
-      r2 = t;
-    }
-    qr[nq++] = r1;
-    qr[nq++] = r2;
+    const double u = cbrt(-0.5 * Q3 - copysign(sq, Q3));
+    t = (u != 0.0) ? u - P3 / (3.0 * u) : 0.0;
+  } else {  // three real roots: the largest
+    const double rr = sqrt(fmax(-P3 / 3.0, 0.0));
+    double ca = (rr > 0.0) ? -0.5 * Q3 / (rr * rr * rr) : 0.0;
+    ca = fmin(1.0, fmax(-1.0, ca));
+    t = 2.0 * rr * cos(acos(ca) / 3.0);
   }
-  double cr[3];
-  const int nc = roots_between(c3, 3, qr, nq, -B, B, cr);
-  return roots_between(q, 4, cr, nc, 0.0, B, out);
+  double m = t - A / 3.0;
+  for (int it = 0; it < 2; ++it) {  // polish on the resolvent
+    const double f = ((m + A) * m + B) * m + C, df = (3.0 * m + 2.0 * A) * m + B;
+    if (df != 0.0) m -= f / df;
+  }
+  double y[4];
+  int ny = 0;
+  const double s2 = 2.0 * m - p;
+  if (s2 > 1e-14 * (fabs(p) + fabs(m) + 1e-300)) {
+    const double s = sqrt(s2), h = q / (2.0 * s);
+    const double d1 = s2 - 4.0 * (m - h), d2 = s2 - 4.0 * (m + h);
+    if (d1 >= 0.0) {
+      const double e = sqrt(d1);
+      y[ny++] = 0.5 * (-s - e);
+      y[ny++] = 0.5 * (-s + e);
+    }
+    if (d2 >= 0.0) {
+      const double e = sqrt(d2);
+      y[ny++] = 0.5 * (s - e);
+      y[ny++] = 0.5 * (s + e);
+    }
+  } else {  // biquadratic
+    const double dz = p * p - 4.0 * r;
+    if (dz >= 0.0) {
+      const double e = sqrt(dz);
+      const double z1 = 0.5 * (-p - e), z2 = 0.5 * (-p + e);
+      for (double z : {z1, z2})
+        if (z >= 0.0) {
+          const double w = sqrt(z);
+          y[ny++] = -w;
+          y[ny++] = w;
+        }
+    }
+  }
+  int n = 0;
+  for (int k = 0; k < ny; ++k) {
+    double x = y[k] - 0.25 * a;
+    for (int it = 0; it < 2; ++it) {
+      const double f = (((x + a) * x + b) * x + c) * x + d;
+      const double df = ((4.0 * x + 3.0 * a) * x + 2.0 * b) * x + c;
+      if (df != 0.0) x -= f / df;
+    }
+    out[n++] = x;
+  }
+  for (int i = 1; i < n; ++i)  // ascending (insertion sort, n <= 4)
+    for (int j = i; j > 0 && out[j - 1] > out[j]; --j) {
+      const double tmp = out[j];
+      out[j] = out[j - 1];
+      out[j - 1] = tmp;
+    }
+  return n;
 }
 
 __device__ void frame3(const double* P0, const double* P1, const double* P2, double F[3][3], bool* ok) {
@@ -284,7 +297,7 @@ __device__ void frame3(const double* P0, const double* P1, const double* P2, dou
   }
 }
 
-__global__ void __launch_bounds__(128) k_pnp_p3p(const double* __restrict__ X64, const float2* __restrict__ pix,
+__global__ void __launch_bounds__(32) k_pnp_p3p(const double* __restrict__ X64, const float2* __restrict__ pix,
                                                  const State* __restrict__ st, const uint32_t* __restrict__ words,
                                                  int n_hyp, Cam cam, double* __restrict__ poses64,
                                                  float4* __restrict__ poses32, int* __restrict__ counts) {
@@ -336,7 +349,7 @@ __global__ void __launch_bounds__(128) k_pnp_p3p(const double* __restrict__ X64,
     for (int j = 0; j < 2; ++j) Q[i + j] -= 4.0 * cg * N[i] * D[j];
   if (Q[4] == 0.0) return;
   double roots[4];
-  const int nr = quartic_positive_roots(Q, roots);
+  const int nr = quartic_real_roots(Q, roots);
   int ns = 0;
   double FX[3][3];
   bool okx;
@@ -560,14 +573,16 @@ __device__ void se3_left(const double xi[6], double T[kPose]) {
   const double t2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
   const double th = sqrt(t2);
   double a, b, c;
-  if (th < 1e-6) {
-    a = 1.0 - t2 / 6.0;
-    b = 0.5 - t2 / 24.0;
-    c = 1.0 / 6.0 - t2 / 120.0;
+  if (th < 0.05) {  // Maclaurin series of sin t / t, (1 - cos t) / t^2, (t - sin t) / t^3 to t^8 (< 1e-20 left)
+    a = 1.0 + t2 * (-1.0 / 6 + t2 * (1.0 / 120 + t2 * (-1.0 / 5040 + t2 * (1.0 / 362880))));
+    b = 0.5 + t2 * (-1.0 / 24 + t2 * (1.0 / 720 + t2 * (-1.0 / 40320 + t2 * (1.0 / 3628800))));
+    c = 1.0 / 6 + t2 * (-1.0 / 120 + t2 * (1.0 / 5040 + t2 * (-1.0 / 362880 + t2 * (1.0 / 39916800))));
   } else {
-    a = sin(th) / th;
-    b = (1.0 - cos(th)) / t2;
-    c = (th - sin(th)) / (t2 * th);
+    double sn, cs;
+    sincos(th, &sn, &cs);
+    a = sn / th;
+    b = (1.0 - cs) / t2;
+    c = (th - sn) / (t2 * th);
   }
   const double Kx[3][3] = {{0.0, -w[2], w[1]}, {w[2], 0.0, -w[0]}, {-w[1], w[0], 0.0}};
   double E[3][3], V[3][3];
@@ -587,17 +602,27 @@ __device__ void se3_left(const double xi[6], double T[kPose]) {
   for (int q = 0; q < 3; ++q) T[9 + q] = t[q];
 }
 
-__global__ void __launch_bounds__(32) k_pnp_gn_solve(const double* __restrict__ partials, State* __restrict__ st) {
+constexpr int kSolveParts = 8;  // partial sums per component in the solve kernel
+
+__global__ void __launch_bounds__(kGnVals * kSolveParts) k_pnp_gn_solve(const double* __restrict__ partials,
+                                                                         State* __restrict__ st) {
+  __shared__ double part[kGnVals][kSolveParts];
   __shared__ double s[kGnVals];
   if (!st->active) return;
-  const int k = threadIdx.x;
-  if (k < kGnVals) {
+  {  // component k, blocks j, j + 8, ... in order; then the 8 parts in order
+    const int k = threadIdx.x / kSolveParts, j = threadIdx.x % kSolveParts;
     double a = 0.0;
-    for (int b = 0; b < kGnBlocks; ++b) a += partials[(size_t)b * kGnVals + k];
-    s[k] = a;
+    for (int b = j; b < kGnBlocks; b += kSolveParts) a += partials[(size_t)b * kGnVals + k];
+    part[k][j] = a;
   }
-  __syncwarp();
-  if (k != 0) return;
+  __syncthreads();
+  if (threadIdx.x < kGnVals) {
+    double a = 0.0;
+    for (int j = 0; j < kSolveParts; ++j) a += part[threadIdx.x][j];
+    s[threadIdx.x] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   if (s[27] < 3.0) {
     st->active = 0;
     return;
@@ -610,30 +635,34 @@ __global__ void __launch_bounds__(32) k_pnp_gn_solve(const double* __restrict__ 
       H[c][r] = s[q];
       ++q;
     }
-  for (int j = 0; j < 6; ++j) {  // Cholesky H = L L^T
+  // Cholesky H = L L^T with the reciprocal diagonal: one reciprocal square
+  // root per column and multiplications (fp64 division is a long sequence here)
+  double inv[6];
+  for (int j = 0; j < 6; ++j) {
     double d = H[j][j];
     for (int m = 0; m < j; ++m) d -= L[j][m] * L[j][m];
     if (!(d > 0.0)) {
       st->active = 0;
       return;
     }
-    L[j][j] = sqrt(d);
+    inv[j] = rsqrt(d);
+    L[j][j] = d * inv[j];
     for (int i = j + 1; i < 6; ++i) {
       double e = H[i][j];
       for (int m = 0; m < j; ++m) e -= L[i][m] * L[j][m];
-      L[i][j] = e / L[j][j];
+      L[i][j] = e * inv[j];
     }
   }
   double y[6], xi[6];
   for (int i = 0; i < 6; ++i) {  // L y = -g
     double e = -s[21 + i];
     for (int m = 0; m < i; ++m) e -= L[i][m] * y[m];
-    y[i] = e / L[i][i];
+    y[i] = e * inv[i];
   }
   for (int i = 5; i >= 0; --i) {  // L^T xi = y
     double e = y[i];
     for (int m = i + 1; m < 6; ++m) e -= L[m][i] * xi[m];
-    xi[i] = e / L[i][i];
+    xi[i] = e * inv[i];
   }
   double T[kPose];
   for (int p = 0; p < kPose; ++p) T[p] = st->T[p];
@@ -692,6 +721,12 @@ struct gs_pnp {
   double* partials = nullptr;
   State* st = nullptr;
   State* st_host = nullptr;
+  // phase timing (gs_pnp_set_timing): events around lift, P3P, scoring, argmax,
+  // refinement and the final inlier pass
+  bool timing = false;
+  cudaEvent_t ev[GS_PNP_PHASES + 1] = {};
+  double kt_ms[GS_PNP_PHASES] = {};
+  int64_t kt_n = 0;
 };
 
 namespace {
@@ -711,11 +746,34 @@ gs_status pnp_fail(gs_status s, const std::string& msg) {
 
 extern "C" {
 
+gs_status gs_pnp_set_timing(gs_pnp* s, int enable) {
+  gsr::set_last_error("");
+  if (!s) return pnp_fail(GS_ERR_INVALID_ARG, "solver is NULL");
+  PNP_CUDA(cudaSetDevice(s->device));
+  if (enable)
+    for (cudaEvent_t& e : s->ev)
+      if (!e) PNP_CUDA(cudaEventCreate(&e));
+  s->timing = enable != 0;
+  return GS_OK;
+}
+
+gs_status gs_pnp_phase_times(gs_pnp* s, double* total_ms, int64_t* calls) {
+  gsr::set_last_error("");
+  if (!s || !total_ms) return pnp_fail(GS_ERR_INVALID_ARG, "solver and total_ms are required");
+  for (int k = 0; k < GS_PNP_PHASES; ++k) {
+    total_ms[k] = s->kt_ms[k];
+    s->kt_ms[k] = 0.0;
+  }
+  if (calls) *calls = s->kt_n;
+  s->kt_n = 0;
+  return GS_OK;
+}
+
 gs_pnp_opts gs_pnp_defaults(void) {
   gs_pnp_opts o;
   o.tau_px = 2.0f;
   o.min_alpha = 0.5f;
-  o.refine_iters = 10;
+  o.refine_iters = 5;
   return o;
 }
 
@@ -728,6 +786,8 @@ void gs_pnp_destroy(gs_pnp* s) {
                   (void*)s->st})
     if (p) cudaFree(p);
   if (s->st_host) cudaFreeHost(s->st_host);
+  for (cudaEvent_t e : s->ev)
+    if (e) cudaEventDestroy(e);
   delete s;
 }
 
@@ -800,6 +860,8 @@ gs_status gs_pnp_solve(gs_pnp* s, const gs_camera* cam, const gs_pose* T_render,
   c.fy = cam->fy;
   c.cx = cam->cx;
   c.cy = cam->cy;
+  c.ifx = 1.0 / c.fx;
+  c.ify = 1.0 / c.fy;
   c.W = cam->width;
   c.H = cam->height;
   Pose12 Tr;
@@ -808,6 +870,8 @@ gs_status gs_pnp_solve(gs_pnp* s, const gs_camera* cam, const gs_pose* T_render,
     Tr.v[9 + i] = T_render->T_cw[4 * i + 3];
   }
   const float fx = cam->fx, fy = cam->fy, tau = opts->tau_px;
+  auto mark = [&](int k) -> cudaError_t { return s->timing ? cudaEventRecord(s->ev[k], st) : cudaSuccess; };
+  PNP_CUDA(mark(0));
   PNP_CUDA(cudaMemsetAsync(s->st, 0, sizeof(State), st));
   if (n_matches > 0) PNP_CUDA(cudaMemsetAsync(s->mask, 0, (size_t)n_matches, st));
   const int nb = (int)((n_matches + kCompact - 1) / kCompact);
@@ -822,11 +886,15 @@ gs_status gs_pnp_solve(gs_pnp* s, const gs_camera* cam, const gs_pose* T_render,
                                         s->X32, s->nab, s->pix, s->vidx);
     PNP_CUDA(cudaGetLastError());
   }
+  PNP_CUDA(mark(1));
   const int n_poses = n_hypotheses * kSol;
   if (n_hypotheses > 0) {
-    k_pnp_p3p<<<(n_hypotheses + 127) / 128, 128, 0, st>>>(s->X64, s->pix, s->st, words, n_hypotheses, c,
+    k_pnp_p3p<<<(n_hypotheses + 31) / 32, 32, 0, st>>>(s->X64, s->pix, s->st, words, n_hypotheses, c,
                                                           s->poses64, s->poses32, s->counts);
     PNP_CUDA(cudaGetLastError());
+  }
+  PNP_CUDA(mark(2));
+  if (n_hypotheses > 0) {
     if (n_matches > 0) {
       const dim3 grid((unsigned)((n_matches + kThreads * kRow - 1) / (kThreads * kRow)),
                       (unsigned)((n_poses + kScorePoses - 1) / kScorePoses));
@@ -834,21 +902,33 @@ gs_status gs_pnp_solve(gs_pnp* s, const gs_camera* cam, const gs_pose* T_render,
       PNP_CUDA(cudaGetLastError());
     }
   }
+  PNP_CUDA(mark(3));
   k_pnp_best<<<1, 1024, 0, st>>>(s->counts, n_poses, s->poses64, Tr, s->st);
   PNP_CUDA(cudaGetLastError());
+  PNP_CUDA(mark(4));
   for (int it = 0; it < opts->refine_iters; ++it) {
     k_pnp_gn<<<kGnBlocks, kThreads, 0, st>>>(s->X32, s->nab, s->st, s->partials, fx, fy, tau);
     PNP_CUDA(cudaGetLastError());
-    k_pnp_gn_solve<<<1, 32, 0, st>>>(s->partials, s->st);
+    k_pnp_gn_solve<<<1, kGnVals * kSolveParts, 0, st>>>(s->partials, s->st);
     PNP_CUDA(cudaGetLastError());
   }
+  PNP_CUDA(mark(5));
   if (n_matches > 0) {
     const int g = std::min<int64_t>((n_matches + kThreads - 1) / kThreads, (int64_t)s->sm_count * 8);
     k_pnp_final<<<g, kThreads, 0, st>>>(s->X32, s->nab, s->vidx, s->st, s->mask, fx, fy, tau);
     PNP_CUDA(cudaGetLastError());
   }
+  PNP_CUDA(mark(6));
   PNP_CUDA(cudaMemcpyAsync(s->st_host, s->st, sizeof(State), cudaMemcpyDeviceToHost, st));
   PNP_CUDA(cudaStreamSynchronize(st));
+  if (s->timing) {
+    for (int k = 0; k < GS_PNP_PHASES; ++k) {
+      float ms = 0.0f;
+      PNP_CUDA(cudaEventElapsedTime(&ms, s->ev[k], s->ev[k + 1]));
+      s->kt_ms[k] += ms;
+    }
+    s->kt_n += 1;
+  }
   const State& h = *s->st_host;
   std::memset(out, 0, sizeof(*out));
   for (int i = 0; i < 3; ++i) {

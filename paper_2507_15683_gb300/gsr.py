@@ -128,6 +128,8 @@ def _load():
         "gs_pmm_match": [vp, vp, vp, ctypes.c_float, P(gs_pmm_result), vp],
         "gs_pnp_create": [i64, st, P(vp)],
         "gs_pose_difference": [P(gs_pose), P(gs_pose), P(ctypes.c_double), P(ctypes.c_double)],
+        "gs_pnp_set_timing": [vp, st],
+        "gs_pnp_phase_times": [vp, vp, vp],
         "gs_dense_localize": [vp, vp, vp, P(gs_camera), P(gs_pose), vp, vp, P(gs_localize_opts),
                               P(gs_localize_result), vp],
         "gs_scene_shape": [vp, vp, vp, vp],
@@ -658,6 +660,20 @@ def gs_pnp_solve(h, cam: gs_camera, T_render: gs_pose, depth: int, alpha: int, m
     return r
 
 
+PNP_PHASES = ("lift", "p3p", "score", "best", "refine", "final")
+
+
+def gs_pnp_set_timing(h, enable: bool) -> None:
+    _check(lib.gs_pnp_set_timing(h, int(bool(enable))))
+
+
+def gs_pnp_phase_times(h):
+    ms = np.zeros(len(PNP_PHASES), np.float64)
+    n = ctypes.c_int64()
+    _check(lib.gs_pnp_phase_times(h, ms.ctypes.data, ctypes.byref(n)))
+    return ms, n.value
+
+
 class PnP:
     """Dense PnP + RANSAC on rendered depth; ``solve`` returns the pose and copies
     of the device results."""
@@ -676,7 +692,7 @@ class PnP:
         except Exception:
             pass
 
-    def solve(self, cam, T_render, depth, alpha, matches, words, tau=2.0, min_alpha=0.5, refine_iters=10) -> dict:
+    def solve(self, cam, T_render, depth, alpha, matches, words, tau=2.0, min_alpha=0.5, refine_iters=5) -> dict:
         """depth, alpha: (H, W) float32 CUDA tensors rendered at T_render; matches:
         (K, 3) int32 CUDA tensor (PMM fine layout); words: (n_hyp, 3) int32 or
         uint32-bits CUDA tensor of random words."""
@@ -716,7 +732,7 @@ def gs_localize_defaults() -> gs_localize_opts:
 
 
 def dense_localize(scene, matcher, solver, cam, T_init, feat_query, words, n_rounds=3, n_hypotheses=None,
-                   pmm_tau=0.1, max_angle_deg=20.0, tau=2.0, min_alpha=0.5, refine_iters=10) -> dict:
+                   pmm_tau=0.1, max_angle_deg=20.0, tau=2.0, min_alpha=0.5, refine_iters=5) -> dict:
     """Algorithm 2 around n rounds of render -> PMM -> PnP. feat_query: (32, H, W)
     float32 CUDA tensor; words: (n_rounds, n_hypotheses, 3) 32-bit CUDA tensor."""
     import torch

@@ -60,6 +60,8 @@ VIS_BACKWARD_DRAM_BYTES = 37_491_200
 # x - a z, y - b z (2 FMA), the scaled squares (2 mul + 1 FMA), tau z twice (2 mul),
 # the threshold difference (1 FMA) and 2 compares: 33 fp32 operations (FMA = 2)
 FLOPS_PER_PNP_PAIR = 33
+# DRAM bytes of one scoring launch on this workload (ncu, 313 solutions x 491,752 matches)
+PNP_SCORE_DRAM_BYTES = 11_834_880
 
 
 def parse():
@@ -710,7 +712,7 @@ def bench_dense(gsr, synth, torch, steps, warmup, pk_src, with_oracle):
            "start_error": dict(zip(("rot_deg", "centre_m"), _pose_errors(T_r, T_q))),
            "roofline": {"bound": "alu", "kernel": "k_pnp_score (every P3P solution against every match)",
                         "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
-                        "traffic": None,
+                        "traffic": PNP_SCORE_DRAM_BYTES,
                         "work": "%d solutions x %d matches x %d fp32 ops" % (n_sol, int(r["n_valid"]),
                                                                          FLOPS_PER_PNP_PAIR),
                         "peak_source": "%d SMs x 128 fp32 lanes x 2 x %.0f MHz (%s max clock)"

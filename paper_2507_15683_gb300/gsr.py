@@ -387,7 +387,24 @@ def pose(T) -> gs_pose:
 
 
 def _ptr(t):
-    return 0 if t is None else t.data_ptr()
+    """Raw pointer of a dense tensor: the C ABI reads every array in row-major
+    order, so a strided view (a transpose, a slice) is refused, not misread."""
+    if t is None:
+        return 0
+    if not t.is_contiguous():
+        raise ValueError("arrays passed to the library must be contiguous (got strides %s for shape %s)"
+                         % (tuple(t.stride()), tuple(t.shape)))
+    return t.data_ptr()
+
+
+def _f32(t, name):
+    """_ptr of a float32 CUDA tensor (None passes through)."""
+    if t is None:
+        return 0
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float32):
+        raise ValueError("%s must be a float32 CUDA tensor" % name)
+    return _ptr(t)
 
 
 def _stream():
@@ -486,8 +503,9 @@ class Scene:
         return out
 
     def render_pose_grad(self, cam, T, target_rgb, target_depth, pixel_weight=None, depth_weight=0.1, out=None):
-        return gs_render_pose_grad(self.handle, camera(cam), pose(T), _ptr(target_rgb), _ptr(target_depth),
-                                   _ptr(pixel_weight) or None, depth_weight,
+        return gs_render_pose_grad(self.handle, camera(cam), pose(T), _f32(target_rgb, "target_rgb"),
+                                   _f32(target_depth, "target_depth"), _f32(pixel_weight, "pixel_weight") or None,
+                                   depth_weight,
                                    self.outputs_struct(out) if out is not None else None, _stream())
 
     def render_pose_grad_host(self, cam, T, target_rgb, target_depth, pixel_weight=None, depth_weight=0.1,
@@ -513,8 +531,9 @@ class Scene:
         """Batched pose gradient; tensors are per-view lists. Returns (loss[n], grad[n,6])
         synchronously, or None in graph mode (results: device float64 tensor (n, 8))."""
         return gs_render_pose_grad_batch(
-            self.handle, [camera(c) for c in cams], [pose(T) for T in poses], [_ptr(t) for t in target_rgb],
-            [_ptr(t) for t in target_depth], None if pixel_weight is None else [_ptr(t) for t in pixel_weight],
+            self.handle, [camera(c) for c in cams], [pose(T) for T in poses],
+            [_f32(t, "target_rgb") for t in target_rgb], [_f32(t, "target_depth") for t in target_depth],
+            None if pixel_weight is None else [_f32(t, "pixel_weight") for t in pixel_weight],
             depth_weight, None if outs is None else [self.outputs_struct(o) for o in outs],
             _ptr(results), GS_BATCH_GRAPH if graph else 0, _stream())
 

@@ -155,8 +155,8 @@ def _targets_for(oracle, scene, cams, poses):
     for c, T in zip(cams, poses):
         r = oracle.render(scene, c, T, geom64=True, n_threads=8)
         H, W = c["height"], c["width"]
-        out.append((torch.from_numpy(r["rgb"].T.reshape(3, H, W).astype(np.float32)).cuda(),
-                    torch.from_numpy(r["depth"].reshape(H, W).astype(np.float32)).cuda()))
+        out.append((torch.from_numpy(np.ascontiguousarray(r["rgb"].T.reshape(3, H, W), np.float32)).cuda(),
+                    torch.from_numpy(np.ascontiguousarray(r["depth"].reshape(H, W), np.float32)).cuda()))
     return out
 
 

@@ -21,7 +21,8 @@ pytestmark = pytest.mark.gpu
 def _targets(oracle, scene, cam, T_gt):
     tgt = oracle.render(scene, cam, T_gt, geom64=True, n_threads=16)
     H, W = cam["height"], cam["width"]
-    return (tgt["rgb"].T.reshape(3, H, W).astype(np.float32), tgt["depth"].reshape(H, W).astype(np.float32))
+    return (np.ascontiguousarray(tgt["rgb"].T.reshape(3, H, W), np.float32),
+            np.ascontiguousarray(tgt["depth"].reshape(H, W), np.float32))
 
 
 def _compare(oracle, gsr, scene, cam, T_gt, T_q, depth_weight=0.1, weight=None):

@@ -24,8 +24,8 @@ def _centre(T):
 def _targets(oracle, scene, cam, T):
     r = oracle.render(scene, cam, T, geom64=True, n_threads=16)
     H, W = cam["height"], cam["width"]
-    return (torch.from_numpy(r["rgb"].T.reshape(3, H, W).astype(np.float32)).cuda(),
-            torch.from_numpy(r["depth"].reshape(H, W).astype(np.float32)).cuda())
+    return (torch.from_numpy(np.ascontiguousarray(r["rgb"].T.reshape(3, H, W), np.float32)).cuda(),
+            torch.from_numpy(np.ascontiguousarray(r["depth"].reshape(H, W), np.float32)).cuda())
 
 
 def test_refinement_converges_on_the_refine_workload(oracle, gsr):

@@ -403,7 +403,9 @@ def main():
         "fwd_mpix_s": world * P / (ms_fwd * 1e-3) / 1e6, "fwd_ms": ms_fwd,
         "clocks": clk,
         "e2e": {"value": world * P / (e2e_ms * 1e-3) / 1e6, "unit": "Mpix/s", "ms_per_step": e2e_ms,
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 7 * 8},
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 7 * 8,
+                "transfer": "pinned host targets read in place by the compositing pass over the CPU-GPU link; "
+                            "(loss, gradient) copied back"},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roof, "kernels": kernels,
         "refine": refine, "batched": batched, "large": large, "pmm": pmm, "visibility": vis, "dense": dense,

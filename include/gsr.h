@@ -149,12 +149,15 @@ gs_status gs_render_pose_grad(gs_scene* scene, const gs_camera* cam, const gs_po
 
 /* gs_render_pose_grad with the loss inputs in host memory: target_rgb
  * (3 x H x W), target_depth (H x W) and pixel_weight (H x W or NULL) are host
- * pointers, copied into a scene-owned device buffer on a side stream that runs
- * beside the projection and binning kernels; only the compositing pass waits
- * for the copies. Page-locked (pinned) host memory makes the copies
- * asynchronous; pageable memory works but is copied before the kernels start.
- * The host buffers may be reused once the call returns. Everything else as
- * gs_render_pose_grad. Errors: INVALID_ARG, OOM, CUDA. */
+ * pointers. When all of them are page-locked (pinned) memory mapped into the
+ * device's address space (cudaMallocHost / cudaHostRegister on a unified-
+ * addressing system), the compositing pass reads them in place over the
+ * CPU-GPU link, each pixel once at the end of its tile. Otherwise they are
+ * copied into a scene-owned device buffer on a side stream, in bands of tile
+ * rows, and each band of the compositing pass waits only for its rows. The
+ * host buffers may be reused once the call returns. Everything else as
+ * gs_render_pose_grad (the results are bit-identical to it). Errors:
+ * INVALID_ARG, OOM, CUDA. */
 gs_status gs_render_pose_grad_host(gs_scene* scene, const gs_camera* cam, const gs_pose* pose,
                                    const float* target_rgb, const float* target_depth, const float* pixel_weight,
                                    float depth_weight, const gs_outputs* out, double* loss_out,

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -83,6 +84,16 @@ struct GradIn {
 };
 
 constexpr int kResultStride = 8;  // (loss, grad rho, grad phi, pad) per view
+constexpr int kUploadBands = 4;   // tile-row bands of a host-target pose-gradient call
+
+// Loss targets uploaded in bands of tile rows (single-view host-target calls):
+// band b covers tile rows [tile_row[b], tile_row[b + 1]) and its rows are on
+// the device once ready[b] has completed; its tangent pass waits for nothing else.
+struct Bands {
+  int n = 0;
+  uint32_t tile_row[kMaxBands + 1] = {};
+  cudaEvent_t ready[kMaxBands] = {};
+};
 
 // Outputs of a visibility-check call (device pointers; uv is never NULL: the
 // caller's array or the scene's scratch).
@@ -156,6 +167,17 @@ struct gs_scene {
   DevBuf vis_T, vis_last, vis_acc, vis_uv, vis_blk;
   cudaStream_t copy_st = nullptr;
   cudaEvent_t ev_call = nullptr, ev_targets = nullptr;
+  // pinned copy of the call table for synchronous calls: its upload must not
+  // queue behind large host-to-device copies (a pageable source is staged and
+  // copied in order with them)
+  char* table_host = nullptr;
+  size_t table_host_bytes = 0;
+  // banded tangent pass: two streams that take the bands in turn, and the
+  // events between the binning, the band uploads and the band launches
+  cudaStream_t band_st[2] = {nullptr, nullptr};
+  cudaEvent_t ev_binned = nullptr;
+  cudaEvent_t ev_band[kMaxBands] = {};
+  cudaEvent_t ev_band_done[kMaxBands] = {};
   // kernel timing: one set of GS_KERNEL_COUNT + 1 events per timed call
   bool timing = false;
   struct TimedCall {
@@ -349,9 +371,13 @@ void fill_table(const gs_scene* s, const std::vector<View>& hv, const std::vecto
   std::memcpy(dst + table_ranges_bytes(s), hv.data(), hv.size() * sizeof(View));
 }
 
+// `graph`: the call is being captured (no timing events). `after_table`, if
+// given, is called once the table upload is on the stream (the host-target
+// path issues its target copies there, so that the table goes first).
 gs_status enqueue(gs_scene* s, const std::vector<View>& hv, const std::vector<int4>& ranges, uint64_t n_tiles,
                   const GradIn* g, cudaStream_t st, const char* upload_src, cudaEvent_t targets_ready = nullptr,
-                  const VisOut* vis = nullptr) {
+                  const VisOut* vis = nullptr, const Bands* bands = nullptr, bool graph = false,
+                  const std::function<gs_status()>* after_table = nullptr) {
   const int nv = (int)hv.size();
   const bool jac = g != nullptr || vis != nullptr;  // per-record pose Jacobian
   GS_TRY(grow_tiles(s, n_tiles));
@@ -377,6 +403,7 @@ gs_status enqueue(gs_scene* s, const std::vector<View>& hv, const std::vector<in
     fill_table(s, hv, ranges, tab.data());
     GS_CUDA(cudaMemcpyAsync(s->views.p, tab.data(), tab.size(), cudaMemcpyHostToDevice, st));
   }
+  if (after_table) GS_TRY((*after_table)());
   Work w = work_of(s, (uint32_t)n_tiles);
   w.ranges = dp<int4>(s->views);
   if (g) {
@@ -388,7 +415,7 @@ gs_status enqueue(gs_scene* s, const std::vector<View>& hv, const std::vector<in
   GS_CUDA(cudaMemsetAsync(w.ctr, 0, sizeof(Counters), st));
   const SceneDev sc = scene_dev(s);
   std::vector<cudaEvent_t> ev;
-  const bool timed = s->timing && upload_src == nullptr;  // no events inside captured graphs
+  const bool timed = s->timing && !graph;  // no events inside captured graphs
   if (timed) {
     if (!s->ev_free.empty()) {
       ev = std::move(s->ev_free.back());
@@ -419,8 +446,28 @@ gs_status enqueue(gs_scene* s, const std::vector<View>& hv, const std::vector<in
     // the tangent pass re-renders the same values (without features) and adds
     // the loss and its pose gradient
     double* res = g->result ? g->result : w.result;
-    if (targets_ready) GS_CUDA(cudaStreamWaitEvent(st, targets_ready, 0));  // only this pass reads the targets
-    GS_CUDA(launch_composite_tangent(sc, dviews, nv, w, res, s->sm_count * composite_blocks_per_sm(0, true), st));
+    const int grid = s->sm_count * composite_blocks_per_sm(0, true);
+    if (bands && bands->n > 0 && nv == 1) {
+      // band b of the tangent pass starts when the binning is done and its
+      // target rows are on the device; consecutive bands run on two streams so
+      // that one band's last tiles overlap the next band's first ones (the
+      // per-chunk fp64 reduction completes in whichever launch ends a chunk)
+      GS_CUDA(cudaEventRecord(s->ev_binned, st));
+      const View& V = hv[0];
+      for (int b = 0; b < bands->n; ++b) {
+        const cudaStream_t bs = s->band_st[b & 1];
+        GS_CUDA(cudaStreamWaitEvent(bs, s->ev_binned, 0));
+        GS_CUDA(cudaStreamWaitEvent(bs, bands->ready[b], 0));
+        const uint32_t t0 = V.tile_base + bands->tile_row[b] * (uint32_t)V.tiles_x;
+        const uint32_t t1 = V.tile_base + bands->tile_row[b + 1] * (uint32_t)V.tiles_x;
+        GS_CUDA(launch_composite_tangent_range(sc, dviews, nv, w, res, grid, bs, t0, t1, &w.ctr->band_queue[b]));
+        GS_CUDA(cudaEventRecord(s->ev_band_done[b], bs));
+      }
+      for (int b = 0; b < bands->n; ++b) GS_CUDA(cudaStreamWaitEvent(st, s->ev_band_done[b], 0));
+    } else {
+      if (targets_ready) GS_CUDA(cudaStreamWaitEvent(st, targets_ready, 0));  // only this pass reads the targets
+      GS_CUDA(launch_composite_tangent(sc, dviews, nv, w, res, grid, st));
+    }
   }
   GS_CUDA(mark(6));
   if (vis) {
@@ -588,11 +635,23 @@ gs_status read_counters(gs_scene* s, cudaStream_t st, Counters& c) {
 // With a pose gradient the (loss, gradient) of the first view are copied to
 // s->result_host in the same round trip as the counters.
 gs_status run_sync(gs_scene* s, const std::vector<View>& hv, uint64_t n_tiles, const GradIn* g, cudaStream_t st,
-                   cudaEvent_t targets_ready = nullptr, const VisOut* vis = nullptr) {
+                   cudaEvent_t targets_ready = nullptr, const VisOut* vis = nullptr, const Bands* bands = nullptr,
+                   const std::function<gs_status()>* after_table = nullptr) {
   std::vector<int4> ranges;
   GS_TRY(prepare_call(s, hv, st, ranges));
+  // the table from pinned memory: a synchronous call's previous upload is done
+  const size_t tb = table_bytes(s, (int)hv.size());
+  if (s->table_host_bytes < tb) {
+    if (s->table_host) cudaFreeHost(s->table_host);
+    s->table_host = nullptr;
+    s->table_host_bytes = 0;
+    GS_CUDA(cudaMallocHost(&s->table_host, tb));
+    s->table_host_bytes = tb;
+  }
+  fill_table(s, hv, ranges, s->table_host);
   for (int attempt = 0; attempt < 4; ++attempt) {
-    GS_TRY(enqueue(s, hv, ranges, n_tiles, g, st, nullptr, targets_ready, vis));
+    GS_TRY(enqueue(s, hv, ranges, n_tiles, g, st, s->table_host, targets_ready, vis, bands, false,
+                   attempt == 0 ? after_table : nullptr));
     GS_CUDA(cudaMemcpyAsync(s->ctr_host, s->ctr.p, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     if (g && !g->result)
       GS_CUDA(cudaMemcpyAsync(s->result_host, s->result.p, 7 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -682,7 +741,7 @@ gs_status run_graph(gs_scene* s, GraphCache& G, const std::vector<char>& key, co
     GS_CUDA(cudaStreamSynchronize(st));
     cudaGraph_t graph = nullptr;
     GS_CUDA(cudaStreamBeginCapture(G.capture, cudaStreamCaptureModeThreadLocal));
-    const gs_status est = enqueue(s, hv, ranges, n_tiles, g, G.capture, G.host_table);
+    const gs_status est = enqueue(s, hv, ranges, n_tiles, g, G.capture, G.host_table, nullptr, nullptr, nullptr, true);
     const cudaError_t ce = cudaStreamEndCapture(G.capture, &graph);
     if (est != GS_OK) {
       if (graph) cudaGraphDestroy(graph);
@@ -902,9 +961,17 @@ void gs_destroy_scene(gs_scene* s) {
   for (void* h : {(void*)s->h_pos, (void*)s->h_cov, (void*)s->h_sh, (void*)s->h_feat})
     if (h) cudaFreeHost(h);
   if (s->ctr_host) cudaFreeHost(s->ctr_host);
+  if (s->table_host) cudaFreeHost(s->table_host);
   if (s->result_host) cudaFreeHost(s->result_host);
   release(s->targets);
   if (s->copy_st) cudaStreamDestroy(s->copy_st);
+  for (cudaStream_t b : s->band_st)
+    if (b) cudaStreamDestroy(b);
+  if (s->ev_binned) cudaEventDestroy(s->ev_binned);
+  for (int b = 0; b < kMaxBands; ++b) {
+    if (s->ev_band[b]) cudaEventDestroy(s->ev_band[b]);
+    if (s->ev_band_done[b]) cudaEventDestroy(s->ev_band_done[b]);
+  }
   if (s->ev_call) cudaEventDestroy(s->ev_call);
   if (s->ev_targets) cudaEventDestroy(s->ev_targets);
   delete s;
@@ -978,21 +1045,85 @@ gs_status gs_render_pose_grad_host(gs_scene* s, const gs_camera* cam, const gs_p
   GS_TRY(check_cam(*cam));
   const cudaStream_t st = (cudaStream_t)stream;
   const size_t P = (size_t)cam->width * cam->height;
+  // Pinned (page-locked, device-mapped) host targets are read in place by the
+  // tangent pass over the CPU-GPU link: each pixel's targets once, at the end
+  // of its tile, spread over the whole pass. A bulk copy instead slows the
+  // memory-bound projection and binning kernels it overlaps by about a quarter.
+  {
+    const void* dev[3] = {nullptr, nullptr, nullptr};
+    const void* hp[3] = {target_rgb, target_depth, pixel_weight};
+    bool mapped = true;
+    for (int k = 0; k < 3 && mapped; ++k) {
+      if (!hp[k]) continue;
+      cudaPointerAttributes a;
+      if (cudaPointerGetAttributes(&a, hp[k]) != cudaSuccess) {
+        cudaGetLastError();
+        mapped = false;
+      } else {
+        mapped = a.type == cudaMemoryTypeHost && a.devicePointer != nullptr;
+        dev[k] = a.devicePointer;
+      }
+    }
+    if (mapped) {
+      const float* tr = static_cast<const float*>(dev[0]);
+      const float* td = static_cast<const float*>(dev[1]);
+      const float* tw = static_cast<const float*>(dev[2]);
+      GradIn g{&tr, &td, &tw, depth_weight, nullptr};
+      std::vector<View> hv;
+      uint64_t n_tiles;
+      GS_TRY(build_views(s, 1, cam, pose, out, &g, hv, n_tiles));
+      GS_TRY(run_sync(s, hv, n_tiles, &g, st));
+      if (loss_out) *loss_out = s->result_host[0];
+      if (grad_xi_out)
+        for (int k = 0; k < 6; ++k) grad_xi_out[k] = s->result_host[1 + k];
+      return GS_OK;
+    }
+  }
+  // pageable targets: uploaded by the copy engine, in bands
   GS_TRY(ensure(s->targets, (pixel_weight ? 5 : 4) * P * sizeof(float)));
   if (!s->copy_st) GS_CUDA(cudaStreamCreateWithFlags(&s->copy_st, cudaStreamNonBlocking));
   if (!s->ev_call) GS_CUDA(cudaEventCreateWithFlags(&s->ev_call, cudaEventDisableTiming));
   if (!s->ev_targets) GS_CUDA(cudaEventCreateWithFlags(&s->ev_targets, cudaEventDisableTiming));
+  if (!s->ev_binned) {
+    GS_CUDA(cudaEventCreateWithFlags(&s->ev_binned, cudaEventDisableTiming));
+    for (int b = 0; b < kMaxBands; ++b) {
+      GS_CUDA(cudaEventCreateWithFlags(&s->ev_band[b], cudaEventDisableTiming));
+      GS_CUDA(cudaEventCreateWithFlags(&s->ev_band_done[b], cudaEventDisableTiming));
+    }
+    for (cudaStream_t& b : s->band_st) GS_CUDA(cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking));
+  }
   float* d_rgb = dp<float>(s->targets);
   float* d_dep = d_rgb + 3 * P;
   float* d_w = pixel_weight ? d_rgb + 4 * P : nullptr;
-  // the uploads start after the work already on the caller's stream (which may
-  // still read the buffers) and run beside this call's projection and binning
-  GS_CUDA(cudaEventRecord(s->ev_call, st));
-  GS_CUDA(cudaStreamWaitEvent(s->copy_st, s->ev_call, 0));
-  GS_CUDA(cudaMemcpyAsync(d_rgb, target_rgb, 3 * P * sizeof(float), cudaMemcpyHostToDevice, s->copy_st));
-  GS_CUDA(cudaMemcpyAsync(d_dep, target_depth, P * sizeof(float), cudaMemcpyHostToDevice, s->copy_st));
-  if (d_w) GS_CUDA(cudaMemcpyAsync(d_w, pixel_weight, P * sizeof(float), cudaMemcpyHostToDevice, s->copy_st));
-  GS_CUDA(cudaEventRecord(s->ev_targets, s->copy_st));
+  // The uploads (16 or 20 B per pixel at the host link's ~200 GB/s) start after
+  // the work already on the caller's stream, which may still read the buffers,
+  // and after the call table, which the first kernel needs (queued behind tens
+  // of MB of targets it would hold everything back). They go in bands of tile
+  // rows: band b's tangent pass needs only its rows, so the later bands upload
+  // while the projection, the binning and the earlier bands run.
+  const int W = cam->width, H = cam->height;
+  const int tiles_y = (H + kTile - 1) / kTile;
+  Bands bands;
+  bands.n = std::min(kUploadBands, tiles_y);
+  for (int b = 0; b <= bands.n; ++b) bands.tile_row[b] = (uint32_t)((int64_t)tiles_y * b / bands.n);
+  for (int b = 0; b < bands.n; ++b) bands.ready[b] = s->ev_band[b];
+  // issued once the call table is on the stream (see enqueue)
+  const std::function<gs_status()> upload = [&]() -> gs_status {
+    GS_CUDA(cudaEventRecord(s->ev_call, st));
+    GS_CUDA(cudaStreamWaitEvent(s->copy_st, s->ev_call, 0));
+    for (int b = 0; b < bands.n; ++b) {
+      const size_t y0 = (size_t)bands.tile_row[b] * kTile;
+      const size_t y1 = std::min((size_t)bands.tile_row[b + 1] * kTile, (size_t)H);
+      const size_t off = y0 * W, bytes = (y1 - y0) * W * sizeof(float);
+      // the three colour planes of the band in one strided copy
+      GS_CUDA(cudaMemcpy2DAsync(d_rgb + off, P * sizeof(float), target_rgb + off, P * sizeof(float), bytes, 3,
+                                cudaMemcpyHostToDevice, s->copy_st));
+      GS_CUDA(cudaMemcpyAsync(d_dep + off, target_depth + off, bytes, cudaMemcpyHostToDevice, s->copy_st));
+      if (d_w) GS_CUDA(cudaMemcpyAsync(d_w + off, pixel_weight + off, bytes, cudaMemcpyHostToDevice, s->copy_st));
+      GS_CUDA(cudaEventRecord(s->ev_band[b], s->copy_st));
+    }
+    return GS_OK;
+  };
   const float* tr = d_rgb;
   const float* td = d_dep;
   const float* tw = d_w;
@@ -1000,7 +1131,7 @@ gs_status gs_render_pose_grad_host(gs_scene* s, const gs_camera* cam, const gs_p
   std::vector<View> hv;
   uint64_t n_tiles;
   GS_TRY(build_views(s, 1, cam, pose, out, &g, hv, n_tiles));
-  GS_TRY(run_sync(s, hv, n_tiles, &g, st, s->ev_targets));
+  GS_TRY(run_sync(s, hv, n_tiles, &g, st, nullptr, nullptr, &bands, &upload));
   if (loss_out) *loss_out = s->result_host[0];
   if (grad_xi_out)
     for (int k = 0; k < 6; ++k) grad_xi_out[k] = s->result_host[1 + k];

@@ -21,6 +21,7 @@ constexpr int kWarpSortMax = 256;  // longest tile list sorted by one warp (regi
 constexpr int kVisAcc = 8;         // floats per record of the visibility check's accumulator
 constexpr int kVisBlock = 2048;    // Gaussians per block of the visibility compaction
 constexpr int kRecRegions = 64;    // record-allocation counters (block index mod 64)
+constexpr int kMaxBands = 8;       // tile-row bands of a tangent pass that overlaps its target upload
 
 // Per-view parameters (device copy built on the host for every call).
 struct View {
@@ -65,6 +66,7 @@ struct Counters {
   unsigned int vis_count;   // Gaussians the visibility check keeps (M = M^r and M^i)
   unsigned long long blends;  // (pixel, Gaussian) pairs blended by the tangent or visibility reverse pass
   unsigned long long evals;   // (pixel, Gaussian) pairs the visibility reverse pass evaluated
+  unsigned int band_queue[kMaxBands];  // tile queues of a tangent pass launched in bands of tile rows
 };
 
 // Scene arena (device pointers).
@@ -106,6 +108,11 @@ struct Work {
   // Gaussian index ranges the projection walks (partitions in view):
   // ranges[0] = (count, total length, 0, 0), ranges[1 + k] = (begin, end, prefix, 0)
   const int4* ranges;
+  // tiles [tile_begin, tile_end) of the tangent pass taken from *queue (NULL:
+  // the whole tile space from the counters' own queue)
+  uint32_t tile_begin = 0;
+  uint32_t tile_end = 0xffffffffu;
+  unsigned int* queue = nullptr;
 };
 
 // launchers (return the CUDA error of the launch)
@@ -127,6 +134,11 @@ cudaError_t launch_composite(const SceneDev& sc, const View* views, int n_views,
 // doubles per view (loss, dL/drho, dL/dphi)
 cudaError_t launch_composite_tangent(const SceneDev& sc, const View* views, int n_views, const Work& w,
                                      double* result, int grid, cudaStream_t st);
+// the same pass over tiles [tile_begin, tile_end) with its own queue counter
+// (the per-chunk fp64 reduction completes across such launches)
+cudaError_t launch_composite_tangent_range(const SceneDev& sc, const View* views, int n_views, const Work& w,
+                                           double* result, int grid, cudaStream_t st, uint32_t tile_begin,
+                                           uint32_t tile_end, unsigned int* queue);
 
 // Algorithm 1 visibility check, after a forward render of one view that wrote
 // final_T and last_idx and a shading pass that wrote the pose Jacobian:

@@ -372,10 +372,13 @@ __global__ void __launch_bounds__(kTileThreads, TAN ? 4 : FEAT ? 3 : 5) k_compos
   uint32_t n_blend = 0;  // tangent pass: blended (pixel, Gaussian) pairs of this thread
   for (;;) {
     // the tangent pass keeps its own queue: it can follow a feature render
-    if (tid == 0) s_tile = atomicAdd(TAN ? &w.ctr->tan_queue : &w.ctr->fwd_queue, 1u);
+    if (tid == 0) {
+      unsigned int* q = w.queue ? w.queue : (TAN ? &w.ctr->tan_queue : &w.ctr->fwd_queue);
+      s_tile = w.tile_begin + atomicAdd(q, 1u);
+    }
     __syncthreads();
     const uint32_t tile = s_tile;
-    if (tile >= w.n_tiles) {
+    if (tile >= min(w.n_tiles, w.tile_end)) {
       if (TAN) {
         const uint32_t nb = __reduce_add_sync(0xffffffffu, n_blend);
         if (lane == 0 && nb) atomicAdd(&w.ctr->blends, (unsigned long long)nb);
@@ -808,6 +811,21 @@ cudaError_t launch_composite_tangent(const SceneDev& sc, const View* views, int 
   const int g = (uint32_t)grid < w.n_tiles ? grid : (int)w.n_tiles;
   composite_occ<0, true>();
   k_composite<0, true><<<g, kTileThreads, composite_smem<0, true>(), st>>>(sc, views, n_views, w, result);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_composite_tangent_range(const SceneDev& sc, const View* views, int n_views, const Work& w,
+                                           double* result, int grid, cudaStream_t st, uint32_t tile_begin,
+                                           uint32_t tile_end, unsigned int* queue) {
+  if (tile_end > w.n_tiles) tile_end = w.n_tiles;
+  if (tile_begin >= tile_end) return cudaSuccess;
+  Work wb = w;
+  wb.tile_begin = tile_begin;
+  wb.tile_end = tile_end;
+  wb.queue = queue;
+  const int g = (uint32_t)grid < tile_end - tile_begin ? grid : (int)(tile_end - tile_begin);
+  composite_occ<0, true>();
+  k_composite<0, true><<<g, kTileThreads, composite_smem<0, true>(), st>>>(sc, views, n_views, wb, result);
   return cudaGetLastError();
 }
 

@@ -129,8 +129,9 @@ def test_blend_count_matches_oracle(oracle, gsr):
 
 
 def test_host_targets_equal_device_targets(oracle, gsr):
-    # gs_render_pose_grad_host uploads the targets itself (beside the projection
-    # and binning kernels): same loss and gradient bits as the device-pointer call
+    # gs_render_pose_grad_host copies pageable targets itself (in bands of tile
+    # rows) and reads pinned ones in place: the same loss and gradient bits as
+    # the device-pointer call either way
     scene, cam, T_gt = _small_aerial(34)
     T_q = synth.perturb_pose(T_gt, synth.rng(34), 1.0, 1.0)
     trgb, tdep = _targets(oracle, scene, cam, T_gt)

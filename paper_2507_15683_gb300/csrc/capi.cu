@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <functional>
@@ -45,8 +46,14 @@ struct DevBuf {
   size_t bytes = 0;
 };
 
+// Bumped by every device (re)allocation of a workspace buffer: a captured
+// graph holds the buffers' addresses and is replayed only while this is
+// unchanged since its capture.
+std::atomic<uint64_t> g_alloc_gen{0};
+
 gs_status ensure(DevBuf& b, size_t bytes) {
   if (b.bytes >= bytes && b.p) return GS_OK;
+  g_alloc_gen.fetch_add(1);
   if (b.p) cudaFree(b.p);
   b.p = nullptr;
   b.bytes = 0;
@@ -114,6 +121,7 @@ struct GraphCache {
   cudaEvent_t done = nullptr;
   cudaStream_t capture = nullptr;
   int n_views = 0;
+  uint64_t gen = 0;  // g_alloc_gen at capture
 };
 
 }  // namespace
@@ -193,6 +201,7 @@ struct gs_scene {
   uint32_t last_tiles = 0;
   GraphCache graph;       // forward batches
   GraphCache graph_grad;  // pose-gradient batches
+  GraphCache graph_sync;  // synchronous single-view pose gradients
 };
 
 namespace {
@@ -718,9 +727,10 @@ gs_status run_graph(gs_scene* s, GraphCache& G, const std::vector<char>& key, co
                     uint64_t n_tiles, const GradIn* g, cudaStream_t st) {
   const int n_views = (int)hv.size();
   std::vector<int4> ranges;
-  if (G.valid && G.key == key) GS_CUDA(cudaEventSynchronize(G.done));  // previous replay read the table
+  const bool ready = G.valid && G.key == key && G.gen == g_alloc_gen.load();
+  if (ready) GS_CUDA(cudaEventSynchronize(G.done));  // previous replay read the table
   GS_TRY(prepare_call(s, hv, st, ranges));  // uploads partitions on st before the graph runs
-  if (!(G.valid && G.key == key)) {
+  if (!ready) {
     if (G.exec) cudaGraphExecDestroy(G.exec);
     G.exec = nullptr;
     G.valid = false;
@@ -753,6 +763,7 @@ gs_status run_graph(gs_scene* s, GraphCache& G, const std::vector<char>& key, co
     if (ie != cudaSuccess) return fail(GS_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
     G.key = key;
     G.n_views = n_views;
+    G.gen = g_alloc_gen.load();
     G.valid = true;
   } else {
     fill_table(s, hv, ranges, G.host_table);
@@ -768,6 +779,37 @@ template <typename T>
 void append_bytes(std::vector<char>& key, const T* p, size_t n) {
   const char* b = reinterpret_cast<const char*>(p);
   key.insert(key.end(), b, b + n * sizeof(T));
+}
+
+// A synchronous single-view pose gradient replayed from a CUDA graph: one
+// launch instead of the call's memsets, table upload and six kernel launches.
+// The graph is keyed on everything but the pose (the view with its pose fields
+// cleared); a call that overflows the workspace is redone by the regrow path
+// and the next call captures again. With kernel timing on, the ordinary path
+// runs (graphs carry no timing events).
+gs_status run_sync_graphed(gs_scene* s, const std::vector<View>& hv, uint64_t n_tiles, const GradIn* g,
+                           cudaStream_t st) {
+  if (s->timing || hv.size() != 1 || g->result) return run_sync(s, hv, n_tiles, g, st);
+  View k = hv[0];
+  std::memset(k.R, 0, sizeof(k.R));
+  std::memset(k.t, 0, sizeof(k.t));
+  std::memset(k.Rl, 0, sizeof(k.Rl));
+  std::memset(k.tl, 0, sizeof(k.tl));
+  std::memset(k.cw, 0, sizeof(k.cw));
+  std::vector<char> key;
+  append_bytes(key, &k, 1);
+  append_bytes(key, &n_tiles, 1);
+  GS_TRY(run_graph(s, s->graph_sync, key, hv, n_tiles, g, st));
+  GS_CUDA(cudaMemcpyAsync(s->ctr_host, s->ctr.p, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+  GS_CUDA(cudaMemcpyAsync(s->result_host, s->result.p, 7 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  GS_CUDA(cudaStreamSynchronize(st));
+  const Counters& c = *s->ctr_host;
+  if (c.error) return fail(GS_ERR_INTERNAL, "device consistency check failed");
+  if (c.overflow) {
+    s->graph_sync.valid = false;
+    return run_sync(s, hv, n_tiles, g, st);
+  }
+  return GS_OK;
 }
 
 }  // namespace
@@ -944,7 +986,7 @@ void gs_destroy_scene(gs_scene* s) {
   if (!s) return;
   cudaSetDevice(s->device);
   cudaDeviceSynchronize();
-  for (GraphCache* G : {&s->graph, &s->graph_grad}) {
+  for (GraphCache* G : {&s->graph, &s->graph_grad, &s->graph_sync}) {
     if (G->exec) cudaGraphExecDestroy(G->exec);
     if (G->host_table) cudaFreeHost(G->host_table);
     if (G->done) cudaEventDestroy(G->done);
@@ -1026,7 +1068,7 @@ gs_status gs_render_pose_grad(gs_scene* s, const gs_camera* cam, const gs_pose* 
   uint64_t n_tiles;
   GS_TRY(build_views(s, 1, cam, pose, out, &g, hv, n_tiles));
   const cudaStream_t st = (cudaStream_t)stream;
-  GS_TRY(run_sync(s, hv, n_tiles, &g, st));
+  GS_TRY(run_sync_graphed(s, hv, n_tiles, &g, st));
   if (loss_out) *loss_out = s->result_host[0];
   if (grad_xi_out)
     for (int k = 0; k < 6; ++k) grad_xi_out[k] = s->result_host[1 + k];
@@ -1072,7 +1114,7 @@ gs_status gs_render_pose_grad_host(gs_scene* s, const gs_camera* cam, const gs_p
       std::vector<View> hv;
       uint64_t n_tiles;
       GS_TRY(build_views(s, 1, cam, pose, out, &g, hv, n_tiles));
-      GS_TRY(run_sync(s, hv, n_tiles, &g, st));
+      GS_TRY(run_sync_graphed(s, hv, n_tiles, &g, st));
       if (loss_out) *loss_out = s->result_host[0];
       if (grad_xi_out)
         for (int k = 0; k < 6; ++k) grad_xi_out[k] = s->result_host[1 + k];

@@ -162,8 +162,7 @@ extern "C" gs_status gs_render_noalloc(const gs_scene_desc* d, const gs_camera* 
   float4* sh = reinterpret_cast<float4*>(base + Layout::sh);
   uint4* feat = reinterpret_cast<uint4*>(base + Layout::feat);
   View* dview = reinterpret_cast<View*>(base + Layout::view);
-  Work w;
-  std::memset(&w, 0, sizeof(w));
+  Work w{};  // zero, except the members with defaults (the whole tile space)
   w.rec_a = reinterpret_cast<float4*>(base + Layout::rec_a);
   w.rec_b = reinterpret_cast<float4*>(base + Layout::rec_b);
   w.rec_c = reinterpret_cast<float4*>(base + Layout::rec_c);

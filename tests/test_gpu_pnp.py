@@ -195,6 +195,14 @@ def test_pnp_edge_cases(gsr):
         S.solve(cam, T_r, t(depth), t(alpha), t(matches[:11]), t(words[:4].view(np.int32)))
     with pytest.raises(gsr.GsError):
         S.solve(cam, T_r, t(depth), t(alpha), t(matches[:10]), t(words[:4].view(np.int32)), tau=0.0)
+    # phase timing: one timed call, six non-negative phases, then reset
+    gsr.gs_pnp_set_timing(S.handle, True)
+    S.solve(cam, T_r, t(depth), t(alpha), t(matches[:10]), t(words[:4].view(np.int32)))
+    ms, calls = gsr.gs_pnp_phase_times(S.handle)
+    assert calls == 1 and ms.shape == (6,) and np.all(ms >= 0) and ms.sum() > 0
+    ms, calls = gsr.gs_pnp_phase_times(S.handle)
+    assert calls == 0 and not ms.any()
+    gsr.gs_pnp_set_timing(S.handle, False)
     S.close()
 
 

@@ -87,6 +87,16 @@ def test_visibility_tiny_scene(oracle, gsr):
     _consistent(g, cam)
     _check(g, o)
     assert 0 < g["n_visible"] < len(sc["means"])
+    # the reverse pass walks back through exactly the pairs the render blended:
+    # the oracle's per-pixel blend counts, up to pixels with a near-tie decision
+    S = gsr.Scene(sc)
+    S.visibility(cam, T)
+    blended, evaluated = gsr.gs_scene_work_counts(S.handle)
+    S.close()
+    r = oracle.render(sc, cam, T, geom64=True)
+    ok = (r["flags"] & oracle.TIE_IMAGE) == 0
+    assert abs(blended - int(r["n_blend"].sum())) <= int(r["n_blend"][~ok].sum())
+    assert evaluated >= blended > 0
 
 
 def test_visibility_structural_cases(oracle, gsr):

@@ -466,12 +466,14 @@ __global__ void k_pmm_mnn_scatter(int n, const int* __restrict__ row_best, const
 __global__ void __launch_bounds__(kWin) k_pmm_fine(const float* __restrict__ Fq, const float* __restrict__ Fr, int H,
                                                    int W, int Wc, const int* __restrict__ coarse, float inv_tau,
                                                    float s_exp, float s_two, int* __restrict__ slot_r,
-                                                   float* __restrict__ slot_p, int* __restrict__ win_count) {
+                                                   float* __restrict__ slot_p, int* __restrict__ win_count,
+                                                   const int* __restrict__ n_coarse) {
   __shared__ __align__(16) float ur[kWin][kC];  // rendered unit vectors (read as float4 broadcasts)
   __shared__ float Mf[kWin][kWin + 1];
   __shared__ float lr[kWin], lc[kWin];
   __shared__ int rbest[kWin], cbest[kWin];
   const int k = blockIdx.x, a = threadIdx.x;
+  if (k >= *n_coarse) return;  // launched for every cell; the coarse count is known on the device only
   const int ci = coarse[2 * k], cj = coarse[2 * k + 1];
   const size_t HW = (size_t)H * W;
   const int qy = (ci / Wc) * kRatio + a / kRatio, qx = (ci % Wc) * kRatio + a % kRatio;
@@ -557,8 +559,10 @@ __global__ void __launch_bounds__(kWin) k_pmm_fine(const float* __restrict__ Fq,
 
 // exclusive scan of n_win counts (one CTA): offsets and the total
 __global__ void __launch_bounds__(kScanThreads) k_pmm_scan(int n_win, const int* __restrict__ cnt,
-                                                           int* __restrict__ off, int* __restrict__ total) {
+                                                           int* __restrict__ off, int* __restrict__ total,
+                                                           const int* __restrict__ n_dev) {
   __shared__ uint32_t wsum[32];
+  if (n_dev) n_win = *n_dev;  // a count produced on the device (the coarse matches)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int per = (n_win + 31) / 32;  // a contiguous chunk per warp, read in coalesced steps of 32
   const int b = w * per, e = min(n_win, b + per);
@@ -599,9 +603,10 @@ __global__ void __launch_bounds__(kWin) k_pmm_fine_scatter(int W, int Wc, const 
                                                            const int* __restrict__ slot_r,
                                                            const float* __restrict__ slot_p,
                                                            const int* __restrict__ off, int* __restrict__ fine,
-                                                           float* __restrict__ prob) {
+                                                           float* __restrict__ prob, const int* __restrict__ n_coarse) {
   __shared__ int w0;
   const int k = blockIdx.x, a = threadIdx.x;
+  if (k >= *n_coarse) return;
   const int r = slot_r[(size_t)k * kWin + a];
   const unsigned bal = __ballot_sync(0xffffffffu, r >= 0);
   if (a == 0) w0 = __popc(bal);
@@ -785,25 +790,21 @@ gs_status gs_pmm_match(gs_pmm* m, const float* feat_query, const float* feat_ren
   // mutual nearest neighbours in ascending query order
   k_pmm_mnn<<<rg, 256, 0, st>>>(n, m->row_best, m->col_best, m->codes_q, m->codes_r, m->lse_row, m->lse_col, s_two,
                                 m->win_cnt, m->slot_p);
-  k_pmm_scan<<<1, kScanThreads, 0, st>>>(n, m->win_cnt, m->win_off, m->counters);
+  k_pmm_scan<<<1, kScanThreads, 0, st>>>(n, m->win_cnt, m->win_off, m->counters, nullptr);
   k_pmm_mnn_scatter<<<rg, 256, 0, st>>>(n, m->row_best, m->win_cnt, m->win_off, m->slot_p, m->coarse, m->coarse_p);
+  PMM_CUDA(cudaGetLastError());
+  // fine level without a round trip: one CTA per cell (the most coarse matches
+  // there can be); those past the device-side coarse count return at once
+  k_pmm_fine<<<n, kWin, 0, st>>>(feat_query, feat_render, m->H, m->W, m->Wc, m->coarse, inv_tau, s_exp, s_two,
+                                 m->slot_r, m->slot_p, m->win_cnt, m->counters);
+  k_pmm_scan<<<1, kScanThreads, 0, st>>>(0, m->win_cnt, m->win_off, m->counters + 1, m->counters);
+  k_pmm_fine_scatter<<<n, kWin, 0, st>>>(m->W, m->Wc, m->coarse, m->slot_r, m->slot_p, m->win_off, m->fine,
+                                         m->fine_p, m->counters);
   PMM_CUDA(cudaGetLastError());
   PMM_CUDA(cudaMemcpyAsync(m->host, m->counters, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
   PMM_CUDA(cudaStreamSynchronize(st));
   if (m->host[3]) return pmm_fail(GS_ERR_INTERNAL, "tensor-core completion wait timed out");
   const int n_coarse = m->host[0];
-  if (n_coarse > 0) {
-    k_pmm_fine<<<n_coarse, kWin, 0, st>>>(feat_query, feat_render, m->H, m->W, m->Wc, m->coarse, inv_tau, s_exp,
-                                          s_two, m->slot_r, m->slot_p, m->win_cnt);
-    k_pmm_scan<<<1, kScanThreads, 0, st>>>(n_coarse, m->win_cnt, m->win_off, m->counters + 1);
-    k_pmm_fine_scatter<<<n_coarse, kWin, 0, st>>>(m->W, m->Wc, m->coarse, m->slot_r, m->slot_p, m->win_off, m->fine,
-                                                  m->fine_p);
-    PMM_CUDA(cudaGetLastError());
-    PMM_CUDA(cudaMemcpyAsync(m->host + 1, m->counters + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
-    PMM_CUDA(cudaStreamSynchronize(st));
-  } else {
-    m->host[1] = 0;
-  }
   out->n_cells = n;
   out->codes_q = reinterpret_cast<const uint16_t*>(m->codes_q);
   out->codes_r = reinterpret_cast<const uint16_t*>(m->codes_r);

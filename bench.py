@@ -85,6 +85,30 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+# Replicas only: each rank renders its own query pose of the same scene (independent
+# units, no collective on the data path); timing takes the slowest rank, and the
+# whole-job value counts every rank's pixels.
+def barrier(world: int) -> None:
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mpix_per_s(world: int, pixels: int, ms: float) -> float:
+    """Whole-job throughput: every rank's pixels over the slowest rank's step time."""
+    return world * pixels / (ms * 1e-3) / 1e6
+
+
 # --------------------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -243,17 +267,6 @@ def main():
         torch.cuda.set_device(0)
     from paper_2507_15683_gb300 import gsr, synth
 
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
-
     scene, cam, T_ref, T_q = make_workload(rank)
     H, W = cam["height"], cam["width"]
     P = H * W
@@ -284,7 +297,7 @@ def main():
 
     def timed(fn, k):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
-        barrier()
+        barrier(world)
         torch.cuda.synchronize()
         for a, b in ev:
             flush.zero_()
@@ -292,7 +305,7 @@ def main():
             fn()
             b.record()
         torch.cuda.synchronize()
-        barrier()
+        barrier(world)
         return float(np.mean([a.elapsed_time(b) for a, b in ev]))
 
     bus = None
@@ -303,12 +316,12 @@ def main():
     clocks = ClockSampler(bus)
     clocks.start()
     ms_grad = timed(grad_step, args.steps)
-    ms_grad = max_over_ranks(ms_grad)
+    ms_grad = max_over_ranks(ms_grad, world)
     st, _, _ = S.status()
     assert st == 0
     for _ in range(args.warmup):
         fwd_step()
-    ms_fwd = max_over_ranks(timed(fwd_step, args.steps))
+    ms_fwd = max_over_ranks(timed(fwd_step, args.steps), world)
 
     # per-kernel device time over the same steps (events recorded by the library)
     gsr.gs_scene_set_timing(S.handle, True)
@@ -354,13 +367,13 @@ def main():
 
     for _ in range(args.warmup):
         e2e_step()
-    barrier()
+    barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps)
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, world)
     h2d = (h_rgb.numel() + h_dep.numel()) * 4
 
     # pose refinement (500k Gaussians, 960x540, 50 Adam iterations), single and 8 poses batched
@@ -390,7 +403,7 @@ def main():
         cpu = cpu_baseline(scene, cam, T_ref, T_q, args.cpu_seconds)
 
     launches_per_step = 6  # project, shade, scan, scatter, sort, composite (tangent pass + reduction)
-    value = world * P / (ms_grad * 1e-3) / 1e6
+    value = job_mpix_per_s(world, P, ms_grad)
     line = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_grad, "higher_is_better": True, "scaling": "weak",
@@ -400,9 +413,9 @@ def main():
                    "l2": "flushed (256 MB write) between timed steps, outside the timed events",
                    "parallelism": "replicas" if world > 1 else "single"},
         "pose_grad_iters_per_s": world / (ms_grad * 1e-3),
-        "fwd_mpix_s": world * P / (ms_fwd * 1e-3) / 1e6, "fwd_ms": ms_fwd,
+        "fwd_mpix_s": job_mpix_per_s(world, P, ms_fwd), "fwd_ms": ms_fwd,
         "clocks": clk,
-        "e2e": {"value": world * P / (e2e_ms * 1e-3) / 1e6, "unit": "Mpix/s", "ms_per_step": e2e_ms,
+        "e2e": {"value": job_mpix_per_s(world, P, e2e_ms), "unit": "Mpix/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 7 * 8,
                 "transfer": "pinned host targets read in place by the compositing pass over the CPU-GPU link; "
                             "(loss, gradient) copied back"},

@@ -226,15 +226,22 @@ gs_refine_opts gs_refine_defaults(void);
 
 /* Refine one pose in place (pose: host, updated). Targets and weights as in
  * gs_render_pose_grad. loss_history: host array of opts->iterations (the loss
- * before each update) or NULL. Synchronous. Errors: those of
- * gs_render_pose_grad, INVALID_ARG for bad options. */
+ * before each update) or NULL. Synchronous.
+ * On a scene of one partition that is not streamed, the Adam step and the pose
+ * update run on the device (fp64) after every pass and the iterations after
+ * the first replay one CUDA graph without a host round trip; the workspace is
+ * sized by the first pass with 50% headroom, and a later pass that outgrows it
+ * doubles it and restarts the refinement. Other scenes take the step on the
+ * host after every pass (their partitions are culled per pose).
+ * Errors: those of gs_render_pose_grad, INVALID_ARG for bad options, OOM. */
 gs_status gs_refine_pose(gs_scene* scene, const gs_camera* cam, gs_pose* pose, const float* target_rgb,
                          const float* target_depth, const float* pixel_weight, const gs_refine_opts* opts,
                          double* loss_history, void* stream);
 
 /* Refine n_views poses together (poses: host array, updated in place): every
- * iteration is one batched pose-gradient pass (replayed CUDA graph after the
- * first), then one Adam update per view. Targets and weights as in
+ * iteration is one batched pose-gradient pass, then one Adam update per view,
+ * on the device or the host as for gs_refine_pose. Each view's poses equal
+ * those of gs_refine_pose on that view alone. Targets and weights as in
  * gs_render_pose_grad_batch. loss_history: host array n_views x iterations or
  * NULL. Synchronous. */
 gs_status gs_refine_poses_batch(gs_scene* scene, int n_views, const gs_camera* cams, gs_pose* poses,

@@ -386,7 +386,7 @@ void fill_table(const gs_scene* s, const std::vector<View>& hv, const std::vecto
 gs_status enqueue(gs_scene* s, const std::vector<View>& hv, const std::vector<int4>& ranges, uint64_t n_tiles,
                   const GradIn* g, cudaStream_t st, const char* upload_src, cudaEvent_t targets_ready = nullptr,
                   const VisOut* vis = nullptr, const Bands* bands = nullptr, bool graph = false,
-                  const std::function<gs_status()>* after_table = nullptr) {
+                  const std::function<gs_status()>* after_table = nullptr, bool keep_table = false) {
   const int nv = (int)hv.size();
   const bool jac = g != nullptr || vis != nullptr;  // per-record pose Jacobian
   GS_TRY(grow_tiles(s, n_tiles));
@@ -405,7 +405,9 @@ gs_status enqueue(gs_scene* s, const std::vector<View>& hv, const std::vector<in
     GS_TRY(ensure(s->vis_blk, ((size_t)s->n / kVisBlock + 1) * sizeof(uint32_t)));
   }
   View* dviews = reinterpret_cast<View*>(static_cast<char*>(s->views.p) + table_ranges_bytes(s));
-  if (upload_src) {
+  if (keep_table) {
+    // the device table is current (a device-side pose update rewrote it)
+  } else if (upload_src) {
     GS_CUDA(cudaMemcpyAsync(s->views.p, upload_src, table_bytes(s, nv), cudaMemcpyHostToDevice, st));
   } else {
     std::vector<char> tab(table_bytes(s, nv));
@@ -1468,3 +1470,273 @@ gs_status gs_get_records(gs_scene* s, int view, int32_t* rec, int64_t capacity, 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Pose refinement with the Adam step on the device. After a first synchronous
+// iteration (which sizes the workspace), every iteration is the pose-gradient
+// launch sequence followed by one small kernel that takes the Adam step from
+// the gradient in the result buffer, applies T <- Exp(-step) T in fp64 and
+// rewrites the view's pose fields in the device call table. One iteration is
+// captured as a CUDA graph and replayed, so the host enqueues all iterations
+// without waiting for any of them.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct RefineState {
+  double T[16];
+  double m[6], v[6];
+  double b1t, b2t;  // beta1^t, beta2^t after t iterations
+  int it;           // iterations taken
+  int pad;
+};
+
+// One warp per view: lanes 0-5 take the Adam step of one tangent coordinate,
+// lanes 0-11 one entry of the updated 3x4 pose and of the view's pose fields.
+// sticky: bits 0-2 the overflow bits of a call, bit 8 a device consistency failure.
+__global__ void __launch_bounds__(128) k_refine_update(View* __restrict__ views, int nv,
+                                                       const double* __restrict__ result,
+                                                       RefineState* __restrict__ rs, gs_refine_opts o, int iters,
+                                                       double* __restrict__ hist,
+                                                       const Counters* __restrict__ ctr,
+                                                       unsigned int* __restrict__ sticky) {
+  const int v = blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (v >= nv) return;
+  const unsigned int bad = ctr->overflow | (ctr->error ? 0x100u : 0u);
+  if (bad) {  // this iteration's render is incomplete: stop updating
+    if (lane == 0) atomicOr(sticky, bad);
+    return;
+  }
+  if (*sticky) return;
+  RefineState& S = rs[v];
+  const int it = S.it;
+  if (it >= iters) return;
+  const double* r = result + (size_t)v * kResultStride;
+  if (hist && lane == 0) hist[(size_t)v * iters + it] = r[0];
+  const double b1t = S.b1t * o.beta1, b2t = S.b2t * o.beta2;
+  double xi = 0.0;  // this lane's coordinate of -step
+  if (lane < 6) {
+    const double g = r[1 + lane];
+    const double m = o.beta1 * S.m[lane] + (1.0 - o.beta1) * g;
+    const double vv = o.beta2 * S.v[lane] + (1.0 - o.beta2) * g * g;
+    S.m[lane] = m;
+    S.v[lane] = vv;
+    const double lr = lane < 3 ? o.lr_trans : o.lr_rot;
+    xi = -(lr * (m / (1.0 - b1t)) / (sqrt(vv / (1.0 - b2t)) + o.eps));
+  }
+  double x[6];
+  for (int k = 0; k < 6; ++k) x[k] = __shfl_sync(0xffffffffu, xi, k);
+  // Exp of the twist (rho, phi) = x: R = I + a K + b K^2, V = I + b K + c K^2
+  const double* w = x + 3;
+  const double t2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+  const double t = sqrt(t2);
+  double a, b, c;
+  if (t < 1e-6) {  // series of sin t / t, (1 - cos t) / t^2, (t - sin t) / t^3
+    a = 1.0 - t2 / 6.0;
+    b = 0.5 - t2 / 24.0;
+    c = 1.0 / 6.0 - t2 / 120.0;
+  } else {
+    double sn, cs;
+    sincos(t, &sn, &cs);
+    const double it2 = 1.0 / t2;
+    a = sn / t;
+    b = (1.0 - cs) * it2;
+    c = (t - sn) * it2 / t;
+  }
+  double out = 0.0;
+  const int i = lane >> 2, j = lane & 3;  // lanes 0-11: entry (i, j) of the new 3x4 pose
+  if (lane < 12) {
+    // row i of K = [phi]x and of K^2 = phi phi^T - |phi|^2 I
+    const double kr[3] = {i == 0 ? 0.0 : (i == 1 ? w[2] : -w[1]), i == 0 ? -w[2] : (i == 1 ? 0.0 : w[0]),
+                          i == 0 ? w[1] : (i == 1 ? -w[0] : 0.0)};
+    const double wi = i == 0 ? w[0] : (i == 1 ? w[1] : w[2]);
+    double e[4];  // row i of Exp
+    double tv = 0.0;
+    for (int q = 0; q < 3; ++q) {
+      const double id = (i == q) ? 1.0 : 0.0;
+      const double k2 = wi * w[q] - id * t2;
+      e[q] = id + a * kr[q] + b * k2;
+      tv += (id + b * kr[q] + c * k2) * x[q];
+    }
+    e[3] = tv;
+    out = e[0] * S.T[j] + e[1] * S.T[4 + j] + e[2] * S.T[8 + j] + e[3] * S.T[12 + j];
+  }
+  __syncwarp();
+  if (lane < 12) S.T[4 * i + j] = out;
+  if (lane == 0) {
+    S.b1t = b1t;
+    S.b2t = b2t;
+    S.it = it + 1;
+  }
+  // the view's pose fields, split as the host splits them (rounded products and sums)
+  View& V = views[v];
+  if (lane < 12) {
+    const float hi = (float)out, lo = (float)(out - (double)hi);
+    if (j < 3) {
+      V.R[3 * i + j] = hi;
+      V.Rl[3 * i + j] = lo;
+    } else {
+      V.t[i] = hi;
+      V.tl[i] = lo;
+    }
+  }
+  const int l3 = lane < 3 ? lane : 0;  // column l3 of R against the translation
+  const double r0 = __shfl_sync(0xffffffffu, out, l3), r1 = __shfl_sync(0xffffffffu, out, 4 + l3);
+  const double r2 = __shfl_sync(0xffffffffu, out, 8 + l3);
+  const double t0 = __shfl_sync(0xffffffffu, out, 3), t1 = __shfl_sync(0xffffffffu, out, 7);
+  const double tz = __shfl_sync(0xffffffffu, out, 11);
+  if (lane < 3) V.cw[lane] = (float)(-__dadd_rn(__dadd_rn(__dmul_rn(r0, t0), __dmul_rn(r1, t1)), __dmul_rn(r2, tz)));
+}
+
+}  // namespace
+
+namespace gsr {
+
+gs_status refine_on_device(gs_scene* s, int nv, const gs_camera* cams, gs_pose* poses,
+                           const float* const* target_rgb, const float* const* target_depth,
+                           const float* const* pixel_weight, const gs_refine_opts* o, double* loss_history,
+                           cudaStream_t st, bool* used) {
+  *used = false;
+  if (s->streaming || s->parts.size() != 1) return GS_OK;  // partitions culled per pose: the host loop
+  *used = true;
+  if (o->iterations == 0) return GS_OK;
+  GS_TRY(set_device(s));
+  for (int v = 0; v < nv; ++v) GS_TRY(check_grad_args(target_rgb[v], target_depth[v], o->depth_weight));
+  GradIn g{target_rgb, target_depth, pixel_weight, o->depth_weight, nullptr};
+  const int iters = o->iterations;
+  std::vector<RefineState> h0(nv);
+  for (int v = 0; v < nv; ++v) {
+    std::memcpy(h0[v].T, poses[v].T_cw, sizeof(h0[v].T));
+    std::fill(h0[v].m, h0[v].m + 6, 0.0);
+    std::fill(h0[v].v, h0[v].v + 6, 0.0);
+    h0[v].b1t = 1.0;
+    h0[v].b2t = 1.0;
+    h0[v].it = 0;
+    h0[v].pad = 0;
+  }
+  RefineState* drs = nullptr;
+  double* dhist = nullptr;
+  unsigned int* dsticky = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  auto cleanup = [&]() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (cap) cudaStreamDestroy(cap);
+    if (drs) cudaFree(drs);
+    if (dhist) cudaFree(dhist);
+    if (dsticky) cudaFree(dsticky);
+  };
+  if (cudaMalloc(&drs, nv * sizeof(RefineState)) != cudaSuccess ||
+      cudaMalloc(&dhist, (size_t)nv * iters * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&dsticky, sizeof(unsigned int)) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return fail(GS_ERR_OOM, "refinement state allocation failed");
+  }
+  const int blocks = (nv + 3) / 4;
+  gs_status status = GS_OK;
+  auto launch_update = [&](cudaStream_t on) -> gs_status {
+    View* dviews = reinterpret_cast<View*>(static_cast<char*>(s->views.p) + table_ranges_bytes(s));
+    k_refine_update<<<blocks, 128, 0, on>>>(dviews, nv, dp<double>(s->result), drs, *o, iters, dhist,
+                                            dp<Counters>(s->ctr), dsticky);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+  };
+  for (int attempt = 0;; ++attempt) {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    std::vector<View> hv;
+    uint64_t n_tiles;
+    status = build_views(s, nv, cams, poses, nullptr, &g, hv, n_tiles);
+    if (status != GS_OK) break;
+    // iteration 0 synchronously: sizes the workspace and fills the device call table
+    status = run_sync(s, hv, n_tiles, &g, st);
+    if (status != GS_OK) break;
+    {  // headroom for the records and pairs of the poses to come
+      const Counters c = *s->ctr_host;
+      const uint64_t need = records_capacity_needed(c);
+      status = grow_records(s, need + need / 2 + 1024, true);
+      if (status == GS_OK) status = grow_pairs(s, (uint64_t)c.pair_total + c.pair_total / 2 + 4096);
+      if (status != GS_OK) break;
+    }
+    std::vector<int4> ranges;
+    status = prepare_call(s, hv, st, ranges);
+    if (status != GS_OK) break;
+    if (cudaMemcpyAsync(drs, h0.data(), nv * sizeof(RefineState), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(dsticky, 0, sizeof(unsigned int), st) != cudaSuccess) {
+      status = fail(GS_ERR_CUDA, "refinement state upload failed");
+      break;
+    }
+    status = launch_update(st);
+    if (status != GS_OK) break;
+    if (iters > 1 && !s->timing) {
+      // one iteration as a graph (kernel timing needs the eager path's events)
+      if (!cap && cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+        status = fail(GS_ERR_CUDA, "capture stream creation failed");
+        break;
+      }
+      cudaGraph_t graph = nullptr;
+      if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        status = fail(GS_ERR_CUDA, "cudaStreamBeginCapture failed");
+        break;
+      }
+      gs_status est = enqueue(s, hv, ranges, n_tiles, &g, cap, nullptr, nullptr, nullptr, nullptr, true, nullptr,
+                              true);
+      if (est == GS_OK) est = launch_update(cap);
+      const cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+      if (est == GS_OK && ce != cudaSuccess)
+        est = fail(GS_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ce));
+      if (est == GS_OK) {
+        const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+        if (ie != cudaSuccess) est = fail(GS_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+      }
+      if (graph) cudaGraphDestroy(graph);
+      status = est;
+      for (int it = 1; it < iters && status == GS_OK; ++it) {
+        const cudaError_t le = cudaGraphLaunch(exec, st);
+        if (le != cudaSuccess) status = fail(GS_ERR_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(le));
+      }
+    } else {
+      for (int it = 1; it < iters && status == GS_OK; ++it) {
+        status = enqueue(s, hv, ranges, n_tiles, &g, st, nullptr, nullptr, nullptr, nullptr, false, nullptr, true);
+        if (status == GS_OK) status = launch_update(st);
+      }
+    }
+    if (status != GS_OK) break;
+    unsigned int sticky = 0;
+    std::vector<RefineState> h1(nv);
+    if (cudaMemcpyAsync(&sticky, dsticky, sizeof(sticky), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(h1.data(), drs, nv * sizeof(RefineState), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        (loss_history && cudaMemcpyAsync(loss_history, dhist, (size_t)nv * iters * sizeof(double),
+                                         cudaMemcpyDeviceToHost, st) != cudaSuccess) ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      status = fail(GS_ERR_CUDA, "refinement read-back failed");
+      break;
+    }
+    if (sticky & 0x100u) {
+      status = fail(GS_ERR_INTERNAL, "device consistency check failed");
+      break;
+    }
+    if (sticky & 4u) {
+      status = fail(GS_ERR_CAPACITY, "more than 2^32 (tile, Gaussian) pairs in one call");
+      break;
+    }
+    if (sticky) {  // a later pose outgrew the workspace: double it and start again
+      if (attempt == 3) {
+        status = fail(GS_ERR_CAPACITY, "refinement workspace did not converge");
+        break;
+      }
+      status = grow_records(s, (uint64_t)s->rec_cap * 2, true);
+      if (status == GS_OK) status = grow_pairs(s, (uint64_t)s->pair_cap * 2);
+      if (status != GS_OK) break;
+      continue;
+    }
+    for (int v = 0; v < nv; ++v) std::memcpy(poses[v].T_cw, h1[v].T, sizeof(poses[v].T_cw));
+    break;
+  }
+  if (status != GS_OK) cudaStreamSynchronize(st);  // nothing of this call may still use its state
+  cleanup();
+  return status;
+}
+
+}  // namespace gsr

@@ -156,6 +156,14 @@ cudaError_t launch_vis_chain(const View* views, const Work& w, const float* acc,
 cudaError_t launch_vis_compact(const uint8_t* mask, const float2* uv, int n, uint32_t* blk, int32_t* vis_gid,
                                float2* vis_uv, cudaStream_t st);
 
+// Adam pose refinement with the update on the device (single-partition,
+// non-streamed scenes; *used = false otherwise, and nothing is done). n views
+// refined together; loss_history: host, n x iterations or NULL.
+gs_status refine_on_device(gs_scene* s, int n_views, const gs_camera* cams, gs_pose* poses,
+                           const float* const* target_rgb, const float* const* target_depth,
+                           const float* const* pixel_weight, const gs_refine_opts* opts, double* loss_history,
+                           cudaStream_t st, bool* used);
+
 // occupancy-derived persistent grid sizes (per SM)
 int composite_blocks_per_sm(int feat_dim, bool tangent);
 

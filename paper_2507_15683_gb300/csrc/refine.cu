@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "gsr.h"
+#include "gsr_internal.h"
 
 namespace gsr {
 void set_last_error(const std::string& msg);
@@ -114,6 +114,13 @@ gs_status gs_refine_pose(gs_scene* scene, const gs_camera* cam, gs_pose* pose, c
   }
   const gs_status so = check_opts(opts);
   if (so != GS_OK) return so;
+  if (scene && cam) {
+    bool used = false;
+    const gs_status sd = gsr::refine_on_device(scene, 1, cam, pose, &target_rgb, &target_depth,
+                                               pixel_weight ? &pixel_weight : nullptr, opts, loss_history,
+                                               (cudaStream_t)stream, &used);
+    if (used) return sd;
+  }
   Adam adam;
   for (int it = 0; it < opts->iterations; ++it) {
     double loss = 0.0, g[6], step[6];
@@ -138,6 +145,12 @@ gs_status gs_refine_poses_batch(gs_scene* scene, int n_views, const gs_camera* c
   const gs_status so = check_opts(opts);
   if (so != GS_OK) return so;
   const cudaStream_t st = (cudaStream_t)stream;
+  if (scene && cams && target_rgb && target_depth) {
+    bool used = false;
+    const gs_status sd = gsr::refine_on_device(scene, n_views, cams, poses, target_rgb, target_depth, pixel_weight,
+                                               opts, loss_history, st, &used);
+    if (used) return sd;
+  }
   // first iteration synchronously (sizes the workspace), then graph replays
   std::vector<Adam> adam(n_views);
   std::vector<double> loss(n_views), grad(6 * (size_t)n_views), res(8 * (size_t)n_views);

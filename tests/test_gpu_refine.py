@@ -122,3 +122,66 @@ def test_device_adam_matches_a_host_adam_loop(oracle, gsr):
     np.testing.assert_allclose(T_dev[:3, :3], T[:3, :3], rtol=0, atol=1e-7)
     np.testing.assert_allclose(T_dev[:3, 3], T[:3, 3], rtol=0, atol=1e-5)
     S.close()
+
+
+def test_device_refinement_restarts_when_a_later_pose_outgrows_the_workspace(gsr):
+    """A nadir camera 5 m over a flat field of 100k Gaussians with a wide lens,
+    a depth target of 1000 m everywhere and a translation rate of 500 m: the
+    first Adam step lifts the camera to about 505 m, where it sees the whole
+    field. The first pass needs a few thousand records, the later ones more
+    than the scene's first workspace (65,536 records), so the device loop
+    overflows in a replayed iteration, doubles the workspace, restarts from the
+    caller's pose, and must still agree with the loop written here."""
+    n = 100_000
+    scene = synth.aerial_scene(62, n, extent=(0.0, 200.0, 0.0, 200.0), n_clusters=1, building_frac=0.0)
+    scene["means"][:, 2] = synth.rng(63).normal(0.0, 0.2, n).astype(np.float32)
+    cam = synth.camera(240, 136, 40.0)
+    q = synth.look_pose((100.0, 100.0, 5.0), 0.0, 0.0)
+    S = gsr.Scene(scene)
+    H = gsr.Scene(scene)
+    out = S.render(cam, q)
+    r = out["rgb"].clone()
+    d = torch.full_like(out["depth"], 1000.0)
+    opts = gsr.gs_refine_defaults()
+    opts.iterations = 3
+    opts.lr_trans = 500.0
+    opts.lr_rot = 0.0
+    opts.depth_weight = 10.0
+    T = np.array(q, np.float64)
+    m = np.zeros(6)
+    v = np.zeros(6)
+    lr = np.array([opts.lr_trans] * 3 + [opts.lr_rot] * 3)
+    losses, needs = [], []
+    for it in range(opts.iterations):
+        loss, g = H.render_pose_grad(cam, T, r, d, depth_weight=opts.depth_weight)
+        needs.append(H.status()[1])
+        losses.append(loss)
+        m = opts.beta1 * m + (1 - opts.beta1) * g
+        v = opts.beta2 * v + (1 - opts.beta2) * g * g
+        step = lr * (m / (1 - opts.beta1 ** (it + 1))) / (np.sqrt(v / (1 - opts.beta2 ** (it + 1))) + opts.eps)
+        w = -step[3:]
+        assert not w.any()
+        T = T.copy()
+        T[:3, 3] -= step[:3]  # Exp of a pure translation twist
+    print("records needed per pass", needs, "camera height %.1f m" % (-(T[:3, :3].T @ T[:3, 3]))[2])
+    assert needs[0] < 65536 < max(needs[1:])
+    p = gsr.pose(q)
+    hist = gsr.gs_refine_pose(S.handle, gsr.camera(cam), p, r.data_ptr(), d.data_ptr(), None, opts,
+                              torch.cuda.current_stream().cuda_stream)
+    np.testing.assert_allclose(hist, losses, rtol=1e-6)
+    np.testing.assert_allclose(gsr.pose_matrix(p), T, rtol=0, atol=1e-6)
+    # the same through the batched driver, beside a second view that stays small
+    q2 = synth.look_pose((50.0, 50.0, 8.0), 0.3, 0.0)
+    o2 = S.render(cam, q2)
+    p_single = gsr.pose(q2)
+    gsr.gs_refine_pose(S.handle, gsr.camera(cam), p_single, o2["rgb"].data_ptr(), o2["depth"].data_ptr(), None,
+                       opts, torch.cuda.current_stream().cuda_stream)
+    poses = [gsr.pose(q), gsr.pose(q2)]
+    hb = gsr.gs_refine_poses_batch(S.handle, [gsr.camera(cam)] * 2, poses, [r.data_ptr(), o2["rgb"].data_ptr()],
+                                   [d.data_ptr(), o2["depth"].data_ptr()], None, opts,
+                                   torch.cuda.current_stream().cuda_stream)
+    np.testing.assert_array_equal(gsr.pose_matrix(poses[0]), gsr.pose_matrix(p))
+    np.testing.assert_array_equal(gsr.pose_matrix(poses[1]), gsr.pose_matrix(p_single))
+    np.testing.assert_array_equal(hb[0], hist)
+    S.close()
+    H.close()

@@ -11,50 +11,80 @@ namespace gsr {
 namespace {
 
 constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 8;                             // counts per thread and chunk
+constexpr int kScanChunk = kScanThreads * kScanPer;     // counts per chunk (32 KB of shared memory)
 
 // Exclusive scan of tile_count[0..n) into tile_offset[0..n] and tile_cursor,
-// by one CTA: each thread owns a contiguous chunk. Also publishes the total
-// and flags an overflow of the pair capacity.
+// by one CTA, in chunks of kScanChunk counts with a 64-bit carry: coalesced
+// loads into shared memory, each thread then sums kScanPer consecutive counts,
+// a block scan of those sums, and coalesced stores of the offsets. Also
+// publishes the total and flags an overflow of the pair capacity.
 __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(Work w) {
+  __shared__ uint32_t sv[kScanChunk];
   __shared__ unsigned long long warp_tot[kScanThreads / 32];
+  __shared__ unsigned long long s_carry;
   const uint32_t n = w.n_tiles;
-  const uint32_t per = (n + kScanThreads - 1) / kScanThreads;
-  const uint32_t b = threadIdx.x * per;
-  const uint32_t e = b + per < n ? b + per : n;
-  unsigned long long s = 0;
-  for (uint32_t k = b; k < e; ++k) s += w.tile_count[k];
-  // block exclusive scan of s
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  unsigned long long incl = s;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) s_carry = 0ull;
+  for (uint32_t base = 0; base < n; base += kScanChunk) {  // block-uniform
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
-  }
-  if (lane == 31) warp_tot[wid] = incl;
-  __syncthreads();
-  if (wid == 0) {
-    unsigned long long x = warp_tot[lane];
-    unsigned long long y = x;
+    for (int i = 0; i < kScanPer; ++i) {
+      const uint32_t k = base + (uint32_t)(i * kScanThreads + tid);
+      sv[i * kScanThreads + tid] = k < n ? w.tile_count[k] : 0u;
+    }
+    __syncthreads();
+    uint32_t c[kScanPer];
+    unsigned long long s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) {
+      c[i] = sv[tid * kScanPer + i];
+      s += c[i];
+    }
+    // block exclusive scan of s
+    unsigned long long incl = s;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long t = __shfl_up_sync(0xffffffffu, y, o);
-      if (lane >= o) y += t;
+      const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
     }
-    warp_tot[lane] = y - x;  // exclusive warp offsets
-  }
-  __syncthreads();
-  unsigned long long run = warp_tot[wid] + incl - s;
-  for (uint32_t k = b; k < e; ++k) {
-    w.tile_offset[k] = (uint32_t)run;
-    w.tile_cursor[k] = (uint32_t)run;
-    run += w.tile_count[k];
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      const unsigned long long x = warp_tot[lane];
+      unsigned long long y = x;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, y, o);
+        if (lane >= o) y += t;
+      }
+      warp_tot[lane] = y - x;  // exclusive warp offsets
+    }
+    __syncthreads();
+    const unsigned long long carry = s_carry;
+    unsigned long long run = carry + warp_tot[wid] + incl - s;
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) {
+      sv[tid * kScanPer + i] = (uint32_t)run;
+      run += c[i];
+    }
+    __syncthreads();  // every thread has read s_carry and written its offsets
+    if (tid == kScanThreads - 1) s_carry = run;
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) {
+      const uint32_t k = base + (uint32_t)(i * kScanThreads + tid);
+      if (k < n) {
+        const uint32_t o = sv[i * kScanThreads + tid];
+        w.tile_offset[k] = o;
+        w.tile_cursor[k] = o;
+      }
+    }
+    __syncthreads();  // sv and s_carry are reused by the next chunk
   }
   // counters of the backward's chunked reduction start at zero every call
-  for (uint32_t k = threadIdx.x; k < w.n_chunks; k += kScanThreads) w.chunk_ctr[k] = 0u;
-  for (uint32_t k = threadIdx.x; k < w.n_views && w.n_chunks; k += kScanThreads) w.view_ctr[k] = 0u;
-  if (threadIdx.x == kScanThreads - 1) {
-    const unsigned long long total = run;
+  for (uint32_t k = tid; k < w.n_chunks; k += kScanThreads) w.chunk_ctr[k] = 0u;
+  for (uint32_t k = tid; k < w.n_views && w.n_chunks; k += kScanThreads) w.view_ctr[k] = 0u;
+  if (tid == 0) {
+    const unsigned long long total = s_carry;
     w.tile_offset[n] = (uint32_t)total;
     w.ctr->pair_total = total > 0xffffffffull ? 0xffffffffu : (uint32_t)total;
     if (total > 0xffffffffull) atomicOr(&w.ctr->overflow, 4u);

@@ -117,6 +117,21 @@ def test_visibility_structural_cases(oracle, gsr):
     assert g["uv"][4, 0] < 0
 
 
+def test_visibility_exact_image_edges(oracle, gsr):
+    """Algorithm 1's half-open image: centres projected exactly onto the left and
+    top edges are in, exactly onto the right and bottom edges are out (16 x 16
+    image, f = c = 8, z = 1: x = -1 gives u = 0, x = 1 gives u = 16)."""
+    cam = {"width": 16, "height": 16, "fx": 8.0, "fy": 8.0, "cx": 8.0, "cy": 8.0}
+    means = [[-1.0, 0.0, 1.0], [1.0, 0.0, 1.0], [0.0, -1.0, 1.0], [0.0, 1.0, 1.0]]
+    sc = scene_of(means, [[0.05] * 3] * 4, opacities=[0.9] * 4, dc=[[0.5, 0.5, 0.5]] * 4)
+    o = oracle.visibility(sc, cam, np.eye(4), want_grad=False)
+    g = _gpu(gsr, sc, cam, np.eye(4))
+    _consistent(g, cam)
+    np.testing.assert_array_equal(g["uv"], [[0.0, 8.0], [16.0, 8.0], [8.0, 0.0], [8.0, 16.0]])
+    np.testing.assert_array_equal((g["mask"] & 4) != 0, o["M_i"])
+    assert list(o["M_i"]) == [True, False, True, False]
+
+
 def test_visibility_small_aerial(oracle, gsr):
     """240 x 136 (15 x 9 tiles, ragged last row), 20,000 Gaussians, view-dependent
     colour: every Gaussian's M^i, and M^r / gradient of every Gaussian without a

@@ -183,6 +183,10 @@ struct gs_scene {
   // banded tangent pass: two streams that take the bands in turn, and the
   // events between the binning, the band uploads and the band launches
   cudaStream_t band_st[2] = {nullptr, nullptr};
+  // the shading pass runs on side_st beside the binning (fork after the
+  // projection, join before the compositing)
+  cudaStream_t side_st = nullptr;
+  cudaEvent_t ev_proj = nullptr, ev_shade = nullptr;
   cudaEvent_t ev_binned = nullptr;
   cudaEvent_t ev_band[kMaxBands] = {};
   cudaEvent_t ev_band_done[kMaxBands] = {};
@@ -440,13 +444,27 @@ gs_status enqueue(gs_scene* s, const std::vector<View>& hv, const std::vector<in
   GS_CUDA(mark(0));
   GS_CUDA(launch_project(sc, dviews, nv, w, s->sm_count * 8, st));
   GS_CUDA(mark(1));
-  GS_CUDA(launch_shade(sc, dviews, w, jac, s->sm_count * 8, st));
+  // The shading pass reads only what the projection wrote, and the binning
+  // (scan, scatter, sort) reads nothing the shading writes (the sort's tie key,
+  // the Gaussian index in rec_b.w, is written by the projection alone), so the
+  // two run side by side and join before the compositing. Kernel timing keeps
+  // them in order.
+  const bool fork = !timed && s->side_st != nullptr;
+  if (fork) {
+    GS_CUDA(cudaEventRecord(s->ev_proj, st));
+    GS_CUDA(cudaStreamWaitEvent(s->side_st, s->ev_proj, 0));
+    GS_CUDA(launch_shade(sc, dviews, w, jac, s->sm_count * 8, s->side_st));
+    GS_CUDA(cudaEventRecord(s->ev_shade, s->side_st));
+  } else {
+    GS_CUDA(launch_shade(sc, dviews, w, jac, s->sm_count * 8, st));
+  }
   GS_CUDA(mark(2));
   GS_CUDA(launch_scan_tiles(w, st));
   GS_CUDA(mark(3));
   GS_CUDA(launch_scatter(dviews, w, s->sm_count * 8, st));
   GS_CUDA(mark(4));
   GS_CUDA(launch_sort_tiles(w, s->sm_count * 8, st));
+  if (fork) GS_CUDA(cudaStreamWaitEvent(st, s->ev_shade, 0));
   GS_CUDA(mark(5));
   bool feats = false;
   for (const View& V : hv) feats = feats || V.feats != nullptr;
@@ -860,6 +878,10 @@ gs_status gs_create_scene(const gs_scene_desc* d, gs_scene** out) {
   e = cudaGetDeviceProperties(&prop, s->device);
   if (e != cudaSuccess) return cleanup(fail(GS_ERR_CUDA, std::string("cudaGetDeviceProperties: ") + cudaGetErrorString(e)));
   s->sm_count = prop.multiProcessorCount;
+  e = cudaStreamCreateWithFlags(&s->side_st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_proj, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_shade, cudaEventDisableTiming);
+  if (e != cudaSuccess) return cleanup(fail(GS_ERR_CUDA, std::string("stream / event creation: ") + cudaGetErrorString(e)));
   const size_t n = (size_t)d->n;
   gs_status st;
   if ((st = ensure(s->pos, n * sizeof(float4))) != GS_OK) return cleanup(st);
@@ -1011,6 +1033,9 @@ void gs_destroy_scene(gs_scene* s) {
   if (s->copy_st) cudaStreamDestroy(s->copy_st);
   for (cudaStream_t b : s->band_st)
     if (b) cudaStreamDestroy(b);
+  if (s->side_st) cudaStreamDestroy(s->side_st);
+  if (s->ev_proj) cudaEventDestroy(s->ev_proj);
+  if (s->ev_shade) cudaEventDestroy(s->ev_shade);
   if (s->ev_binned) cudaEventDestroy(s->ev_binned);
   for (int b = 0; b < kMaxBands; ++b) {
     if (s->ev_band[b]) cudaEventDestroy(s->ev_band[b]);

@@ -444,7 +444,10 @@ __global__ void __launch_bounds__(256, 3) k_shade(SceneDev sc, const View* __res
     const ff fv = ff_project(fpy, fpz, V.fy, V.cy);
     const __half2 lo2 = __floats2half2_rn(fu.lo, fv.lo);
     w.rec_a[slot] = make_float4(fu.hi, fv.hi, A, B);
-    w.rec_b[slot] = make_float4(C, c1.z, pz, __int_as_float(i));
+    // rec_b.w (the Gaussian index, the sort's tie key) stays as the projection wrote it
+    float* rb = reinterpret_cast<float*>(w.rec_b + slot);
+    *reinterpret_cast<float2*>(rb) = make_float2(C, c1.z);
+    rb[2] = pz;
     w.rec_c[slot] = make_float4(rgb[0], rgb[1], rgb[2], *reinterpret_cast<const float*>(&lo2));
 
     if (GRAD) {

@@ -454,6 +454,10 @@ gs_status enqueue(gs_scene* s, const std::vector<View>& hv, const std::vector<in
     GS_CUDA(cudaEventRecord(s->ev_proj, st));
     GS_CUDA(cudaStreamWaitEvent(s->side_st, s->ev_proj, 0));
     GS_CUDA(launch_shade(sc, dviews, w, jac, s->sm_count * 8, s->side_st));
+    if (vis) {  // Algorithm 1's in-image test and the reverse pass's zeroed accumulator need no binning
+      GS_CUDA(cudaMemsetAsync(dp<float>(s->vis_acc), 0, (size_t)s->rec_cap * kVisAcc * sizeof(float), s->side_st));
+      GS_CUDA(launch_vis_inimage(sc, dviews, vis->mask, vis->uv, vis->grad, s->sm_count * 8, s->side_st));
+    }
     GS_CUDA(cudaEventRecord(s->ev_shade, s->side_st));
   } else {
     GS_CUDA(launch_shade(sc, dviews, w, jac, s->sm_count * 8, st));
@@ -502,10 +506,10 @@ gs_status enqueue(gs_scene* s, const std::vector<View>& hv, const std::vector<in
   if (vis) {
     // Algorithm 1: reverse pass of sum RGB, then the per-Gaussian tests
     float* acc = dp<float>(s->vis_acc);
-    GS_CUDA(cudaMemsetAsync(acc, 0, (size_t)s->rec_cap * kVisAcc * sizeof(float), st));
+    if (!fork) GS_CUDA(cudaMemsetAsync(acc, 0, (size_t)s->rec_cap * kVisAcc * sizeof(float), st));
     GS_CUDA(launch_vis_backward(dviews, nv, w, acc, s->sm_count, st));
     GS_CUDA(mark(7));
-    GS_CUDA(launch_vis_inimage(sc, dviews, vis->mask, vis->uv, vis->grad, s->sm_count * 8, st));
+    if (!fork) GS_CUDA(launch_vis_inimage(sc, dviews, vis->mask, vis->uv, vis->grad, s->sm_count * 8, st));
     GS_CUDA(launch_vis_chain(dviews, w, acc, vis->mask, vis->grad, s->sm_count * 8, st));
     GS_CUDA(launch_vis_compact(vis->mask, vis->uv, (int)s->n, dp<uint32_t>(s->vis_blk), vis->vis_gid, vis->vis_uv,
                                st));

@@ -397,32 +397,64 @@ __global__ void __launch_bounds__(kTileThreads) k_pmm_tiles(const uint4* __restr
   }
 }
 
-// fixed-order reductions of the per-tile partials (thread per row / column)
-__global__ void k_pmm_lse(const float* __restrict__ part, int nb, int n, float inv_tau, float* __restrict__ lse) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+// Fixed-order reductions of the per-tile partials: a CTA takes 32 rows (or
+// columns), warp g of its 8 the partials g, g + 8, ... in ascending order
+// (coalesced over the 32 rows), then the 8 warp results are combined in order.
+constexpr int kRedRows = 32;
+constexpr int kRedWarps = 8;
+
+__global__ void __launch_bounds__(kRedRows * kRedWarps) k_pmm_lse(const float* __restrict__ part, int nb, int n,
+                                                                  float inv_tau, float* __restrict__ lse) {
+  __shared__ float sp[kRedWarps][kRedRows];
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int i = blockIdx.x * kRedRows + lane;
   float s = 0.0f;
-#pragma unroll 8
-  for (int b = 0; b < nb; ++b) s += part[(size_t)b * n + i];
-  lse[i] = inv_tau + logf(s);  // log sum exp(M / tau) = 1 / tau + log sum exp((M - 1) / tau)
+  if (i < n) {
+#pragma unroll 4
+    for (int b = g; b < nb; b += kRedWarps) s += part[(size_t)b * n + i];
+  }
+  sp[g][lane] = s;
+  __syncthreads();
+  if (g == 0 && i < n) {
+    float t = sp[0][lane];
+#pragma unroll
+    for (int k = 1; k < kRedWarps; ++k) t += sp[k][lane];
+    lse[i] = inv_tau + logf(t);  // log sum exp(M / tau) = 1 / tau + log sum exp((M - 1) / tau)
+  }
 }
 
-__global__ void k_pmm_best(const float* __restrict__ pv, const int* __restrict__ pi, int nb, int n,
-                           int* __restrict__ best) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+__global__ void __launch_bounds__(kRedRows * kRedWarps) k_pmm_best(const float* __restrict__ pv,
+                                                                   const int* __restrict__ pi, int nb, int n,
+                                                                   int* __restrict__ best) {
+  __shared__ float sv[kRedWarps][kRedRows];
+  __shared__ int si[kRedWarps][kRedRows];
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int i = blockIdx.x * kRedRows + lane;
   float bv = -INFINITY;
   int bi = 0x7fffffff;
-#pragma unroll 8
-  for (int b = 0; b < nb; ++b) {
-    const float v = pv[(size_t)b * n + i];
-    const int x = pi[(size_t)b * n + i];
-    if (better(v, x, bv, bi)) {
-      bv = v;
-      bi = x;
+  if (i < n) {
+#pragma unroll 4
+    for (int b = g; b < nb; b += kRedWarps) {
+      const float v = pv[(size_t)b * n + i];
+      const int x = pi[(size_t)b * n + i];
+      if (better(v, x, bv, bi)) {
+        bv = v;
+        bi = x;
+      }
     }
   }
-  best[i] = bi;
+  sv[g][lane] = bv;
+  si[g][lane] = bi;
+  __syncthreads();
+  if (g == 0 && i < n) {
+#pragma unroll
+    for (int k = 1; k < kRedWarps; ++k)
+      if (better(sv[k][lane], si[k][lane], bv, bi)) {
+        bv = sv[k][lane];
+        bi = si[k][lane];
+      }
+    best[i] = bi;
+  }
 }
 
 __device__ __forceinline__ float dot_codes(const __nv_bfloat16* a, const __nv_bfloat16* b) {
@@ -777,15 +809,16 @@ gs_status gs_pmm_match(gs_pmm* m, const float* feat_query, const float* feat_ren
   k_pmm_tiles<1><<<grid, kTileThreads, kTileSmemBytes, st>>>(cq, cr, n, nb, s_exp, s_two, nullptr, m->prow_v,
                                                              nullptr, m->pcol_v, err);
   PMM_CUDA(cudaGetLastError());
-  k_pmm_lse<<<rg, 256, 0, st>>>(m->prow_v, nb, n, inv_tau, m->lse_row);
-  k_pmm_lse<<<rg, 256, 0, st>>>(m->pcol_v, nb, n, inv_tau, m->lse_col);
+  const int rd = (n + kRedRows - 1) / kRedRows;
+  k_pmm_lse<<<rd, kRedRows * kRedWarps, 0, st>>>(m->prow_v, nb, n, inv_tau, m->lse_row);
+  k_pmm_lse<<<rd, kRedRows * kRedWarps, 0, st>>>(m->pcol_v, nb, n, inv_tau, m->lse_col);
   // pass 2: row argmax of log P_M, then (operands swapped) its column argmax
   k_pmm_tiles<2><<<grid, kTileThreads, kTileSmemBytes, st>>>(cq, cr, n, nb, s_exp, s_two, m->lse_col, m->prow_v,
                                                              m->prow_i, nullptr, err);
-  k_pmm_best<<<rg, 256, 0, st>>>(m->prow_v, m->prow_i, nb, n, m->row_best);
+  k_pmm_best<<<rd, kRedRows * kRedWarps, 0, st>>>(m->prow_v, m->prow_i, nb, n, m->row_best);
   k_pmm_tiles<2><<<grid, kTileThreads, kTileSmemBytes, st>>>(cr, cq, n, nb, s_exp, s_two, m->lse_row, m->prow_v,
                                                              m->prow_i, nullptr, err);
-  k_pmm_best<<<rg, 256, 0, st>>>(m->prow_v, m->prow_i, nb, n, m->col_best);
+  k_pmm_best<<<rd, kRedRows * kRedWarps, 0, st>>>(m->prow_v, m->prow_i, nb, n, m->col_best);
   PMM_CUDA(cudaGetLastError());
   // mutual nearest neighbours in ascending query order
   k_pmm_mnn<<<rg, 256, 0, st>>>(n, m->row_best, m->col_best, m->codes_q, m->codes_r, m->lse_row, m->lse_col, s_two,

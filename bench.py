@@ -205,11 +205,37 @@ def cpu_baseline(scene, cam, T_ref, T_q, budget_s: float):
         if dt > budget_s / 3 or n_pix >= H * W:
             break
         n_pix = min(H * W, int(n_pix * max(2.0, budget_s / 2 / max(dt, 1e-3))))
+    # the same step on one core, on a sample sized for about a fifth of the budget
+    n1 = max(1024, min(H * W, int(n_pix * (budget_s / 5) / max(dt * n_thr, 1e-3))))
+    pix1 = np.sort(g.choice(H * W, n1, replace=False))
+    w1 = np.zeros((H, W), np.float32)
+    w1.reshape(-1)[pix1] = 1.0
+    t0 = time.perf_counter()
+    O.render(scene, cam, T_q, geom64=True, want_grad=True, pixels=pix1, target_rgb=trgb, target_depth=tdep,
+             pixel_weight=w1, n_threads=1)
+    dt1 = time.perf_counter() - t0
     return {"value": n_pix / dt / 1e6, "unit": "Mpix/s", "cores": n_thr, "kind": "oracle",
             "sample": "fp64 oracle pose-gradient step (projection of all 1M Gaussians, binning, fp64 "
                       "compositing + forward-mode se(3) gradient) on %d random pixels of the 1080p frame; "
                       "%.2f s per step" % (n_pix, dt),
+            "single_thread": {"value": n1 / dt1 / 1e6, "unit": "Mpix/s", "cores": 1,
+                              "sample": "the same step on %d random pixels, %.2f s" % (n1, dt1)},
+            "cpu_model": cpu_model(),
             "loss": r["loss"], "target_render_s": t_ref}
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), else the machine type."""
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.machine()
 
 
 def run_reference(args):

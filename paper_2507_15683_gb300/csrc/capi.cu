@@ -1656,7 +1656,7 @@ gs_status refine_on_device(gs_scene* s, int nv, const gs_camera* cams, gs_pose* 
     if (dsticky) cudaFree(dsticky);
   };
   if (cudaMalloc(&drs, nv * sizeof(RefineState)) != cudaSuccess ||
-      cudaMalloc(&dhist, (size_t)nv * iters * sizeof(double)) != cudaSuccess ||
+      (loss_history && cudaMalloc(&dhist, (size_t)nv * iters * sizeof(double)) != cudaSuccess) ||
       cudaMalloc(&dsticky, sizeof(unsigned int)) != cudaSuccess) {
     cudaGetLastError();
     cleanup();

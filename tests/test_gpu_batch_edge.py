@@ -212,3 +212,26 @@ def test_short_lists_with_equal_depths(oracle, gsr, n):
     np.testing.assert_array_equal(ggids, gids)
     compare_images(to_numpy(out, 64, 64), oracle.render(scene, cam, np.eye(4), geom64=True), oracle)
     S.close()
+
+
+def test_kernel_timing_changes_no_result(gsr):
+    """With kernel timing on, the shading pass runs in order after the
+    projection instead of beside the binning: images and the pose gradient
+    must be bit-identical either way."""
+    scene = _scene()
+    cams, poses = _views()
+    cam, T = cams[0], poses[0]
+    S = gsr.Scene(scene)
+    ref = S.render(cam, T)
+    tr, td = ref["rgb"].clone(), ref["depth"].clone()
+    Tq = synth.perturb_pose(T, synth.rng(5), 1.0, 1.0)
+    a = S.render(cam, Tq)
+    la, ga = S.render_pose_grad(cam, Tq, tr, td)
+    gsr.gs_scene_set_timing(S.handle, True)
+    b = S.render(cam, Tq)
+    lb, gb = S.render_pose_grad(cam, Tq, tr, td)
+    gsr.gs_scene_set_timing(S.handle, False)
+    _eq(a, b)
+    assert la == lb
+    np.testing.assert_array_equal(ga, gb)
+    S.close()

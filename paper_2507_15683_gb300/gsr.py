@@ -639,12 +639,19 @@ class Matcher:
         except Exception:
             pass
 
-    def match(self, feat_query, feat_render, tau: float = 0.1) -> dict:
+    def match_raw(self, feat_query, feat_render, tau: float = 0.1):
+        """The gs_pmm_match call alone: its result struct, whose device arrays
+        belong to the matcher until its next call."""
         import torch
         for f in (feat_query, feat_render):
             if not (f.is_cuda and f.dtype == torch.float32 and f.is_contiguous() and f.shape[1:] == (self.H, self.W)):
                 raise ValueError("feature maps must be contiguous float32 CUDA tensors of shape (32, H, W)")
-        r = gs_pmm_match(self.handle, feat_query.data_ptr(), feat_render.data_ptr(), tau, _stream())
+        return gs_pmm_match(self.handle, feat_query.data_ptr(), feat_render.data_ptr(), tau, _stream())
+
+    def match(self, feat_query, feat_render, tau: float = 0.1) -> dict:
+        """match_raw, with copies of the matcher's device outputs."""
+        import torch
+        r = self.match_raw(feat_query, feat_render, tau)
         n, nc, nf = r.n_cells, r.n_coarse, r.n_fine
         v = lambda p, shape, t: torch.as_tensor(_DevView(p, shape, t), device="cuda").clone()
         return {"codes_q": v(r.codes_q, (n, 32), "<u2"), "codes_r": v(r.codes_r, (n, 32), "<u2"),
@@ -711,10 +718,10 @@ class PnP:
         except Exception:
             pass
 
-    def solve(self, cam, T_render, depth, alpha, matches, words, tau=2.0, min_alpha=0.5, refine_iters=5) -> dict:
-        """depth, alpha: (H, W) float32 CUDA tensors rendered at T_render; matches:
-        (K, 3) int32 CUDA tensor (PMM fine layout); words: (n_hyp, 3) int32 or
-        uint32-bits CUDA tensor of random words."""
+    def solve_raw(self, cam, T_render, depth, alpha, matches, words, tau=2.0, min_alpha=0.5,
+                  refine_iters=5) -> "gs_pnp_result":
+        """The gs_pnp_solve call alone: its result struct, whose device arrays
+        belong to the solver until its next call."""
         import torch
         for t, dt in ((depth, torch.float32), (alpha, torch.float32), (matches, torch.int32)):
             if not (t.is_cuda and t.dtype == dt and t.is_contiguous()):
@@ -723,8 +730,17 @@ class PnP:
             raise ValueError("words must be a contiguous 32-bit CUDA tensor")
         o = gs_pnp_opts(tau, min_alpha, refine_iters)
         K, nh = int(matches.shape[0]), int(words.shape[0])
-        r = gs_pnp_solve(self.handle, camera(cam), pose(T_render), depth.data_ptr(), alpha.data_ptr(),
-                         matches.data_ptr() if K else None, K, words.data_ptr() if nh else None, nh, o, _stream())
+        return gs_pnp_solve(self.handle, camera(cam), pose(T_render), depth.data_ptr(), alpha.data_ptr(),
+                            matches.data_ptr() if K else None, K, words.data_ptr() if nh else None, nh, o,
+                            _stream())
+
+    def solve(self, cam, T_render, depth, alpha, matches, words, tau=2.0, min_alpha=0.5, refine_iters=5) -> dict:
+        """depth, alpha: (H, W) float32 CUDA tensors rendered at T_render; matches:
+        (K, 3) int32 CUDA tensor (PMM fine layout); words: (n_hyp, 3) int32 or
+        uint32-bits CUDA tensor of random words."""
+        import torch
+        r = self.solve_raw(cam, T_render, depth, alpha, matches, words, tau, min_alpha, refine_iters)
+        K, nh = int(matches.shape[0]), int(words.shape[0])
         nv = r.n_valid
         v = lambda p, shape, t: torch.as_tensor(_DevView(p, shape, t), device="cuda").clone()
         empty = lambda shape, dt: torch.zeros(shape, dtype=dt, device="cuda")

@@ -495,61 +495,84 @@ __global__ void k_pmm_mnn_scatter(int n, const int* __restrict__ row_best, const
 // ---------------------------------------------------------------------------
 // fine level: one CTA of 64 threads per coarse match
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kWin) k_pmm_fine(const float* __restrict__ Fq, const float* __restrict__ Fr, int H,
-                                                   int W, int Wc, const int* __restrict__ coarse, float inv_tau,
-                                                   float s_exp, float s_two, int* __restrict__ slot_r,
-                                                   float* __restrict__ slot_p, int* __restrict__ win_count,
-                                                   const int* __restrict__ n_coarse) {
+constexpr int kQs = kC + 1;  // row stride of the staged query vectors (conflict-free reads by row)
+
+__global__ void __launch_bounds__(kWin, 8) k_pmm_fine(const float* __restrict__ Fq, const float* __restrict__ Fr,
+                                                      int H, int W, int Wc, const int* __restrict__ coarse,
+                                                      float inv_tau, float s_exp, float s_two,
+                                                      int* __restrict__ slot_r, float* __restrict__ slot_p,
+                                                      int* __restrict__ win_count, const int* __restrict__ n_coarse) {
   __shared__ __align__(16) float ur[kWin][kC];  // rendered unit vectors (read as float4 broadcasts)
-  __shared__ float Mf[kWin][kWin + 1];
+  __shared__ float Mf[kWin][kWin + 1];          // similarities; first the query unit vectors (row stride kQs)
   __shared__ float lr[kWin], lc[kWin];
+  __shared__ float rsh[2][kWin];                // row exp sums of the two column halves
   __shared__ int rbest[kWin], cbest[kWin];
+  static_assert(kWin * kQs <= kWin * (kWin + 1), "the staged query vectors fit in the similarity buffer");
   const int k = blockIdx.x, a = threadIdx.x;
   if (k >= *n_coarse) return;  // launched for every cell; the coarse count is known on the device only
   const int ci = coarse[2 * k], cj = coarse[2 * k + 1];
   const size_t HW = (size_t)H * W;
   const int qy = (ci / Wc) * kRatio + a / kRatio, qx = (ci % Wc) * kRatio + a % kRatio;
   const int ry = (cj / Wc) * kRatio + a / kRatio, rx = (cj % Wc) * kRatio + a % kRatio;
-  float uq[kC];  // this thread's query unit vector (fp32, channel order)
-  {
-    float vr[kC];
+  float* uqs = &Mf[0][0];
+  {  // thread a normalises query vector a and rendered vector a (fp32, channel order)
+    float vq[kC], vr[kC];
     float sq = 0.0f, sr = 0.0f;
 #pragma unroll
     for (int c = 0; c < kC; ++c) {
-      uq[c] = Fq[c * HW + (size_t)qy * W + qx];
+      vq[c] = Fq[c * HW + (size_t)qy * W + qx];
       vr[c] = Fr[c * HW + (size_t)ry * W + rx];
-      sq = fmaf(uq[c], uq[c], sq);
+      sq = fmaf(vq[c], vq[c], sq);
       sr = fmaf(vr[c], vr[c], sr);
     }
     const float iq = sq > 0.0f ? 1.0f / sqrtf(sq) : 0.0f, ir = sr > 0.0f ? 1.0f / sqrtf(sr) : 0.0f;
 #pragma unroll
     for (int c = 0; c < kC; ++c) {
-      uq[c] *= iq;
+      uqs[a * kQs + c] = vq[c] * iq;
       ur[a][c] = vr[c] * ir;
     }
   }
   __syncthreads();
-  float rs = 0.0f;  // row a: similarities and exp sum, four columns at a time (independent chains)
-  for (int b = 0; b < kWin; b += 4) {
-    float m[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  // thread a: query rows r0 and r0 + 32 against the 32 columns of half h, so
+  // that every broadcast of a rendered vector feeds both rows
+  const int r0 = a & 31, h = a >> 5;
+  float q0[kC], q1[kC];
+#pragma unroll
+  for (int c = 0; c < kC; ++c) {
+    q0[c] = uqs[r0 * kQs + c];
+    q1[c] = uqs[(r0 + 32) * kQs + c];
+  }
+  __syncthreads();  // the query vectors are in registers before the similarities overwrite them
+  float rs0 = 0.0f, rs1 = 0.0f;  // exp sums of rows r0 and r0 + 32 over this half
+  for (int b = 32 * h; b < 32 * h + 32; b += 4) {
+    float m0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, m1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int q = 0; q < kC / 4; ++q) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const float4 x = reinterpret_cast<const float4*>(ur[b + u])[q];
-        m[u] = fmaf(uq[4 * q], x.x, m[u]);
-        m[u] = fmaf(uq[4 * q + 1], x.y, m[u]);
-        m[u] = fmaf(uq[4 * q + 2], x.z, m[u]);
-        m[u] = fmaf(uq[4 * q + 3], x.w, m[u]);
+        m0[u] = fmaf(q0[4 * q], x.x, m0[u]);
+        m0[u] = fmaf(q0[4 * q + 1], x.y, m0[u]);
+        m0[u] = fmaf(q0[4 * q + 2], x.z, m0[u]);
+        m0[u] = fmaf(q0[4 * q + 3], x.w, m0[u]);
+        m1[u] = fmaf(q1[4 * q], x.x, m1[u]);
+        m1[u] = fmaf(q1[4 * q + 1], x.y, m1[u]);
+        m1[u] = fmaf(q1[4 * q + 2], x.z, m1[u]);
+        m1[u] = fmaf(q1[4 * q + 3], x.w, m1[u]);
       }
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      Mf[a][b + u] = m[u];
-      rs += exp2f((m[u] - 1.0f) * s_exp);
+      Mf[r0][b + u] = m0[u];
+      Mf[r0 + 32][b + u] = m1[u];
+      rs0 += exp2f((m0[u] - 1.0f) * s_exp);
+      rs1 += exp2f((m1[u] - 1.0f) * s_exp);
     }
   }
-  lr[a] = inv_tau + logf(rs);
+  rsh[h][r0] = rs0;
+  rsh[h][r0 + 32] = rs1;
+  __syncthreads();
+  lr[a] = inv_tau + logf(rsh[0][a] + rsh[1][a]);
   __syncthreads();
   float cs = 0.0f;  // column a
   for (int i = 0; i < kWin; ++i) cs += exp2f((Mf[i][a] - 1.0f) * s_exp);

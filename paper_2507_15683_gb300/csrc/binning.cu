@@ -104,6 +104,10 @@ __global__ void __launch_bounds__(256) k_scatter(const View* __restrict__ views,
   __shared__ uint32_t s_incl[8][32];
   __shared__ uint4 s_m[8][32];
   if (w.ctr->overflow) return;
+  // every slot a tile cursor hands out lies below the scanned total when the
+  // projection's tile counts and the records' rectangles agree; a slot past it
+  // is a consistency failure: reported (Counters.error), never written
+  const uint32_t pair_total = w.ctr->pair_total;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t nw = gridDim.x * 8;
   for (uint32_t base = (blockIdx.x * 8 + wid) * 32; base < w.rec_cap; base += nw * 32) {  // warp-uniform
@@ -151,8 +155,11 @@ __global__ void __launch_bounds__(256) k_scatter(const View* __restrict__ views,
         }
       }
 #pragma unroll
-      for (int u = 0; u < kScatterUnroll; ++u)
-        if (pos[u] != 0xffffffffu) w.pairs[pos[u]] = val[u];
+      for (int u = 0; u < kScatterUnroll; ++u) {
+        if (pos[u] == 0xffffffffu) continue;
+        if (pos[u] < pair_total) w.pairs[pos[u]] = val[u];
+        else atomicOr(&w.ctr->error, 1u);
+      }
     }
     __syncwarp();
   }

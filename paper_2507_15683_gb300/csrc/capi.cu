@@ -690,7 +690,7 @@ gs_status run_sync(gs_scene* s, const std::vector<View>& hv, uint64_t n_tiles, c
       GS_CUDA(cudaMemcpyAsync(s->result_host, s->result.p, 7 * sizeof(double), cudaMemcpyDeviceToHost, st));
     GS_CUDA(cudaStreamSynchronize(st));
     const Counters c = *s->ctr_host;
-    if (c.error) return fail(GS_ERR_INTERNAL, "device consistency check failed");
+    if (c.error) return fail(GS_ERR_INTERNAL, "device consistency check failed: the binning handed out a pair slot past the scanned tile counts");
     if (!c.overflow) return GS_OK;
     if (c.overflow & 4u) return fail(GS_ERR_CAPACITY, "more than 2^32 (tile, Gaussian) pairs in one call");
     const uint64_t need = records_capacity_needed(c);
@@ -828,7 +828,7 @@ gs_status run_sync_graphed(gs_scene* s, const std::vector<View>& hv, uint64_t n_
   GS_CUDA(cudaMemcpyAsync(s->result_host, s->result.p, 7 * sizeof(double), cudaMemcpyDeviceToHost, st));
   GS_CUDA(cudaStreamSynchronize(st));
   const Counters& c = *s->ctr_host;
-  if (c.error) return fail(GS_ERR_INTERNAL, "device consistency check failed");
+  if (c.error) return fail(GS_ERR_INTERNAL, "device consistency check failed: the binning handed out a pair slot past the scanned tile counts");
   if (c.overflow) {
     s->graph_sync.valid = false;
     return run_sync(s, hv, n_tiles, g, st);
@@ -1413,7 +1413,7 @@ gs_status gs_scene_status(gs_scene* s, void* stream, int64_t* needed_records, in
   GS_TRY(read_counters(s, (cudaStream_t)stream, c));
   if (needed_records) *needed_records = (int64_t)records_capacity_needed(c);
   if (needed_pairs) *needed_pairs = c.pair_total;
-  if (c.error) return fail(GS_ERR_INTERNAL, "device consistency check failed");
+  if (c.error) return fail(GS_ERR_INTERNAL, "device consistency check failed: the binning handed out a pair slot past the scanned tile counts");
   if (c.overflow) return fail(GS_ERR_CAPACITY, "workspace too small for the last asynchronous call");
   return GS_OK;
 }
@@ -1743,7 +1743,7 @@ gs_status refine_on_device(gs_scene* s, int nv, const gs_camera* cams, gs_pose* 
       break;
     }
     if (sticky & 0x100u) {
-      status = fail(GS_ERR_INTERNAL, "device consistency check failed");
+      status = fail(GS_ERR_INTERNAL, "device consistency check failed: the binning handed out a pair slot past the scanned tile counts");
       break;
     }
     if (sticky & 4u) {

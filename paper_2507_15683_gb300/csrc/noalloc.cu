@@ -34,6 +34,10 @@ unsigned char* g_scratch_addr[kMaxDevices] = {};
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// projection blocks of 256 Gaussians: one per block at the Gaussian limit
+constexpr int kProjBlocks = GS_NOALLOC_MAX_GAUSSIANS / 256;
+static_assert(GS_NOALLOC_MAX_GAUSSIANS % (256 * kRecRegions) == 0, "two projection blocks per record segment");
+
 // Byte offsets of each buffer inside the scratch array, for the stated limits.
 struct Layout {
   static constexpr size_t G = GS_NOALLOC_MAX_GAUSSIANS;
@@ -169,9 +173,10 @@ extern "C" gs_status gs_render_noalloc(const gs_scene_desc* d, const gs_camera* 
   w.rec_m = reinterpret_cast<uint4*>(base + Layout::rec_m);
   w.rec_j = nullptr;
   w.rec_cap = GS_NOALLOC_MAX_GAUSSIANS;
-  // Segment b % 64 receives the records of projection blocks b: with at most
-  // 32768 Gaussians the projection runs 128 blocks of 256, so a segment holds
-  // at most 2 x 256 = 512 = rec_cap / 64 records and cannot overflow.
+  // Segment b % 64 receives the records of projection block b. The projection
+  // below always runs kProjBlocks = 32768 / 256 = 128 blocks, one per 256
+  // Gaussians whatever the SM count, so a segment takes the records of two
+  // blocks, at most 2 x 256 = 512 = rec_cap / 64, and cannot overflow.
   w.rec_seg = GS_NOALLOC_MAX_GAUSSIANS / kRecRegions;
   w.tile_count = reinterpret_cast<uint32_t*>(base + Layout::tcount);
   w.tile_offset = reinterpret_cast<uint32_t*>(base + Layout::toffset);
@@ -202,7 +207,7 @@ extern "C" gs_status gs_render_noalloc(const gs_scene_desc* d, const gs_camera* 
   NA_CUDA(cudaMemcpyAsync(dranges, hranges, sizeof(hranges), cudaMemcpyHostToDevice, st));
   NA_CUDA(launch_pack_scene(d->means, d->scales, d->quats, d->opacities, d->sh, K3, d->feats_bf16, d->feat_dim, n,
                             nsh4, pos, cov, sh, d->feat_dim ? feat : nullptr, st));
-  NA_CUDA(launch_project(sc, dview, 1, w, sm_count * 8, st));
+  NA_CUDA(launch_project(sc, dview, 1, w, kProjBlocks, st));
   NA_CUDA(launch_shade(sc, dview, w, false, sm_count * 8, st));
   NA_CUDA(launch_scan_tiles(w, st));
   NA_CUDA(launch_scatter(dview, w, sm_count * 8, st));
@@ -212,6 +217,8 @@ extern "C" gs_status gs_render_noalloc(const gs_scene_desc* d, const gs_camera* 
   Counters c;
   NA_CUDA(cudaMemcpyAsync(&c, w.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
   NA_CUDA(cudaStreamSynchronize(st));
+  if (c.overflow & 1u)  // cannot happen with the fixed projection grid; reported apart from the pairs
+    return nfail(GS_ERR_INTERNAL, "a record segment overflowed in the no-alloc render");
   if (c.overflow)
     return nfail(GS_ERR_CAPACITY, "the view needs " + std::to_string(c.pair_total) +
                                       " (tile, Gaussian) pairs; the no-alloc limit is " +

@@ -411,7 +411,10 @@ def main():
     # large streamed scene: 6M Gaussians in 16 partitions, 8 poses through a 4-level pyramid
     large = None if args.no_large else bench_large(gsr, synth, torch)
     # dense matching of rendered feature maps (PMM, Eq. 11) at 1920x1080: 32,400 x 32,400 similarities
-    pmm = None if args.no_pmm else bench_pmm(gsr, synth, torch, pk_for_pmm(), max(3, args.steps // 4), args.warmup)
+    pmm = None
+    if not args.no_pmm:
+        pmm = bench_pmm(gsr, synth, torch, pk_for_pmm(), max(3, args.steps // 4), args.warmup,
+                        with_oracle=rank == 0 and world == 1 and not args.no_cpu)
     # Algorithm 1 visibility check of all 1M Gaussians from the query pose
     vis = None
     if not args.no_vis:
@@ -580,9 +583,12 @@ def pk_for_pmm():
     return pk, src
 
 
-def bench_pmm(gsr, synth, torch, pk_src, steps, warmup):
+def bench_pmm(gsr, synth, torch, pk_src, steps, warmup, with_oracle=False):
     """PMM (Sec. 3.4, Eq. 11) of the query-pose feature map against the reference
-    one, both rendered by the library from 1M Gaussians with 32 BF16 channels."""
+    one, both rendered by the library from 1M Gaussians with 32 BF16 channels.
+    With the oracle: the coarse decisions of the fp64 definition on the same
+    maps at 960x536, against the library's and against a single-bf16
+    contraction's."""
     pk, src = pk_src
     scene = synth.aerial_scene(2, 1_000_000, feat_dim=32)
     cam = synth.aerial_camera()
@@ -612,11 +618,14 @@ def bench_pmm(gsr, synth, torch, pk_src, steps, warmup):
     M.close()
     n = (H // 8) * (W // 8)
     sims = float(n) * n
-    mma_flops = 2 * 2 * 32 * sims  # two passes over the tiles, K = 32
+    mma_flops = 3 * 2 * 2 * 32 * sims  # three split products, two passes over the tiles, K = 32
     sm = torch.cuda.get_device_properties(0).multi_processor_count
     mufu_peak = sm * 16 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6  # exp2 per second (16 per SM per clock)
+    decisions = pmm_decisions(gsr, synth, torch, scene, T_ref, T_q) if with_oracle else None
     return {"workload": "PMM of 1920x1080 32-channel feature maps rendered from 1M Gaussians (query 2 deg / 5 m "
                         "off the reference): 8x8 coarse cells, tau 0.1, coarse MNN + 8x8-window fine MNN",
+            "coarse_precision": "split bf16 (hi + lo) operands, hi.hi + lo.hi + hi.lo, fp32 accumulation",
+            "decisions_vs_fp64_definition": decisions,
             "cells": n, "similarities": int(sims), "ms": ms, "coarse_matches": int(res["coarse"].shape[0]),
             "fine_matches": int(res["fine"].shape[0]),
             "similarities_per_s": sims / (ms * 1e-3),
@@ -626,6 +635,42 @@ def bench_pmm(gsr, synth, torch, pk_src, steps, warmup):
                        "note": "K = 32: the contraction is small; the epilogue (exp, reductions, argmax) bounds"},
             "exp": {"count": int(sims), "achieved_per_s": sims / (ms * 1e-3), "mufu_peak_per_s": mufu_peak,
                     "frac": sims / (ms * 1e-3) / mufu_peak}}
+
+
+def pmm_decisions(gsr, synth, torch, scene, T_ref, T_q):
+    """Coarse decisions of the library against the fp64 definition of Eq. 11 (the
+    oracle) on 960x536 feature maps rendered by the library: the fraction of
+    decisions clear of ties, the library's changes among those (must be 0), and
+    what a single-bf16 contraction (the oracle's precision layer) would change."""
+    from oracle import pmm as OP
+    cam = synth.aerial_camera(960, 536, 700.0)  # both sides multiples of the coarse ratio 8
+    S = gsr.Scene(scene)
+    maps = []
+    for T in (T_q, T_ref):
+        o = S.alloc_outputs(cam, feat_dim=32, last_idx=False)
+        S.render(cam, T, o)
+        maps.append(o["feats"].contiguous())
+    S.close()
+    M = gsr.Matcher(536, 960)
+    g = {k: v.cpu().numpy() for k, v in M.match(maps[0], maps[1]).items()}
+    M.close()
+    Fq, Fr = (m.cpu().numpy() for m in maps)
+    t0 = time.perf_counter()
+    d = OP.coarse_pmm(Fq, Fr)
+    dt = time.perf_counter() - t0
+    b = OP.coarse_pmm_bf16(Fq, Fr)
+    rok, cok = ~d["row_flag"], ~d["col_flag"]
+    gm = {tuple(x) for x in g["coarse"].tolist()}
+    dm = {tuple(x) for x in d["matches"].tolist()}
+    clear = lambda ij: rok[ij[0]] and cok[ij[1]]
+    return {"maps": "960x536 (8,040 coarse cells), library renders of the same scene and poses",
+            "clear_of_ties": {"rows": float(rok.mean()), "cols": float(cok.mean()), "tie_gap_logP": OP.TIE_GAP},
+            "library_vs_definition_clear": {
+                "rows": float((g["row_best"][rok] != d["row_best"][rok]).mean()),
+                "cols": float((g["col_best"][cok] != d["col_best"][cok]).mean()),
+                "matches": len({x for x in gm if clear(x)} ^ {x for x in dm if clear(x)}) / max(1, len(dm))},
+            "single_bf16_layer_vs_definition": OP.decision_changes(b, d),
+            "oracle_s": dt}
 
 
 def bench_visibility(gsr, torch, S, scene, cam, T, flush, steps, warmup, with_oracle):

@@ -56,7 +56,7 @@ typedef enum {
   GS_ERR_CUDA = 2,        /* a CUDA runtime call failed (message has the CUDA error) */
   GS_ERR_OOM = 3,         /* device or pinned host allocation failed */
   GS_ERR_CAPACITY = 4,    /* an asynchronous call outgrew the reserved workspace */
-  GS_ERR_TIMEOUT = 5,     /* reserved: bounded device waits expired */
+  GS_ERR_TIMEOUT = 5,     /* a bounded device wait ran out (gs_pmm_match); the context stays usable */
   GS_ERR_INTERNAL = 6     /* a device-side consistency check failed */
 } gs_status;
 

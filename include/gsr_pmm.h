@@ -10,10 +10,12 @@
  * coarse correspondence give the fine correspondences.
  *
  * Readings (the paper is silent): the coarse maps are the 8 x 8 block means of
- * the fine maps; vectors are L2-normalised (zero stays zero); the coarse unit
- * vectors are rounded to bfloat16, the precision of the similarity contraction
- * (fp32 accumulation) and so of the coarse decisions; ties in an argmax go to
- * the lower index; the fine window of a coarse position is its 8 x 8 block.
+ * the fine maps; vectors are L2-normalised (zero stays zero); tau = 0.1; ties
+ * in an argmax go to the lower index; the fine window of a coarse position is
+ * its 8 x 8 block. The coarse similarities are fp32-accurate cosines of the
+ * unrounded cell means: each binary32 unit mean u is split into bfloat16
+ * hi = bf16(u) and lo = bf16(u - hi) for the tensor cores, and M = hi.hi +
+ * lo.hi + hi.lo with fp32 accumulation (error about 2^-17).
  *
  * All pointers named feat_* and every pointer in gs_pmm_result are device
  * memory. Thread safety: one matcher per stream at a time.
@@ -46,8 +48,8 @@ gs_status gs_pmm_shape(const gs_pmm* matcher, int* channels, int* height, int* w
  * position, index cy * (W / 8) + cx; a pixel is y * W + x. */
 typedef struct {
   int32_t n_cells;           /* (H / 8) * (W / 8) */
-  const uint16_t* codes_q;   /* n_cells x 32 bfloat16: unit coarse query vectors */
-  const uint16_t* codes_r;   /* n_cells x 32: rendered */
+  const uint16_t* codes_q;   /* n_cells x 64 bfloat16: unit coarse query vectors u as hi[32], lo[32] (u = hi + lo) */
+  const uint16_t* codes_r;   /* n_cells x 64: rendered */
   const float* lse_row;      /* n_cells: log sum_j exp(M_ij / tau), query cell i */
   const float* lse_col;      /* n_cells: log sum_i exp(M_ij / tau), rendered cell j */
   const int32_t* row_best;   /* n_cells: argmax_j P_M[i, j] */
@@ -64,10 +66,22 @@ typedef struct {
  * planar (the layout of gs_outputs.feats), with temperature tau (>= 0.025, so
  * that exp(-2 / tau) stays a normal binary32 number; 0.1 in the paper's
  * setting). Synchronous on `stream`: the counts in *out are valid on return.
- * Errors: INVALID_ARG, CUDA, INTERNAL (a tensor-core completion wait timed
- * out; the matcher stays usable). */
+ * Errors: INVALID_ARG, CUDA, TIMEOUT (a tensor-core completion wait ran out
+ * of polls: the tile kernel drains the MMA in flight, frees its tensor
+ * memory and stops, the later kernels find no match, and the matcher stays
+ * usable for the next call). */
 gs_status gs_pmm_match(gs_pmm* matcher, const float* feat_query, const float* feat_render, float tau,
                        gs_pmm_result* out, void* stream);
+
+/* The bound on every tensor-core completion wait of the matcher's tile
+ * kernels, in mbarrier polls (default GS_PMM_DEFAULT_WAIT_POLLS, far beyond
+ * the two MMAs of a tile). A wait that runs out sets a device error flag and
+ * gs_pmm_match returns GS_ERR_TIMEOUT instead of spinning on. polls = 0 makes
+ * every first wait give up at once: the host-visible way to exercise that
+ * path without a fault (the drain that follows keeps the default bound).
+ * Errors: INVALID_ARG (NULL matcher, polls < 0). */
+#define GS_PMM_DEFAULT_WAIT_POLLS (1 << 22)
+gs_status gs_pmm_set_wait_limit(gs_pmm* matcher, int polls);
 
 #ifdef __cplusplus
 }

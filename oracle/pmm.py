@@ -15,11 +15,9 @@ Readings where the paper is silent (the same in the CUDA path):
 * coarse maps are the 8 x 8 block means of the fine maps (H, W multiples of 8);
 * feature vectors are L2-normalised before the dot product (cosine); a zero
   vector stays zero (similarity 0 with everything);
-* the coarse unit vectors are rounded to bfloat16, the precision in which both
-  sides take the argmax decisions: the block mean and the normalisation are
-  binary32 in one fixed operation order (sequential sums in row-major block
-  order, then over channels; no contraction), then round to nearest even;
-  the similarity of the bf16 vectors is exact in fp64 here;
+* the definition has no rounding of its own: the coarse level here is binary64
+  throughout (block means of the binary32 fine map, their norms and the
+  cosine matrix), i.e. Eq. 11 on the unrounded cell means;
 * tau = 0.1;
 * MNN: i and j match when j is the first index of the maximum of row i of P_M
   and i the first index of the maximum of column j;
@@ -31,6 +29,12 @@ Readings where the paper is silent (the same in the CUDA path):
 Decisions taken within rounding of a tie (the best and second-best log P_M of a
 row or column closer than ``TIE_GAP``) are flagged; parity tests compare the
 unflagged decisions exactly.
+
+A second, documented precision layer (``coarse_codes_bf16``,
+``coarse_pmm_bf16``) rounds the coarse unit vectors to bfloat16, as a plain
+single-bf16 tensor-core contraction would: it is not the definition, and it
+exists to measure how many coarse decisions and matches such a contraction
+changes against the definition (``decision_changes``).
 """
 from __future__ import annotations
 
@@ -51,8 +55,25 @@ def bf16_to_f64(bits: np.ndarray) -> np.ndarray:
     return (np.asarray(bits, np.uint16).astype(np.uint32) << 16).view(np.float32).astype(np.float64)
 
 
-def coarse_codes(F: np.ndarray, ratio: int = RATIO) -> np.ndarray:
-    """Coarse unit feature vectors as bfloat16 bits, (Hc * Wc, C) row-major.
+def coarse_unit_means(F: np.ndarray, ratio: int = RATIO) -> np.ndarray:
+    """The coarse unit feature vectors of the definition, (Hc * Wc, C) fp64.
+
+    F: (C, H, W) fine feature map (binary32 values, widened exactly). Cell
+    (cy, cx) is the mean of its ratio x ratio block, divided by its Euclidean
+    norm; a zero mean stays zero."""
+    F = np.asarray(F, np.float32)
+    C, H, W = F.shape
+    assert H % ratio == 0 and W % ratio == 0, "feature maps must be multiples of the coarse ratio"
+    Hc, Wc = H // ratio, W // ratio
+    m = F.astype(np.float64).reshape(C, Hc, ratio, Wc, ratio).mean(axis=(2, 4)).reshape(C, Hc * Wc).T
+    n = np.linalg.norm(m, axis=1, keepdims=True)
+    return np.where(n > 0, m / np.where(n > 0, n, 1.0), 0.0)
+
+
+def coarse_codes_bf16(F: np.ndarray, ratio: int = RATIO) -> np.ndarray:
+    """Precision layer, not the definition: coarse unit feature vectors rounded
+    to bfloat16 bits, (Hc * Wc, C) row-major, as a single-bf16 contraction
+    would take them.
 
     F: (C, H, W) fine feature map (binary32). Block mean: s = sum over the block
     in row-major order, then s * (1 / ratio^2) (exact); norm: sequential sum of
@@ -116,15 +137,48 @@ def mnn(logP: np.ndarray, tie_gap: float = TIE_GAP):
 
 
 def coarse_pmm(Fq: np.ndarray, Fr: np.ndarray, tau: float = TAU, ratio: int = RATIO) -> dict:
-    """Coarse level of Sec. 3.4: bf16 coarse codes, fp64 cosine matrix, Eq. 11,
-    MNN. Returns mnn()'s dict plus the codes and the row / column log-sum-exps."""
-    cq = coarse_codes(Fq, ratio)
-    cr = coarse_codes(Fr, ratio)
+    """Coarse level of Sec. 3.4 (the definition): fp64 unit cell means, their
+    cosine matrix M, Eq. 11, MNN. Returns mnn()'s dict plus the unit means
+    ("units_q", "units_r"), the row / column log-sum-exps and M."""
+    uq = coarse_unit_means(Fq, ratio)
+    ur = coarse_unit_means(Fr, ratio)
+    M = uq @ ur.T
+    logP, r, c = log_dual_softmax(M, tau)
+    out = mnn(logP)
+    out.update({"units_q": uq, "units_r": ur, "lse_row": r, "lse_col": c, "M": M})
+    return out
+
+
+def coarse_pmm_bf16(Fq: np.ndarray, Fr: np.ndarray, tau: float = TAU, ratio: int = RATIO) -> dict:
+    """Precision layer, not the definition: the coarse level on bf16-rounded
+    unit means (exact fp64 products of the rounded vectors)."""
+    cq = coarse_codes_bf16(Fq, ratio)
+    cr = coarse_codes_bf16(Fr, ratio)
     M = bf16_to_f64(cq) @ bf16_to_f64(cr).T
     logP, r, c = log_dual_softmax(M, tau)
     out = mnn(logP)
     out.update({"codes_q": cq, "codes_r": cr, "lse_row": r, "lse_col": c, "M": M})
     return out
+
+
+def decision_changes(a: dict, ref: dict) -> dict:
+    """How many coarse decisions and matches of `a` differ from those of `ref`
+    (two outputs of coarse_pmm-like functions on the same maps): fractions of
+    row argmaxes, column argmaxes and of the union of the match sets, overall
+    and among the decisions that `ref` takes clear of a tie."""
+    rd = a["row_best"] != ref["row_best"]
+    cd = a["col_best"] != ref["col_best"]
+    ma = {tuple(x) for x in np.asarray(a["matches"]).tolist()}
+    mr = {tuple(x) for x in np.asarray(ref["matches"]).tolist()}
+    rok, cok = ~ref["row_flag"], ~ref["col_flag"]
+    clear = lambda ij: rok[ij[0]] and cok[ij[1]]
+    ca, cr = {x for x in ma if clear(x)}, {x for x in mr if clear(x)}
+    return {"row": float(rd.mean()), "col": float(cd.mean()),
+            "row_clear": float(rd[rok].mean()) if rok.any() else 0.0,
+            "col_clear": float(cd[cok].mean()) if cok.any() else 0.0,
+            "matches": len(ma ^ mr) / max(1, len(ma | mr)),
+            "matches_clear": len(ca ^ cr) / max(1, len(ca | cr)),
+            "row_flagged": float(ref["row_flag"].mean()), "col_flagged": float(ref["col_flag"].mean())}
 
 
 def _window(F: np.ndarray, cell: int, Wc: int, ratio: int) -> np.ndarray:
@@ -162,13 +216,18 @@ def fine_pmm(Fq: np.ndarray, Fr: np.ndarray, coarse_matches: np.ndarray, tau: fl
 
 
 def coarse_pmm_chunked(Fq: np.ndarray, Fr: np.ndarray, tau: float = TAU, ratio: int = RATIO,
-                       chunk: int = 2048, tie_gap: float = TIE_GAP) -> dict:
-    """coarse_pmm for maps whose full similarity matrix does not fit in memory:
-    the same formulas over blocks of query rows (M is never stored whole).
-    Returns the same keys except "M"."""
-    cq = coarse_codes(Fq, ratio)
-    cr = coarse_codes(Fr, ratio)
-    Q, R = bf16_to_f64(cq), bf16_to_f64(cr)
+                       chunk: int = 2048, tie_gap: float = TIE_GAP, bf16: bool = False) -> dict:
+    """coarse_pmm (or, with bf16=True, the precision layer coarse_pmm_bf16) for
+    maps whose full similarity matrix does not fit in memory: the same
+    formulas over blocks of query rows (M is never stored whole). Returns the
+    same keys except "M"."""
+    if bf16:
+        cq, cr = coarse_codes_bf16(Fq, ratio), coarse_codes_bf16(Fr, ratio)
+        Q, R = bf16_to_f64(cq), bf16_to_f64(cr)
+        extra = {"codes_q": cq, "codes_r": cr}
+    else:
+        Q, R = coarse_unit_means(Fq, ratio), coarse_unit_means(Fr, ratio)
+        extra = {"units_q": Q, "units_r": R}
     n_q, n_r = Q.shape[0], R.shape[0]
     # pass 1: row log-sum-exps; column log-sum-exps from per-block maxima and sums
     r = np.empty(n_q)
@@ -208,6 +267,8 @@ def coarse_pmm_chunked(Fq: np.ndarray, Fr: np.ndarray, tau: float = TAU, ratio: 
     mutual = cb[rb] == i
     mi, mj = i[mutual], rb[mutual]
     prob = np.exp(2.0 * np.einsum("ij,ij->i", Q[mi], R[mj]) / tau - r[mi] - c[mj])
-    return {"row_best": rb, "col_best": cb, "row_gap": rgap, "col_gap": cgap, "row_flag": rgap < tie_gap,
-            "col_flag": cgap < tie_gap, "matches": np.stack([mi, mj], 1).astype(np.int64), "prob": prob,
-            "codes_q": cq, "codes_r": cr, "lse_row": r, "lse_col": c}
+    out = {"row_best": rb, "col_best": cb, "row_gap": rgap, "col_gap": cgap, "row_flag": rgap < tie_gap,
+           "col_flag": cgap < tie_gap, "matches": np.stack([mi, mj], 1).astype(np.int64), "prob": prob,
+           "lse_row": r, "lse_col": c}
+    out.update(extra)
+    return out

@@ -2,11 +2,15 @@
 // coarse to fine: Hi^2-GSLoc Sec. 3.4, Eq. 11.
 //
 // Coarse level. Each 8 x 8 block of the fine maps becomes one coarse cell: its
-// mean, L2-normalised and rounded to bfloat16 (k_pmm_codes, binary32 in a fixed
-// operation order). The cosine matrix M of all query cells against all
-// rendered cells is a 32-deep contraction, computed tile by tile on the 5th
-// generation tensor cores (tcgen05.mma, bf16 operands in shared memory, fp32
-// accumulator in tensor memory) and never stored. Two passes over the tiles:
+// mean, L2-normalised in binary32 (k_pmm_codes) and split into two bfloat16
+// vectors, hi = bf16(u) and lo = bf16(u - hi), which carry u to about 2^-17.
+// The cosine matrix M of all query cells against all rendered cells is the
+// 32-deep contraction hi_q . hi_r + lo_q . hi_r + hi_q . lo_r (the lo . lo term
+// is below 2^-17), computed tile by tile on the 5th generation tensor cores
+// (tcgen05.mma, bf16 operands in shared memory, fp32 accumulator in tensor
+// memory) and never stored: M is the fp32-accurate cosine of the unrounded
+// cell means, not that of bf16-rounded ones (which would move the dual-softmax
+// decisions whose margins are below about 1e-2). Two passes over the tiles:
 //   1. row and column sums of exp((M - 1) / tau), hence the row and column
 //      log-sum-exps r_i, c_j of M / tau (|M| <= 1 makes 1 / tau a fixed
 //      shift, so one exponential serves the row and the column);
@@ -39,10 +43,24 @@ constexpr int kC = 32;         // channels
 constexpr int kRatio = 8;      // H_f / H_c
 constexpr int kTile = 128;     // cells per tile side (MMA M = N = 128)
 constexpr uint32_t kTmemCols = 128;
-constexpr int kWaitLimit = 1 << 22;  // polls of an mbarrier before giving up (far beyond a 2-MMA tile)
+constexpr int kWaitLimit = GS_PMM_DEFAULT_WAIT_POLLS;  // polls of an mbarrier before giving up (far beyond a 2-MMA tile)
 constexpr int kMaxCells = 1 << 18;
 constexpr int kScanThreads = 1024;
 constexpr int kWin = kRatio * kRatio;  // fine vectors per window
+constexpr int kCode = 2 * kC;          // bf16 per coarse code: hi[32], then lo[32]
+static_assert(kWin == 64, "k_pmm_fine splits the 64 window rows into two halves of 32 columns");
+
+// Tensor-core operand layout of a block of kTile codes (no swizzle, K-major):
+// the byte offset of the 16-byte chunk (row r, k-chunk c) is that of core
+// matrix (r / 8, c), 128 bytes each, with the 8 k-chunks of a row group (hi
+// 0..3, lo 0..3) adjacent, so row groups are kChunks x 128 = 1024 bytes apart.
+// The codes kernel also writes every block of kTile cells in this layout, so
+// that a tile's operand is one contiguous kTileBytes bulk copy.
+constexpr int kChunks = kCode * 2 / 16;         // 16-byte k-chunks per code
+constexpr int kTileBytes = kTile * kCode * 2;   // one operand block (16 KB)
+__host__ __device__ __forceinline__ int core_off(int r, int c) {
+  return ((r >> 3) * kChunks + c) * 128 + (r & 7) * 16;
+}
 
 // ---------------------------------------------------------------------------
 // coarse codes: a CTA takes 32 horizontally adjacent cells; warp c sums channel c
@@ -50,10 +68,11 @@ constexpr int kWin = kRatio * kRatio;  // fine vectors per window
 // pixels), warp 0 forms the norms, and the codes leave as one contiguous block
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_pmm_codes(const float* __restrict__ F, int H, int W, int Wc, int n_cells,
-                                                    unsigned short* __restrict__ codes) {
+                                                    unsigned short* __restrict__ codes,
+                                                    unsigned char* __restrict__ tiled) {
   __shared__ float m_s[kC][32];
   __shared__ float inv_s[32];
-  __shared__ unsigned short u_s[32][kC];
+  __shared__ unsigned short u_s[32][kCode + 2];  // padded rows: the per-channel stores hit distinct banks
   const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cy = blockIdx.y, cx = blockIdx.x * 32 + lane;
   const bool ok = cx < Wc;
@@ -87,12 +106,23 @@ __global__ void __launch_bounds__(1024) k_pmm_codes(const float* __restrict__ F,
   __syncthreads();
   const float n = inv_s[lane];
   const float u = n > 0.0f ? __fdiv_rn(m, n) : 0.0f;
-  u_s[lane][c] = __bfloat16_as_ushort(__float2bfloat16_rn(u));
+  const __nv_bfloat16 hi = __float2bfloat16_rn(u);
+  const __nv_bfloat16 lo = __float2bfloat16_rn(__fsub_rn(u, __bfloat162float(hi)));  // exact difference
+  u_s[lane][c] = __bfloat16_as_ushort(hi);
+  u_s[lane][kC + c] = __bfloat16_as_ushort(lo);
   __syncthreads();
   const int cell0 = cy * Wc + blockIdx.x * 32;
   const int ncell = min(32, Wc - blockIdx.x * 32);
-  const int t = threadIdx.x;  // 32 cells x 32 channels, contiguous in the output
-  if (t < ncell * kC) codes[(size_t)cell0 * kC + t] = u_s[t / kC][t % kC];
+  // 32 cells x 64 bf16, contiguous in the output: two 16-bit values per thread
+  const int t = threadIdx.x;
+  if (t < ncell * kC) {
+    const int e = 2 * t;
+    const uint32_t v = (uint32_t)u_s[e / kCode][e % kCode] | ((uint32_t)u_s[e / kCode][e % kCode + 1] << 16);
+    reinterpret_cast<uint32_t*>(codes + (size_t)cell0 * kCode)[t] = v;
+    const int cell = cell0 + e / kCode, el = e % kCode;  // the same two values in the tiled copy
+    const size_t off = (size_t)(cell / kTile) * kTileBytes + core_off(cell % kTile, el / 8) + (el % 8) * 2;
+    *reinterpret_cast<uint32_t*>(tiled + off) = v;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -133,9 +163,10 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-// bounded wait for the phase `parity` of an mbarrier; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (int it = 0; it < kWaitLimit; ++it) {
+// bounded wait for the phase `parity` of an mbarrier: at most `limit` polls,
+// false when they run out (limit 0 gives up at once)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit) {
+  for (int it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -173,13 +204,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 constexpr int kTileThreads = 256;  // warp w: tensor-memory lanes 32 (w % 4) .. +31, columns 64 (w / 4) .. +63
 
 struct TileSmem {
-  uint4 a[kTile * kC * 2 / 16];  // A codes (rows of M), core-matrix layout (8 KB)
-  uint4 b[kTile * kC * 2 / 16];  // B codes (columns of M) (8 KB)
+  uint4 a[kTile * kCode * 2 / 16];  // A codes (rows of M), hi then lo, core-matrix layout (16 KB)
+  uint4 b[kTile * kCode * 2 / 16];  // B codes (columns of M) (16 KB)
   float colv[4][kTile];          // pass 1: column partials per row quarter
   float rowv[2][kTile];          // row partials per column half
   int rowi[2][kTile];            // pass 2: their column index
   float lse_c[kTile];            // pass 2: log-sum-exp of the tile's columns
-  unsigned long long bar;
+  unsigned long long bar;       // MMA completion
+  unsigned long long load_bar;  // operand bulk copies
   uint32_t tmem;
 };
 // one CTA uses 128 of the 512 tensor-memory columns of an SM; the dynamic
@@ -187,9 +219,6 @@ struct TileSmem {
 constexpr size_t kTileSmemBytes = 48 * 1024;
 static_assert(sizeof(TileSmem) <= kTileSmemBytes, "tile shared memory");
 
-// byte offset of the 16-byte chunk (row r, k-chunk c) in the core-matrix layout:
-// core matrix (r / 8, c) is 128 bytes, k-chunks of a row group are adjacent
-__device__ __forceinline__ int core_off(int r, int c) { return ((r >> 3) * 4 + c) * 128 + (r & 7) * 16; }
 
 // lane l ends with the sum over the warp's lanes of v[l & 15] (the 16 columns of
 // a chunk, each summed over the warp's 32 rows)
@@ -227,11 +256,13 @@ __device__ __forceinline__ bool better(float v, int i, float bv, int bi) { retur
 //         and lse_c = column log-sum-exps this is the row argmax of log P_M; with
 //         the operands swapped and the row log-sum-exps, its column argmax.
 template <int PASS>
-__global__ void __launch_bounds__(kTileThreads) k_pmm_tiles(const uint4* __restrict__ ca, const uint4* __restrict__ cb,
+__global__ void __launch_bounds__(kTileThreads, 4) k_pmm_tiles(const unsigned char* __restrict__ ca,
+                                                               const unsigned char* __restrict__ cb,
                                                             int n, int nb, float s_exp, float s_two,
                                                             const float* __restrict__ lse_c,
                                                             float* __restrict__ prow_v, int* __restrict__ prow_i,
-                                                            float* __restrict__ pcol_v, int* __restrict__ err) {
+                                                            float* __restrict__ pcol_v, int* __restrict__ err,
+                                                            int wait_limit) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   TileSmem& S = *reinterpret_cast<TileSmem*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -244,8 +275,10 @@ __global__ void __launch_bounds__(kTileThreads) k_pmm_tiles(const uint4* __restr
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  const uint32_t load_bar = smem_u32(&S.load_bar);
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(load_bar) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc_fence_before();
@@ -254,51 +287,64 @@ __global__ void __launch_bounds__(kTileThreads) k_pmm_tiles(const uint4* __restr
   const uint32_t tmem = S.tmem;
   const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 64);
   const uint32_t sa = smem_u32(S.a), sb = smem_u32(S.b);
-  unsigned char* pa = reinterpret_cast<unsigned char*>(S.a);
-  unsigned char* pb = reinterpret_cast<unsigned char*>(S.b);
-  // operand staging: thread t moves k-chunks 2 (t / 128) and 2 (t / 128) + 1 of row t % 128
-  const int srow = tid & (kTile - 1), sc0 = (tid >> 7) * 2;
-  auto load_ops = [&](int t, uint4 (&ra)[2], uint4 (&rb)[2]) {
+  // Operand staging: each tile's two operand blocks (A = codes of its row
+  // block, B = of its column block) are contiguous kTileBytes blocks of the
+  // tiled codes, already in the MMA layout, so one thread moves them with two
+  // bulk copies that complete on load_bar (no load/store instructions, no
+  // register staging). The next tile's copies start as soon as this tile's
+  // MMAs have read the operands, and overlap the epilogue.
+  auto stage_ops = [&](int t) {  // thread 0 only
     const int rb_ = t / nb, cb_ = t - rb_ * nb;
-    const int ar = rb_ * kTile + srow, br = cb_ * kTile + srow;
-    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      ra[c] = ar < n ? ca[(size_t)ar * 4 + sc0 + c] : z;
-      rb[c] = br < n ? cb[(size_t)br * 4 + sc0 + c] : z;
-    }
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(load_bar), "r"(2 * kTileBytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(sa), "l"(ca + (size_t)rb_ * kTileBytes), "r"(kTileBytes), "r"(load_bar)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(sb), "l"(cb + (size_t)cb_ * kTileBytes), "r"(kTileBytes), "r"(load_bar)
+                 : "memory");
   };
-  uint32_t phase = 0;
+  uint32_t phase = 0, load_phase = 0;
   const int n_tiles = nb * nb;
-  uint4 ra[2], rbv[2];
-  if ((int)blockIdx.x < n_tiles) load_ops(blockIdx.x, ra, rbv);
+  if (tid == 0 && (int)blockIdx.x < n_tiles) stage_ops(blockIdx.x);
   for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {  // block-uniform
     const int rb_ = t / nb, cb_ = t - rb_ * nb;
     const int grow = rb_ * kTile + lrow;  // global row (A index) of this thread
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      *reinterpret_cast<uint4*>(pa + core_off(srow, sc0 + c)) = ra[c];
-      *reinterpret_cast<uint4*>(pb + core_off(srow, sc0 + c)) = rbv[c];
-    }
     if (PASS == 2 && tid < kTile) S.lse_c[tid] = cb_ * kTile + tid < n ? lse_c[cb_ * kTile + tid] : 0.0f;
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // operands visible to the tensor core
     tc_fence_before();  // the previous tile's accumulator reads are done
     __syncthreads();
-    if (tid == 0) {
+    // Thread 0 waits for the operands, issues the MMAs and polls their
+    // completion; the other warps wait at the barrier (their polls would crowd
+    // the MIO queue the other CTAs' epilogues use), which then orders every
+    // thread's tensor-memory reads after the completion.
+    bool done = true;
+    if (tid == 0 && !mbar_wait(load_bar, load_phase, kWaitLimit)) {  // operands never arrived
+      atomicExch(err, 1);
+      done = false;
+      mbar_wait(load_bar, load_phase, kWaitLimit);  // drain before the shared memory is released
+    } else if (tid == 0) {
       tc_fence_after();
-      // K = 32 as two K = 16 steps: k-chunks (0, 1), then (2, 3) at +256 bytes
-      mma_bf16(tmem, smem_desc(sa, 128, 512), smem_desc(sb, 128, 512), 0u);
-      mma_bf16(tmem, smem_desc(sa + 256, 128, 512), smem_desc(sb + 256, 128, 512), 1u);
+      // hi . hi, lo . hi, hi . lo, each K = 32 as two K = 16 steps (k-chunks
+      // (0, 1) then (2, 3) at +256 bytes); the lo half starts 512 bytes in
+      constexpr uint32_t kSbo = kChunks * 128;
+      mma_bf16(tmem, smem_desc(sa, 128, kSbo), smem_desc(sb, 128, kSbo), 0u);
+      mma_bf16(tmem, smem_desc(sa + 256, 128, kSbo), smem_desc(sb + 256, 128, kSbo), 1u);
+      mma_bf16(tmem, smem_desc(sa + 512, 128, kSbo), smem_desc(sb, 128, kSbo), 1u);
+      mma_bf16(tmem, smem_desc(sa + 768, 128, kSbo), smem_desc(sb + 256, 128, kSbo), 1u);
+      mma_bf16(tmem, smem_desc(sa, 128, kSbo), smem_desc(sb + 512, 128, kSbo), 1u);
+      mma_bf16(tmem, smem_desc(sa + 256, 128, kSbo), smem_desc(sb + 768, 128, kSbo), 1u);
       mma_commit(bar);
+      done = mbar_wait(bar, phase, wait_limit);
+      if (!done) {
+        atomicExch(err, 1);
+        mbar_wait(bar, phase, kWaitLimit);  // the MMA in flight completes before tensor memory is freed
+      } else if (t + (int)gridDim.x < n_tiles) {
+        stage_ops(t + gridDim.x);  // the MMAs have read the operands: copy the next tile's
+      }
     }
-    if (t + (int)gridDim.x < n_tiles) load_ops(t + gridDim.x, ra, rbv);  // next operands, during the MMA
-    const bool done = mbar_wait(bar, phase);
     phase ^= 1u;
-    if (__syncthreads_or(!done)) {  // the accumulator never arrived: report, drain, stop
-      if (tid == 0) atomicExch(err, 1);
-      mbar_wait(bar, phase ^ 1u);
-      break;
-    }
+    load_phase ^= 1u;
+    if (__syncthreads_or(!done)) break;  // the accumulator did not arrive in time: reported, drained
     tc_fence_after();
     const bool row_ok = grow < n;
     // interior tiles (every row and column below n) take the unmasked path
@@ -457,27 +503,37 @@ __global__ void __launch_bounds__(kRedRows * kRedWarps) k_pmm_best(const float* 
   }
 }
 
+// the coarse similarity of two split codes, with the three products of the tiles
 __device__ __forceinline__ float dot_codes(const __nv_bfloat16* a, const __nv_bfloat16* b) {
   float s = 0.0f;
 #pragma unroll
-  for (int k = 0; k < kC; ++k) s = fmaf(__bfloat162float(a[k]), __bfloat162float(b[k]), s);
+  for (int k = 0; k < kC; ++k) {
+    const float ah = __bfloat162float(a[k]), al = __bfloat162float(a[kC + k]);
+    const float bh = __bfloat162float(b[k]), bl = __bfloat162float(b[kC + k]);
+    s = fmaf(ah, bh, fmaf(al, bh, fmaf(ah, bl, s)));
+  }
   return s;
 }
 
 
 // mutual nearest neighbours: flag[i] = 1 when query cell i and rendered cell
 // row_best[i] are each other's argmax, with P_M of the pair (an argmax left at
-// its sentinel by non-finite features matches nothing)
+// its sentinel by non-finite features matches nothing). After a timed-out
+// tile pass (*err set) nothing matches, so the fine level has no work.
 __global__ void k_pmm_mnn(int n, const int* __restrict__ row_best, const int* __restrict__ col_best,
                           const __nv_bfloat16* __restrict__ cq, const __nv_bfloat16* __restrict__ cr,
                           const float* __restrict__ lse_row, const float* __restrict__ lse_col, float s_two,
-                          int* __restrict__ flag, float* __restrict__ prob) {
+                          int* __restrict__ flag, float* __restrict__ prob, const int* __restrict__ err) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  if (*err) {
+    flag[i] = 0;
+    return;
+  }
   const int j = row_best[i];
   const bool mutual = j >= 0 && j < n && col_best[j] == i;
   flag[i] = mutual ? 1 : 0;
-  if (mutual) prob[i] = expf(dot_codes(cq + (size_t)i * kC, cr + (size_t)j * kC) * s_two - lse_row[i] - lse_col[j]);
+  if (mutual) prob[i] = expf(dot_codes(cq + (size_t)i * kCode, cr + (size_t)j * kCode) * s_two - lse_row[i] - lse_col[j]);
 }
 
 // the matches at their scanned positions, in ascending query order
@@ -686,12 +742,14 @@ struct gs_pmm {
   int C = 0, H = 0, W = 0, Hc = 0, Wc = 0, n = 0, nb = 0;
   void* arena = nullptr;
   __nv_bfloat16 *codes_q = nullptr, *codes_r = nullptr;
+  unsigned char *tiled_q = nullptr, *tiled_r = nullptr;  // the codes in the tensor-core operand layout
   float *prow_v = nullptr, *pcol_v = nullptr, *lse_row = nullptr, *lse_col = nullptr;
   int *prow_i = nullptr, *pcol_i = nullptr, *row_best = nullptr, *col_best = nullptr;
   int *coarse = nullptr, *fine = nullptr, *slot_r = nullptr, *counters = nullptr, *win_cnt = nullptr,
       *win_off = nullptr;
   float *coarse_p = nullptr, *fine_p = nullptr, *slot_p = nullptr;
   int* host = nullptr;  // pinned: counts and error flag
+  int wait_limit = kWaitLimit;  // polls of a tensor-core completion wait
 };
 
 namespace {
@@ -738,7 +796,9 @@ gs_status gs_pmm_create(int channels, int height, int width, gs_pmm** out) {
     off = align_up(off + bytes);
     return o;
   };
-  const size_t o_cq = take(nn * kC * 2), o_cr = take(nn * kC * 2);
+  const size_t o_cq = take(nn * kCode * 2), o_cr = take(nn * kCode * 2);
+  const size_t tiled_bytes = (size_t)m->nb * kTileBytes;  // whole blocks: rows past n stay zero
+  const size_t o_tq = take(tiled_bytes), o_tr = take(tiled_bytes);
   const size_t o_prv = take(part * 4), o_pri = take(part * 4), o_pcv = take(part * 4), o_pci = take(part * 4);
   const size_t o_lr = take(nn * 4), o_lc = take(nn * 4), o_rb = take(nn * 4), o_cb = take(nn * 4);
   const size_t o_co = take(nn * 8), o_cp = take(nn * 4);
@@ -747,6 +807,8 @@ gs_status gs_pmm_create(int channels, int height, int width, gs_pmm** out) {
   const size_t o_wc = take(nn * 4), o_wo = take(nn * 4);
   const size_t o_ct = take(4 * 4);
   if (e == cudaSuccess) e = cudaMalloc(&m->arena, off);
+  // rows of the tiled codes past n are never written: zero operands of the ragged last block
+  if (e == cudaSuccess) e = cudaMemset(static_cast<char*>(m->arena) + o_tq, 0, o_tr + tiled_bytes - o_tq);
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&m->host), 4 * sizeof(int));
   if (e != cudaSuccess) {
     gs_pmm_destroy(m);
@@ -756,6 +818,8 @@ gs_status gs_pmm_create(int channels, int height, int width, gs_pmm** out) {
   char* base = static_cast<char*>(m->arena);
   m->codes_q = reinterpret_cast<__nv_bfloat16*>(base + o_cq);
   m->codes_r = reinterpret_cast<__nv_bfloat16*>(base + o_cr);
+  m->tiled_q = reinterpret_cast<unsigned char*>(base + o_tq);
+  m->tiled_r = reinterpret_cast<unsigned char*>(base + o_tr);
   m->prow_v = reinterpret_cast<float*>(base + o_prv);
   m->prow_i = reinterpret_cast<int*>(base + o_pri);
   m->pcol_v = reinterpret_cast<float*>(base + o_pcv);
@@ -774,6 +838,13 @@ gs_status gs_pmm_create(int channels, int height, int width, gs_pmm** out) {
   m->win_off = reinterpret_cast<int*>(base + o_wo);
   m->counters = reinterpret_cast<int*>(base + o_ct);
   *out = m;
+  return GS_OK;
+}
+
+gs_status gs_pmm_set_wait_limit(gs_pmm* m, int polls) {
+  if (!m) return pmm_fail(GS_ERR_INVALID_ARG, "matcher is NULL");
+  if (polls < 0) return pmm_fail(GS_ERR_INVALID_ARG, "polls must be >= 0");
+  m->wait_limit = polls;
   return GS_OK;
 }
 
@@ -813,8 +884,8 @@ gs_status gs_pmm_match(gs_pmm* m, const float* feat_query, const float* feat_ren
   const dim3 cgrid((unsigned)((m->Wc + 31) / 32), (unsigned)m->Hc);
   unsigned short* cq16 = reinterpret_cast<unsigned short*>(m->codes_q);
   unsigned short* cr16 = reinterpret_cast<unsigned short*>(m->codes_r);
-  k_pmm_codes<<<cgrid, 1024, 0, st>>>(feat_query, m->H, m->W, m->Wc, n, cq16);
-  k_pmm_codes<<<cgrid, 1024, 0, st>>>(feat_render, m->H, m->W, m->Wc, n, cr16);
+  k_pmm_codes<<<cgrid, 1024, 0, st>>>(feat_query, m->H, m->W, m->Wc, n, cq16, m->tiled_q);
+  k_pmm_codes<<<cgrid, 1024, 0, st>>>(feat_render, m->H, m->W, m->Wc, n, cr16, m->tiled_r);
   PMM_CUDA(cudaGetLastError());
   static bool attr = false;
   if (!attr) {
@@ -824,28 +895,28 @@ gs_status gs_pmm_match(gs_pmm* m, const float* feat_query, const float* feat_ren
   }
   const int tiles = nb * nb;
   const int grid = tiles < 4 * m->sm_count ? tiles : 4 * m->sm_count;
-  const uint4* cq = reinterpret_cast<const uint4*>(m->codes_q);
-  const uint4* cr = reinterpret_cast<const uint4*>(m->codes_r);
+  const unsigned char* cq = m->tiled_q;
+  const unsigned char* cr = m->tiled_r;
   int* err = m->counters + 3;
   const int rg = (n + 255) / 256;
   // pass 1: row and column exp sums, then the log-sum-exps
   k_pmm_tiles<1><<<grid, kTileThreads, kTileSmemBytes, st>>>(cq, cr, n, nb, s_exp, s_two, nullptr, m->prow_v,
-                                                             nullptr, m->pcol_v, err);
+                                                             nullptr, m->pcol_v, err, m->wait_limit);
   PMM_CUDA(cudaGetLastError());
   const int rd = (n + kRedRows - 1) / kRedRows;
   k_pmm_lse<<<rd, kRedRows * kRedWarps, 0, st>>>(m->prow_v, nb, n, inv_tau, m->lse_row);
   k_pmm_lse<<<rd, kRedRows * kRedWarps, 0, st>>>(m->pcol_v, nb, n, inv_tau, m->lse_col);
   // pass 2: row argmax of log P_M, then (operands swapped) its column argmax
   k_pmm_tiles<2><<<grid, kTileThreads, kTileSmemBytes, st>>>(cq, cr, n, nb, s_exp, s_two, m->lse_col, m->prow_v,
-                                                             m->prow_i, nullptr, err);
+                                                             m->prow_i, nullptr, err, m->wait_limit);
   k_pmm_best<<<rd, kRedRows * kRedWarps, 0, st>>>(m->prow_v, m->prow_i, nb, n, m->row_best);
   k_pmm_tiles<2><<<grid, kTileThreads, kTileSmemBytes, st>>>(cr, cq, n, nb, s_exp, s_two, m->lse_row, m->prow_v,
-                                                             m->prow_i, nullptr, err);
+                                                             m->prow_i, nullptr, err, m->wait_limit);
   k_pmm_best<<<rd, kRedRows * kRedWarps, 0, st>>>(m->prow_v, m->prow_i, nb, n, m->col_best);
   PMM_CUDA(cudaGetLastError());
   // mutual nearest neighbours in ascending query order
   k_pmm_mnn<<<rg, 256, 0, st>>>(n, m->row_best, m->col_best, m->codes_q, m->codes_r, m->lse_row, m->lse_col, s_two,
-                                m->win_cnt, m->slot_p);
+                                m->win_cnt, m->slot_p, err);
   k_pmm_scan<<<1, kScanThreads, 0, st>>>(n, m->win_cnt, m->win_off, m->counters, nullptr);
   k_pmm_mnn_scatter<<<rg, 256, 0, st>>>(n, m->row_best, m->win_cnt, m->win_off, m->slot_p, m->coarse, m->coarse_p);
   PMM_CUDA(cudaGetLastError());
@@ -859,7 +930,9 @@ gs_status gs_pmm_match(gs_pmm* m, const float* feat_query, const float* feat_ren
   PMM_CUDA(cudaGetLastError());
   PMM_CUDA(cudaMemcpyAsync(m->host, m->counters, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
   PMM_CUDA(cudaStreamSynchronize(st));
-  if (m->host[3]) return pmm_fail(GS_ERR_INTERNAL, "tensor-core completion wait timed out");
+  if (m->host[3])
+    return pmm_fail(GS_ERR_TIMEOUT, "a tensor-core completion wait ran out of polls (limit " +
+                                        std::to_string(m->wait_limit) + "); the matcher stays usable");
   const int n_coarse = m->host[0];
   out->n_cells = n;
   out->codes_q = reinterpret_cast<const uint16_t*>(m->codes_q);

@@ -134,6 +134,7 @@ def _load():
                               P(gs_localize_result), vp],
         "gs_scene_shape": [vp, vp, vp, vp],
         "gs_pmm_shape": [vp, vp, vp, vp],
+        "gs_pmm_set_wait_limit": [vp, st],
         "gs_pnp_solve": [vp, P(gs_camera), P(gs_pose), vp, vp, vp, i64, vp, st, P(gs_pnp_opts), P(gs_pnp_result), vp],
     }
     for name, args in sigs.items():
@@ -607,6 +608,13 @@ def gs_pmm_destroy(h) -> None:
     lib.gs_pmm_destroy(h)
 
 
+GS_PMM_DEFAULT_WAIT_POLLS = 1 << 22
+
+
+def gs_pmm_set_wait_limit(h, polls: int) -> None:
+    _check(lib.gs_pmm_set_wait_limit(h, int(polls)))
+
+
 def gs_pmm_match(h, feat_query: int, feat_render: int, tau: float, stream: int) -> gs_pmm_result:
     r = gs_pmm_result()
     _check(lib.gs_pmm_match(h, feat_query, feat_render, float(tau), ctypes.byref(r), stream))
@@ -654,7 +662,7 @@ class Matcher:
         r = self.match_raw(feat_query, feat_render, tau)
         n, nc, nf = r.n_cells, r.n_coarse, r.n_fine
         v = lambda p, shape, t: torch.as_tensor(_DevView(p, shape, t), device="cuda").clone()
-        return {"codes_q": v(r.codes_q, (n, 32), "<u2"), "codes_r": v(r.codes_r, (n, 32), "<u2"),
+        return {"codes_q": v(r.codes_q, (n, 64), "<u2"), "codes_r": v(r.codes_r, (n, 64), "<u2"),
                 "lse_row": v(r.lse_row, (n,), "<f4"), "lse_col": v(r.lse_col, (n,), "<f4"),
                 "row_best": v(r.row_best, (n,), "<i4"), "col_best": v(r.col_best, (n,), "<i4"),
                 "coarse": v(r.coarse, (nc, 2), "<i4") if nc else torch.zeros((0, 2), dtype=torch.int32, device="cuda"),

@@ -26,11 +26,11 @@ def test_coarse_grid_gives_the_printed_search_space_reduction():
     assert PM.RATIO == r
     H, W = 64, 96
     F = np.random.default_rng(0).standard_normal((32, H, W)).astype(np.float32)
-    n_cells = PM.coarse_codes(F).shape[0]
+    n_cells = PM.coarse_unit_means(F).shape[0]
     assert n_cells == (H // r) * (W // r)
     assert ((H * W) ** 2) // (n_cells ** 2) == _val("search_space_reduction")
     with pytest.raises(AssertionError):
-        PM.coarse_codes(F[:, :60])  # not a multiple of the ratio
+        PM.coarse_unit_means(F[:, :60])  # not a multiple of the ratio
 
 
 def test_fine_windows_are_the_coarse_blocks():

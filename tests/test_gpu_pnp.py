@@ -84,6 +84,8 @@ def _check(g, o, cam, tau):
     np.testing.assert_allclose(g["points"], o["X"], rtol=1e-9, atol=1e-9)
     rs = o["ransac"]
     n_hyp = len(rs["hyps"])
+    f = OP.bearings(o["p"], cam)
+    pert = np.random.default_rng(99).choice([-1.0, 1.0], (3, 3))
     # hypotheses
     compared, loose = 0, 0
     for h in range(n_hyp):
@@ -92,15 +94,28 @@ def _check(g, o, cam, tau):
         if rs["near_root"][h]:
             continue
         assert int((gc >= 0).sum()) == len(sols), (h, gc, len(sols))
+        sel = rs["idx"][h]
+        solp = None
         for s, (R, t, _) in enumerate(sols):
             P = g["hyp_poses"][h, s]
             dr = _rot_deg(P[:9].reshape(3, 3), R)
             dt = np.linalg.norm(P[9:] - t) / (1 + np.linalg.norm(t))
-            # an ill-conditioned sample amplifies the 1e-16 differences of the lifted points
+            # an ill-conditioned sample amplifies the rounding differences of the lifted points
             assert dr < 1e-3 and dt < 1e-3, (h, s, dr, dt)
-            loose += not (dr < 1e-6 and dt < 1e-6)
+            if not (dr < 1e-6 and dt < 1e-6):
+                # sensitivity of the oracle's own solution to a 1e-10 relative change of the
+                # sample's points: a solution may miss the 1e-6 bar only if it amplifies by >= 100
+                if solp is None:
+                    solp, _ = OP.p3p(o["X"][sel] * (1.0 + 1e-10 * pert), f[sel])
+                kappa = np.inf
+                if len(solp) == len(sols):
+                    R2, t2, _ = solp[s]
+                    kappa = max(np.linalg.norm(R - R2), np.linalg.norm(t - t2) / (1 + np.linalg.norm(t))) / 1e-10
+                print("solution h %d s %d off by %.3g deg, %.3g rel; oracle sensitivity %.3g" % (h, s, dr, dt, kappa))
+                loose += kappa < 100.0
             assert abs(int(gc[s]) - rs["counts"][h][s]) <= rs["ambiguous"][h][s], (h, s, gc[s], rs["counts"][h][s])
             compared += 1
+    # well-conditioned solutions agree to 1e-6 (up to 1 % of them may not)
     assert compared > 0 and loose <= max(1, compared // 100), (loose, compared)
     # winner
     flat = [(c, a, h, s) for h in range(n_hyp) for s, (c, a) in enumerate(zip(rs["counts"][h], rs["ambiguous"][h]))]

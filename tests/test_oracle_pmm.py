@@ -20,11 +20,38 @@ def _blocks_to_map(cells, Hc, Wc, ratio=R, jitter=None):
     return F
 
 
-def test_coarse_codes_match_binary32_brute_force():
+def test_coarse_unit_means_match_plain_loops():
+    # the definition's coarse vectors: block means and norms by plain Python float loops
+    g = np.random.default_rng(10)
+    F = g.standard_normal((5, 16, 24)).astype(np.float32)
+    F[:, 8:16, 0:8] = 0.0  # one zero cell stays zero
+    u = pmm.coarse_unit_means(F)
+    C, H, W = F.shape
+    for cy in range(H // R):
+        for cx in range(W // R):
+            m = []
+            for c in range(C):
+                s = 0.0
+                for dy in range(R):
+                    for dx in range(R):
+                        s += float(F[c, cy * R + dy, cx * R + dx])
+                m.append(s / 64.0)
+            nrm = math.sqrt(sum(v * v for v in m))
+            exp = [v / nrm if nrm > 0 else 0.0 for v in m]
+            np.testing.assert_allclose(u[cy * (W // R) + cx], exp, rtol=1e-13, atol=1e-15)
+    assert not u[1 * (W // R) + 0].any()
+    nz = np.linalg.norm(u, axis=1)
+    np.testing.assert_allclose(nz[nz > 0], 1.0, rtol=1e-14)
+    # scaling a map leaves its unit means unchanged
+    np.testing.assert_allclose(pmm.coarse_unit_means((F * np.float32(4.0)).astype(np.float32)), u, rtol=1e-14,
+                               atol=1e-15)
+
+
+def test_bf16_precision_layer_matches_binary32_brute_force():
     # plain loops over np.float32 scalars in the stated order give the same bits
     g = np.random.default_rng(0)
     F = g.standard_normal((4, 16, 24)).astype(np.float32)
-    codes = pmm.coarse_codes(F)
+    codes = pmm.coarse_codes_bf16(F)
     C, H, W = F.shape
     for cy in range(H // R):
         for cx in range(W // R):
@@ -43,18 +70,40 @@ def test_coarse_codes_match_binary32_brute_force():
             np.testing.assert_array_equal(codes[cy * (W // R) + cx], pmm._bf16_round_bits(u))
 
 
-def test_coarse_codes_are_rounded_unit_means():
+def test_bf16_precision_layer_rounds_the_unit_means():
     g = np.random.default_rng(1)
     F = g.standard_normal((32, 40, 64)).astype(np.float32)
-    codes = pmm.bf16_to_f64(pmm.coarse_codes(F))
-    mean = F.astype(np.float64).reshape(32, 5, 8, 8, 8).mean(axis=(2, 4)).reshape(32, -1).T
-    unit = mean / np.linalg.norm(mean, axis=1, keepdims=True)
-    np.testing.assert_allclose(codes, unit, rtol=2 ** -8, atol=1e-6)  # bf16 keeps 8 significant bits
+    codes = pmm.bf16_to_f64(pmm.coarse_codes_bf16(F))
+    np.testing.assert_allclose(codes, pmm.coarse_unit_means(F), rtol=2 ** -8, atol=1e-6)  # 8 significant bits
     # zero map: zero codes; constant map: one code everywhere
-    assert not pmm.coarse_codes(np.zeros((32, 16, 16), np.float32)).any()
+    assert not pmm.coarse_codes_bf16(np.zeros((32, 16, 16), np.float32)).any()
     const = np.broadcast_to(g.standard_normal((32, 1, 1)).astype(np.float32), (32, 16, 16))
-    cc = pmm.coarse_codes(const)
+    cc = pmm.coarse_codes_bf16(const)
     assert (cc == cc[0]).all()
+
+
+def test_decision_changes_counts_a_flip_of_the_bf16_layer():
+    # query cell 0 and rendered cells 0 and 1 are unit vectors in one plane, at
+    # angles whose cosines with the query differ by 3.4e-4 (rendered cell 0
+    # nearer); rounded to bf16 (8 significant bits) cell 1 comes out 2e-3 nearer
+    C = 32
+    a, t0, t1 = 0.5915012152990735, 1.0673854012188002, 1.0699896623145377
+    q = np.zeros(C)
+    q[0], q[1] = a, math.sqrt(1 - a * a)
+    r0 = np.zeros(C)
+    r0[0], r0[1] = math.cos(t0), math.sin(t0)
+    r1 = np.zeros(C)
+    r1[0], r1[1] = math.cos(t1), math.sin(t1)
+    fill = np.eye(C)[3:5]  # two more cells on each side, matching each other
+    Fq = _blocks_to_map(np.stack([q, fill[0], fill[1]]), 1, 3)
+    Fr = _blocks_to_map(np.stack([r0, r1, fill[0], fill[1]]), 1, 4)
+    d = pmm.coarse_pmm(Fq, Fr)
+    b = pmm.coarse_pmm_bf16(Fq, Fr)
+    assert d["row_best"][0] == 0 and b["row_best"][0] == 1
+    ch = pmm.decision_changes(b, d)
+    assert ch["row"] == pytest.approx(1 / 3)
+    same = pmm.decision_changes(d, d)
+    assert same["row"] == same["col"] == same["matches"] == 0.0
 
 
 def test_dual_softmax_is_product_of_row_and_column_softmax():
@@ -79,6 +128,7 @@ def test_orthonormal_codes_closed_form():
     F = _blocks_to_map(cells, Hc, Wc)
     out = pmm.coarse_pmm(F, F)
     np.testing.assert_array_equal(out["M"], np.eye(N))
+    np.testing.assert_array_equal(pmm.coarse_pmm_bf16(F, F)["M"], np.eye(N))
     np.testing.assert_array_equal(out["matches"], np.stack([np.arange(N)] * 2, 1))
     z = math.exp(1 / pmm.TAU) + N - 1
     np.testing.assert_allclose(out["prob"], math.exp(2 / pmm.TAU) / z ** 2, rtol=1e-12)
@@ -138,9 +188,9 @@ def test_chunked_equals_dense():
     cells = g.standard_normal((9 * 11, 32))
     Fq = _blocks_to_map(cells, 9, 11, jitter=0.3 * g.standard_normal((32, 72, 88)))
     Fr = _blocks_to_map(cells[g.permutation(99)], 9, 11, jitter=0.3 * g.standard_normal((32, 72, 88)))
-    d = pmm.coarse_pmm(Fq, Fr)
-    c = pmm.coarse_pmm_chunked(Fq, Fr, chunk=16)
-    for k in ("row_best", "col_best", "matches"):
-        np.testing.assert_array_equal(c[k], d[k])
-    for k in ("lse_row", "lse_col", "row_gap", "col_gap", "prob"):
-        np.testing.assert_allclose(c[k], d[k], rtol=1e-12, atol=1e-12)
+    for d, c in ((pmm.coarse_pmm(Fq, Fr), pmm.coarse_pmm_chunked(Fq, Fr, chunk=16)),
+                 (pmm.coarse_pmm_bf16(Fq, Fr), pmm.coarse_pmm_chunked(Fq, Fr, chunk=16, bf16=True))):
+        for k in ("row_best", "col_best", "matches"):
+            np.testing.assert_array_equal(c[k], d[k])
+        for k in ("lse_row", "lse_col", "row_gap", "col_gap", "prob"):
+            np.testing.assert_allclose(c[k], d[k], rtol=1e-12, atol=1e-12)

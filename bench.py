@@ -77,6 +77,7 @@ def parse():
     p.add_argument("--no-vis", action="store_true")
     p.add_argument("--no-dense", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-errors", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     return p.parse_args()
 
@@ -361,14 +362,16 @@ def main():
     tx, ty = (W + 15) // 16, (H + 15) // 16
     wt = np.minimum(16, W - 16 * np.arange(tx))
     ht = np.minimum(16, H - 16 * np.arange(ty))
-    evals = int((counts * np.outer(ht, wt).reshape(-1)).sum())
+    pair_pixels = int((counts * np.outer(ht, wt).reshape(-1)).sum())  # every pixel of every listed tile
     pk, pk_src = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
     n_sm = torch.cuda.get_device_properties(0).multi_processor_count
     fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FMA = 2
     dom = max(per_kernel, key=per_kernel.get)
     kernels = {k: {"ms": v, "share": v / max(sum(per_kernel.values()), 1e-12)} for k, v in per_kernel.items()}
-    blends = gsr.gs_scene_blend_count(S.handle)
+    # the step's work units, counted by the tangent pass itself: pairs blended,
+    # and list entries examined before each pixel's stop (the definition's walk)
+    blends, evals = gsr.gs_scene_work_counts(S.handle)
     if dom == "composite":
         flops = evals * FLOPS_PER_EVAL + blends * FLOPS_PER_BLEND
         ach = flops / (per_kernel[dom] * 1e-3) / 1e12
@@ -409,7 +412,17 @@ def main():
     if not args.no_batched:
         batched = bench_batched(gsr, synth, torch, flush, max(2, args.steps // 4), args.warmup)
     # large streamed scene: 6M Gaussians in 16 partitions, 8 poses through a 4-level pyramid
-    large = None if args.no_large else bench_large(gsr, synth, torch)
+    with_oracle = rank == 0 and world == 1 and not args.no_cpu and not args.no_errors
+    large_errors = []
+    large = None if args.no_large else bench_large(gsr, synth, torch, large_errors if with_oracle else None)
+    # error of every output and of the pose gradient against the fp64 oracle
+    errors = None
+    if with_oracle:
+        errors = {"sample": "%d random pixels per view (fixed seed); pixels whose decisions the oracle flags as "
+                            "near-ties are excluded from the image errors and weighted 0 in both gradients"
+                            % ERR_PIXELS,
+                  "aerial_1080p": view_errors(gsr, torch, S, scene, cam, T_ref, T_q, 1),
+                  "large_pyramid": large_errors or None}
     # dense matching of rendered feature maps (PMM, Eq. 11) at 1920x1080: 32,400 x 32,400 similarities
     pmm = None
     if not args.no_pmm:
@@ -438,7 +451,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_grad, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "gaussians": 1_000_000, "width": W, "height": H, "sh_degree": 3,
-                   "records": int(n_rec), "pairs": int(n_pairs), "evaluations": evals, "blended": int(blends),
+                   "records": int(n_rec), "pairs": int(n_pairs), "evaluations": int(evals),
+                   "pair_pixels": pair_pixels, "blended": int(blends),
                    "l2": "flushed (256 MB write) between timed steps, outside the timed events",
                    "parallelism": "replicas" if world > 1 else "single"},
         "pose_grad_iters_per_s": world / (ms_grad * 1e-3),
@@ -451,6 +465,7 @@ def main():
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roof, "kernels": kernels,
         "refine": refine, "batched": batched, "large": large, "pmm": pmm, "visibility": vis, "dense": dense,
+        "errors": errors,
         "cpu_baseline": cpu,
     }
     if rank == 0:
@@ -532,17 +547,26 @@ def bench_refine(gsr, synth, torch):
                                   "does not converge (the batch equals the single-pose runs bit for bit)"}}
 
 
-def bench_large(gsr, synth, torch):
+def bench_large(gsr, synth, torch, errors=None):
+    """6M streamed Gaussians, 8 poses, 4-level pyramid of batched Adam refinement.
+    errors: a list to receive view_errors() of the first pose at each level
+    (the oracle's fp64 reference; None skips it)."""
     t0 = time.perf_counter()
-    scene = synth.partitioned_scene(5, 4, 4, 375_000, cell_m=500.0, sh_degree=3, feat_dim=32)
+    scene = synth.partitioned_scene(5, 4, 4, 375_000, cell_m=500.0, sh_degree=3, feat_dim=32,
+                                    keep_f32=errors is not None)
     t_gen = time.perf_counter() - t0
     S = gsr.Scene(scene, stream_partitions=True)
-    del scene
     stream = torch.cuda.current_stream().cuda_stream
     g = synth.rng(12)
     refs = [synth.look_pose((g.uniform(700, 1300), g.uniform(700, 1300), g.uniform(250, 350)),
                             g.uniform(0, 2 * math.pi), math.radians(g.uniform(15, 35))) for _ in range(8)]
-    poses = [gsr.pose(synth.perturb_pose(T, g, 1.0, 2.0)) for T in refs]
+    qs = [synth.perturb_pose(T, g, 1.0, 2.0) for T in refs]
+    if errors is not None:
+        for level in range(4):
+            cam = synth.camera(480 * 2 ** level, 270 * 2 ** level, 350.0 * 2 ** level)
+            errors.append(view_errors(gsr, torch, S, scene, cam, refs[0], qs[0], 100 + level))
+    del scene
+    poses = [gsr.pose(T) for T in qs]
     start_err = [_pose_errors(gsr.pose_matrix(p), T) for p, T in zip(poses, refs)]
     levels = []
     for level in range(4):
@@ -576,6 +600,72 @@ def bench_large(gsr, synth, torch):
             "start_rot_err_deg_median": float(np.median([e[0] for e in start_err])),
             "start_centre_err_m_median": float(np.median([e[1] for e in start_err])),
             "levels": levels}
+
+
+ERR_PIXELS = 20_000
+
+
+def _err_stats(d):
+    d = np.abs(np.asarray(d, np.float64))
+    return {"max_abs": float(d.max()) if d.size else 0.0, "rms": float(np.sqrt((d ** 2).mean())) if d.size else 0.0}
+
+
+def view_errors(gsr, torch, S, scene, cam, T_ref, T_q, seed):
+    """Max-abs and RMS error of every output of the library's render at T_q
+    (rgb, depth, alpha, final T and, with features, the 32 feature channels)
+    against the fp64 oracle on ERR_PIXELS random pixels, and of the pose
+    gradient of the L1 loss against targets rendered by the library at T_ref,
+    component by component. With features, the error of their bf16 storage
+    (the oracle blending the unrounded binary32 vectors against the bf16 ones)
+    is reported apart from the fp32 blending error."""
+    from oracle import oracle as O
+    O.build()
+    n_thr = os.cpu_count() or 1
+    H, W = cam["height"], cam["width"]
+    feats = scene.get("feats_bf16") is not None
+    tgt = S.render(cam, T_ref, S.alloc_outputs(cam, last_idx=False))
+    trgb, tdep = tgt["rgb"].contiguous(), tgt["depth"].contiguous()
+    out = S.render(cam, T_q, S.alloc_outputs(cam, feat_dim=32 if feats else 0, last_idx=False))
+    gpu = {k: v.cpu().numpy().reshape(v.shape[0] if v.dim() == 3 else 1, H * W).T for k, v in out.items()}
+    pix = np.sort(np.random.default_rng(seed).choice(H * W, min(ERR_PIXELS, H * W), replace=False))
+    mask = np.zeros((H, W), np.float32)
+    mask.reshape(-1)[pix] = 1.0
+    trgb_h, tdep_h = trgb.cpu().numpy(), tdep.cpu().numpy()
+    osc = O.OracleScene(scene)
+    t0 = time.perf_counter()
+    orc = O.render(osc, cam, T_q, geom64=True, pixels=pix, target_rgb=trgb_h, target_depth=tdep_h,
+                   pixel_weight=mask, n_threads=n_thr)
+    ok = (orc["flags"] & O.TIE_IMAGE) == 0
+    res = {"width": W, "height": H, "pixels": int(len(pix)), "excluded_near_ties": int((~ok).sum()), "outputs": {}}
+    for k in ("rgb", "depth", "alpha", "final_T") + (("feats",) if feats else ()):
+        g = gpu[k][pix][ok]
+        o = np.asarray(orc[k]).reshape(len(pix), -1)[ok]
+        res["outputs"][k] = dict(_err_stats(g - o), oracle_max=float(np.abs(o).max()))
+    if feats:  # bf16 storage error, apart from the blending error above
+        o32 = O.render(O.OracleScene(scene, unrounded_feats=True), cam, T_q, geom64=True, pixels=pix[ok],
+                       n_threads=n_thr)
+        res["outputs"]["feats_bf16_storage"] = dict(_err_stats(orc["feats"][ok] - o32["feats"]),
+                                                    note="oracle with bf16 features minus oracle with the "
+                                                         "unrounded binary32 features")
+    # pose gradient: pixels of the sample without any near-tie decision
+    w = np.zeros((H, W), np.float32)
+    w.reshape(-1)[pix[orc["flags"] == 0]] = 1.0
+    og = O.render(osc, cam, T_q, geom64=True, want_grad=True, pixels=pix, target_rgb=trgb_h, target_depth=tdep_h,
+                  pixel_weight=w, n_threads=n_thr, want_feats=False)
+    res["oracle_s"] = time.perf_counter() - t0
+    loss, grad = S.render_pose_grad(cam, T_q, trgb, tdep, torch.from_numpy(w).cuda())
+    og_g = np.asarray(og["grad"], np.float64)
+    comp = []
+    for k, name in enumerate(("rho_x", "rho_y", "rho_z", "phi_x", "phi_y", "phi_z")):
+        e = abs(float(grad[k]) - og_g[k])
+        comp.append({"component": name, "gpu": float(grad[k]), "oracle": float(og_g[k]), "abs_err": e,
+                     "rel_err": e / max(abs(og_g[k]), 1e-300)})
+    blocks = []
+    for sl in (slice(0, 3), slice(3, 6)):
+        blocks.append(float(np.linalg.norm(np.asarray(grad[sl]) - og_g[sl]) / max(np.linalg.norm(og_g[sl]), 1e-300)))
+    res["gradient"] = {"pixels": int(w.sum()), "loss_rel_err": abs(loss - og["loss"]) / max(abs(og["loss"]), 1e-300),
+                       "components": comp, "block_rel_err": {"rho": blocks[0], "phi": blocks[1]}}
+    return res
 
 
 def pk_for_pmm():

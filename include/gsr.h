@@ -319,10 +319,14 @@ gs_status gs_scene_blend_count(gs_scene* scene, void* stream, int64_t* blended);
 /* Work units of the last call's backward walk, for roofline accounting:
  * blended = (pixel, Gaussian) pairs blended (as gs_scene_blend_count; after a
  * gs_visibility call, the pairs its reverse pass walked back through), and
- * evaluated = (pixel, Gaussian) pairs whose footprint the visibility reverse
- * pass evaluated (a pair before the pixel's last blended Gaussian whose tile
- * entry hits the pixel's 8 x 4 block; 0 after any other call). Waits for
- * `stream`; host pointers, either may be NULL. Errors: INVALID_ARG, CUDA. */
+ * evaluated = after a pose-gradient call, the tile-list entries its pixels
+ * examined before their stop (each pixel's list up to and including the
+ * entry that stopped it, else the whole list: the per-pixel walk of the
+ * definition); after gs_visibility, the (pixel, Gaussian) pairs whose
+ * footprint the reverse pass evaluated (a pair before the pixel's last
+ * blended Gaussian whose tile entry hits the pixel's 8 x 4 block); 0 after a
+ * forward-only call. Waits for `stream`; host pointers, either may be NULL.
+ * Errors: INVALID_ARG, CUDA. */
 gs_status gs_scene_work_counts(gs_scene* scene, void* stream, int64_t* blended, int64_t* evaluated);
 
 /* Render-gradient visibility check with projection filtering (Sec. 3.2,

@@ -573,7 +573,7 @@ static void composite_pixel(const gprep* prep, const int32_t* vis, const uint32_
   memset(r, 0, sizeof(*r));
   r->T[0] = 1.0;
   r->hash = 1469598103934665603ull;
-  const int fd = (feat_out && sc->feats_bf16) ? sc->feat_dim : 0;
+  const int fd = (feat_out && (sc->feats_bf16 || sc->feats_f32)) ? sc->feat_dim : 0;
   for (int c = 0; c < fd; ++c) feat_out[c] = 0.0;
   for (int64_t j = 0; j < len; ++j) {
     const uint32_t gid = list[j];
@@ -630,12 +630,17 @@ static void composite_pixel(const gprep* prep, const int32_t* vis, const uint32_
     r->depth[0] += w[0] * z[0];
     for (int k = 1; k < nd; ++k) r->depth[k] += w[k] * z[0] + w[0] * z[k];
     if (fd) {
-      const uint16_t* f = sc->feats_bf16 + (int64_t)gid * sc->feat_dim;
-      for (int c = 0; c < fd; ++c) {
-        uint32_t bits = (uint32_t)f[c] << 16;
-        float fv;
-        memcpy(&fv, &bits, 4);
-        feat_out[c] += w[0] * (double)fv;
+      if (sc->feats_f32) {
+        const float* f = sc->feats_f32 + (int64_t)gid * sc->feat_dim;
+        for (int c = 0; c < fd; ++c) feat_out[c] += w[0] * (double)f[c];
+      } else {
+        const uint16_t* f = sc->feats_bf16 + (int64_t)gid * sc->feat_dim;
+        for (int c = 0; c < fd; ++c) {
+          uint32_t bits = (uint32_t)f[c] << 16;
+          float fv;
+          memcpy(&fv, &bits, 4);
+          feat_out[c] += w[0] * (double)fv;
+        }
       }
     }
     r->T[0] = Tn;
@@ -683,7 +688,7 @@ static void* render_worker(void* arg) {
   orc_out* out = jb->out;
   const int W = cam->width, H = cam->height;
   const double P = (double)W * (double)H;
-  const int fd = jb->sc->feats_bf16 ? jb->sc->feat_dim : 0;
+  const int fd = (jb->sc->feats_bf16 || jb->sc->feats_f32) ? jb->sc->feat_dim : 0;
   uint32_t* tmp_list = NULL;
   if (jb->brute) tmp_list = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(jb->n_order > 0 ? jb->n_order : 1));
   double* fbuf = (double*)malloc(sizeof(double) * (size_t)(fd > 0 ? fd : 1));

@@ -44,6 +44,9 @@ typedef struct {
   const float* opacities;  /* n, in (0, 1) */
   const float* sh;         /* n x (deg+1)^2 x 3, coefficient-major */
   const uint16_t* feats_bf16; /* n x feat_dim bfloat16 bit patterns, or NULL */
+  const float* feats_f32;  /* n x feat_dim binary32 features, or NULL; when given they are blended
+                              instead of feats_bf16 (the unrounded vectors, to separate the error of
+                              bf16 storage from that of the blending) */
 } orc_scene;
 
 /* Per-Gaussian discrete record written by orc_project_f32. */

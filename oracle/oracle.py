@@ -62,7 +62,8 @@ class _Camera(ctypes.Structure):
 class _Scene(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("sh_degree", ctypes.c_int), ("feat_dim", ctypes.c_int),
                 ("means", ctypes.c_void_p), ("scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
-                ("opacities", ctypes.c_void_p), ("sh", ctypes.c_void_p), ("feats_bf16", ctypes.c_void_p)]
+                ("opacities", ctypes.c_void_p), ("sh", ctypes.c_void_p), ("feats_bf16", ctypes.c_void_p),
+                ("feats_f32", ctypes.c_void_p)]
 
 
 class _Opts(ctypes.Structure):
@@ -173,9 +174,14 @@ def sh_basis(deg: int, d):
 
 
 class OracleScene:
-    """Holds contiguous copies of the scene arrays for the C oracle."""
+    """Holds contiguous copies of the scene arrays for the C oracle.
 
-    def __init__(self, scene: dict):
+    unrounded_feats=True blends the scene's binary32 features ("feats_f32")
+    instead of their bf16 rounding: the difference of the two renders is the
+    error of bf16 feature storage alone (Sec. 3.1 features, blended like the
+    colour)."""
+
+    def __init__(self, scene: dict, unrounded_feats: bool = False):
         self.means = _f32(scene["means"]).reshape(-1, 3)
         self.n = self.means.shape[0]
         self.scales = _f32(scene["scales"]).reshape(-1, 3)
@@ -187,8 +193,12 @@ class OracleScene:
         f = scene.get("feats_bf16")
         self.feats = None if f is None else np.ascontiguousarray(f, np.uint16).reshape(self.n, -1)
         self.feat_dim = 0 if self.feats is None else self.feats.shape[1]
+        self.feats32 = None
+        if unrounded_feats:
+            self.feats32 = _f32(scene["feats_f32"]).reshape(self.n, -1)
+            self.feat_dim = self.feats32.shape[1]
         self._c = _Scene(self.n, self.sh_degree, self.feat_dim, _p(self.means), _p(self.scales),
-                         _p(self.quats), _p(self.opacities), _p(self.sh), _p(self.feats))
+                         _p(self.quats), _p(self.opacities), _p(self.sh), _p(self.feats), _p(self.feats32))
 
 
 def render(scene, cam, T, *, geom64=False, want_grad=False, n_threads=1, pixels=None,

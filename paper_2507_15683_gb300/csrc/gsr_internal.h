@@ -65,7 +65,8 @@ struct Counters {
   unsigned int error;       // device-side consistency failure
   unsigned int vis_count;   // Gaussians the visibility check keeps (M = M^r and M^i)
   unsigned long long blends;  // (pixel, Gaussian) pairs blended by the tangent or visibility reverse pass
-  unsigned long long evals;   // (pixel, Gaussian) pairs the visibility reverse pass evaluated
+  unsigned long long evals;   // list entries the tangent pass's pixels examined before their stop, or
+                              // (pixel, Gaussian) pairs the visibility reverse pass evaluated
   unsigned int band_queue[kMaxBands];  // tile queues of a tangent pass launched in bands of tile rows
 };
 

@@ -370,6 +370,7 @@ __global__ void __launch_bounds__(kTileThreads, TAN ? 4 : FEAT ? 3 : 5) k_compos
   const float pxc = (float)lx + 0.5f, pyc = (float)ly + 0.5f;
   const float4* rec_j4 = reinterpret_cast<const float4*>(w.rec_j);
   uint32_t n_blend = 0;  // tangent pass: blended (pixel, Gaussian) pairs of this thread
+  uint32_t n_eval = 0;   // tangent pass: list entries its pixels examined before their stop
   for (;;) {
     // the tangent pass keeps its own queue: it can follow a feature render
     if (tid == 0) {
@@ -381,7 +382,9 @@ __global__ void __launch_bounds__(kTileThreads, TAN ? 4 : FEAT ? 3 : 5) k_compos
     if (tile >= min(w.n_tiles, w.tile_end)) {
       if (TAN) {
         const uint32_t nb = __reduce_add_sync(0xffffffffu, n_blend);
+        const uint32_t ne = __reduce_add_sync(0xffffffffu, n_eval);
         if (lane == 0 && nb) atomicAdd(&w.ctr->blends, (unsigned long long)nb);
+        if (lane == 0 && ne) atomicAdd(&w.ctr->evals, (unsigned long long)ne);
       }
       break;
     }
@@ -432,6 +435,7 @@ __global__ void __launch_bounds__(kTileThreads, TAN ? 4 : FEAT ? 3 : 5) k_compos
       dC0[k] = dC1[k] = dC2[k] = dD[k] = dT[k] = make_float2(0.f, 0.f);
     }
     uint32_t last = 0;
+    uint32_t stop_pos = 0;  // 1 + list position of the entry that stopped the walk (0: none)
     bool done = !inside;
     for (int bs = 0; bs < n; bs += kB) {
       if (__syncthreads_count(done) == kTileThreads) break;
@@ -529,6 +533,7 @@ __global__ void __launch_bounds__(kTileThreads, TAN ? 4 : FEAT ? 3 : 5) k_compos
         if (TAN) n_blend += acc ? 1u : 0u;
         T = acc ? Tn : T;
         last = acc ? (uint32_t)(bs + j + 1) : last;
+        if (TAN) stop_pos = stop ? (uint32_t)(bs + j + 1) : stop_pos;
         done = done || stop;
       };
       const uint32_t wbit = 1u << wid;
@@ -564,6 +569,8 @@ __global__ void __launch_bounds__(kTileThreads, TAN ? 4 : FEAT ? 3 : 5) k_compos
     }
     const size_t HW = (size_t)V.width * V.height;
     const size_t p = (size_t)py * V.width + px;
+    // the entries a pixel examines: its list up to the stop, or the whole list
+    if (TAN && inside) n_eval += stop_pos ? stop_pos : (uint32_t)n;
     if (inside) {
       if (V.rgb) {
         V.rgb[p] = C0;

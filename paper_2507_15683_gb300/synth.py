@@ -121,8 +121,10 @@ def tiny_camera() -> dict:
 
 
 def aerial_scene(seed: int, n: int, extent=(0.0, 1000.0, 0.0, 1000.0), n_clusters: int | None = None,
-                 sh_degree: int = 3, feat_dim: int = 0, building_frac: float = 0.05) -> dict:
-    """Ground plane (z ~ N(0, 20 m)) plus clustered 'building' Gaussians."""
+                 sh_degree: int = 3, feat_dim: int = 0, building_frac: float = 0.05,
+                 keep_f32: bool = False) -> dict:
+    """Ground plane (z ~ N(0, 20 m)) plus clustered 'building' Gaussians.
+    keep_f32 also returns the unrounded binary32 features ("feats_f32")."""
     g = rng(seed)
     x0, x1, y0, y1 = extent
     nb = int(round(n * building_frac))
@@ -150,8 +152,11 @@ def aerial_scene(seed: int, n: int, extent=(0.0, 1000.0, 0.0, 1000.0), n_cluster
         f = g.standard_normal((n, feat_dim)).astype(np.float32)
         f /= np.linalg.norm(f, axis=1, keepdims=True)
         feats = to_bf16_bits(f)
-    return {"means": means, "scales": scales, "quats": quats, "opacities": opac, "sh": sh,
-            "sh_degree": sh_degree, "feats_bf16": feats}
+    out = {"means": means, "scales": scales, "quats": quats, "opacities": opac, "sh": sh,
+           "sh_degree": sh_degree, "feats_bf16": feats}
+    if keep_f32 and feat_dim:
+        out["feats_f32"] = f
+    return out
 
 
 def aerial_camera(width=1920, height=1080, f=1400.0) -> dict:
@@ -172,7 +177,7 @@ def refine_workload(seed: int = 3, n: int = 500_000):
 
 
 def partitioned_scene(seed: int, cells_x: int, cells_y: int, per_cell: int, cell_m: float = 500.0,
-                      sh_degree: int = 3, feat_dim: int = 32) -> dict:
+                      sh_degree: int = 3, feat_dim: int = 32, keep_f32: bool = False) -> dict:
     """Scene made of a grid of square cells; Gaussians are stored cell by cell
     and ``partition_offsets`` gives each cell's index range."""
     parts = []
@@ -180,9 +185,11 @@ def partitioned_scene(seed: int, cells_x: int, cells_y: int, per_cell: int, cell
         for cx in range(cells_x):
             parts.append(aerial_scene(seed * 1000 + cy * cells_x + cx, per_cell,
                                       extent=(cx * cell_m, (cx + 1) * cell_m, cy * cell_m, (cy + 1) * cell_m),
-                                      sh_degree=sh_degree, feat_dim=feat_dim))
+                                      sh_degree=sh_degree, feat_dim=feat_dim, keep_f32=keep_f32))
     out = {k: np.concatenate([p[k] for p in parts]) for k in ("means", "scales", "quats", "opacities", "sh")}
     out["feats_bf16"] = np.concatenate([p["feats_bf16"] for p in parts]) if feat_dim else None
+    if keep_f32 and feat_dim:
+        out["feats_f32"] = np.concatenate([p["feats_f32"] for p in parts])
     out["sh_degree"] = sh_degree
     out["partition_offsets"] = np.arange(0, per_cell * len(parts) + 1, per_cell, dtype=np.int64)
     return out

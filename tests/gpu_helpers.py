@@ -57,3 +57,9 @@ def block_rel_err(g, ref):
     for s in (slice(0, 3), slice(3, 6)):
         out.append(float(np.linalg.norm(g[s] - ref[s]) / max(np.linalg.norm(ref[s]), 1e-30)))
     return out
+
+
+def component_rel_err(g, ref):
+    """Relative error of each of the six gradient components, |g_k - ref_k| / |ref_k|."""
+    g, ref = np.asarray(g, np.float64), np.asarray(ref, np.float64)
+    return [float(abs(g[k] - ref[k]) / max(abs(ref[k]), 1e-300)) for k in range(6)]

@@ -213,6 +213,31 @@ def test_features_identical_blending(oracle):
     np.testing.assert_allclose(r["feats"][:, 3], 0.0, atol=0)
 
 
+def test_unrounded_features_are_blended_like_the_bf16_ones(oracle):
+    # the binary32 feature input (used to separate the error of bf16 storage):
+    # given the bf16 values it reproduces the bf16 render exactly, and by
+    # linearity in the features the storage error is the render of the
+    # rounding residuals
+    g = np.random.default_rng(11)
+    sc = synth.tiny_scene(6, sh_degree=1)
+    n = sc["means"].shape[0]
+    f = g.standard_normal((n, 8)).astype(np.float32)
+    sc = _with_feats(sc, f)
+    fb = synth.bf16_bits_to_f32(sc["feats_bf16"])
+    cam = synth.tiny_camera()
+    rb = oracle.render(sc, cam, np.eye(4), geom64=True)
+    same = dict(sc, feats_f32=fb)
+    r1 = oracle.render(oracle.OracleScene(same, unrounded_feats=True), cam, np.eye(4), geom64=True)
+    np.testing.assert_array_equal(r1["feats"], rb["feats"])
+    np.testing.assert_array_equal(r1["rgb"], rb["rgb"])
+    r32 = oracle.render(oracle.OracleScene(dict(sc, feats_f32=f), unrounded_feats=True), cam, np.eye(4),
+                        geom64=True)
+    resid = oracle.render(oracle.OracleScene(dict(sc, feats_f32=(f - fb).astype(np.float32)),
+                                             unrounded_feats=True), cam, np.eye(4), geom64=True)
+    np.testing.assert_allclose(r32["feats"] - rb["feats"], resid["feats"], rtol=0, atol=1e-15)
+    assert np.abs(resid["feats"]).max() > 0
+
+
 def test_depth_of_flat_scene(oracle):
     sc = synth.tiny_scene(5)
     sc["means"][:, 2] = 6.0

@@ -342,10 +342,19 @@ def main():
         pass
     clocks = ClockSampler(bus)
     clocks.start()
+    # the default launch configuration, then the autotuner's for this call shape
+    ms_grad_default = max_over_ranks(timed(grad_step, args.steps), world)
+    tune_grad = gsr.gs_autotune(S.handle, gsr.GS_MODE_POSE_GRAD, [cam], [T_q], reps=10)
+    for _ in range(args.warmup):
+        grad_step()
     ms_grad = timed(grad_step, args.steps)
     ms_grad = max_over_ranks(ms_grad, world)
     st, _, _ = S.status()
     assert st == 0
+    for _ in range(args.warmup):
+        fwd_step()
+    ms_fwd_default = max_over_ranks(timed(fwd_step, args.steps), world)
+    tune_fwd = gsr.gs_autotune(S.handle, gsr.GS_MODE_FORWARD, [cam], [T_q], reps=10)
     for _ in range(args.warmup):
         fwd_step()
     ms_fwd = max_over_ranks(timed(fwd_step, args.steps), world)
@@ -454,7 +463,12 @@ def main():
                    "records": int(n_rec), "pairs": int(n_pairs), "evaluations": int(evals),
                    "pair_pixels": pair_pixels, "blended": int(blends),
                    "l2": "flushed (256 MB write) between timed steps, outside the timed events",
-                   "parallelism": "replicas" if world > 1 else "single"},
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "launch": {"pose_grad": tune_grad["best"], "forward": tune_fwd["best"],
+                              "note": "chosen by the library's autotuner (gs_autotune) for this call shape"}},
+        "untuned": {"ms_per_step": ms_grad_default, "fwd_ms": ms_fwd_default,
+                    "value": job_mpix_per_s(world, P, ms_grad_default),
+                    "note": "the same steps under the default launch configuration"},
         "pose_grad_iters_per_s": world / (ms_grad * 1e-3),
         "fwd_mpix_s": job_mpix_per_s(world, P, ms_fwd), "fwd_ms": ms_fwd,
         "clocks": clk,
@@ -579,6 +593,9 @@ def bench_large(gsr, synth, torch, errors=None):
         td = [o["depth"] for o in outs]
         opts = gsr.gs_refine_defaults()
         opts.iterations = 20
+        # the autotuner's configuration for this level's 8-view pose-gradient batch
+        tune = gsr.gs_autotune(S.handle, gsr.GS_MODE_POSE_GRAD, [cam] * 8, [gsr.pose_matrix(p) for p in poses],
+                               reps=3)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         hist = gsr.gs_refine_poses_batch(S.handle, [gsr.camera(cam)] * 8, poses, [a.data_ptr() for a in tr],
@@ -587,6 +604,7 @@ def bench_large(gsr, synth, torch, errors=None):
         b1, res, act = S.stream_stats()
         errs = [_pose_errors(gsr.pose_matrix(p), T) for p, T in zip(poses, refs)]
         levels.append({"width": cam["width"], "height": cam["height"], "iterations": 20, "seconds": dt,
+                       "launch": tune,
                        "pose_iters_per_s": 8 * 20 / dt, "mpix_per_s": 8 * 20 * cam["width"] * cam["height"] / dt / 1e6,
                        "h2d_bytes": b1 - b0, "resident_partitions": res,
                        "loss_first_last": [float(hist[:, 0].mean()), float(hist[:, -1].mean())],
@@ -925,7 +943,38 @@ def bench_dense(gsr, synth, torch, steps, warmup, pk_src, with_oracle):
     return out
 
 
+FLOPS_PER_FEAT_BLEND = 12 + 2 * 32  # a blend of the forward pass: blend 12, then 32 feature FMAs
+
+
+def fp32_peak_tflops(torch):
+    pk, src = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    return n_sm * 128 * 2 * sm_max * 1e6 / 1e12, "%d SMs x 128 fp32 lanes x 2 x %.0f MHz (%s max clock)" % (
+        n_sm, sm_max, src)
+
+
+def kernel_times(gsr, S, fn, reps):
+    """Per-kernel device times (ms per call) of `fn` from the library's own
+    events (the passes then run in order, without the shading stream)."""
+    gsr.gs_scene_set_timing(S.handle, True)
+    gsr.gs_scene_kernel_times(S.handle)
+    for _ in range(reps):
+        fn()
+    kms, kn = gsr.gs_scene_kernel_times(S.handle)
+    gsr.gs_scene_set_timing(S.handle, False)
+    per = {name: kms[i] / reps for i, name in enumerate(gsr.KERNEL_NAMES) if kn[i]}
+    tot = max(sum(per.values()), 1e-12)
+    return {k: {"ms": v, "share": v / tot} for k, v in per.items()}
+
+
 def bench_batched(gsr, synth, torch, flush, steps, warmup):
+    """84 candidate poses at three pyramid levels (64 @ 480x270, 16 @ 960x540,
+    4 @ 1920x1080), 2M Gaussians with 32 BF16 features: one graph launch
+    against 84 single-view launches, forward (with the feature map) and pose
+    gradient, under the default launch configurations and after the
+    autotuner has picked one per call shape (the batch, and each level's
+    single view). Per-kernel times and the dominant kernel's roofline."""
     scene = synth.partitioned_scene(4, 2, 2, 500_000, sh_degree=3, feat_dim=32)
     cams, poses = synth.batched_views()
     S = gsr.Scene(scene)
@@ -937,6 +986,10 @@ def bench_batched(gsr, synth, torch, flush, steps, warmup):
     tg = [(o["rgb"].clone(), o["depth"].clone()) for o in outs]
     qs = [synth.perturb_pose(T, synth.rng(500 + k), 1.0, 1.0) for k, T in enumerate(poses)]
     loss, grad = S.render_pose_grad_batch(cams, qs, [a for a, _ in tg], [b for _, b in tg])  # sizes the workspace
+    q_blends, q_evals = gsr.gs_scene_work_counts(S.handle)
+    # the forward pass walks the same lists as a pose gradient at the same poses
+    S.render_pose_grad_batch(cams, poses, [a for a, _ in tg], [b for _, b in tg])
+    f_blends, f_evals = gsr.gs_scene_work_counts(S.handle)
     _, n_rec, n_pairs = S.status()
     S.reserve(int(n_rec * 1.2) + 1024, int(n_pairs * 1.2) + 4096)
     cc = [gsr.camera(c) for c in cams]
@@ -961,35 +1014,75 @@ def bench_batched(gsr, synth, torch, flush, steps, warmup):
         gsr.gs_render_pose_grad_batch(S.handle, cc, qq, [a.data_ptr() for a, _ in tg], [b.data_ptr() for _, b in tg],
                                       None, 0.1, None, res_batch.data_ptr(), gsr.GS_BATCH_GRAPH, stream)
 
-    res = {}
-    for name, fn in (("single", single), ("batched", batch), ("single_grad", single_grad),
-                     ("batched_grad", batch_grad)):
-        for _ in range(warmup):
-            fn()
-        torch.cuda.synchronize()
-        st = S.status()[0]
-        assert st == 0, "batched workspace overflow"
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        for a, b in ev:
-            flush.zero_()
-            a.record()
-            fn()
-            b.record()
-        torch.cuda.synchronize()
-        res[name] = float(np.mean([a.elapsed_time(b) for a, b in ev]))
-    torch.testing.assert_close(res_single, res_batch, rtol=0, atol=0)
+    def time_all():
+        res = {}
+        for name, fn in (("single", single), ("batched", batch), ("single_grad", single_grad),
+                         ("batched_grad", batch_grad)):
+            for _ in range(warmup):
+                fn()
+            torch.cuda.synchronize()
+            st = S.status()[0]
+            assert st == 0, "batched workspace overflow"
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for a, b in ev:
+                flush.zero_()
+                a.record()
+                fn()
+                b.record()
+            torch.cuda.synchronize()
+            res[name] = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        torch.testing.assert_close(res_single, res_batch, rtol=0, atol=0)
+        return res
+
     px = sum(c["width"] * c["height"] for c in cams)
+
+    def summary(res):
+        return {"forward": {"single_ms": res["single"], "batched_ms": res["batched"],
+                            "single_mpix_s": px / (res["single"] * 1e-3) / 1e6,
+                            "batched_mpix_s": px / (res["batched"] * 1e-3) / 1e6,
+                            "speedup": res["single"] / res["batched"]},
+                "pose_grad": {"single_ms": res["single_grad"], "batched_ms": res["batched_grad"],
+                              "single_pose_iters_per_s": len(cams) / (res["single_grad"] * 1e-3),
+                              "batched_pose_iters_per_s": len(cams) / (res["batched_grad"] * 1e-3),
+                              "speedup": res["single_grad"] / res["batched_grad"]}}
+
+    default = summary(time_all())
+    # the autotuner, per call shape: the 84-view batch and each level's single view
+    tuning = {}
+    levels = sorted({(c["width"], c["height"]) for c in cams})
+    for mode, name in ((gsr.GS_MODE_FEATURES, "forward"), (gsr.GS_MODE_POSE_GRAD, "pose_grad")):
+        tp = qs if mode == gsr.GS_MODE_POSE_GRAD else poses
+        r = gsr.gs_autotune(S.handle, mode, cams, tp, reps=5)
+        tuning[name] = {"batch": r}
+        for (w, h) in levels:
+            k = next(i for i, c in enumerate(cams) if (c["width"], c["height"]) == (w, h))
+            tuning[name]["%dx%d" % (w, h)] = gsr.gs_autotune(S.handle, mode, [cams[k]], [tp[k]], reps=5)
+    tuned = summary(time_all())
+    # per-kernel device times of one batch call (library events, non-graph, passes in order)
+    kf = kernel_times(gsr, S, lambda: S.render_batch(cams, poses, outs), 3)
+    kg = kernel_times(gsr, S, lambda: S.render_pose_grad_batch(cams, qs, [a for a, _ in tg], [b for _, b in tg]), 3)
+    peak, peak_src = fp32_peak_tflops(torch)
+
+    def roof(kern, evals, blends, per_blend, what):
+        t = kern["composite"]["ms"]
+        fl = evals * FLOPS_PER_EVAL + blends * per_blend
+        ach = fl / (t * 1e-3) / 1e12
+        return {"bound": "alu", "kernel": what, "ms": t, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "peak_source": peak_src,
+                "work": "%d list entries examined before the stop x %d + %d blended pairs x %d"
+                        % (evals, FLOPS_PER_EVAL, blends, per_blend)}
+
     S.close()
-    return {"views": len(cams), "gaussians": 2_000_000, "feat_dim": 32, "mpix": px / 1e6,
-            "forward": {"single_ms": res["single"], "batched_ms": res["batched"],
-                        "single_mpix_s": px / (res["single"] * 1e-3) / 1e6,
-                        "batched_mpix_s": px / (res["batched"] * 1e-3) / 1e6,
-                        "speedup": res["single"] / res["batched"], "outputs": "rgb, depth, alpha, T, 32 features"},
-            "pose_grad": {"single_ms": res["single_grad"], "batched_ms": res["batched_grad"],
-                          "single_pose_iters_per_s": len(cams) / (res["single_grad"] * 1e-3),
-                          "batched_pose_iters_per_s": len(cams) / (res["batched_grad"] * 1e-3),
-                          "speedup": res["single_grad"] / res["batched_grad"]},
-            "records": int(n_rec), "pairs": int(n_pairs)}
+    out = {"views": len(cams), "gaussians": 2_000_000, "feat_dim": 32, "mpix": px / 1e6,
+           "outputs": "rgb, depth, alpha, T, 32 features", "default_launch": default, "tuned": tuned,
+           "tuning": tuning,
+           "kernels": {"forward": kf, "pose_grad": kg},
+           "roofline": {"forward": roof(kf, f_evals, f_blends, FLOPS_PER_FEAT_BLEND,
+                                        "composite, forward with the 32-channel feature map"),
+                        "pose_grad": roof(kg, q_evals, q_blends, FLOPS_PER_BLEND, "composite, tangent pass")},
+           "records": int(n_rec), "pairs": int(n_pairs)}
+    out.update(tuned)
+    return out
 
 
 if __name__ == "__main__":

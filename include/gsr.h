@@ -329,6 +329,73 @@ gs_status gs_scene_blend_count(gs_scene* scene, void* stream, int64_t* blended);
  * Errors: INVALID_ARG, CUDA. */
 gs_status gs_scene_work_counts(gs_scene* scene, void* stream, int64_t* blended, int64_t* evaluated);
 
+/* ---- Launch configurations and the autotuner ----------------------------
+ * The dense stage renders candidate poses at the levels of a coarse-to-fine
+ * pyramid (Sec. 3.4: H_f / H_c = 8; 480x270 to 3840x2160 views here), and one
+ * launch shape does not suit every level or batch. A launch configuration
+ * applies to one call shape: the multiset of the call's view sizes (a
+ * single view, or every view of a batch call), for one mode. It sets
+ *   - the compositor variant (variant 0 is the default): the number of
+ *     Gaussians staged in shared memory per batch, and the resident CTAs per
+ *     SM its register allocation allows for;
+ *   - the persistent compositor grid, in CTAs per SM (0: as many as the
+ *     variant's occupancy allows);
+ *   - the CTAs per SM of the projection, shading, scatter and sort kernels.
+ * No configuration changes a result: the blending order and every reduction
+ * order are fixed by the tile lists, so every configuration gives the same
+ * bits. Shapes without a configuration use the defaults. Changing one makes
+ * the next graph-mode batch call capture its graph again. */
+#define GS_MODE_FORWARD 0     /* forward render without features */
+#define GS_MODE_FEATURES 1    /* forward render with the feature map */
+#define GS_MODE_POSE_GRAD 2   /* pose-gradient call (the tangent pass) */
+#define GS_COMPOSITE_VARIANTS 4
+
+typedef struct {
+  int variant;      /* compositor variant, 0..GS_COMPOSITE_VARIANTS-1 */
+  int ctas_per_sm;  /* persistent compositor CTAs per SM; 0 = the variant's occupancy */
+  int grid_mult;    /* CTAs per SM of projection, shading, scatter and sort, 1..64 (default 8) */
+  /* filled in by gs_scene_get_launch and gs_autotune, ignored on input: */
+  int batch;        /* Gaussians the variant stages per batch */
+  int min_blocks;   /* resident CTAs per SM its registers allow for */
+  int occupancy;    /* resident CTAs per SM on this device */
+} gs_launch;
+
+/* Set (or read back, with the effective CTAs per SM and the variant's
+ * figures) the configuration of `mode` for the call shape of cams[0..n_views)
+ * (host array; only the sizes matter). Errors: INVALID_ARG (mode, sizes, a
+ * field out of range), CUDA. */
+gs_status gs_scene_set_launch(gs_scene* scene, int mode, int n_views, const gs_camera* cams, const gs_launch* cfg);
+gs_status gs_scene_get_launch(gs_scene* scene, int mode, int n_views, const gs_camera* cams, gs_launch* cfg);
+
+typedef struct {
+  gs_launch best;     /* the configuration chosen (now set for the shape) */
+  double ms_default;  /* median device time of one call under the defaults */
+  double ms_best;     /* the same under the chosen configuration (<= ms_default) */
+  int candidates;     /* configurations timed */
+} gs_tune_result;
+
+/* Autotuner: time one call of `mode` on the views (cams, poses: host arrays
+ * of n_views) under candidate configurations -- every compositor variant
+ * with its occupancy and the two next-smaller persistent grids, then the
+ * projection-side grid at 2, 4, 16 and 32 CTAs per SM -- and keep the
+ * fastest for the shape. Each candidate's time is the median of `reps`
+ * (< 1: 5) asynchronous calls on `stream`, measured with CUDA events, after
+ * one warm-up call. The views are rendered into buffers of the tuner's own;
+ * GS_MODE_POSE_GRAD uses those renders as its targets. Synchronous; do not
+ * call during stream capture. result (host) may be NULL. Errors: INVALID_ARG,
+ * OOM, CUDA, CAPACITY. */
+gs_status gs_autotune(gs_scene* scene, int mode, int n_views, const gs_camera* cams, const gs_pose* poses, int reps,
+                      gs_tune_result* result, void* stream);
+
+/* The configuration cache file: one text line per (device, mode, shape),
+ * "device name/SM count|mode|shape|variant ctas_per_sm grid_mult". save
+ * writes every configuration of the scene for its device and keeps the lines
+ * of other devices and shapes; load applies the lines of this device (the
+ * count in *loaded, may be NULL). Errors: INVALID_ARG (path unreadable or
+ * unwritable, a malformed line). */
+gs_status gs_tune_save(const gs_scene* scene, const char* path);
+gs_status gs_tune_load(gs_scene* scene, const char* path, int* loaded);
+
 /* Render-gradient visibility check with projection filtering (Sec. 3.2,
  * Algorithm 1) of every Gaussian of the scene from one pose.
  *

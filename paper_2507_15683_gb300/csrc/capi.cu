@@ -10,8 +10,10 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <functional>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -46,8 +48,9 @@ struct DevBuf {
   size_t bytes = 0;
 };
 
-// Bumped by every device (re)allocation of a workspace buffer: a captured
-// graph holds the buffers' addresses and is replayed only while this is
+// Bumped by every device (re)allocation of a workspace buffer and by every
+// change of a launch configuration: a captured graph holds the buffers'
+// addresses and the launch shapes, and is replayed only while this is
 // unchanged since its capture.
 std::atomic<uint64_t> g_alloc_gen{0};
 
@@ -145,6 +148,10 @@ struct Part {
 struct gs_scene {
   int device = 0;
   int sm_count = 1;
+  std::string device_name;
+  // launch configurations by call shape (the views' sizes), set by the
+  // autotuner, gs_scene_set_launch or gs_tune_load; absent shapes use the defaults
+  std::map<std::string, LaunchCfg> launch;
   int64_t n = 0;
   int sh_degree = 0, feat_dim = 0, nsh4 = 1;
   DevBuf pos, cov, sh, feat;
@@ -209,6 +216,31 @@ struct gs_scene {
 };
 
 namespace {
+
+// Call-shape key of a launch configuration: the views' sizes as a sorted
+// multiset, "WxH*count" joined by commas.
+std::string shape_key(const std::vector<std::pair<int, int>>& sizes) {
+  std::map<std::pair<int, int>, int> m;
+  for (const auto& wh : sizes) ++m[wh];
+  std::string k;
+  for (const auto& e : m) {
+    if (!k.empty()) k += ',';
+    k += std::to_string(e.first.first) + "x" + std::to_string(e.first.second) + "*" + std::to_string(e.second);
+  }
+  return k;
+}
+
+std::string shape_key(const std::vector<View>& hv) {
+  std::vector<std::pair<int, int>> sz;
+  for (const View& V : hv) sz.emplace_back(V.width, V.height);
+  return shape_key(sz);
+}
+
+LaunchCfg launch_cfg(const gs_scene* s, const std::vector<View>& hv) {
+  if (s->launch.empty()) return LaunchCfg{};
+  const auto it = s->launch.find(shape_key(hv));
+  return it == s->launch.end() ? LaunchCfg{} : it->second;
+}
 
 SceneDev scene_dev(const gs_scene* s) {
   SceneDev d;
@@ -441,8 +473,13 @@ gs_status enqueue(gs_scene* s, const std::vector<View>& hv, const std::vector<in
     }
   }
   auto mark = [&](int k) -> cudaError_t { return timed ? cudaEventRecord(ev[k], st) : cudaSuccess; };
+  bool feats = false;
+  for (const View& V : hv) feats = feats || V.feats != nullptr;
+  const LaunchCfg cfg = launch_cfg(s, hv);
+  const int mode = g ? kModeTan : (feats && s->feat_dim) ? kModeFwdFeat : kModeFwd;
+  const int grid = s->sm_count * std::max(1, cfg.grid_mult[mode]);  // projection, shading, scatter, sort
   GS_CUDA(mark(0));
-  GS_CUDA(launch_project(sc, dviews, nv, w, s->sm_count * 8, st));
+  GS_CUDA(launch_project(sc, dviews, nv, w, grid, st));
   GS_CUDA(mark(1));
   // The shading pass reads only what the projection wrote, and the binning
   // (scan, scatter, sort) reads nothing the shading writes (the sort's tie key,
@@ -453,33 +490,28 @@ gs_status enqueue(gs_scene* s, const std::vector<View>& hv, const std::vector<in
   if (fork) {
     GS_CUDA(cudaEventRecord(s->ev_proj, st));
     GS_CUDA(cudaStreamWaitEvent(s->side_st, s->ev_proj, 0));
-    GS_CUDA(launch_shade(sc, dviews, w, jac, s->sm_count * 8, s->side_st));
+    GS_CUDA(launch_shade(sc, dviews, w, jac, grid, s->side_st));
     if (vis) {  // Algorithm 1's in-image test and the reverse pass's zeroed accumulator need no binning
       GS_CUDA(cudaMemsetAsync(dp<float>(s->vis_acc), 0, (size_t)s->rec_cap * kVisAcc * sizeof(float), s->side_st));
       GS_CUDA(launch_vis_inimage(sc, dviews, vis->mask, vis->uv, vis->grad, s->sm_count * 8, s->side_st));
     }
     GS_CUDA(cudaEventRecord(s->ev_shade, s->side_st));
   } else {
-    GS_CUDA(launch_shade(sc, dviews, w, jac, s->sm_count * 8, st));
+    GS_CUDA(launch_shade(sc, dviews, w, jac, grid, st));
   }
   GS_CUDA(mark(2));
   GS_CUDA(launch_scan_tiles(w, st));
   GS_CUDA(mark(3));
-  GS_CUDA(launch_scatter(dviews, w, s->sm_count * 8, st));
+  GS_CUDA(launch_scatter(dviews, w, grid, st));
   GS_CUDA(mark(4));
-  GS_CUDA(launch_sort_tiles(w, s->sm_count * 8, st));
+  GS_CUDA(launch_sort_tiles(w, grid, st));
   if (fork) GS_CUDA(cudaStreamWaitEvent(st, s->ev_shade, 0));
   GS_CUDA(mark(5));
-  bool feats = false;
-  for (const View& V : hv) feats = feats || V.feats != nullptr;
-  if (!g || feats)
-    GS_CUDA(launch_composite(sc, dviews, nv, w, feats,
-                             s->sm_count * composite_blocks_per_sm(feats ? s->feat_dim : 0, false), st));
+  if (!g || feats) GS_CUDA(launch_composite(sc, dviews, nv, w, feats, cfg, s->sm_count, st));
   if (g) {
     // the tangent pass re-renders the same values (without features) and adds
     // the loss and its pose gradient
     double* res = g->result ? g->result : w.result;
-    const int grid = s->sm_count * composite_blocks_per_sm(0, true);
     if (bands && bands->n > 0 && nv == 1) {
       // band b of the tangent pass starts when the binning is done and its
       // target rows are on the device; consecutive bands run on two streams so
@@ -493,13 +525,14 @@ gs_status enqueue(gs_scene* s, const std::vector<View>& hv, const std::vector<in
         GS_CUDA(cudaStreamWaitEvent(bs, bands->ready[b], 0));
         const uint32_t t0 = V.tile_base + bands->tile_row[b] * (uint32_t)V.tiles_x;
         const uint32_t t1 = V.tile_base + bands->tile_row[b + 1] * (uint32_t)V.tiles_x;
-        GS_CUDA(launch_composite_tangent_range(sc, dviews, nv, w, res, grid, bs, t0, t1, &w.ctr->band_queue[b]));
+        GS_CUDA(launch_composite_tangent_range(sc, dviews, nv, w, res, cfg, s->sm_count, bs, t0, t1,
+                                               &w.ctr->band_queue[b]));
         GS_CUDA(cudaEventRecord(s->ev_band_done[b], bs));
       }
       for (int b = 0; b < bands->n; ++b) GS_CUDA(cudaStreamWaitEvent(st, s->ev_band_done[b], 0));
     } else {
       if (targets_ready) GS_CUDA(cudaStreamWaitEvent(st, targets_ready, 0));  // only this pass reads the targets
-      GS_CUDA(launch_composite_tangent(sc, dviews, nv, w, res, grid, st));
+      GS_CUDA(launch_composite_tangent(sc, dviews, nv, w, res, cfg, s->sm_count, st));
     }
   }
   GS_CUDA(mark(6));
@@ -882,6 +915,7 @@ gs_status gs_create_scene(const gs_scene_desc* d, gs_scene** out) {
   e = cudaGetDeviceProperties(&prop, s->device);
   if (e != cudaSuccess) return cleanup(fail(GS_ERR_CUDA, std::string("cudaGetDeviceProperties: ") + cudaGetErrorString(e)));
   s->sm_count = prop.multiProcessorCount;
+  s->device_name = prop.name;
   e = cudaStreamCreateWithFlags(&s->side_st, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_proj, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_shade, cudaEventDisableTiming);
@@ -1003,9 +1037,9 @@ gs_status gs_create_scene(const gs_scene_desc* d, gs_scene** out) {
     release(staging);
     if (e != cudaSuccess) return cleanup(fail(GS_ERR_CUDA, std::string("pack: ") + cudaGetErrorString(e)));
   }
-  // occupancy queries outside any stream capture
-  composite_blocks_per_sm(s->feat_dim, false);
-  composite_blocks_per_sm(0, true);
+  // occupancy queries of every compositor variant outside any stream capture
+  for (int m = 0; m < kModeCount; ++m)
+    for (int v = 0; v < kCompVariants; ++v) composite_variant_info(m, v);
   *out = s;
   return GS_OK;
 }
@@ -1403,6 +1437,272 @@ gs_status gs_scene_work_counts(gs_scene* s, void* stream, int64_t* blended, int6
   if (blended) *blended = (int64_t)c.blends;
   if (evaluated) *evaluated = (int64_t)c.evals;
   return GS_OK;
+}
+
+// ---- launch configurations and the autotuner ------------------------------
+
+}  // extern "C"
+
+namespace {
+
+gs_status check_mode_cams(int mode, int n_views, const gs_camera* cams) {
+  if (mode < 0 || mode >= kModeCount) return fail(GS_ERR_INVALID_ARG, "mode must be GS_MODE_FORWARD, _FEATURES or _POSE_GRAD");
+  if (n_views < 1 || !cams) return fail(GS_ERR_INVALID_ARG, "n_views >= 1 and cams are required");
+  for (int v = 0; v < n_views; ++v) GS_TRY(check_cam(cams[v]));
+  return GS_OK;
+}
+
+std::string cams_key(int n_views, const gs_camera* cams) {
+  std::vector<std::pair<int, int>> sz;
+  for (int v = 0; v < n_views; ++v) sz.emplace_back(cams[v].width, cams[v].height);
+  return shape_key(sz);
+}
+
+void fill_launch(const LaunchCfg& c, int mode, gs_launch* out) {
+  const CompVariantInfo vi = composite_variant_info(mode, c.variant[mode]);
+  out->variant = c.variant[mode];
+  out->ctas_per_sm = c.per_sm[mode] > 0 && c.per_sm[mode] < vi.occupancy ? c.per_sm[mode] : vi.occupancy;
+  out->grid_mult = c.grid_mult[mode];
+  out->batch = vi.batch;
+  out->min_blocks = vi.min_blocks;
+  out->occupancy = vi.occupancy;
+}
+
+gs_status set_cfg(gs_scene* s, int mode, const std::string& key, int variant, int per_sm, int grid_mult) {
+  if (variant < 0 || variant >= kCompVariants) return fail(GS_ERR_INVALID_ARG, "variant out of range");
+  if (per_sm < 0 || per_sm > 64) return fail(GS_ERR_INVALID_ARG, "ctas_per_sm must be 0..64");
+  if (grid_mult < 1 || grid_mult > 64) return fail(GS_ERR_INVALID_ARG, "grid_mult must be 1..64");
+  LaunchCfg& c = s->launch[key];
+  c.variant[mode] = variant;
+  c.per_sm[mode] = per_sm;
+  c.grid_mult[mode] = grid_mult;
+  g_alloc_gen.fetch_add(1);  // captured graphs hold the old launch shapes
+  return GS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gs_status gs_scene_set_launch(gs_scene* s, int mode, int n_views, const gs_camera* cams, const gs_launch* cfg) {
+  g_err.clear();
+  GS_TRY(check_scene(s));
+  GS_TRY(check_mode_cams(mode, n_views, cams));
+  if (!cfg) return fail(GS_ERR_INVALID_ARG, "cfg is required");
+  return set_cfg(s, mode, cams_key(n_views, cams), cfg->variant, cfg->ctas_per_sm, cfg->grid_mult);
+}
+
+gs_status gs_scene_get_launch(gs_scene* s, int mode, int n_views, const gs_camera* cams, gs_launch* cfg) {
+  g_err.clear();
+  GS_TRY(check_scene(s));
+  GS_TRY(check_mode_cams(mode, n_views, cams));
+  if (!cfg) return fail(GS_ERR_INVALID_ARG, "cfg is required");
+  GS_TRY(set_device(s));
+  const auto it = s->launch.find(cams_key(n_views, cams));
+  fill_launch(it == s->launch.end() ? LaunchCfg{} : it->second, mode, cfg);
+  return GS_OK;
+}
+
+gs_status gs_autotune(gs_scene* s, int mode, int n_views, const gs_camera* cams, const gs_pose* poses, int reps,
+                      gs_tune_result* result, void* stream) {
+  g_err.clear();
+  GS_TRY(check_scene(s));
+  GS_TRY(check_mode_cams(mode, n_views, cams));
+  if (!poses) return fail(GS_ERR_INVALID_ARG, "poses are required");
+  for (int v = 0; v < n_views; ++v) GS_TRY(check_pose(poses[v]));
+  if (mode == kModeFwdFeat && !s->feat_dim) return fail(GS_ERR_INVALID_ARG, "GS_MODE_FEATURES needs a scene with features");
+  if (reps < 1) reps = 5;
+  GS_TRY(set_device(s));
+  const cudaStream_t st = (cudaStream_t)stream;
+  const std::string key = cams_key(n_views, cams);
+  // output buffers of every view (the tuner's own); the pose-gradient mode uses
+  // the forward renders at the same poses as its targets
+  std::vector<DevBuf> bufs((size_t)n_views);
+  auto free_all = [&]() {
+    cudaStreamSynchronize(st);
+    for (DevBuf& b : bufs) release(b);
+  };
+  std::vector<gs_outputs> outs((size_t)n_views);
+  for (int v = 0; v < n_views; ++v) {
+    const size_t P = (size_t)cams[v].width * cams[v].height;
+    const size_t nf = mode == kModeFwdFeat ? 32 : 0;
+    const gs_status e = ensure(bufs[v], (6 + nf) * P * sizeof(float));
+    if (e != GS_OK) {
+      free_all();
+      return e;
+    }
+    float* b = static_cast<float*>(bufs[v].p);
+    outs[v] = gs_outputs{b, b + 3 * P, b + 4 * P, b + 5 * P, nf ? b + 6 * P : nullptr, nullptr};
+  }
+  std::vector<const float*> trgb((size_t)n_views), tdep((size_t)n_views);
+  for (int v = 0; v < n_views; ++v) {
+    trgb[v] = outs[v].rgb;
+    tdep[v] = outs[v].depth;
+  }
+  GradIn g{trgb.data(), tdep.data(), nullptr, 0.1f, nullptr};
+  std::vector<View> hv;
+  uint64_t n_tiles = 0;
+  gs_status stt = build_views(s, n_views, cams, poses, outs.data(), mode == kModeTan ? &g : nullptr, hv, n_tiles);
+  if (stt != GS_OK) {
+    free_all();
+    return stt;
+  }
+  if (mode == kModeTan) {  // the targets, and a first synchronous call that sizes the workspace
+    std::vector<View> hf;
+    uint64_t nt = 0;
+    stt = build_views(s, n_views, cams, poses, outs.data(), nullptr, hf, nt);
+    if (stt == GS_OK) stt = run_sync(s, hf, nt, nullptr, st);
+  }
+  if (stt == GS_OK) stt = run_sync(s, hv, n_tiles, mode == kModeTan ? &g : nullptr, st);
+  if (stt != GS_OK) {
+    free_all();
+    return stt;
+  }
+  const LaunchCfg saved = s->launch.count(key) ? s->launch[key] : LaunchCfg{};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  GS_CUDA(cudaEventCreate(&e0));
+  GS_CUDA(cudaEventCreate(&e1));
+  std::vector<int4> ranges;
+  // median device time of `reps` asynchronous calls under configuration c
+  auto time_cfg = [&](const LaunchCfg& c, double& ms) -> gs_status {
+    s->launch[key] = c;
+    GS_TRY(prepare_call(s, hv, st, ranges));
+    GS_TRY(enqueue(s, hv, ranges, n_tiles, mode == kModeTan ? &g : nullptr, st, nullptr));  // warm
+    std::vector<double> t;
+    for (int r = 0; r < reps; ++r) {
+      GS_CUDA(cudaEventRecord(e0, st));
+      GS_TRY(enqueue(s, hv, ranges, n_tiles, mode == kModeTan ? &g : nullptr, st, nullptr));
+      GS_CUDA(cudaEventRecord(e1, st));
+      GS_CUDA(cudaEventSynchronize(e1));
+      float f = 0.f;
+      GS_CUDA(cudaEventElapsedTime(&f, e0, e1));
+      t.push_back(f);
+    }
+    Counters c2;
+    GS_TRY(read_counters(s, st, c2));
+    if (c2.overflow) return fail(GS_ERR_CAPACITY, "workspace overflow while tuning");
+    std::sort(t.begin(), t.end());
+    ms = t[t.size() / 2];
+    return GS_OK;
+  };
+  LaunchCfg best = saved, cur = saved;
+  best.variant[mode] = 0;
+  best.per_sm[mode] = 0;
+  best.grid_mult[mode] = 8;
+  double ms_default = 0.0, ms_best = 0.0;
+  int tried = 0;
+  gs_status err = time_cfg(best, ms_default);
+  ms_best = ms_default;
+  ++tried;
+  // compositor variant x persistent CTAs per SM, at the default grid multiple
+  for (int v = 0; v < kCompVariants && err == GS_OK; ++v) {
+    const int occ = composite_variant_info(mode, v).occupancy;
+    for (int p = occ; p >= std::max(1, occ - 2) && err == GS_OK; --p) {
+      if (v == 0 && p == occ) continue;  // the default, timed above
+      cur = best;
+      cur.variant[mode] = v;
+      cur.per_sm[mode] = p == occ ? 0 : p;
+      double ms = 0.0;
+      err = time_cfg(cur, ms);
+      ++tried;
+      if (err == GS_OK && ms < ms_best) {
+        ms_best = ms;
+        best = cur;
+      }
+    }
+  }
+  // then the CTAs per SM of the projection, shading, scatter and sort
+  for (int gm : {2, 4, 16, 32}) {
+    if (err != GS_OK) break;
+    cur = best;
+    cur.grid_mult[mode] = gm;
+    double ms = 0.0;
+    err = time_cfg(cur, ms);
+    ++tried;
+    if (err == GS_OK && ms < ms_best) {
+      ms_best = ms;
+      best = cur;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  free_all();
+  if (err != GS_OK) {
+    s->launch[key] = saved;
+    g_alloc_gen.fetch_add(1);
+    return err;
+  }
+  s->launch[key] = best;
+  g_alloc_gen.fetch_add(1);  // captured graphs hold the old launch shapes
+  if (result) {
+    fill_launch(best, mode, &result->best);
+    result->ms_default = ms_default;
+    result->ms_best = ms_best;
+    result->candidates = tried;
+  }
+  return GS_OK;
+}
+
+gs_status gs_tune_save(const gs_scene* s, const char* path) {
+  g_err.clear();
+  GS_TRY(check_scene(s));
+  if (!path) return fail(GS_ERR_INVALID_ARG, "path is required");
+  // keep the lines of other devices and shapes, replace this device's entries for this scene's shapes
+  std::vector<std::string> keep;
+  if (FILE* f = std::fopen(path, "r")) {
+    char line[1024];
+    while (std::fgets(line, sizeof line, f)) {
+      std::string l(line);
+      while (!l.empty() && (l.back() == '\n' || l.back() == '\r')) l.pop_back();
+      if (l.empty() || l.rfind("#", 0) == 0) continue;
+      const size_t a = l.find('|'), b = l.find('|', a + 1), c = l.find('|', b + 1);
+      if (a == std::string::npos || b == std::string::npos || c == std::string::npos) continue;
+      const std::string dev = l.substr(0, a), key = l.substr(b + 1, c - b - 1);
+      if (dev == s->device_name + "/" + std::to_string(s->sm_count) && s->launch.count(key)) continue;
+      keep.push_back(l);
+    }
+    std::fclose(f);
+  }
+  FILE* f = std::fopen(path, "w");
+  if (!f) return fail(GS_ERR_INVALID_ARG, std::string("cannot write ") + path);
+  std::fprintf(f, "# libgsr launch configurations: device/SMs|mode|shape|variant ctas_per_sm grid_mult\n");
+  for (const std::string& l : keep) std::fprintf(f, "%s\n", l.c_str());
+  for (const auto& e : s->launch)
+    for (int m = 0; m < kModeCount; ++m)
+      std::fprintf(f, "%s/%d|%d|%s|%d %d %d\n", s->device_name.c_str(), s->sm_count, m, e.first.c_str(),
+                   e.second.variant[m], e.second.per_sm[m], e.second.grid_mult[m]);
+  const bool ok = std::fclose(f) == 0;
+  return ok ? GS_OK : fail(GS_ERR_INVALID_ARG, std::string("cannot write ") + path);
+}
+
+gs_status gs_tune_load(gs_scene* s, const char* path, int* loaded) {
+  g_err.clear();
+  GS_TRY(check_scene(s));
+  if (!path) return fail(GS_ERR_INVALID_ARG, "path is required");
+  FILE* f = std::fopen(path, "r");
+  if (!f) return fail(GS_ERR_INVALID_ARG, std::string("cannot read ") + path);
+  const std::string dev = s->device_name + "/" + std::to_string(s->sm_count);
+  int n = 0;
+  char line[1024];
+  gs_status st = GS_OK;
+  while (st == GS_OK && std::fgets(line, sizeof line, f)) {
+    std::string l(line);
+    while (!l.empty() && (l.back() == '\n' || l.back() == '\r')) l.pop_back();
+    if (l.empty() || l.rfind("#", 0) == 0) continue;
+    const size_t a = l.find('|'), b = l.find('|', a + 1), c = l.find('|', b + 1);
+    if (a == std::string::npos || b == std::string::npos || c == std::string::npos || l.substr(0, a) != dev) continue;
+    int mode = -1, v = 0, p = 0, gm = 0;
+    if (std::sscanf(l.c_str() + a + 1, "%d", &mode) != 1 || std::sscanf(l.c_str() + c + 1, "%d %d %d", &v, &p, &gm) != 3 ||
+        mode < 0 || mode >= kModeCount) {
+      st = fail(GS_ERR_INVALID_ARG, "malformed line in " + std::string(path) + ": " + l);
+      break;
+    }
+    st = set_cfg(s, mode, l.substr(b + 1, c - b - 1), v, p, gm);
+    n += st == GS_OK;
+  }
+  std::fclose(f);
+  if (loaded) *loaded = n;
+  return st;
 }
 
 gs_status gs_scene_status(gs_scene* s, void* stream, int64_t* needed_records, int64_t* needed_pairs) {

@@ -12,8 +12,6 @@ namespace gsr {
 constexpr int kTile = 16;          // tile edge in pixels
 constexpr int kTileThreads = 256;  // one thread per pixel of a tile
 constexpr int kSortCap = 2048;     // (tile, Gaussian) pairs a tile sorts in shared memory
-constexpr int kBatchF = 256;       // Gaussians staged per forward batch
-constexpr int kBatchT = 128;       // Gaussians staged per batch in tangent (pose-gradient) mode
 constexpr int kJacStride = 48;     // floats per record of the pose Jacobian (45 used)
 constexpr int kPartialStride = 8;  // doubles per tile partial (loss + 6 grad + pad)
 constexpr int kChunkTiles = 64;    // tiles per first-level chunk of the fp64 pose reduction
@@ -116,6 +114,26 @@ struct Work {
   unsigned int* queue = nullptr;
 };
 
+// Compositor modes and their variants (staging batch x resident-CTA bound);
+// variant 0 of each mode is the default, the autotuner may pick another.
+enum { kModeFwd = 0, kModeFwdFeat = 1, kModeTan = 2, kModeCount = 3 };
+constexpr int kCompVariants = 4;
+struct CompVariantInfo {
+  int batch;       // Gaussians staged per batch
+  int min_blocks;  // resident CTAs per SM its registers allow for
+  int occupancy;   // resident CTAs per SM on this device (registers and shared memory)
+};
+CompVariantInfo composite_variant_info(int mode, int variant);
+
+// Launch configuration of one call shape: per compositor mode, the variant,
+// the persistent CTAs per SM (0: the variant's occupancy) and the CTAs per SM
+// of the projection, shading, scatter and sort kernels.
+struct LaunchCfg {
+  int variant[kModeCount] = {0, 0, 0};
+  int per_sm[kModeCount] = {0, 0, 0};
+  int grid_mult[kModeCount] = {8, 8, 8};
+};
+
 // launchers (return the CUDA error of the launch)
 cudaError_t launch_pack_scene(const float* means, const float* scales, const float* quats,
                               const float* opacities, const float* sh, int sh_k3, const uint16_t* feats,
@@ -128,18 +146,19 @@ cudaError_t launch_shade(const SceneDev& sc, const View* views, const Work& w, b
 cudaError_t launch_scan_tiles(const Work& w, cudaStream_t st);
 cudaError_t launch_sort_tiles(const Work& w, int grid, cudaStream_t st);
 cudaError_t launch_scatter(const View* views, const Work& w, int grid, cudaStream_t st);
-// feats: some view writes the feature map (else the feature-free kernel runs)
+// feats: some view writes the feature map (else the feature-free kernel runs);
+// persistent grid from cfg and the SM count
 cudaError_t launch_composite(const SceneDev& sc, const View* views, int n_views, const Work& w, bool feats,
-                             int grid, cudaStream_t st);
+                             const LaunchCfg& cfg, int sm_count, cudaStream_t st);
 // forward render plus the pose gradient (tangent mode); result: kPartialStride
 // doubles per view (loss, dL/drho, dL/dphi)
 cudaError_t launch_composite_tangent(const SceneDev& sc, const View* views, int n_views, const Work& w,
-                                     double* result, int grid, cudaStream_t st);
+                                     double* result, const LaunchCfg& cfg, int sm_count, cudaStream_t st);
 // the same pass over tiles [tile_begin, tile_end) with its own queue counter
 // (the per-chunk fp64 reduction completes across such launches)
 cudaError_t launch_composite_tangent_range(const SceneDev& sc, const View* views, int n_views, const Work& w,
-                                           double* result, int grid, cudaStream_t st, uint32_t tile_begin,
-                                           uint32_t tile_end, unsigned int* queue);
+                                           double* result, const LaunchCfg& cfg, int sm_count, cudaStream_t st,
+                                           uint32_t tile_begin, uint32_t tile_end, unsigned int* queue);
 
 // Algorithm 1 visibility check, after a forward render of one view that wrote
 // final_T and last_idx and a shading pass that wrote the pose Jacobian:
@@ -165,7 +184,5 @@ gs_status refine_on_device(gs_scene* s, int n_views, const gs_camera* cams, gs_p
                            const float* const* pixel_weight, const gs_refine_opts* opts, double* loss_history,
                            cudaStream_t st, bool* used);
 
-// occupancy-derived persistent grid sizes (per SM)
-int composite_blocks_per_sm(int feat_dim, bool tangent);
 
 }  // namespace gsr

@@ -213,7 +213,7 @@ extern "C" gs_status gs_render_noalloc(const gs_scene_desc* d, const gs_camera* 
   NA_CUDA(launch_scatter(dview, w, sm_count * 8, st));
   NA_CUDA(launch_sort_tiles(w, sm_count * 8, st));
   const bool feats = d->feat_dim && out && out->feats;
-  NA_CUDA(launch_composite(sc, dview, 1, w, feats, sm_count * composite_blocks_per_sm(feats ? d->feat_dim : 0, false), st));
+  NA_CUDA(launch_composite(sc, dview, 1, w, feats, LaunchCfg{}, sm_count, st));
   Counters c;
   NA_CUDA(cudaMemcpyAsync(&c, w.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
   NA_CUDA(cudaStreamSynchronize(st));

@@ -189,17 +189,18 @@ constexpr int kSmBufB = kSortCap * 8;
 constexpr int kSmHist = 2 * kSortCap * 8;
 constexpr int kSmStage = kSmBufB;
 constexpr int kSmFwd = kSmHist + kWarps * 256 * 4;
-constexpr int kSmFeat = kSmHist;  // 16 KB of BF16 features: hist + 8 KB more
-constexpr int kSmFwdFeat = (kSmFeat + kBatchF * 64) > kSmFwd ? (kSmFeat + kBatchF * 64) : kSmFwd;
+constexpr int kSmFeat = kSmHist;  // BF16 features of the staged batch, from the histogram on (64 B each)
 // Tangent mode reads the sorted list back from global memory, so after the
 // sort the staged pose Jacobians take the two sort buffers and the staged
 // batch takes the histogram.
 constexpr int kSmJac = 0;
 constexpr int kSmStageT = kSmHist;
 constexpr int kSmTan = kSmFwd;
-static_assert(kBatchT * kJacStride * 4 <= kSmHist, "staged Jacobians must fit in the sort buffers");
-static_assert(kSmStageT + kBatchT * 52 <= kSmTan, "tangent staging must fit in the histogram");
-static_assert(4 * kBatchF * 16 <= kSortCap * 8, "staging must fit in the second sort buffer");
+// dynamic shared memory of a compositor variant (staged batch of KB Gaussians)
+template <int FEAT, bool TAN, int KB>
+constexpr int comp_smem() {
+  return TAN ? kSmTan : FEAT ? ((kSmFeat + KB * 64) > kSmFwd ? (kSmFeat + KB * 64) : kSmFwd) : kSmFwd;
+}
 
 // Warp w covers the 8 x 4 pixel block at (8 (w & 1), 4 (w >> 1)) of the tile.
 __device__ __forceinline__ void warp_block(int tid, int& lx, int& ly, int& bx, int& by) {
@@ -344,11 +345,18 @@ __device__ void reduce_tile(float (&v)[7], const View& V, int vi, uint32_t lt, i
 // dL/dxi = sum over pixels of g . (dC, dD) with g the per-pixel L1
 // subgradient, reduced in fp32 per tile and in fp64 across tiles.
 // ---------------------------------------------------------------------------
-template <int FEAT, bool TAN>
-__global__ void __launch_bounds__(kTileThreads, TAN ? 4 : FEAT ? 3 : 5) k_composite(SceneDev sc, const View* __restrict__ views, int n_views,
-                                                            Work w, double* __restrict__ result) {
+// KB: Gaussians staged per batch; MINB: resident CTAs per SM the register
+// allocation must allow (the autotuner's compositor variants, all giving the
+// same bits: the blending order and every reduction order are fixed by the
+// tile lists, not by the batching or the grid)
+template <int FEAT, bool TAN, int KB, int MINB>
+__global__ void __launch_bounds__(kTileThreads, MINB) k_composite(SceneDev sc, const View* __restrict__ views,
+                                                                  int n_views, Work w, double* __restrict__ result) {
   static_assert(!(TAN && FEAT), "tangent mode renders without features");
-  constexpr int kB = TAN ? kBatchT : kBatchF;
+  static_assert(!TAN || KB * kJacStride * 4 <= kSmHist, "staged Jacobians must fit in the sort buffers");
+  static_assert(!TAN || kSmStageT + KB * 52 <= kSmTan, "tangent staging must fit in the histogram");
+  static_assert(TAN || 4 * KB * 16 <= kSortCap * 8, "staging must fit in the second sort buffer");
+  constexpr int kB = KB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint2* bufA = reinterpret_cast<uint2*>(smem_raw + kSmBufA);
   uint2* bufB = reinterpret_cast<uint2*>(smem_raw + kSmBufB);
@@ -357,8 +365,8 @@ __global__ void __launch_bounds__(kTileThreads, TAN ? 4 : FEAT ? 3 : 5) k_compos
   float4* sb = sa + kB;
   float4* scol = sb + kB;
   uint32_t* smask = reinterpret_cast<uint32_t*>(scol + kB);
-  uint4* sf = reinterpret_cast<uint4*>(smem_raw + kSmFeat);  // FEAT: kBatchF x 4 (aliases hist)
-  float4* sj = reinterpret_cast<float4*>(smem_raw + kSmJac);  // TAN: kBatchT x 12
+  uint4* sf = reinterpret_cast<uint4*>(smem_raw + kSmFeat);  // FEAT: KB x 4 (aliases hist)
+  float4* sj = reinterpret_cast<float4*>(smem_raw + kSmJac);  // TAN: KB x 12
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_tmp[kWarps];
   __shared__ float s_red[kWarps][8];
@@ -756,43 +764,66 @@ __global__ void __launch_bounds__(kTileThreads, 7) k_vis_backward(const View* __
   }
 }
 
-template <int FEAT, bool TAN>
-size_t composite_smem() {
-  return TAN ? (size_t)kSmTan : FEAT ? (size_t)kSmFwdFeat : (size_t)kSmFwd;
+// The compositor variants of each mode; index 0 is the default.
+using CompFn = void (*)(SceneDev, const View*, int, Work, double*);
+struct Variant {
+  CompFn fn;
+  int smem, batch, min_blocks;
+};
+template <int FEAT, bool TAN, int KB, int MINB>
+Variant variant() {
+  return {k_composite<FEAT, TAN, KB, MINB>, comp_smem<FEAT, TAN, KB>(), KB, MINB};
+}
+const Variant* variant_table(int mode) {
+  static const Variant fwd[kCompVariants] = {variant<0, false, 256, 5>(), variant<0, false, 128, 5>(),
+                                             variant<0, false, 256, 4>(), variant<0, false, 64, 5>()};
+  static const Variant feat[kCompVariants] = {variant<32, false, 256, 3>(), variant<32, false, 128, 3>(),
+                                              variant<32, false, 128, 4>(), variant<32, false, 64, 4>()};
+  static const Variant tan[kCompVariants] = {variant<0, true, 128, 4>(), variant<0, true, 64, 4>(),
+                                             variant<0, true, 128, 3>(), variant<0, true, 64, 3>()};
+  return mode == kModeTan ? tan : mode == kModeFwdFeat ? feat : fwd;
 }
 
-template <int FEAT, bool TAN>
-int composite_occ() {
-  static int occ = -1;
-  if (occ < 0) {
-    cudaFuncSetAttribute(k_composite<FEAT, TAN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)composite_smem<FEAT, TAN>());
+// resident CTAs per SM of a variant (its shared memory and registers), once per process
+int variant_occupancy(int mode, int v) {
+  static int occ[kModeCount][kCompVariants] = {};
+  if (occ[mode][v] == 0) {
+    const Variant& V = variant_table(mode)[v];
+    cudaFuncSetAttribute(V.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, V.smem);
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_composite<FEAT, TAN>, kTileThreads,
-                                                      composite_smem<FEAT, TAN>()) != cudaSuccess)
-      b = 1;
-    occ = b > 0 ? b : 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, V.fn, kTileThreads, V.smem) != cudaSuccess || b < 1) b = 1;
+    occ[mode][v] = b;
   }
-  return occ;
+  return occ[mode][v];
+}
+
+int clamp_variant(int v) { return v >= 0 && v < kCompVariants ? v : 0; }
+
+// persistent grid: per_sm CTAs per SM (0 or above the occupancy: the occupancy), at most one per tile
+int comp_grid(int mode, int v, int per_sm, int sm_count, uint32_t n_units) {
+  const int occ = variant_occupancy(mode, v);
+  const int p = per_sm > 0 && per_sm < occ ? per_sm : occ;
+  const uint32_t g = (uint32_t)(p * sm_count);
+  return (int)(g < n_units ? g : n_units);
 }
 
 }  // namespace
 
-int composite_blocks_per_sm(int feat_dim, bool tangent) {
-  return tangent ? composite_occ<0, true>() : feat_dim ? composite_occ<32, false>() : composite_occ<0, false>();
+CompVariantInfo composite_variant_info(int mode, int v) {
+  mode = mode >= 0 && mode < kModeCount ? mode : 0;
+  v = clamp_variant(v);
+  const Variant& V = variant_table(mode)[v];
+  return {V.batch, V.min_blocks, variant_occupancy(mode, v)};
 }
 
 cudaError_t launch_composite(const SceneDev& sc, const View* views, int n_views, const Work& w, bool feats,
-                             int grid, cudaStream_t st) {
+                             const LaunchCfg& cfg, int sm_count, cudaStream_t st) {
   if (w.n_tiles == 0) return cudaSuccess;
-  const int g = (uint32_t)grid < w.n_tiles ? grid : (int)w.n_tiles;
-  if (sc.feat_dim && feats) {
-    composite_occ<32, false>();
-    k_composite<32, false><<<g, kTileThreads, composite_smem<32, false>(), st>>>(sc, views, n_views, w, nullptr);
-  } else {
-    composite_occ<0, false>();
-    k_composite<0, false><<<g, kTileThreads, composite_smem<0, false>(), st>>>(sc, views, n_views, w, nullptr);
-  }
+  const int mode = (sc.feat_dim && feats) ? kModeFwdFeat : kModeFwd;
+  const int v = clamp_variant(cfg.variant[mode]);
+  const Variant& V = variant_table(mode)[v];
+  const int g = comp_grid(mode, v, cfg.per_sm[mode], sm_count, w.n_tiles);
+  V.fn<<<g, kTileThreads, V.smem, st>>>(sc, views, n_views, w, nullptr);
   return cudaGetLastError();
 }
 
@@ -813,26 +844,28 @@ cudaError_t launch_vis_backward(const View* views, int n_views, const Work& w, f
 }
 
 cudaError_t launch_composite_tangent(const SceneDev& sc, const View* views, int n_views, const Work& w,
-                                     double* result, int grid, cudaStream_t st) {
+                                     double* result, const LaunchCfg& cfg, int sm_count, cudaStream_t st) {
   if (w.n_tiles == 0) return cudaSuccess;
-  const int g = (uint32_t)grid < w.n_tiles ? grid : (int)w.n_tiles;
-  composite_occ<0, true>();
-  k_composite<0, true><<<g, kTileThreads, composite_smem<0, true>(), st>>>(sc, views, n_views, w, result);
+  const int v = clamp_variant(cfg.variant[kModeTan]);
+  const Variant& V = variant_table(kModeTan)[v];
+  const int g = comp_grid(kModeTan, v, cfg.per_sm[kModeTan], sm_count, w.n_tiles);
+  V.fn<<<g, kTileThreads, V.smem, st>>>(sc, views, n_views, w, result);
   return cudaGetLastError();
 }
 
 cudaError_t launch_composite_tangent_range(const SceneDev& sc, const View* views, int n_views, const Work& w,
-                                           double* result, int grid, cudaStream_t st, uint32_t tile_begin,
-                                           uint32_t tile_end, unsigned int* queue) {
+                                           double* result, const LaunchCfg& cfg, int sm_count, cudaStream_t st,
+                                           uint32_t tile_begin, uint32_t tile_end, unsigned int* queue) {
   if (tile_end > w.n_tiles) tile_end = w.n_tiles;
   if (tile_begin >= tile_end) return cudaSuccess;
   Work wb = w;
   wb.tile_begin = tile_begin;
   wb.tile_end = tile_end;
   wb.queue = queue;
-  const int g = (uint32_t)grid < tile_end - tile_begin ? grid : (int)(tile_end - tile_begin);
-  composite_occ<0, true>();
-  k_composite<0, true><<<g, kTileThreads, composite_smem<0, true>(), st>>>(sc, views, n_views, wb, result);
+  const int v = clamp_variant(cfg.variant[kModeTan]);
+  const Variant& V = variant_table(kModeTan)[v];
+  const int g = comp_grid(kModeTan, v, cfg.per_sm[kModeTan], sm_count, tile_end - tile_begin);
+  V.fn<<<g, kTileThreads, V.smem, st>>>(sc, views, n_views, wb, result);
   return cudaGetLastError();
 }
 

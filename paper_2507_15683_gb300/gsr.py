@@ -65,6 +65,23 @@ class gs_pmm_result(ctypes.Structure):
                 ("fine_prob", ctypes.c_void_p)]
 
 
+class gs_launch(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("grid_mult", ctypes.c_int),
+                ("batch", ctypes.c_int), ("min_blocks", ctypes.c_int), ("occupancy", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class gs_tune_result(ctypes.Structure):
+    _fields_ = [("best", gs_launch), ("ms_default", ctypes.c_double), ("ms_best", ctypes.c_double),
+                ("candidates", ctypes.c_int)]
+
+
+GS_MODE_FORWARD, GS_MODE_FEATURES, GS_MODE_POSE_GRAD = 0, 1, 2
+GS_COMPOSITE_VARIANTS = 4
+
+
 class gs_pnp_opts(ctypes.Structure):
     _fields_ = [("tau_px", ctypes.c_float), ("min_alpha", ctypes.c_float), ("refine_iters", ctypes.c_int)]
 
@@ -135,6 +152,11 @@ def _load():
         "gs_scene_shape": [vp, vp, vp, vp],
         "gs_pmm_shape": [vp, vp, vp, vp],
         "gs_pmm_set_wait_limit": [vp, st],
+        "gs_scene_set_launch": [vp, st, st, P(gs_camera), P(gs_launch)],
+        "gs_scene_get_launch": [vp, st, st, P(gs_camera), P(gs_launch)],
+        "gs_autotune": [vp, st, st, P(gs_camera), P(gs_pose), st, P(gs_tune_result), vp],
+        "gs_tune_save": [vp, ctypes.c_char_p],
+        "gs_tune_load": [vp, ctypes.c_char_p, P(ctypes.c_int)],
         "gs_pnp_solve": [vp, P(gs_camera), P(gs_pose), vp, vp, vp, i64, vp, st, P(gs_pnp_opts), P(gs_pnp_result), vp],
     }
     for name, args in sigs.items():
@@ -606,6 +628,42 @@ def gs_pmm_create(channels: int, height: int, width: int):
 
 def gs_pmm_destroy(h) -> None:
     lib.gs_pmm_destroy(h)
+
+
+def _cams(cams):
+    arr = (gs_camera * len(cams))(*[c if isinstance(c, gs_camera) else camera(c) for c in cams])
+    return len(cams), arr
+
+
+def gs_scene_set_launch(h, mode: int, cams, variant: int, ctas_per_sm: int = 0, grid_mult: int = 8) -> None:
+    n, arr = _cams(cams)
+    cfg = gs_launch(int(variant), int(ctas_per_sm), int(grid_mult), 0, 0, 0)
+    _check(lib.gs_scene_set_launch(h, int(mode), n, arr, ctypes.byref(cfg)))
+
+
+def gs_scene_get_launch(h, mode: int, cams) -> dict:
+    n, arr = _cams(cams)
+    cfg = gs_launch()
+    _check(lib.gs_scene_get_launch(h, int(mode), n, arr, ctypes.byref(cfg)))
+    return cfg.as_dict()
+
+
+def gs_autotune(h, mode: int, cams, poses, reps: int = 5, stream=None) -> dict:
+    n, arr = _cams(cams)
+    pp = (gs_pose * n)(*[p if isinstance(p, gs_pose) else pose(p) for p in poses])
+    r = gs_tune_result()
+    _check(lib.gs_autotune(h, int(mode), n, arr, pp, int(reps), ctypes.byref(r), _stream() if stream is None else stream))
+    return {"best": r.best.as_dict(), "ms_default": r.ms_default, "ms_best": r.ms_best, "candidates": r.candidates}
+
+
+def gs_tune_save(h, path: str) -> None:
+    _check(lib.gs_tune_save(h, path.encode()))
+
+
+def gs_tune_load(h, path: str) -> int:
+    n = ctypes.c_int()
+    _check(lib.gs_tune_load(h, path.encode(), ctypes.byref(n)))
+    return n.value
 
 
 GS_PMM_DEFAULT_WAIT_POLLS = 1 << 22

@@ -249,17 +249,20 @@ __device__ __forceinline__ bool ellipse_hits(float4 a, float C, float thr, float
 }
 
 // Bit w set when the staged Gaussian can reach the floor in warp w's 8 x 4
-// block (ellipse_hits); a slightly widened bounding box of the ellipse rejects
-// most blocks first. Computed once per staged Gaussian by its staging thread.
-__device__ __forceinline__ uint32_t warp_hit_mask(float4 a, float C, float thr) {
+// block (ellipse_hits), for the warps w0 <= w < w1; a slightly widened bounding
+// box of the ellipse rejects most blocks first. Computed once per staged
+// Gaussian and warp block by a staging thread.
+template <int W0 = 0, int W1 = kWarps>
+__device__ __forceinline__ uint32_t warp_hit_mask(float4 a, float C, float thr, int w0 = W0, int w1 = W1) {
   if (!(thr > 0.0f)) return 0u;
   const float A = a.z, B = a.w;
   const float detq = A * C - B * B;
-  if (!(A > 0.0f) || !(C > 0.0f) || !(detq > 0.0f)) return 0xffu;
+  if (!(A > 0.0f) || !(C > 0.0f) || !(detq > 0.0f)) return (1u << w1) - (1u << w0);
   const float ex = sqrtf(thr * C / detq) * 1.0001f + 1e-3f, ey = sqrtf(thr * A / detq) * 1.0001f + 1e-3f;
   uint32_t mask = 0u;
 #pragma unroll
-  for (int wv = 0; wv < kWarps; ++wv) {
+  for (int wv = W0; wv < W1; ++wv) {
+    if (wv < w0 || wv >= w1) continue;
     const float x0 = (float)((wv & 1) * 8) + 0.5f, x1 = x0 + 7.0f;
     const float y0 = (float)((wv >> 1) * 4) + 0.5f, y1 = y0 + 3.0f;
     if (a.x + ex < x0 || a.x - ex > x1 || a.y + ey < y0 || a.y - ey > y1) continue;
@@ -268,6 +271,13 @@ __device__ __forceinline__ uint32_t warp_hit_mask(float4 a, float C, float thr) 
   return mask;
 }
 
+
+// 16-byte asynchronous copy global -> shared (both 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+               "l"(gsrc)
+               : "memory");
+}
 
 // (loss, dL/dxi) of one tile: a fixed fp32 tree over each warp's lanes, then
 // the warps in order (GB300 runs fp64 at 1/64 of the fp32 rate, so fp64 starts
@@ -354,7 +364,10 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_composite(SceneDev sc, c
                                                                   int n_views, Work w, double* __restrict__ result) {
   static_assert(!(TAN && FEAT), "tangent mode renders without features");
   static_assert(!TAN || KB * kJacStride * 4 <= kSmHist, "staged Jacobians must fit in the sort buffers");
-  static_assert(!TAN || kSmStageT + KB * 52 <= kSmTan, "tangent staging must fit in the histogram");
+  static_assert(!TAN || kSmStageT + KB * 48 + kTileThreads * 4 <= kSmTan,
+                "tangent staging (records and the per-part hit masks) must fit in the histogram");
+  static_assert(!TAN || (kTileThreads % KB == 0 && kWarps % (kTileThreads / KB) == 0),
+                "tangent staging splits the warp blocks evenly over the threads of an entry");
   static_assert(TAN || 4 * KB * 16 <= kSortCap * 8, "staging must fit in the second sort buffer");
   constexpr int kB = KB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -448,7 +461,42 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_composite(SceneDev sc, c
     for (int bs = 0; bs < n; bs += kB) {
       if (__syncthreads_count(done) == kTileThreads) break;
       const int bn = min(kB, n - bs);
-      if (tid < bn) {
+      if (TAN) {
+        // Pose Jacobians (bn x 12 float4) by cp.async, without registers:
+        // consecutive threads copy consecutive 16-byte pieces of a record; the
+        // list entries of all of a thread's pieces are loaded first.
+        constexpr int kJ4 = kJacStride / 4;
+        constexpr int kJPer = (kB * kJ4 + kTileThreads - 1) / kTileThreads;
+        uint32_t jr[kJPer];
+#pragma unroll
+        for (int i = 0; i < kJPer; ++i) {
+          const int q = tid + kTileThreads * i;
+          jr[i] = q < bn * kJ4 ? list[bs + q / kJ4].y : 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < kJPer; ++i) {
+          const int q = tid + kTileThreads * i;
+          if (q < bn * kJ4) cp_async16(sj + q, rec_j4 + (size_t)jr[i] * kJ4 + (q % kJ4));
+        }
+        // records and hit masks: kParts threads per entry, each testing the
+        // warp blocks of its part, so that every warp stages
+        constexpr int kParts = kTileThreads / kB;
+        constexpr int kPW = kWarps / kParts;  // warp blocks per part
+        const int e = tid % kB, part = tid / kB;
+        if (e < bn) {
+          const uint32_t r = list[bs + e].y;
+          const float4 cc = w.rec_c[r];
+          const float4 a = tile_local(w.rec_a[r], cc.w, X0, Y0);
+          const float4 bb = w.rec_b[r];
+          if (part == 0) {
+            sa[e] = a;
+            sb[e] = bb;
+            scol[e] = cc;
+          }
+          smask[part * kB + e] = warp_hit_mask(a, bb.x, floor_threshold(bb.y), part * kPW, part * kPW + kPW);
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+      } else if (tid < bn) {
         const uint32_t r = list[bs + tid].y;
         const float4 cc = w.rec_c[r];
         const float4 a = tile_local(w.rec_a[r], cc.w, X0, Y0);
@@ -461,12 +509,6 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_composite(SceneDev sc, c
           const uint4* fp = sc.feat + (size_t)__float_as_int(bb.w) * 4;
 #pragma unroll
           for (int q = 0; q < 4; ++q) sf[tid * 4 + q] = __ldg(fp + q);
-        }
-      }
-      if (TAN) {
-        for (int q = tid; q < bn * (kJacStride / 4); q += kTileThreads) {
-          const int jj = q / (kJacStride / 4), k = q % (kJacStride / 4);
-          sj[q] = rec_j4[(size_t)list[bs + jj].y * (kJacStride / 4) + k];
         }
       }
       __syncthreads();
@@ -545,10 +587,12 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_composite(SceneDev sc, c
         done = done || stop;
       };
       const uint32_t wbit = 1u << wid;
+      // tangent mode: this warp's bits sit in the mask array of its part
+      const uint32_t* wmask = TAN ? smask + (wid / (kWarps / (kTileThreads / kB))) * kB : smask;
       bool wdone = __all_sync(0xffffffffu, done);
       for (int c0 = 0; c0 < bn && !wdone; c0 += 32) {
         const int jj = c0 + lane;
-        uint32_t m = __ballot_sync(0xffffffffu, jj < bn && (smask[jj] & wbit));
+        uint32_t m = __ballot_sync(0xffffffffu, jj < bn && (wmask[jj] & wbit));
         while (m) {  // two hits per step: their exponentials overlap, blending stays in order
           const int j1 = c0 + __ffs(m) - 1;
           m &= m - 1;

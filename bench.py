@@ -78,6 +78,11 @@ def parse():
     p.add_argument("--no-dense", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-errors", action="store_true")
+    p.add_argument("--only", default="", choices=["", "batched"],
+                   help="run one section alone (for profiling) and print its result")
+    p.add_argument("--batched-views", type=int, default=0, help="the batched section on its first N views only")
+    p.add_argument("--pin", default="", help="launch configurations to use instead of the autotuner's for the "
+                   "headline view, e.g. 'pose_grad=2,0,8;forward=2,0,8' (variant, CTAs per SM, grid multiple)")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     return p.parse_args()
 
@@ -285,6 +290,13 @@ def main():
         run_reference(args)
         return
     import torch
+    if args.only == "batched":  # one section alone, for profiling
+        torch.cuda.set_device(0)
+        from paper_2507_15683_gb300 import gsr, synth
+        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+        print(json.dumps(bench_batched(gsr, synth, torch, flush, max(1, args.steps), args.warmup,
+                                       args.batched_views or None)), flush=True)
+        return
     rank, world, local = dist_env()
     if world > 1:
         import torch.distributed as dist
@@ -298,6 +310,12 @@ def main():
     H, W = cam["height"], cam["width"]
     P = H * W
     S = gsr.Scene(scene)
+    pins = {}
+    for item in filter(None, args.pin.split(";")):
+        name, vals = item.split("=")
+        mode = {"pose_grad": gsr.GS_MODE_POSE_GRAD, "forward": gsr.GS_MODE_FORWARD}[name.strip()]
+        pins[mode] = [int(x) for x in vals.split(",")]
+        gsr.gs_scene_set_launch(S.handle, mode, [cam], *pins[mode])
     tgt = S.render(cam, T_ref)
     trgb, tdep = tgt["rgb"].clone(), tgt["depth"].clone()
     result = torch.zeros(8, dtype=torch.float64, device="cuda")
@@ -344,7 +362,13 @@ def main():
     clocks.start()
     # the default launch configuration, then the autotuner's for this call shape
     ms_grad_default = max_over_ranks(timed(grad_step, args.steps), world)
-    tune_grad = gsr.gs_autotune(S.handle, gsr.GS_MODE_POSE_GRAD, [cam], [T_q], reps=10)
+
+    def tune(mode):
+        if mode in pins:  # pinned on the command line
+            return {"best": gsr.gs_scene_get_launch(S.handle, mode, [cam]), "pinned": True}
+        return gsr.gs_autotune(S.handle, mode, [cam], [T_q], reps=10)
+
+    tune_grad = tune(gsr.GS_MODE_POSE_GRAD)
     for _ in range(args.warmup):
         grad_step()
     ms_grad = timed(grad_step, args.steps)
@@ -354,7 +378,7 @@ def main():
     for _ in range(args.warmup):
         fwd_step()
     ms_fwd_default = max_over_ranks(timed(fwd_step, args.steps), world)
-    tune_fwd = gsr.gs_autotune(S.handle, gsr.GS_MODE_FORWARD, [cam], [T_q], reps=10)
+    tune_fwd = tune(gsr.GS_MODE_FORWARD)
     for _ in range(args.warmup):
         fwd_step()
     ms_fwd = max_over_ranks(timed(fwd_step, args.steps), world)
@@ -968,7 +992,7 @@ def kernel_times(gsr, S, fn, reps):
     return {k: {"ms": v, "share": v / tot} for k, v in per.items()}
 
 
-def bench_batched(gsr, synth, torch, flush, steps, warmup):
+def bench_batched(gsr, synth, torch, flush, steps, warmup, n_views=None):
     """84 candidate poses at three pyramid levels (64 @ 480x270, 16 @ 960x540,
     4 @ 1920x1080), 2M Gaussians with 32 BF16 features: one graph launch
     against 84 single-view launches, forward (with the feature map) and pose
@@ -977,6 +1001,8 @@ def bench_batched(gsr, synth, torch, flush, steps, warmup):
     single view). Per-kernel times and the dominant kernel's roofline."""
     scene = synth.partitioned_scene(4, 2, 2, 500_000, sh_degree=3, feat_dim=32)
     cams, poses = synth.batched_views()
+    if n_views:
+        cams, poses = cams[:n_views], poses[:n_views]
     S = gsr.Scene(scene)
     outs = [S.alloc_outputs(c, feat_dim=32, last_idx=False) for c in cams]
     structs = [S.outputs_struct(o) for o in outs]

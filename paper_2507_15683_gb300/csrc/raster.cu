@@ -12,6 +12,7 @@
 // The kernel is persistent: CTAs pull tiles from a global queue spanning
 // every view of the call, so views of different resolution share one launch
 // and load-balance.
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -189,17 +190,65 @@ constexpr int kSmBufB = kSortCap * 8;
 constexpr int kSmHist = 2 * kSortCap * 8;
 constexpr int kSmStage = kSmBufB;
 constexpr int kSmFwd = kSmHist + kWarps * 256 * 4;
-constexpr int kSmFeat = kSmHist;  // BF16 features of the staged batch, from the histogram on (64 B each)
 // Tangent mode reads the sorted list back from global memory, so after the
 // sort the staged pose Jacobians take the two sort buffers and the staged
 // batch takes the histogram.
 constexpr int kSmJac = 0;
 constexpr int kSmStageT = kSmHist;
 constexpr int kSmTan = kSmFwd;
+// Feature blending on the tensor cores (FEAT): each warp collects the weights
+// of its hits in slots of kSlots, transposed (slot-major, one row of 32
+// pixels per slot) and split into three bf16 terms w = hi + mid + lo (exact to
+// about 2^-24, the binary32 weight's own precision), then adds
+// W (32 pixels x kSlots) . f (kSlots x 32 channels) to its accumulator
+// fragments with mma.sync (bf16 x bf16 products are exact in fp32, with fp32
+// accumulation). Rows of kWtRow bf16 (80 bytes): the eight 16-byte rows an
+// ldmatrix reads fall in distinct banks.
+// The features of the slots' Gaussians are copied into a per-warp buffer of
+// kSlots rows (same 80-byte stride) when a slot is filled, so that slots span
+// staging batches: a slot group is every kSlots hits of the warp in depth
+// order, whatever the batch size, and the sums come out the same bits under
+// every launch configuration.
+constexpr int kSlots = 16;
+constexpr int kWtRow = 40;
+constexpr int kWtTerms = 3;                   // hi, mid, lo
+constexpr int kWtWarp = kWtTerms * kSlots * kWtRow;  // bf16 per warp: hi rows, mid rows, lo rows
+constexpr int kSmWtBytes = kWarps * kWtWarp * 2;
+constexpr int kSmFbBytes = kWarps * kSlots * kWtRow * 2;  // per-warp slot features (bf16 rows)
+// Feature-mode layout (blend phase; the sorted list is back in global memory,
+// so it may reuse the sort buffers): staged records, staged features, weight
+// slots, slot features.
+template <int KB>
+__host__ __device__ constexpr int feat_off_sf() { return ((KB * 52 + 15) / 16) * 16; }
+template <int KB>
+__host__ __device__ constexpr int feat_off_wt() { return feat_off_sf<KB>() + KB * 64; }
+template <int KB>
+__host__ __device__ constexpr int feat_off_fb() { return feat_off_wt<KB>() + kSmWtBytes; }
+
 // dynamic shared memory of a compositor variant (staged batch of KB Gaussians)
 template <int FEAT, bool TAN, int KB>
 constexpr int comp_smem() {
-  return TAN ? kSmTan : FEAT ? ((kSmFeat + KB * 64) > kSmFwd ? (kSmFeat + KB * 64) : kSmFwd) : kSmFwd;
+  return TAN ? kSmTan
+             : FEAT ? ((feat_off_fb<KB>() + kSmFbBytes) > kSmFwd ? (feat_off_fb<KB>() + kSmFbBytes) : kSmFwd)
+                    : kSmFwd;
+}
+
+// four 8 x 8 b16 matrices from shared memory, transposed (lane l gives the
+// address of row l % 8 of matrix l / 8)
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+
+// d += a . b, m16 n8 k16, bf16 operands, fp32 accumulation
+__device__ __forceinline__ void mma_16816(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                          uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
 // Warp w covers the 8 x 4 pixel block at (8 (w & 1), 4 (w >> 1)) of the tile.
@@ -374,11 +423,18 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_composite(SceneDev sc, c
   uint2* bufA = reinterpret_cast<uint2*>(smem_raw + kSmBufA);
   uint2* bufB = reinterpret_cast<uint2*>(smem_raw + kSmBufB);
   uint32_t* hist = reinterpret_cast<uint32_t*>(smem_raw + kSmHist);
-  float4* sa = reinterpret_cast<float4*>(smem_raw + (TAN ? kSmStageT : kSmStage));
+  float4* sa = reinterpret_cast<float4*>(smem_raw + (TAN ? kSmStageT : FEAT ? 0 : kSmStage));
   float4* sb = sa + kB;
   float4* scol = sb + kB;
   uint32_t* smask = reinterpret_cast<uint32_t*>(scol + kB);
-  uint4* sf = reinterpret_cast<uint4*>(smem_raw + kSmFeat);  // FEAT: KB x 4 (aliases hist)
+  uint4* sf = reinterpret_cast<uint4*>(smem_raw + feat_off_sf<KB>());  // FEAT: KB x 4
+  // FEAT: this warp's transposed weight slots (hi rows, then lo rows) and slot features
+  unsigned short* wt = reinterpret_cast<unsigned short*>(smem_raw + feat_off_wt<KB>()) + (threadIdx.x >> 5) * kWtWarp;
+  unsigned short* fb = reinterpret_cast<unsigned short*>(smem_raw + feat_off_fb<KB>()) +
+                       (threadIdx.x >> 5) * (kSlots * kWtRow);
+  if (FEAT) {  // empty slots multiply stale rows by zero weights: keep the rows finite
+    for (int i = threadIdx.x & 31; i < kSlots * kWtRow; i += 32) fb[i] = 0;
+  }
   float4* sj = reinterpret_cast<float4*>(smem_raw + kSmJac);  // TAN: KB x 12
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_tmp[kWarps];
@@ -430,8 +486,8 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_composite(SceneDev sc, c
         __syncthreads();
       }
       for (int i = tid; i < n; i += kTileThreads) w.pairs[start + i] = bufA[i];
-      if (TAN) __syncthreads();  // the list is read back from global memory
-      list = TAN ? w.pairs + start : bufA;
+      if (TAN || FEAT) __syncthreads();  // the list is read back from global memory
+      list = (TAN || FEAT) ? w.pairs + start : bufA;
     } else {
       uint2* sorted = sort_tile(w.pairs + start, w.pairs_tmp + start, n, hist, s_tmp, w.rec_b);
       if (sorted != w.pairs + start) {
@@ -446,9 +502,43 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_composite(SceneDev sc, c
     const bool inside = px < V.width && py < V.height;
     const float X0 = (float)(tx * kTile), Y0 = (float)(ty * kTile);
     float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
-    float F[FEAT > 0 ? FEAT : 1];
+    // FEAT: accumulator fragments of the warp's 32 pixels x 32 channels
+    // (m-tile of 16 pixels, n-tile of 8 channels, the mma.sync C layout)
+    float F[FEAT ? 2 : 1][FEAT ? 4 : 1][4];
 #pragma unroll
-    for (int c = 0; c < (FEAT > 0 ? FEAT : 1); ++c) F[c] = 0.f;
+    for (int a = 0; a < (FEAT ? 2 : 1); ++a)
+#pragma unroll
+      for (int b = 0; b < (FEAT ? 4 : 1); ++b) F[a][b][0] = F[a][b][1] = F[a][b][2] = F[a][b][3] = 0.f;
+    int nslot = 0;  // FEAT: slots filled (warp-uniform)
+    // FEAT: add the filled slots to the warp's accumulators (empty slots get
+    // zero weights)
+    auto flush_feats = [&]() {
+      for (int sl = nslot; sl < kSlots; ++sl)
+#pragma unroll
+        for (int t = 0; t < kWtTerms; ++t) wt[(t * kSlots + sl) * kWtRow + lane] = 0;
+      __syncwarp();
+      // B: the slots' features, k = slot (lane % 16), 8 channels from (lane / 16) * 8
+      const uint32_t bb = (uint32_t)__cvta_generic_to_shared(fb + (lane & (kSlots - 1)) * kWtRow) +
+                          (uint32_t)(lane >> 4) * 16u;
+      uint32_t b[8];
+      ldsm_x4_trans(bb, b[0], b[1], b[2], b[3]);       // channels 0..15
+      ldsm_x4_trans(bb + 32u, b[4], b[5], b[6], b[7]);  // channels 16..31
+      // A: weights, matrix lane / 8 = (pixels +8 if odd, slots +8 if >= 2)
+      const int kk = (lane & 7) + ((lane >> 4) << 3), pp = ((lane >> 3) & 1) << 3;
+      const uint32_t wa = (uint32_t)__cvta_generic_to_shared(wt) + (uint32_t)(kk * kWtRow + pp) * 2u;
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+#pragma unroll
+        for (int t = kWtTerms - 1; t >= 0; --t) {  // smallest term first
+          uint32_t a0, a1, a2, a3;
+          ldsm_x4_trans(wa + (uint32_t)(t * kSlots * kWtRow * 2 + mt * 32), a0, a1, a2, a3);
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) mma_16816(F[mt][nt], a0, a1, a2, a3, b[2 * nt], b[2 * nt + 1]);
+        }
+      }
+      __syncwarp();
+      nslot = 0;
+    };
     // tangents, pairs over the pose directions (0,1), (2,3), (4,5)
     float2 dC0[3], dC1[3], dC2[3], dD[3], dT[3];
 #pragma unroll
@@ -568,17 +658,16 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_composite(SceneDev sc, c
         C1 = fmaf(wgt, c.y, C1);
         C2 = fmaf(wgt, c.z, C2);
         D = fmaf(wgt, zj, D);
-        if (FEAT) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const uint4 fv = sf[j * 4 + q];
-            const uint32_t u4[4] = {fv.x, fv.y, fv.z, fv.w};
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-              F[8 * q + 2 * h] = fmaf(wgt, __uint_as_float(u4[h] << 16), F[8 * q + 2 * h]);
-              F[8 * q + 2 * h + 1] = fmaf(wgt, __uint_as_float(u4[h] & 0xffff0000u), F[8 * q + 2 * h + 1]);
-            }
-          }
+        if (FEAT && __any_sync(0xffffffffu, wgt != 0.0f)) {  // a slot for a hit some pixel blends
+          const __nv_bfloat16 hi = __float2bfloat16_rn(wgt);
+          const float r1 = __fsub_rn(wgt, __bfloat162float(hi));  // exact differences
+          const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+          const __nv_bfloat16 lo = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(mid)));
+          wt[nslot * kWtRow + lane] = __bfloat16_as_ushort(hi);
+          wt[(kSlots + nslot) * kWtRow + lane] = __bfloat16_as_ushort(mid);
+          wt[(2 * kSlots + nslot) * kWtRow + lane] = __bfloat16_as_ushort(lo);
+          if (lane < 4) reinterpret_cast<uint4*>(fb + nslot * kWtRow)[lane] = sf[j * 4 + lane];
+          if (++nslot == kSlots) flush_feats();
         }
         if (TAN) n_blend += acc ? 1u : 0u;
         T = acc ? Tn : T;
@@ -619,6 +708,7 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_composite(SceneDev sc, c
         wdone = __all_sync(0xffffffffu, done);
       }
     }
+    if (FEAT && nslot) flush_feats();  // the tile's last, partial slot group
     const size_t HW = (size_t)V.width * V.height;
     const size_t p = (size_t)py * V.width + px;
     // the entries a pixel examines: its list up to the stop, or the whole list
@@ -633,10 +723,23 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_composite(SceneDev sc, c
       if (V.alpha) V.alpha[p] = 1.0f - T;
       if (V.final_T) V.final_T[p] = T;
       if (V.last_idx) V.last_idx[p] = last;
-      if (FEAT && V.feats) {
+    }
+    if (FEAT && V.feats) {  // fragment element (mt, nt, e): pixel 16 mt + lane / 4 (+ 8), channel 8 nt + 2 (lane % 4) (+ 1)
 #pragma unroll
-        for (int c = 0; c < (FEAT > 0 ? FEAT : 1); ++c) V.feats[(size_t)c * HW + p] = F[c];
-      }
+      for (int mt = 0; mt < (FEAT ? 2 : 1); ++mt)
+#pragma unroll
+        for (int e2 = 0; e2 < 2; ++e2) {
+          const int q = mt * 16 + (lane >> 2) + e2 * 8;  // the pixel's lane in the warp block
+          const int qx = tx * kTile + bxw + (q & 7), qy = ty * kTile + byw + (q >> 3);
+          if (qx >= V.width || qy >= V.height) continue;
+          const size_t qp = (size_t)qy * V.width + qx;
+#pragma unroll
+          for (int nt = 0; nt < (FEAT ? 4 : 1); ++nt) {
+            const int ch = nt * 8 + (lane & 3) * 2;
+            V.feats[(size_t)ch * HW + qp] = F[mt][nt][2 * e2];
+            V.feats[(size_t)(ch + 1) * HW + qp] = F[mt][nt][2 * e2 + 1];
+          }
+        }
     }
     if (TAN) {
       // per-pixel L1 subgradient g (sign(0) = 0) and loss

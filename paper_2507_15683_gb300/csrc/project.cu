@@ -222,14 +222,17 @@ __device__ __forceinline__ void eval_sh_deg(int deg, const float4* shp, float x,
 // written here: rec_m = (rect, view, depth bits), rec_a = (binary32
 // covariance a, b, c, -), rec_b.w = Gaussian index.
 //
-// Two phases per block, so that the expensive binary32 layer runs on full
-// warps: a cheap conservative test (camera transform, near plane, reach of
-// the footprint) of 256 Gaussians against every view of the call appends the
-// surviving (Gaussian, view) pairs to a shared-memory queue; when the queue
-// could overflow, and at the end, the whole block drains it through the exact
-// discrete layer.
+// Every warp works on its own: it walks chunks of 32 Gaussians (means loaded
+// one chunk ahead), runs a cheap conservative test (camera transform, near
+// plane, reach of the footprint) of each against every view of the call, and
+// appends the surviving (Gaussian, view) pairs to its own queue in shared
+// memory; whenever 32 are queued (and at the end) it drains them through the
+// exact discrete layer with all of its lanes busy. No barrier joins the warps
+// of a block. Block b appends its
+// records to segment b % kRecRegions, and its warps take the Gaussians
+// [256 b, 256 b + 256) first (then every gridDim.x * 256).
 // ---------------------------------------------------------------------------
-constexpr int kProjQ = 2048;  // (Gaussian, view) queue entries per block
+constexpr int kWarpQ = 64;  // (Gaussian, view) queue entries per warp: a drain of 32 leaves at most 31
 
 // camera-space position in the binary32 operation order of the oracle
 __device__ __forceinline__ void cam_xyz(const View& V, float4 p4, float& px, float& py, float& pz) {
@@ -240,14 +243,21 @@ __device__ __forceinline__ void cam_xyz(const View& V, float4 p4, float& px, flo
 
 // Conservative reach: radius <= 3 sqrt(s_max^2 |J|_F^2 + 0.3 + sqrt(0.1)) + 1,
 // with margins for rounding; a Gaussian that fails it has an empty rectangle
-// under the exact rule, so skipping it changes nothing.
+// under the exact rule, so skipping it changes nothing. The test runs for
+// every (Gaussian, view): the camera transform and the near-plane test are
+// the exact layer's, bit for bit, while the division and the square root are
+// the fast approximate ones. Their relative errors (a few 1e-7) move u and v
+// by far less than the test's margins (1 px on the image bounds, 1 % and
+// 3 px on the reach).
 __device__ __forceinline__ bool may_reach(const View& V, float4 p4) {
   float px, py, pz;
   cam_xyz(V, p4, px, py, pz);
   if (!(pz >= 0.2f)) return false;
-  const float u = add(mul(V.fx, dvd(px, pz)), V.cx);
-  const float v = add(mul(V.fy, dvd(py, pz)), V.cy);
-  const float reach = 3.0f * sqrtf((p4.w * p4.w * V.jb2 / (pz * pz) + 0.62f) * 1.01f) + 3.0f;
+  const float iz = __fdividef(1.0f, pz);
+  const float u = fmaf(V.fx * px, iz, V.cx);
+  const float v = fmaf(V.fy * py, iz, V.cy);
+  const float r2 = (p4.w * p4.w * V.jb2 * (iz * iz) + 0.62f) * 1.01f;
+  const float reach = 3.0f * (r2 * rsqrtf(r2)) + 3.0f;
   const float wx = (float)(kTile * V.tiles_x), wy = (float)(kTile * V.tiles_y);
   return u + reach >= -1.0f && u - reach <= wx + 1.0f && v + reach >= -1.0f && v - reach <= wy + 1.0f;
 }
@@ -306,58 +316,55 @@ __device__ __forceinline__ bool discrete_layer(const View& V, float4 p4, float4 
 }
 
 __global__ void __launch_bounds__(256) k_project(SceneDev sc, const View* __restrict__ views, int n_views, Work w) {
-  __shared__ int2 s_q[kProjQ];  // (Gaussian index, view)
-  __shared__ unsigned s_n;
-  const int tid = threadIdx.x, lane = tid & 31;
+  __shared__ int2 s_q[kTileThreads / 32][kWarpQ];  // (Gaussian index, view), per warp
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned lt_mask = (1u << lane) - 1u;
   const unsigned region = blockIdx.x % kRecRegions;
   const int4 hdr = w.ranges[0];  // (ranges, total length): only partitions in view are walked
-  if (tid == 0) s_n = 0u;
-  __syncthreads();
-  // exact layer over the cnt queued pairs by full warps; block-uniform
+  int2* q = s_q[wid];
+  unsigned qn = 0;  // queued pairs (warp-uniform)
+  // the exact layer over queue entries [0, cnt), cnt <= 32, one per lane
   auto drain = [&](unsigned cnt) {
-    for (unsigned q0 = 0; q0 < cnt; q0 += 256) {
-      const unsigned q = q0 + (unsigned)tid;
-      bool vis = false;
-      int i = 0, vi = 0, x0 = 0, x1 = 0, y0 = 0, y1 = 0;
-      float pz = 0.f, ca = 0.f, cb = 0.f, cc = 0.f;
-      if (q < cnt) {
-        const int2 e = s_q[q];
-        i = e.x;
-        vi = e.y;
-        const float4 p4 = __ldg(sc.pos + i);
-        const float4 c0 = __ldg(sc.cov + 2 * i), c1 = __ldg(sc.cov + 2 * i + 1);
-        vis = discrete_layer(views[vi], p4, c0, c1, pz, ca, cb, cc, x0, x1, y0, y1);
-      }
-      const unsigned vmask = __ballot_sync(0xffffffffu, vis);
-      if (vmask == 0u) continue;
-      // warp-aggregated append into this block's record segment
-      unsigned slot0 = 0;
-      const int leader = __ffs(vmask) - 1;
-      if (lane == leader) slot0 = atomicAdd(&w.ctr->rec_region[region], (unsigned)__popc(vmask));
-      slot0 = __shfl_sync(0xffffffffu, slot0, leader);
-      if (!vis) continue;
-      const unsigned local = slot0 + __popc(vmask & lt_mask);
-      if (local >= w.rec_seg) {
-        atomicOr(&w.ctr->overflow, 1u);
-        continue;
-      }
-      const unsigned slot = region * w.rec_seg + local;
-      w.rec_a[slot] = make_float4(ca, cb, cc, 0.0f);
-      w.rec_b[slot] = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(i));
-      w.rec_m[slot] = make_uint4((unsigned)x0 | ((unsigned)x1 << 16), (unsigned)y0 | ((unsigned)y1 << 16),
-                                 (unsigned)vi, __float_as_uint(pz));
-      const View& V = views[vi];
-      for (int ty = y0; ty <= y1; ++ty)
-        for (int tx = x0; tx <= x1; ++tx) atomicAdd(&w.tile_count[V.tile_base + ty * V.tiles_x + tx], 1u);
+    bool vis = false;
+    int i = 0, vi = 0, x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+    float pz = 0.f, ca = 0.f, cb = 0.f, cc = 0.f;
+    if ((unsigned)lane < cnt) {
+      const int2 e = q[lane];
+      i = e.x;
+      vi = e.y;
+      const float4 p4 = __ldg(sc.pos + i);
+      const float4 c0 = __ldg(sc.cov + 2 * i), c1 = __ldg(sc.cov + 2 * i + 1);
+      vis = discrete_layer(views[vi], p4, c0, c1, pz, ca, cb, cc, x0, x1, y0, y1);
     }
-    __syncthreads();
-    if (tid == 0) s_n = 0u;
-    __syncthreads();
+    const unsigned vmask = __ballot_sync(0xffffffffu, vis);
+    if (vmask == 0u) return;
+    // warp-aggregated append into this block's record segment
+    unsigned slot0 = 0;
+    const int leader = __ffs(vmask) - 1;
+    if (lane == leader) slot0 = atomicAdd(&w.ctr->rec_region[region], (unsigned)__popc(vmask));
+    slot0 = __shfl_sync(0xffffffffu, slot0, leader);
+    if (!vis) return;
+    const unsigned local = slot0 + __popc(vmask & lt_mask);
+    if (local >= w.rec_seg) {
+      atomicOr(&w.ctr->overflow, 1u);
+      return;
+    }
+    const unsigned slot = region * w.rec_seg + local;
+    w.rec_a[slot] = make_float4(ca, cb, cc, 0.0f);
+    w.rec_b[slot] = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(i));
+    w.rec_m[slot] = make_uint4((unsigned)x0 | ((unsigned)x1 << 16), (unsigned)y0 | ((unsigned)y1 << 16),
+                               (unsigned)vi, __float_as_uint(pz));
+    const View& V = views[vi];
+    for (int ty = y0; ty <= y1; ++ty)
+      for (int tx = x0; tx <= x1; ++tx) atomicAdd(&w.tile_count[V.tile_base + ty * V.tiles_x + tx], 1u);
   };
-  // Gaussian index of flat position f over the active ranges, or -1
+  // Gaussian index of flat position f over the active ranges, or -1 (one
+  // range, the common call: read once, so that the means' loads do not wait
+  // on it)
+  const int4 rg1 = hdr.x == 1 ? w.ranges[1] : make_int4(0, 0, 0, 0);
   auto gaussian_of = [&](int f) -> int {
     if (f >= hdr.y) return -1;
+    if (hdr.x == 1) return rg1.x + (f - rg1.z);
     int lo = 1, hi = hdr.x;  // last range whose prefix is <= f
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
@@ -366,35 +373,36 @@ __global__ void __launch_bounds__(256) k_project(SceneDev sc, const View* __rest
     const int4 rg = w.ranges[lo];
     return rg.x + (f - rg.z);
   };
-  // the next block of means is loaded before the current one is tested
-  int i_next = gaussian_of(blockIdx.x * 256 + tid);
+  // chunks of 32 Gaussians: this warp's first is 256 blockIdx.x + 32 wid; the
+  // next chunk's means are loaded before the current one is tested
+  const int stride = gridDim.x * kTileThreads;
+  int i_next = gaussian_of(blockIdx.x * kTileThreads + wid * 32 + lane);
   float4 p_next = i_next >= 0 ? __ldg(sc.pos + i_next) : make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int base = blockIdx.x * 256; base < hdr.y; base += gridDim.x * 256) {  // block-uniform loop
+  for (int base = blockIdx.x * kTileThreads + wid * 32; base < hdr.y; base += stride) {  // warp-uniform loop
     const int i = i_next;
     const bool valid = i >= 0;
     const float4 p4 = p_next;
-    i_next = gaussian_of(base + gridDim.x * 256 + tid);
+    i_next = gaussian_of(base + stride + lane);
     if (i_next >= 0) p_next = __ldg(sc.pos + i_next);
     for (int vi = 0; vi < n_views; ++vi) {
       const bool pass = valid && may_reach(views[vi], p4);
       const unsigned pm = __ballot_sync(0xffffffffu, pass);
-      if (pm) {  // warp-aggregated append to the queue
-        unsigned q0 = 0;
-        const int leader = __ffs(pm) - 1;
-        if (lane == leader) q0 = atomicAdd(&s_n, (unsigned)__popc(pm));
-        q0 = __shfl_sync(0xffffffffu, q0, leader);
-        if (pass) s_q[q0 + __popc(pm & lt_mask)] = make_int2(i, vi);
+      if (pass) q[qn + __popc(pm & lt_mask)] = make_int2(i, vi);
+      qn += __popc(pm);
+      if (qn >= 32u) {  // a full warp of work
+        __syncwarp();
+        drain(32u);
+        __syncwarp();
+        const int2 rest = lane + 32u < qn ? q[32 + lane] : make_int2(0, 0);
+        __syncwarp();
+        if (lane + 32u < qn) q[lane] = rest;
+        qn -= 32u;
+        __syncwarp();
       }
-      __syncthreads();
-      const unsigned queued = s_n;
-      __syncthreads();  // read by all before the next appends
-      if (queued + 256u > (unsigned)kProjQ) drain(queued);  // room for the next 256 entries
     }
   }
-  __syncthreads();
-  const unsigned queued = s_n;
-  __syncthreads();
-  drain(queued);
+  __syncwarp();
+  if (qn) drain(qn);
 }
 
 // ---------------------------------------------------------------------------

@@ -48,7 +48,7 @@ FLOPS_PER_BLEND = 180
 # DRAM bytes (read + write) of one tangent-pass launch on this workload, from
 # one ncu capture of this kernel (dram__bytes_read.sum + dram__bytes_write.sum);
 # None whenever the kernel has changed since that capture
-COMPOSITE_DRAM_BYTES = 82_542_336  # 79,773,184 read + 2,769,152 written (the tuned 128 / 3 variant)
+COMPOSITE_DRAM_BYTES = 82_601_472  # 79,756,544 read + 2,844,928 written (the tuned 128 / 3 variant)
 # Visibility reverse pass (Algorithm 1): a (pixel, Gaussian) evaluation shares
 # the forward's FLOPS_PER_EVAL; a blended pair adds the transmittance
 # division, weight, colour sum and running sum (8), dL/dpower and the five

@@ -477,7 +477,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(scene, cam, T_ref, T_q, args.cpu_seconds)
 
-    launches_per_step = 6  # project, shade, scan, scatter, sort, composite (tangent pass + reduction)
+    launches_per_step = 7  # project, shade, scan, scatter, sort, tangent pass, fp64 reduction of its tile partials
     value = job_mpix_per_s(world, P, ms_grad)
     line = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,

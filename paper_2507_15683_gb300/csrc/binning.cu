@@ -80,8 +80,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(Work w) {
     }
     __syncthreads();  // sv and s_carry are reused by the next chunk
   }
-  // counters of the backward's chunked reduction start at zero every call
-  for (uint32_t k = tid; k < w.n_chunks; k += kScanThreads) w.chunk_ctr[k] = 0u;
+  // the view counters of the tangent pass's chunked reduction start at zero every call
   for (uint32_t k = tid; k < w.n_views && w.n_chunks; k += kScanThreads) w.view_ctr[k] = 0u;
   if (tid == 0) {
     const unsigned long long total = s_carry;

@@ -273,11 +273,10 @@ Work work_of(gs_scene* s, uint32_t n_tiles) {
   w.pair_cap = s->pair_cap;
   w.ctr = dp<Counters>(s->ctr);
   w.partials = dp<double>(s->partials);
-  // chunk sums, then the chunk and view counters; one view has at least one
-  // tile, so tile_cap bounds both the chunk and the view count
+  // chunk sums, then the view counters; one view has at least one tile, so
+  // tile_cap bounds both the chunk and the view count
   w.chunk_part = dp<double>(s->chunks);
-  w.chunk_ctr = reinterpret_cast<uint32_t*>(w.chunk_part + (size_t)s->tile_cap * kPartialStride);
-  w.view_ctr = w.chunk_ctr + s->tile_cap;
+  w.view_ctr = reinterpret_cast<uint32_t*>(w.chunk_part + (size_t)s->tile_cap * kPartialStride);
   w.n_chunks = 0;
   w.n_views = 0;
   w.result = dp<double>(s->result);
@@ -318,7 +317,7 @@ gs_status grow_tiles(gs_scene* s, uint64_t n_tiles) {
     GS_TRY(ensure(s->tile_offset, cap * sizeof(uint32_t)));
     GS_TRY(ensure(s->tile_cursor, cap * sizeof(uint32_t)));
     GS_TRY(ensure(s->partials, cap * kPartialStride * sizeof(double)));
-    GS_TRY(ensure(s->chunks, cap * (kPartialStride * sizeof(double) + 2 * sizeof(uint32_t))));
+    GS_TRY(ensure(s->chunks, cap * (kPartialStride * sizeof(double) + sizeof(uint32_t))));
     s->tile_cap = (uint32_t)cap;
   }
   return GS_OK;
@@ -515,8 +514,7 @@ gs_status enqueue(gs_scene* s, const std::vector<View>& hv, const std::vector<in
     if (bands && bands->n > 0 && nv == 1) {
       // band b of the tangent pass starts when the binning is done and its
       // target rows are on the device; consecutive bands run on two streams so
-      // that one band's last tiles overlap the next band's first ones (the
-      // per-chunk fp64 reduction completes in whichever launch ends a chunk)
+      // that one band's last tiles overlap the next band's first ones
       GS_CUDA(cudaEventRecord(s->ev_binned, st));
       const View& V = hv[0];
       for (int b = 0; b < bands->n; ++b) {
@@ -534,6 +532,7 @@ gs_status enqueue(gs_scene* s, const std::vector<View>& hv, const std::vector<in
       if (targets_ready) GS_CUDA(cudaStreamWaitEvent(st, targets_ready, 0));  // only this pass reads the targets
       GS_CUDA(launch_composite_tangent(sc, dviews, nv, w, res, cfg, s->sm_count, st));
     }
+    GS_CUDA(launch_reduce_tangent(dviews, nv, w, res, st));
   }
   GS_CUDA(mark(6));
   if (vis) {

@@ -99,8 +99,7 @@ struct Work {
   Counters* ctr;
   double* partials;    // n_tiles * kPartialStride
   double* chunk_part;  // n_chunks * kPartialStride: fp64 sums of kChunkTiles tile partials
-  uint32_t* chunk_ctr; // n_chunks: tiles of the chunk finished (zeroed by the scan)
-  uint32_t* view_ctr;  // n_views: chunks of the view finished (zeroed by the scan)
+  uint32_t* view_ctr;  // n_views: chunks of the view summed (zeroed by the scan)
   uint32_t n_chunks;
   uint32_t n_views;
   double* result;      // 7 doubles (loss, grad)
@@ -150,15 +149,18 @@ cudaError_t launch_scatter(const View* views, const Work& w, int grid, cudaStrea
 // persistent grid from cfg and the SM count
 cudaError_t launch_composite(const SceneDev& sc, const View* views, int n_views, const Work& w, bool feats,
                              const LaunchCfg& cfg, int sm_count, cudaStream_t st);
-// forward render plus the pose gradient (tangent mode); result: kPartialStride
-// doubles per view (loss, dL/drho, dL/dphi)
+// forward render plus the pose gradient (tangent mode): per-tile fp32 partials
+// of (loss, dL/drho, dL/dphi) in w.partials; launch_reduce_tangent then sums
+// them in fixed order into result (kPartialStride doubles per view)
 cudaError_t launch_composite_tangent(const SceneDev& sc, const View* views, int n_views, const Work& w,
                                      double* result, const LaunchCfg& cfg, int sm_count, cudaStream_t st);
 // the same pass over tiles [tile_begin, tile_end) with its own queue counter
-// (the per-chunk fp64 reduction completes across such launches)
 cudaError_t launch_composite_tangent_range(const SceneDev& sc, const View* views, int n_views, const Work& w,
                                            double* result, const LaunchCfg& cfg, int sm_count, cudaStream_t st,
                                            uint32_t tile_begin, uint32_t tile_end, unsigned int* queue);
+// the fp64 chunk and view sums of the tangent pass's tile partials, once every
+// tile of the call is done
+cudaError_t launch_reduce_tangent(const View* views, int n_views, const Work& w, double* result, cudaStream_t st);
 
 // Algorithm 1 visibility check, after a forward render of one view that wrote
 // final_T and last_idx and a shading pass that wrote the pose Jacobian:

@@ -330,13 +330,13 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
 
 // (loss, dL/dxi) of one tile: a fixed fp32 tree over each warp's lanes, then
 // the warps in order (GB300 runs fp64 at 1/64 of the fp32 rate, so fp64 starts
-// at the tile sums). Then a deterministic fp64 reduction in two fixed levels,
-// done by whichever CTA finishes the last tile of a chunk (kChunkTiles tiles
-// of one view) and then the last chunk of the view: the order depends only on
-// tile indices, so a view gives the same bits alone or inside a batch.
-// Block-uniform control flow; ends with every thread past a barrier.
-__device__ void reduce_tile(float (&v)[7], const View& V, int vi, uint32_t lt, int tid, int lane, int wid, const Work& w,
-                            double* __restrict__ result, float (&s_red)[kWarps][8], bool& s_last) {
+// at the tile sums), written to the tile's slot of w.partials. The fixed-order
+// fp64 sums over chunks of kChunkTiles tiles and over each view's chunks are
+// k_reduce_chunks's, after the pass: the order depends only on tile indices,
+// so a view gives the same bits alone or inside a batch. Block-uniform; ends
+// past a barrier.
+__device__ void tile_partial(float (&v)[7], uint32_t tile, int tid, int lane, int wid, const Work& w,
+                             float (&s_red)[kWarps][8]) {
 #pragma unroll
   for (int k = 0; k < 7; ++k) {
 #pragma unroll
@@ -347,47 +347,61 @@ __device__ void reduce_tile(float (&v)[7], const View& V, int vi, uint32_t lt, i
     for (int k = 0; k < 7; ++k) s_red[wid][k] = v[k];
   }
   __syncthreads();
-  const uint32_t tile = V.tile_base + lt;
   if (tid < 7) {
     float t = s_red[0][tid];
 #pragma unroll
     for (int k = 1; k < kWarps; ++k) t += s_red[k][tid];
     w.partials[(size_t)tile * kPartialStride + tid] = (double)t;
-    __threadfence();
   }
-  __syncthreads();
+}
+
+// The fp64 reductions of the tangent pass's tile partials: block c sums chunk
+// c (kChunkTiles tiles of one view; warp k component k, lanes taking tiles
+// lane and lane + 32, then a fixed shuffle tree), and the block that finishes
+// the last chunk of a view sums the view's chunks (lane-strided, then the same
+// tree) into result.
+__global__ void __launch_bounds__(7 * 32) k_reduce_chunks(const View* __restrict__ views, int n_views, Work w,
+                                                          double* __restrict__ result) {
+  __shared__ bool s_last;
+  if (w.ctr->overflow) return;
+  const uint32_t chunk = blockIdx.x;
+  const int lane = threadIdx.x & 31, k = threadIdx.x >> 5;
+  int vi = 0;
+  {
+    int lo = 0, hi = n_views - 1;  // last view whose first chunk is <= this one
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (views[mid].chunk_base <= chunk) lo = mid; else hi = mid - 1;
+    }
+    vi = lo;
+  }
+  const View& V = views[vi];
   const uint32_t nt = (uint32_t)V.tiles_x * (uint32_t)V.tiles_y;
-  const uint32_t chunk = lt / kChunkTiles, c0 = chunk * kChunkTiles;
+  const uint32_t c0 = (chunk - V.chunk_base) * kChunkTiles;
   const uint32_t cn = min((uint32_t)kChunkTiles, nt - c0);
-  if (tid == 0) s_last = atomicAdd(&w.chunk_ctr[V.chunk_base + chunk], 1u) == cn - 1u;
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  if (wid < 7) {  // warp k sums component k; lanes take tiles lane and lane + 32
-    const double* src = w.partials + (size_t)(V.tile_base + c0) * kPartialStride + wid;
+  {
+    const double* src = w.partials + (size_t)(V.tile_base + c0) * kPartialStride + k;
     double x = (uint32_t)lane < cn ? __ldcg(src + (size_t)lane * kPartialStride) : 0.0;
     if ((uint32_t)lane + 32u < cn) x += __ldcg(src + (size_t)(lane + 32) * kPartialStride);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
     if (lane == 0) {
-      w.chunk_part[(size_t)(V.chunk_base + chunk) * kPartialStride + wid] = x;
+      w.chunk_part[(size_t)chunk * kPartialStride + k] = x;
       __threadfence();
     }
   }
   __syncthreads();
   const uint32_t ncv = (nt + kChunkTiles - 1) / kChunkTiles;
-  if (tid == 0) s_last = atomicAdd(&w.view_ctr[vi], 1u) == ncv - 1u;
+  if (threadIdx.x == 0) s_last = atomicAdd(&w.view_ctr[vi], 1u) == ncv - 1u;
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  if (wid < 7) {
-    double x = 0.0;
-    for (uint32_t c = lane; c < ncv; c += 32)
-      x += __ldcg(w.chunk_part + (size_t)(V.chunk_base + c) * kPartialStride + wid);
+  double x = 0.0;
+  for (uint32_t c = lane; c < ncv; c += 32)
+    x += __ldcg(w.chunk_part + (size_t)(V.chunk_base + c) * kPartialStride + k);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if (lane == 0) result[(size_t)vi * kPartialStride + wid] = x;
-  }
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  if (lane == 0) result[(size_t)vi * kPartialStride + k] = x;
 }
 
 // ---------------------------------------------------------------------------
@@ -402,7 +416,8 @@ __device__ void reduce_tile(float (&v)[7], const View& V, int vi, uint32_t lt, i
 // with dalpha = alpha dpower (0 where the 0.99 cap is active) and dpower from
 // the pixel offset and the Gaussian's staged pose Jacobian. After the walk,
 // dL/dxi = sum over pixels of g . (dC, dD) with g the per-pixel L1
-// subgradient, reduced in fp32 per tile and in fp64 across tiles.
+// subgradient, reduced in fp32 per tile (tile_partial) and in fp64 across
+// tiles (k_reduce_chunks, launched after the pass).
 // ---------------------------------------------------------------------------
 // KB: Gaussians staged per batch; MINB: resident CTAs per SM the register
 // allocation must allow (the autotuner's compositor variants, all giving the
@@ -439,7 +454,7 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_composite(SceneDev sc, c
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_tmp[kWarps];
   __shared__ float s_red[kWarps][8];
-  __shared__ bool s_last;
+  (void)result;  // the tangent pass's fp64 sums are k_reduce_chunks's
   if (w.ctr->overflow) return;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   int lx, ly, bxw, byw;
@@ -766,7 +781,7 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_composite(SceneDev sc, c
           v[2 + 2 * k] = x.y;
         }
       }
-      reduce_tile(v, V, vi, lt, tid, lane, wid, w, result, s_red, s_last);
+      tile_partial(v, V.tile_base + lt, tid, lane, wid, w, s_red);
     }
     __syncthreads();
   }
@@ -997,6 +1012,12 @@ cudaError_t launch_composite_tangent(const SceneDev& sc, const View* views, int 
   const Variant& V = variant_table(kModeTan)[v];
   const int g = comp_grid(kModeTan, v, cfg.per_sm[kModeTan], sm_count, w.n_tiles);
   V.fn<<<g, kTileThreads, V.smem, st>>>(sc, views, n_views, w, result);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_tangent(const View* views, int n_views, const Work& w, double* result, cudaStream_t st) {
+  if (w.n_tiles == 0 || w.n_chunks == 0) return cudaSuccess;
+  k_reduce_chunks<<<w.n_chunks, 7 * 32, 0, st>>>(views, n_views, w, result);
   return cudaGetLastError();
 }
 

@@ -794,13 +794,14 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_composite(SceneDev sc, c
 // with s the channel sum of the normalised colour behind the current
 // Gaussian, dL/dalpha_j = T_j (r_j + g_j + b_j - s) and dL/dc_j = alpha_j T_j
 // per channel. Per blended pair the record accumulates
-//   (e dx, e dy, e dx^2, e dx dy, e dy^2, alpha T, 0, 0),  e = dL/dpower,
+//   (e dx, e dy, e dx^2, e dx dy, e dy^2, alpha T),  e = dL/dpower,
 // (dx, dy) = centre - pixel: the pose Jacobian's rows contract these with
-// (P, Q, dA/2, dB, dC/2) to dL/dxi (see the tangent pass). The eight values
-// are summed over the warp (lane l ends with the total of value l / 4) and
-// added to the record's accumulator, or, when few lanes blended, added by
-// those lanes; a Gaussian nobody blended keeps an exact zero. The order of the atomic additions varies, so the sums are not
-// bit-reproducible; the test the algorithm makes (gradient != 0) is.
+// (P, Q, dA/2, dB, dC/2) to dL/dxi (see the tangent pass). The six values are
+// summed over the warp by a reduce-scatter (8 shuffles) and added to the
+// record's accumulator by six lanes, or, when few lanes blended, added by
+// those lanes; a Gaussian nobody blended keeps an exact zero. The order of
+// the atomic additions varies, so the sums are not bit-reproducible; the test
+// the algorithm makes (gradient != 0) is.
 // ---------------------------------------------------------------------------
 constexpr int kBatchV = kTileThreads;  // entries staged per batch of the reverse pass
 constexpr int kVisDirect = 12;         // at most this many blending lanes add without the warp reduction
@@ -872,6 +873,10 @@ __global__ void __launch_bounds__(kTileThreads, 7) k_vis_backward(const View* __
       for (int c0 = ((bn - 1) >> 5) << 5; c0 >= 0; c0 -= 32) {
         const int jj = c0 + lane;
         uint32_t m = __ballot_sync(0xffffffffu, jj < bn && (uint32_t)(bstart + jj) < wm && (smask[jj] & wbit));
+        {  // the chunk's hits this pixel evaluates: those before its last blended entry
+          const int below = inside ? (int)last - (bstart + c0) : 0;
+          n_eval += (uint32_t)__popc(below >= 32 ? m : below <= 0 ? 0u : m & ((1u << below) - 1u));
+        }
         while (m) {  // back to front
           const int bit = 31 - __clz(m);
           m &= ~(1u << bit);
@@ -884,7 +889,6 @@ __global__ void __launch_bounds__(kTileThreads, 7) k_vis_backward(const View* __
           const float alpha = fminf(kAlphaCap, oe);
           const bool before = inside && (uint32_t)(bstart + j) < last;
           const bool take = before && !(pw > 0.0f) && !(alpha < kAlphaFloor);
-          n_eval += before ? 1u : 0u;
           n_take += take ? 1u : 0u;
           const unsigned tb = __ballot_sync(0xffffffffu, take);
           if (!tb) continue;  // nobody in the warp blended it
@@ -895,7 +899,7 @@ __global__ void __launch_bounds__(kTileThreads, 7) k_vis_backward(const View* __
           T = Tj;
           const float e = (take && oe < kAlphaCap) ? (Tj * d) * alpha : 0.0f;  // dalpha/dpower = alpha
           const float ex = e * dx, ey = e * dy;
-          float g[8] = {ex, ey, ex * dx, ex * dy, ey * dy, wgt, 0.0f, 0.0f};
+          const float g[6] = {ex, ey, ex * dx, ex * dy, ey * dy, wgt};
           if (__popc(tb) <= kVisDirect) {  // few pixels: their own additions beat the reduction
             if (take) {
               float* ap = acc + (size_t)srec[j] * kVisAcc;
@@ -904,21 +908,23 @@ __global__ void __launch_bounds__(kTileThreads, 7) k_vis_backward(const View* __
             }
             continue;
           }
-          // reduce over the warp's pixels: halve the value set across lane bits 4, 3, 2, then
-          // sum over bits 1, 0; lane l ends with the total of value (l >> 2)
+          // reduce the six sums over the warp's pixels (lane bits b4, b3, b2 =
+          // lane & 16, 8, 4): halve the set over b4 (values 3 b4 + 0..2), then
+          // over b3 for the first two with the third summed, then over b2
+          // between those two, and sum over bits 1, 0. Lane l ends with the
+          // total of value 3 b4 + (b2 ? 2 : b3); for b2 both b3 halves hold it.
+          const bool u16 = (lane & 16) != 0, u8 = (lane & 8) != 0, u4 = (lane & 4) != 0;
+          float h[3];
 #pragma unroll
-          for (int s = 4, bitv = 16; s >= 1; s >>= 1, bitv >>= 1) {
-            const bool up = (lane & bitv) != 0;
-#pragma unroll
-            for (int i = 0; i < s; ++i) {
-              const float send = up ? g[i] : g[i + s];
-              const float keep = up ? g[i + s] : g[i];
-              g[i] = keep + __shfl_xor_sync(0xffffffffu, send, bitv);
-            }
-          }
-          float tot = g[0] + __shfl_xor_sync(0xffffffffu, g[0], 2);
+          for (int i = 0; i < 3; ++i)
+            h[i] = (u16 ? g[i + 3] : g[i]) + __shfl_xor_sync(0xffffffffu, u16 ? g[i] : g[i + 3], 16);
+          h[0] = (u8 ? h[1] : h[0]) + __shfl_xor_sync(0xffffffffu, u8 ? h[0] : h[1], 8);
+          h[2] += __shfl_xor_sync(0xffffffffu, h[2], 8);
+          float tot = (u4 ? h[2] : h[0]) + __shfl_xor_sync(0xffffffffu, u4 ? h[0] : h[2], 4);
+          tot += __shfl_xor_sync(0xffffffffu, tot, 2);
           tot += __shfl_xor_sync(0xffffffffu, tot, 1);
-          if ((lane & 3) == 0 && tot != 0.0f) atomicAdd(acc + (size_t)srec[j] * kVisAcc + (lane >> 2), tot);
+          const int vk = (u16 ? 3 : 0) + (u4 ? 2 : (u8 ? 1 : 0));
+          if ((lane & 3) == 0 && !(u4 && u8) && tot != 0.0f) atomicAdd(acc + (size_t)srec[j] * kVisAcc + vk, tot);
         }
       }
     }

@@ -48,14 +48,14 @@ FLOPS_PER_BLEND = 180
 # DRAM bytes (read + write) of one tangent-pass launch on this workload, from
 # one ncu capture of this kernel (dram__bytes_read.sum + dram__bytes_write.sum);
 # None whenever the kernel has changed since that capture
-COMPOSITE_DRAM_BYTES = 82_601_472  # 79,756,544 read + 2,844,928 written (the tuned 128 / 3 variant)
+COMPOSITE_DRAM_BYTES = 82_540_288  # 79,541,760 read + 2,998,528 written (the tuned 128 / 3 variant)
 # Visibility reverse pass (Algorithm 1): a (pixel, Gaussian) evaluation shares
 # the forward's FLOPS_PER_EVAL; a blended pair adds the transmittance
 # division, weight, colour sum and running sum (8), dL/dpower and the five
 # monomials (7) and their share of the per-record sums over pixels (6).
 FLOPS_PER_VIS_BLEND = 21
-# DRAM bytes of one reverse-pass launch (ncu, same kernel): 37,470,720 read + 20,480 written
-VIS_BACKWARD_DRAM_BYTES = 37_491_200
+# DRAM bytes of one reverse-pass launch (ncu, same kernel): 37,543,680 read + 72,448 written
+VIS_BACKWARD_DRAM_BYTES = 37_616_128
 # PnP scoring (Eq. 10 RANSAC): one (solution, match) pair is p = R X + t (9 FMA),
 # x - a z, y - b z (2 FMA), the scaled squares (2 mul + 1 FMA), tau z twice (2 mul),
 # the threshold difference (1 FMA) and 2 compares: 33 fp32 operations (FMA = 2)

@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(Work w) {
 // hundreds of tiles does not serialise one thread; each lane issues its
 // atomics in groups of kScatterUnroll before using any returned slot. Slot
 // order inside a segment is arbitrary; the compositor sorts it.
-constexpr int kScatterUnroll = 4;
+constexpr int kScatterUnroll = 8;
 
 __global__ void __launch_bounds__(256) k_scatter(const View* __restrict__ views, Work w) {
   __shared__ uint32_t s_incl[8][32];

@@ -234,6 +234,13 @@ __device__ __forceinline__ void eval_sh_deg(int deg, const float4* shp, float x,
 // ---------------------------------------------------------------------------
 constexpr int kWarpQ = 64;  // (Gaussian, view) queue entries per warp: a drain of 32 leaves at most 31
 
+// 16-byte asynchronous copy global -> shared (both 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+               "l"(gsrc)
+               : "memory");
+}
+
 // camera-space position in the binary32 operation order of the oracle
 __device__ __forceinline__ void cam_xyz(const View& V, float4 p4, float& px, float& py, float& pz) {
   px = add(add(add(mul(V.R[0], p4.x), mul(V.R[1], p4.y)), mul(V.R[2], p4.z)), V.t[0]);
@@ -316,25 +323,33 @@ __device__ __forceinline__ bool discrete_layer(const View& V, float4 p4, float4 
 }
 
 __global__ void __launch_bounds__(256) k_project(SceneDev sc, const View* __restrict__ views, int n_views, Work w) {
-  __shared__ int2 s_q[kTileThreads / 32][kWarpQ];  // (Gaussian index, view), per warp
+  // per warp, a ring of kWarpQ (Gaussian, view) entries with the Gaussian's
+  // mean and its covariance, copied (cp.async) when the entry is queued so that
+  // a drain finds them in shared memory
+  __shared__ int2 s_q[kTileThreads / 32][kWarpQ];
+  __shared__ float4 s_qp[kTileThreads / 32][kWarpQ];
+  __shared__ float4 s_qc[kTileThreads / 32][kWarpQ][2];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned lt_mask = (1u << lane) - 1u;
   const unsigned region = blockIdx.x % kRecRegions;
   const int4 hdr = w.ranges[0];  // (ranges, total length): only partitions in view are walked
   int2* q = s_q[wid];
-  unsigned qn = 0;  // queued pairs (warp-uniform)
-  // the exact layer over queue entries [0, cnt), cnt <= 32, one per lane
+  float4* qp = s_qp[wid];
+  float4(*qc)[2] = s_qc[wid];
+  unsigned qh = 0, qn = 0;  // ring head and queued entries (warp-uniform)
+  // the exact layer over the cnt <= 32 entries at the head, one per lane
   auto drain = [&](unsigned cnt) {
+    asm volatile("cp.async.wait_all;" ::: "memory");  // this lane's covariance copies
+    __syncwarp();                                      // ... and every other lane's
     bool vis = false;
     int i = 0, vi = 0, x0 = 0, x1 = 0, y0 = 0, y1 = 0;
     float pz = 0.f, ca = 0.f, cb = 0.f, cc = 0.f;
     if ((unsigned)lane < cnt) {
-      const int2 e = q[lane];
-      i = e.x;
-      vi = e.y;
-      const float4 p4 = __ldg(sc.pos + i);
-      const float4 c0 = __ldg(sc.cov + 2 * i), c1 = __ldg(sc.cov + 2 * i + 1);
-      vis = discrete_layer(views[vi], p4, c0, c1, pz, ca, cb, cc, x0, x1, y0, y1);
+      const unsigned e = (qh + (unsigned)lane) & (kWarpQ - 1);
+      const int2 qe = q[e];
+      i = qe.x;
+      vi = qe.y;
+      vis = discrete_layer(views[vi], qp[e], qc[e][0], qc[e][1], pz, ca, cb, cc, x0, x1, y0, y1);
     }
     const unsigned vmask = __ballot_sync(0xffffffffu, vis);
     if (vmask == 0u) return;
@@ -387,17 +402,20 @@ __global__ void __launch_bounds__(256) k_project(SceneDev sc, const View* __rest
     for (int vi = 0; vi < n_views; ++vi) {
       const bool pass = valid && may_reach(views[vi], p4);
       const unsigned pm = __ballot_sync(0xffffffffu, pass);
-      if (pass) q[qn + __popc(pm & lt_mask)] = make_int2(i, vi);
+      if (pass) {
+        const unsigned e = (qh + qn + (unsigned)__popc(pm & lt_mask)) & (kWarpQ - 1);
+        q[e] = make_int2(i, vi);
+        qp[e] = p4;
+        cp_async16(&qc[e][0], sc.cov + 2 * i);
+        cp_async16(&qc[e][1], sc.cov + 2 * i + 1);
+      }
       qn += __popc(pm);
       if (qn >= 32u) {  // a full warp of work
         __syncwarp();
         drain(32u);
-        __syncwarp();
-        const int2 rest = lane + 32u < qn ? q[32 + lane] : make_int2(0, 0);
-        __syncwarp();
-        if (lane + 32u < qn) q[lane] = rest;
+        __syncwarp();  // the drained slots are free again
+        qh = (qh + 32u) & (kWarpQ - 1);
         qn -= 32u;
-        __syncwarp();
       }
     }
   }

@@ -420,6 +420,18 @@ def main():
         roof = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
                 "traffic": None, "kernel": dom, "peak_source": pk_src}
 
+    # the binning-side kernels against the HBM copy bandwidth, each on its algorithmic bytes
+    # (their data mostly stays in the L2, so these fractions measure latency, not bandwidth)
+    n_tiles = tx * ty
+    alg_bytes = {"project": 16 * 1_000_000 + 32 * n_rec,       # means of all, covariances of the visible
+                 "shade": n_rec * (48 + 4 * 48 + 64 + 4 * 48),  # record + SH in, record + pose Jacobian out
+                 "scan_tiles": 12 * n_tiles,                     # counts in, offsets and cursors out
+                 "scatter": 16 * n_rec + 8 * n_pairs,            # record bounds in, (depth, record) pairs out
+                 "sort": 16 * n_pairs}                           # pairs in and out
+    kernel_roofs = {k: {"bytes": b, "gbs": b / (per_kernel[k] * 1e-3) / 1e9,
+                        "frac": b / (per_kernel[k] * 1e-3) / 1e9 / pk["hbm_gbs"]}
+                    for k, b in alg_bytes.items() if per_kernel.get(k)}
+
     # end to end through the public API: pinned host targets -> device, synchronous call, result to host
     h_rgb = trgb.cpu().pin_memory()
     h_dep = tdep.cpu().pin_memory()
@@ -501,7 +513,7 @@ def main():
                 "transfer": "pinned host targets read in place by the compositing pass over the CPU-GPU link; "
                             "(loss, gradient) copied back"},
         "gpu_launches": launches_per_step * args.steps,
-        "roofline": roof, "kernels": kernels,
+        "roofline": roof, "kernels": kernels, "kernel_rooflines": kernel_roofs,
         "refine": refine, "batched": batched, "large": large, "pmm": pmm, "visibility": vis, "dense": dense,
         "errors": errors,
         "cpu_baseline": cpu,

@@ -780,7 +780,7 @@ namespace {
 // Replay the cached graph if the batch layout (key) is unchanged, else capture
 // a new one. Everything the capture needs is allocated before capturing.
 gs_status run_graph(gs_scene* s, GraphCache& G, const std::vector<char>& key, const std::vector<View>& hv,
-                    uint64_t n_tiles, const GradIn* g, cudaStream_t st) {
+                    uint64_t n_tiles, const GradIn* g, cudaStream_t st, bool copy_back = false) {
   const int n_views = (int)hv.size();
   std::vector<int4> ranges;
   const bool ready = G.valid && G.key == key && G.gen == g_alloc_gen.load();
@@ -807,7 +807,13 @@ gs_status run_graph(gs_scene* s, GraphCache& G, const std::vector<char>& key, co
     GS_CUDA(cudaStreamSynchronize(st));
     cudaGraph_t graph = nullptr;
     GS_CUDA(cudaStreamBeginCapture(G.capture, cudaStreamCaptureModeThreadLocal));
-    const gs_status est = enqueue(s, hv, ranges, n_tiles, g, G.capture, G.host_table, nullptr, nullptr, nullptr, true);
+    gs_status est = enqueue(s, hv, ranges, n_tiles, g, G.capture, G.host_table, nullptr, nullptr, nullptr, true);
+    if (est == GS_OK && copy_back) {  // the counters and the (loss, gradient) to the pinned host copies
+      if (cudaMemcpyAsync(s->ctr_host, s->ctr.p, sizeof(Counters), cudaMemcpyDeviceToHost, G.capture) != cudaSuccess ||
+          cudaMemcpyAsync(s->result_host, s->result.p, 7 * sizeof(double), cudaMemcpyDeviceToHost, G.capture) !=
+              cudaSuccess)
+        est = fail(GS_ERR_CUDA, "cudaMemcpyAsync in the captured call failed");
+    }
     const cudaError_t ce = cudaStreamEndCapture(G.capture, &graph);
     if (est != GS_OK) {
       if (graph) cudaGraphDestroy(graph);
@@ -855,9 +861,7 @@ gs_status run_sync_graphed(gs_scene* s, const std::vector<View>& hv, uint64_t n_
   std::vector<char> key;
   append_bytes(key, &k, 1);
   append_bytes(key, &n_tiles, 1);
-  GS_TRY(run_graph(s, s->graph_sync, key, hv, n_tiles, g, st));
-  GS_CUDA(cudaMemcpyAsync(s->ctr_host, s->ctr.p, sizeof(Counters), cudaMemcpyDeviceToHost, st));
-  GS_CUDA(cudaMemcpyAsync(s->result_host, s->result.p, 7 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  GS_TRY(run_graph(s, s->graph_sync, key, hv, n_tiles, g, st, true));  // the graph copies the results back
   GS_CUDA(cudaStreamSynchronize(st));
   const Counters& c = *s->ctr_host;
   if (c.error) return fail(GS_ERR_INTERNAL, "device consistency check failed: the binning handed out a pair slot past the scanned tile counts");

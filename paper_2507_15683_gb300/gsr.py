@@ -402,11 +402,8 @@ def camera(c) -> gs_camera:
 
 
 def pose(T) -> gs_pose:
-    p = gs_pose()
-    flat = np.ascontiguousarray(T, np.float64).reshape(16)
-    for k in range(16):
-        p.T_cw[k] = float(flat[k])
-    return p
+    # one copy of the 16 row-major doubles (a 4 x 4 matrix or 16 values)
+    return gs_pose.from_buffer_copy(np.ascontiguousarray(T, np.float64).reshape(16))
 
 
 def _ptr(t):

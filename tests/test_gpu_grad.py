@@ -169,3 +169,31 @@ def test_host_targets_equal_device_targets(oracle, gsr):
         assert lp == ld
         np.testing.assert_array_equal(gp, gd)
     S.close()
+
+
+def test_graphed_host_call_recovers_from_a_capacity_overflow(gsr):
+    # The first pinned-target call on a scene captures its graph at a guessed
+    # workspace (at least 65,536 records). 200,000 Gaussians all in view need
+    # more: the graph's counters report the overflow, the call grows the
+    # workspace and runs again, and the result equals the device-target call's
+    # bits; the next call replays a graph captured at the grown size.
+    scene = synth.tiny_scene(5, n=200_000)
+    cam = synth.tiny_camera()
+    T_q = synth.perturb_pose(np.eye(4), synth.rng(6), 0.5, 0.05)
+    g = synth.rng(7)
+    trgb = g.uniform(0.0, 1.0, (3, 128, 128)).astype(np.float32)
+    tdep = g.uniform(4.0, 8.0, (128, 128)).astype(np.float32)
+    pr = torch.from_numpy(trgb).pin_memory()
+    pd = torch.from_numpy(tdep).pin_memory()
+    S1 = gsr.Scene(scene)
+    lp1, gp1 = S1.render_pose_grad_host(cam, T_q, pr, pd)
+    _, n_rec, _ = S1.status()
+    assert n_rec > 65_536
+    lp2, gp2 = S1.render_pose_grad_host(cam, T_q, pr, pd)
+    S2 = gsr.Scene(scene)
+    ld, gd = S2.render_pose_grad(cam, T_q, torch.from_numpy(trgb).cuda(), torch.from_numpy(tdep).cuda())
+    for lp, gp in ((lp1, gp1), (lp2, gp2)):
+        assert lp == ld
+        np.testing.assert_array_equal(gp, gd)
+    S1.close()
+    S2.close()

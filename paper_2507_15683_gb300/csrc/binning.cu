@@ -13,6 +13,7 @@ namespace {
 constexpr int kScanThreads = 1024;
 constexpr int kScanPer = 8;                             // counts per thread and chunk
 constexpr int kScanChunk = kScanThreads * kScanPer;     // counts per chunk (32 KB of shared memory)
+static_assert(kScanPer == 8, "a thread reads and writes its counts as two 16-byte vectors");
 
 // Exclusive scan of tile_count[0..n) into tile_offset[0..n] and tile_cursor,
 // by one CTA, in chunks of kScanChunk counts with a 64-bit carry: coalesced
@@ -20,7 +21,7 @@ constexpr int kScanChunk = kScanThreads * kScanPer;     // counts per chunk (32 
 // a block scan of those sums, and coalesced stores of the offsets. Also
 // publishes the total and flags an overflow of the pair capacity.
 __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(Work w) {
-  __shared__ uint32_t sv[kScanChunk];
+  __shared__ __align__(16) uint32_t sv[kScanChunk];
   __shared__ unsigned long long warp_tot[kScanThreads / 32];
   __shared__ unsigned long long s_carry;
   const uint32_t n = w.n_tiles;
@@ -33,13 +34,17 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(Work w) {
       sv[i * kScanThreads + tid] = k < n ? w.tile_count[k] : 0u;
     }
     __syncthreads();
+    // this thread's kScanPer consecutive counts, as two 16-byte reads
     uint32_t c[kScanPer];
+    {
+      const uint4* v4 = reinterpret_cast<const uint4*>(sv) + tid * (kScanPer / 4);
+      const uint4 x = v4[0], y = v4[1];
+      c[0] = x.x; c[1] = x.y; c[2] = x.z; c[3] = x.w;
+      c[4] = y.x; c[5] = y.y; c[6] = y.z; c[7] = y.w;
+    }
     unsigned long long s = 0;
 #pragma unroll
-    for (int i = 0; i < kScanPer; ++i) {
-      c[i] = sv[tid * kScanPer + i];
-      s += c[i];
-    }
+    for (int i = 0; i < kScanPer; ++i) s += c[i];
     // block exclusive scan of s
     unsigned long long incl = s;
 #pragma unroll
@@ -62,10 +67,16 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(Work w) {
     __syncthreads();
     const unsigned long long carry = s_carry;
     unsigned long long run = carry + warp_tot[wid] + incl - s;
+    uint32_t o8[kScanPer];
 #pragma unroll
     for (int i = 0; i < kScanPer; ++i) {
-      sv[tid * kScanPer + i] = (uint32_t)run;
+      o8[i] = (uint32_t)run;
       run += c[i];
+    }
+    {
+      uint4* v4 = reinterpret_cast<uint4*>(sv) + tid * (kScanPer / 4);
+      v4[0] = make_uint4(o8[0], o8[1], o8[2], o8[3]);
+      v4[1] = make_uint4(o8[4], o8[5], o8[6], o8[7]);
     }
     __syncthreads();  // every thread has read s_carry and written its offsets
     if (tid == kScanThreads - 1) s_carry = run;
